@@ -1,0 +1,277 @@
+"""Oracle functions (FP64). Test infrastructure only; see the package docstring."""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+
+import numpy as np
+
+__all__ = [
+    "lib", "num_threads", "window", "window_adjoint", "model_vis", "adjoint", "adjoint_pixels",
+    "pair_model_vis", "data_cost_grad", "data_grad_pixels", "laplacian", "reg_cost_grad",
+    "dish_kernel", "dish_conv", "fusion_cost_grad", "cost_grad", "solve_lbfgsb",
+    "LAPLACIAN_KERNEL",
+]
+
+# Eq. 7: the Laplacian kernel d of the regulariser.
+LAPLACIAN_KERNEL = np.array([[0.0, -1.0, 0.0], [-1.0, 4.0, -1.0], [0.0, -1.0, 0.0]])
+
+_LIB = None
+
+
+def lib():
+    """Load (building first if needed) the oracle's C library."""
+    global _LIB
+    if _LIB is None:
+        from .build import build
+        path = build()
+        L = ctypes.CDLL(path)
+        dp = ctypes.POINTER(ctypes.c_double)
+        ip = ctypes.POINTER(ctypes.c_int32)
+        L.ivo_forward.argtypes = [ctypes.c_int, ctypes.c_double, dp, ctypes.c_int64, dp, dp, dp]
+        L.ivo_adjoint.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_int64, dp, dp, dp, dp]
+        L.ivo_adjoint_pixels.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_int64, dp, dp,
+                                         dp, ctypes.c_int64, ip, ip, dp]
+        L.ivo_num_threads.restype = ctypes.c_int
+        _LIB = L
+    return _LIB
+
+
+def num_threads() -> int:
+    return int(lib().ivo_num_threads())
+
+
+def _dp(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+# ----------------------------------------------------------------------------- windows (Eq. 2)
+def _overlap(c, nb, n):
+    """Window index range [a, b) whose sky pixel c - nb/2 + index lies in [0, n)."""
+    o = c - nb // 2
+    return max(0, -o), min(nb, n - o), o
+
+
+def window(img: np.ndarray, cx: int, cy: int, nb: int) -> np.ndarray:
+    """I'[q, p] = I[cy - nb/2 + q, cx - nb/2 + p], zero where that pixel is off the sky."""
+    out = np.zeros((nb, nb))
+    qa, qb, oy = _overlap(cy, nb, img.shape[0])
+    pa, pb, ox = _overlap(cx, nb, img.shape[1])
+    if qa < qb and pa < pb:
+        out[qa:qb, pa:pb] = img[oy + qa:oy + qb, ox + pa:ox + pb]
+    return out
+
+
+def window_adjoint(win: np.ndarray, cx: int, cy: int, shape) -> np.ndarray:
+    """Transpose of :func:`window`: put the window back on a zero sky of ``shape``."""
+    out = np.zeros(shape)
+    nb = win.shape[0]
+    qa, qb, oy = _overlap(cy, nb, shape[0])
+    pa, pb, ox = _overlap(cx, nb, shape[1])
+    if qa < qb and pa < pb:
+        out[oy + qa:oy + qb, ox + pa:ox + pb] += win[qa:qb, pa:pb]
+    return out
+
+
+# ------------------------------------------------------------- non-uniform DFT (Eq. 3) and adjoint
+def model_vis(f: np.ndarray, cell: float, u: np.ndarray, v: np.ndarray) -> np.ndarray:
+    """Direct DFT  V~_j = sum_{q,p} f[q,p] exp(-2 pi i (u_j l_p + v_j m_q))."""
+    f = _f64(f)
+    nb = f.shape[0]
+    u, v = _f64(u), _f64(v)
+    out = np.zeros(2 * u.shape[0])
+    lib().ivo_forward(nb, cell, _dp(f), u.shape[0], _dp(u), _dp(v), _dp(out))
+    return out[0::2] + 1j * out[1::2]
+
+
+def _cvis(c):
+    c = np.asarray(c, dtype=np.complex128)
+    out = np.empty(2 * c.shape[0])
+    out[0::2], out[1::2] = c.real, c.imag
+    return out
+
+
+def adjoint(c: np.ndarray, nb: int, cell: float, u: np.ndarray, v: np.ndarray) -> np.ndarray:
+    """a[q,p] = sum_j c_j exp(+2 pi i (u_j l_p + v_j m_q)) over the whole window."""
+    u, v = _f64(u), _f64(v)
+    cv = _cvis(c)
+    out = np.zeros(2 * nb * nb)
+    lib().ivo_adjoint(nb, cell, u.shape[0], _dp(u), _dp(v), _dp(cv), _dp(out))
+    return (out[0::2] + 1j * out[1::2]).reshape(nb, nb)
+
+
+def adjoint_pixels(c, nb, cell, u, v, qs, ps) -> np.ndarray:
+    u, v = _f64(u), _f64(v)
+    cv = _cvis(c)
+    qs = np.ascontiguousarray(qs, dtype=np.int32)
+    ps = np.ascontiguousarray(ps, dtype=np.int32)
+    out = np.zeros(2 * qs.shape[0])
+    ip = ctypes.POINTER(ctypes.c_int32)
+    lib().ivo_adjoint_pixels(nb, cell, u.shape[0], _dp(u), _dp(v), _dp(cv), qs.shape[0],
+                             qs.ctypes.data_as(ip), ps.ctypes.data_as(ip), _dp(out))
+    return out[0::2] + 1j * out[1::2]
+
+
+# -------------------------------------------------------------------- data term (Eqs. 3-6)
+def pair_model_vis(prob, sky: np.ndarray, pair, idx=None) -> np.ndarray:
+    """Model visibilities of one (pointing, channel) pair for sky cube ``sky``."""
+    cx, cy = (int(t) for t in prob.centres[pair.k])
+    f = np.asarray(prob.beams[pair.k], dtype=np.float64) * window(sky[pair.chan], cx, cy, prob.nb)
+    uvw = pair.uvw if idx is None else pair.uvw[idx]
+    return model_vis(f, prob.cell_rad, uvw[:, 0], uvw[:, 1])
+
+
+def data_cost_grad(prob, sky: np.ndarray, with_grad: bool = True):
+    """Q = sum_k J_k (Eqs. 5-6) and its gradient
+    dQ/dI = sum_k P_k^T [A_k * Re(sum_j w_j r_j e^{+2 pi i (u l + v m)})]."""
+    sky = _f64(sky)
+    Q = 0.0
+    grad = np.zeros_like(sky) if with_grad else None
+    for pair in prob.pairs:
+        vt = pair_model_vis(prob, sky, pair)
+        r = vt - pair.vis.astype(np.complex128)
+        w = pair.weight.astype(np.float64)
+        Q += 0.5 * float(np.sum(w * (r.real ** 2 + r.imag ** 2)))
+        if with_grad:
+            a = adjoint(w * r, prob.nb, prob.cell_rad, pair.uvw[:, 0], pair.uvw[:, 1])
+            cx, cy = (int(t) for t in prob.centres[pair.k])
+            g = np.asarray(prob.beams[pair.k], dtype=np.float64) * a.real
+            grad[pair.chan] += window_adjoint(g, cx, cy, sky.shape[1:])
+    return Q, grad
+
+
+def data_grad_pixels(prob, sky, chan, ys, xs, residuals=None):
+    """dQ/dI at the listed sky pixels of channel ``chan`` only (sampled checks)."""
+    sky = _f64(sky)
+    out = np.zeros(len(ys))
+    for i, pair in enumerate(prob.pairs):
+        if pair.chan != chan:
+            continue
+        cx, cy = (int(t) for t in prob.centres[pair.k])
+        q = np.asarray(ys) - (cy - prob.nb // 2)
+        p = np.asarray(xs) - (cx - prob.nb // 2)
+        inside = (q >= 0) & (q < prob.nb) & (p >= 0) & (p < prob.nb)
+        if not inside.any():
+            continue
+        if residuals is not None:
+            r = residuals[i]
+        else:
+            r = pair_model_vis(prob, sky, pair) - pair.vis.astype(np.complex128)
+        w = pair.weight.astype(np.float64)
+        a = adjoint_pixels(w * r, prob.nb, prob.cell_rad, pair.uvw[:, 0], pair.uvw[:, 1],
+                           q[inside], p[inside])
+        out[inside] += np.asarray(prob.beams[pair.k], dtype=np.float64)[q[inside], p[inside]] * a.real
+    return out
+
+
+# ------------------------------------------------------------------- regulariser (Eqs. 7-8)
+def laplacian(img: np.ndarray) -> np.ndarray:
+    """D I: convolution with the kernel d (Eq. 7), zero outside the image, same size."""
+    img = _f64(img)
+    pad = np.zeros((img.shape[0] + 2, img.shape[1] + 2))
+    pad[1:-1, 1:-1] = img
+    out = np.zeros_like(img)
+    for dy in range(3):
+        for dx in range(3):
+            w = LAPLACIAN_KERNEL[dy, dx]
+            if w != 0.0:
+                out += w * pad[dy:dy + img.shape[0], dx:dx + img.shape[1]]
+    return out
+
+
+def reg_cost_grad(sky: np.ndarray):
+    """R = sum_nu 1/2 ||D I_nu||^2 (Eq. 8); gradient D^T D I_nu (D is symmetric)."""
+    R = 0.0
+    g = np.zeros_like(_f64(sky))
+    for c in range(sky.shape[0]):
+        di = laplacian(sky[c])
+        R += 0.5 * float(np.sum(di * di))
+        g[c] = laplacian(di)
+    return R, g
+
+
+# ------------------------------------------------------------------ fusion term (Eqs. 11-13)
+def dish_kernel(fwhm_pix: float) -> np.ndarray:
+    """1-D Gaussian dish-beam taps, truncated at +-ceil(4 sigma), unit sum."""
+    s = fwhm_pix / (2.0 * math.sqrt(2.0 * math.log(2.0)))
+    r = int(math.ceil(4.0 * s))
+    t = np.arange(-r, r + 1, dtype=np.float64)
+    b = np.exp(-0.5 * (t / s) ** 2)
+    return b / b.sum()
+
+
+def dish_conv(img: np.ndarray, b: np.ndarray) -> np.ndarray:
+    """B (x) I with B = b b^T: 'same'-size convolution, zero outside the image."""
+    img = _f64(img)
+    r = (b.shape[0] - 1) // 2
+    ny, nx = img.shape
+    pad = np.zeros((ny, nx + 2 * r))
+    pad[:, r:r + nx] = img
+    rows = np.zeros_like(img)
+    for i in range(b.shape[0]):
+        rows += b[i] * pad[:, 2 * r - i:2 * r - i + nx]
+    pad = np.zeros((ny + 2 * r, nx))
+    pad[r:r + ny, :] = rows
+    out = np.zeros_like(img)
+    for i in range(b.shape[0]):
+        out += b[i] * pad[2 * r - i:2 * r - i + ny, :]
+    return out
+
+
+def fusion_cost_grad(sky: np.ndarray, tsd: np.ndarray, sigma_sd, fwhm_pix: float):
+    """K = 1/2 sum ((B (x) I - T) / sigma_sd)^2 (Eq. 13); gradient B^T (B (x) I - T)/sigma_sd^2.
+    B is symmetric, so B^T is the same convolution."""
+    b = dish_kernel(fwhm_pix)
+    sig = np.broadcast_to(np.asarray(sigma_sd, dtype=np.float64), (sky.shape[0],))
+    K = 0.0
+    g = np.zeros_like(_f64(sky))
+    for c in range(sky.shape[0]):
+        resid = dish_conv(sky[c], b) - tsd[c]
+        K += 0.5 * float(np.sum(resid * resid)) / sig[c] ** 2
+        g[c] = dish_conv(resid / sig[c] ** 2, b)
+    return K, g
+
+
+# ------------------------------------------------------------------------ total (Eq. 14)
+def cost_grad(prob, sky: np.ndarray, tsd=None, sigma_sd=None, with_terms: bool = False):
+    """Q_tot = Q + lambda_s K + lambda_r R and its gradient."""
+    sky = _f64(sky).reshape(prob.nchan, prob.n, prob.n)
+    Q, gQ = data_cost_grad(prob, sky)
+    f, g = Q, gQ.copy()
+    K = R = 0.0
+    if prob.lambda_r != 0.0:
+        R, gR = reg_cost_grad(sky)
+        f += prob.lambda_r * R
+        g += prob.lambda_r * gR
+    if prob.lambda_s != 0.0:
+        K, gK = fusion_cost_grad(sky, tsd, sigma_sd, prob.sd_fwhm_pix)
+        f += prob.lambda_s * K
+        g += prob.lambda_s * gK
+    if with_terms:
+        return f, g, (Q, K, R)
+    return f, g
+
+
+# ---------------------------------------------------------------------- solver (Eq. 10)
+def solve_lbfgsb(prob, maxiter: int, m: int = 10, tsd=None, sigma_sd=None, x0=None,
+                 pgtol: float = 1e-5, factr: float = 1e7):
+    """scipy's L-BFGS-B (the optimiser of Sect. 3.4), null initial image, I >= 0 if
+    positivity is on. Returns (x, f, nit, nfev)."""
+    from scipy.optimize import minimize
+    shape = (prob.nchan, prob.n, prob.n)
+    x0 = np.zeros(int(np.prod(shape))) if x0 is None else _f64(x0).ravel()
+
+    def fun(x):
+        f, g = cost_grad(prob, x.reshape(shape), tsd, sigma_sd)
+        return f, g.ravel()
+
+    bounds = [(0.0, None)] * x0.size if prob.positivity else None
+    res = minimize(fun, x0, jac=True, method="L-BFGS-B", bounds=bounds,
+                   options={"maxiter": maxiter, "maxcor": m, "gtol": pgtol,
+                            "ftol": factr * np.finfo(float).eps})
+    return res.x.reshape(shape), float(res.fun), int(res.nit), int(res.nfev)

@@ -1,0 +1,165 @@
+/*
+ * ivis.h -- C ABI of the B300 (sm_103a) engine for Classic3D's cost and gradient.
+ *
+ * The engine evaluates, for a sky cube I[nchan][N][N] (row-major, y then x),
+ *
+ *   Q_tot(I) = Q(I) + lambda_s K(I) + lambda_r R(I)                    (paper Eq. 14)
+ *
+ * with the joint data term Q = sum_k J_k over every (pointing k, channel) pair
+ * (Eqs. 5-6), J_k = 1/2 sum_j w_j |V~_j - V_j|^2, the model visibilities
+ * V~ of the primary-beam-weighted window I'_k (Eqs. 2-3, w-term and n-term
+ * neglected as the paper does), the Laplacian regulariser R (Eqs. 7-8) and
+ * the single-dish fusion term K (Eqs. 11-13); and its analytic gradient.
+ * The bounded quasi-Newton solve of Eq. 10 (I >= 0 when positivity is on) runs
+ * on the device.
+ *
+ * Conventions used by every call:
+ *  - Window of pointing k: I'_k[q][p] = I[cy - nb/2 + q][cx - nb/2 + p] (zero off
+ *    the sky); direction cosines l_p = (p - nb/2) cell, m_q = (q - nb/2) cell;
+ *    V~_j = sum_{q,p} A_k[q][p] I'_k[q][p] exp(-2 pi i (u_j l_p + v_j m_q)).
+ *  - Real arrays whose type follows the plan's precision ("real" below) are
+ *    double for IVIS_FP64 and float for IVIS_FP32. Costs are always double.
+ *  - Pointers named *_dev are device pointers, *_host host pointers. Input
+ *    buffers are borrowed for the duration of the call; set_* calls copy what
+ *    they keep into plan-owned device memory. The caller keeps ownership of
+ *    everything it passes in.
+ *  - All device work is issued on the stream given to ivis_plan. Each call
+ *    returns after its work is complete (it synchronises that stream), except
+ *    where stated.
+ *  - No call aborts the process or throws across the ABI. On error the call
+ *    returns a non-zero ivis_status, ivis_last_error() describes it, and the
+ *    plan remains valid for ivis_destroy (and, unless the status is
+ *    IVIS_ERR_CUDA, for further calls).
+ */
+#ifndef IVIS_H
+#define IVIS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ivis_plan_s *ivis_plan_t;
+
+typedef enum {
+    IVIS_OK = 0,
+    IVIS_ERR_ARG = 1,        /* invalid argument (sizes, indices, null pointers)           */
+    IVIS_ERR_STATE = 2,      /* call out of order (e.g. cost before every pair is set)     */
+    IVIS_ERR_OOM = 3,        /* device allocation failed                                   */
+    IVIS_ERR_CUDA = 4,       /* a CUDA runtime call failed                                 */
+    IVIS_ERR_TIMEOUT = 5,    /* a bounded device wait ran out                              */
+    IVIS_ERR_NONFINITE = 6,  /* NaN / Inf in inputs or in a computed cost                  */
+    IVIS_ERR_LINESEARCH = 7  /* the solver's line search found no decrease                 */
+} ivis_status;
+
+enum { IVIS_FP64 = 0, IVIS_FP32 = 1 };
+
+typedef struct {
+    int n;              /* sky is n x n pixels per channel                                 */
+    int nchan;          /* spectral channels (independent images, Sect. 2)                 */
+    int npoint;         /* mosaic pointings                                                */
+    int nb;             /* pointing window nb x nb, power of two, 16 <= nb <= 2048         */
+    double cell_rad;    /* pixel size (radians); the same grid for sky and windows         */
+    int precision;      /* IVIS_FP64: all arithmetic double. IVIS_FP32: gridding, FFTs and
+                           residuals in float; cost, gradient and solver reductions in double */
+    double nufft_tol;   /* target relative accuracy of the NUFFT when kernel_width == 0    */
+    int kernel_width;   /* ES kernel width w in grid cells (2..16); 0 = chosen from tol     */
+    double lambda_r;    /* weight of R (Eq. 14)                                            */
+    double lambda_s;    /* weight of K (Eq. 14)                                            */
+    int positivity;     /* 1: bound I >= 0 in ivis_solve (Sect. 3.4)                       */
+} ivis_config;
+
+typedef struct {
+    int iterations;     /* accepted quasi-Newton steps                                     */
+    int evaluations;    /* cost+gradient evaluations                                       */
+    double f;           /* final Q_tot                                                     */
+    double pg_inf;      /* final projected-gradient infinity norm                          */
+    double seconds;     /* wall time of the solve                                          */
+    int status;         /* 0 converged (pgtol/ftol), 1 maxiter reached, 2 line search stop */
+} ivis_solve_report;
+
+/* Create a plan. stream: a cudaStream_t (NULL = the legacy default stream).
+ * Errors: IVIS_ERR_ARG for sizes out of range, IVIS_ERR_OOM, IVIS_ERR_CUDA. */
+ivis_status ivis_plan(const ivis_config *cfg, void *stream, ivis_plan_t *out);
+
+/* Pointing k (0 <= k < npoint): window centre at sky pixel (cx, cy) (any integers; the
+ * window may extend past the sky, Eq. 2) and primary beam A_k (Eq. 3), float [nb][nb]
+ * with A_k[q][p] at direction (l_p, m_q). Must be set before ivis_set_vis for k. */
+ivis_status ivis_set_pointing(ivis_plan_t plan, int k, int cx, int cy, const float *beam_dev);
+
+/* Calibrated visibilities of pair (k, chan): m points, uvw float [m][3] in wavelengths
+ * (w ignored: coplanar model of Eq. 3), vis float [m][2] (re, im), weight float [m]
+ * = 1/sigma^2 from the SIGMA column (Eq. 5). m == 0 declares a pair with no data.
+ * The data are copied, converted to oversampled-grid coordinates and sorted by grid
+ * tile on the device. Errors: IVIS_ERR_NONFINITE for NaN/Inf or negative weights. */
+ivis_status ivis_set_vis(ivis_plan_t plan, int k, int chan, int64_t m, const float *uvw_dev,
+                         const float *vis_dev, const float *weight_dev);
+
+/* Single-dish map T_b of channel chan (Eq. 12), float [n][n]; noise sigma_sd (Eq. 13)
+ * and Gaussian dish beam FWHM in pixels (Eq. 11: taps truncated at +-ceil(4 sigma_B),
+ * normalised to unit sum, zero outside the sky). Needed for every channel when
+ * lambda_s != 0. */
+ivis_status ivis_set_sd(ivis_plan_t plan, int chan, const float *tsd_dev, double sigma_sd,
+                        double fwhm_pix);
+
+/* Build work lists, allocate grids and capture the evaluation graph. Called implicitly by
+ * the first evaluation; call it explicitly to keep that cost out of timed regions.
+ * Errors: IVIS_ERR_STATE if a pointing, a channel's single-dish map (lambda_s != 0) or
+ * every pair of a channel is missing. */
+ivis_status ivis_prepare(ivis_plan_t plan);
+
+/* Q_tot and its gradient at sky_dev (real [nchan][n][n]). cost_out (host) receives
+ * Q_tot; terms_out (host, may be NULL) receives {Q, K, R}; grad_dev (real, same shape,
+ * may alias nothing else) receives the gradient. */
+ivis_status ivis_cost_grad(ivis_plan_t plan, const void *sky_dev, double *cost_out,
+                           void *grad_dev, double *terms_out);
+
+/* Same evaluation from HOST buffers: sky_host is copied in and the gradient copied out
+ * inside the call (the end-to-end path of a host-resident caller). */
+ivis_status ivis_cost_grad_host(ivis_plan_t plan, const void *sky_host, double *cost_out,
+                                void *grad_host, double *terms_out);
+
+/* Model visibilities (Eq. 3) of pair (k, chan) for sky_dev, in the caller's order of
+ * ivis_set_vis: real [m][2]. */
+ivis_status ivis_predict(ivis_plan_t plan, const void *sky_dev, int k, int chan,
+                         void *vis_out_dev);
+
+/* Single-dish model B (x) I (Eq. 11) of every channel: real [nchan][n][n]. Uses the
+ * dish beams given by ivis_set_sd. */
+ivis_status ivis_sd_predict(ivis_plan_t plan, const void *sky_dev, void *out_dev);
+
+/* Bounded limited-memory quasi-Newton solve of Eq. 10 on the device, started from
+ * sky_dev (real [nchan][n][n]; the paper starts from a null image) and overwritten with
+ * the result. m_hist correction pairs (<= 32). Stops after maxiter iterations, when the
+ * projected-gradient infinity norm <= pgtol, or when the relative decrease of Q_tot
+ * is <= ftol. Only the cost scalar crosses to the host per evaluation. rep may be NULL. */
+ivis_status ivis_solve(ivis_plan_t plan, void *sky_dev, int maxiter, int m_hist, double pgtol,
+                       double ftol, ivis_solve_report *rep);
+
+/* Kernel width w, ES shape beta and oversampled grid size actually used. */
+ivis_status ivis_get_nufft_params(ivis_plan_t plan, int *w, double *beta, int *nf);
+
+/* Stage timing. enable != 0 records CUDA events around every stage of each evaluation
+ * (on the plan's stream); ivis_stage_times then fills up to cap entries of names[] (static
+ * strings) and ms[] (mean milliseconds per evaluation since enabling) and returns the
+ * number of stages in *count. */
+ivis_status ivis_profile(ivis_plan_t plan, int enable);
+ivis_status ivis_stage_times(ivis_plan_t plan, const char **names, double *ms, int cap,
+                             int *count);
+
+/* Number of kernel launches one evaluation issues (the graph's kernel nodes). */
+ivis_status ivis_launches_per_eval(ivis_plan_t plan, int *count);
+
+/* Release every device resource of the plan. Safe on NULL. */
+ivis_status ivis_destroy(ivis_plan_t plan);
+
+/* Text of the last error on this plan (or of the last failed ivis_plan when plan is
+ * NULL). Valid until the next call on the plan. */
+const char *ivis_last_error(ivis_plan_t plan);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* IVIS_H */

@@ -1,0 +1,75 @@
+// common.cuh -- shared device helpers of the ivis engine (complex arithmetic, ES kernel,
+// block reductions).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace ivis {
+
+template <typename T> struct cplx_of;
+template <> struct cplx_of<float> { typedef float2 type; };
+template <> struct cplx_of<double> { typedef double2 type; };
+
+__device__ __forceinline__ float2 mk(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ double2 mk(double a, double b) { return make_double2(a, b); }
+__device__ __forceinline__ float2 operator+(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 operator-(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ double2 operator+(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 operator-(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+    return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+// a * conj(b)
+__device__ __forceinline__ float2 cmulc(float2 a, float2 b) {
+    return make_float2(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
+}
+__device__ __forceinline__ double2 cmulc(double2 a, double2 b) {
+    return make_double2(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
+}
+
+// Exponential-of-semicircle kernel (Barnett, Magland & af Klinteberg 2019):
+// psi(t) = exp(beta (sqrt(1 - z^2) - 1)), z = t / (w/2), zero for |z| > 1.
+__device__ __forceinline__ float es_kernel(float z, float beta) {
+    float a = 1.0f - z * z;
+    return a >= 0.0f ? expf(beta * (sqrtf(a) - 1.0f)) : 0.0f;
+}
+__device__ __forceinline__ double es_kernel(double z, double beta) {
+    double a = 1.0 - z * z;
+    return a >= 0.0 ? exp(beta * (sqrt(a) - 1.0)) : 0.0;
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Deterministic block sum (fixed tree for a fixed block size). scratch: >= 32 doubles.
+__device__ __forceinline__ double block_sum(double v, double *scratch) {
+    v = warp_sum(v);
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int nw = (blockDim.x + 31) >> 5;
+    __syncthreads();
+    if (lane == 0) scratch[wid] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (wid == 0) {
+        s = lane < nw ? scratch[lane] : 0.0;
+        s = warp_sum(s);
+    }
+    return s;  // valid in thread 0
+}
+
+__device__ __forceinline__ void atomic_add_c(float2 *p, float2 v) {
+    atomicAdd(&p->x, v.x);
+    atomicAdd(&p->y, v.y);
+}
+__device__ __forceinline__ void atomic_add_c(double2 *p, double2 v) {
+    atomicAdd(&p->x, v.x);
+    atomicAdd(&p->y, v.y);
+}
+
+}  // namespace ivis

@@ -1,0 +1,1047 @@
+// ivis.cu -- plan object and C ABI of the engine (see include/ivis.h).
+//
+// A plan owns every device buffer of one imaging problem: the pointing beams, the
+// visibilities of every (pointing, channel) pair converted to fine-grid coordinates and
+// sorted by grid tile, the oversampled grids of all pairs, the image-side buffers and the
+// FP64 partial sums. One evaluation of Q_tot and its gradient is a fixed sequence of kernel
+// launches; it is captured once into a CUDA graph and replayed, so the host issues one graph
+// launch per evaluation and reads back one FP64 cost.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/ivis.h"
+#include "kernels_image.cuh"
+#include "kernels_nufft.cuh"
+#include "kernels_solver.cuh"
+
+using namespace ivis;
+
+namespace {
+
+thread_local std::string g_plan_error;
+
+struct PairHost {
+    bool set = false;
+    int m = 0;
+    void *coord = nullptr, *vis = nullptr, *w = nullptr;
+    int *orig = nullptr;
+    std::vector<int> tile_count;  // per tile of the fine grid
+};
+
+struct Stage {
+    const char *name;
+    cudaEvent_t ev;
+};
+
+}  // namespace
+
+struct ivis_plan_s {
+    ivis_config cfg{};
+    cudaStream_t user_stream = nullptr;      // the caller's stream (may be the legacy default)
+    cudaStream_t stream = nullptr, side = nullptr;  // the plan's own capturable streams
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_in = nullptr;
+    bool fp64 = true;
+    size_t rsz = 8;  // sizeof(real)
+    int nf = 0, lognf = 0, W = 0;
+    double beta = 0.0;
+    int tile = 32, ntx = 0, ntiles = 0;
+    int logc_cols = 0;  // log2 columns per CTA in the column FFT passes
+    std::vector<double> dinv_h;
+    void *dinv_d = nullptr, *tw_d = nullptr, *beams_d = nullptr;
+    std::vector<int> cx, cy;
+    std::vector<char> pset;
+    std::vector<PairHost> pairs;  // index chan * npoint + k
+    // single dish
+    std::vector<char> sdset;
+    std::vector<double> sig_sd, fwhm_sd;
+    void *tsd_d = nullptr;
+    // prepared state
+    bool prepared = false;
+    int nslot = 0;
+    std::vector<int> slot_pair;            // slot -> pair index
+    std::vector<int> chunk_first;          // slot -> first chunk (size nslot + 1)
+    int nchunk = 0;
+    PairInfo *pinfo_d = nullptr;
+    void *pdata_d = nullptr;
+    Chunk *chunks_d = nullptr;
+    int *chan_start_d = nullptr, *chan_list_d = nullptr;
+    int Rsd = 0;
+    void *taps_d = nullptr;
+    double *inv_sig2_d = nullptr;
+    int conv_ty = 64;
+    void *rowbuf = nullptr, *F = nullptr, *G = nullptr, *contrib = nullptr;
+    void *x = nullptr, *g = nullptr, *tmp1 = nullptr, *tmp2 = nullptr, *gradK = nullptr;
+    double *jpart = nullptr, *kpart = nullptr, *rpart = nullptr, *cost_d = nullptr;
+    double *cost_h = nullptr;  // pinned
+    int nkpart = 0, nrpart = 0;
+    void *hstage = nullptr;    // pinned staging for the host-buffer entry point
+    cudaGraphExec_t graph = nullptr;
+    int launches = 0;
+    bool capturing = false;
+    // solver state
+    SolverBufs solver{};
+    // profiling
+    bool profile = false;
+    std::vector<Stage> stages;
+    std::vector<double> stage_ms;
+    long long prof_evals = 0;
+    std::string err;
+};
+
+namespace {
+
+#define CK(call)                                                                    \
+    do {                                                                            \
+        cudaError_t e_ = (call);                                                    \
+        if (e_ != cudaSuccess) {                                                    \
+            return fail(p, IVIS_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+        }                                                                           \
+    } while (0)
+
+ivis_status fail(ivis_plan_s *p, ivis_status s, const std::string &msg) {
+    if (p) p->err = msg;
+    else g_plan_error = msg;
+    return s;
+}
+
+ivis_status alloc(ivis_plan_s *p, void **ptr, size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc(ptr, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *ptr = nullptr;
+        return fail(p, IVIS_ERR_OOM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed: " +
+                                         cudaGetErrorString(e));
+    }
+    return IVIS_OK;
+}
+
+void dfree(void *&ptr) {
+    if (ptr) cudaFree(ptr);
+    ptr = nullptr;
+}
+
+// Order the plan's stream after everything already queued on the caller's stream.
+void enter(ivis_plan_s *p) {
+    cudaEventRecord(p->ev_in, p->user_stream);
+    cudaStreamWaitEvent(p->stream, p->ev_in, 0);
+}
+
+bool is_pow2(long long v) { return v > 0 && (v & (v - 1)) == 0; }
+int ilog2(long long v) {
+    int l = 0;
+    while ((1LL << l) < v) ++l;
+    return l;
+}
+
+// ---------------------------------------------------------------- host-side NUFFT set-up
+// Gauss-Legendre nodes/weights on [-1, 1] by Newton iteration on P_n.
+void gauss_legendre(int n, std::vector<double> &x, std::vector<double> &w) {
+    x.resize(n);
+    w.resize(n);
+    for (int i = 0; i < n; ++i) {
+        double z = std::cos(M_PI * (i + 0.75) / (n + 0.5));
+        for (int it = 0; it < 100; ++it) {
+            double p0 = 1.0, p1 = z;
+            for (int k = 2; k <= n; ++k) {
+                double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+                p0 = p1;
+                p1 = p2;
+            }
+            double dp = n * (z * p1 - p0) / (z * z - 1.0);
+            double dz = p1 / dp;
+            z -= dz;
+            if (std::fabs(dz) < 1e-16) break;
+        }
+        double p0 = 1.0, p1 = z;
+        for (int k = 2; k <= n; ++k) {
+            double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+            p0 = p1;
+            p1 = p2;
+        }
+        double dp = n * (z * p1 - p0) / (z * z - 1.0);
+        x[i] = z;
+        w[i] = 2.0 / ((1.0 - z * z) * dp * dp);
+    }
+}
+
+// Fourier transform of the ES kernel at integer frequency k of an nf grid:
+// psi_hat(k) = int_{-W/2}^{W/2} psi(t) cos(2 pi k t / nf) dt.
+void es_deapod(int nb, int nf, int W, double beta, std::vector<double> &dinv) {
+    std::vector<double> zx, zw;
+    gauss_legendre(200, zx, zw);
+    dinv.resize(nb);
+    for (int p = 0; p < nb; ++p) {
+        int k = p - nb / 2;
+        double acc = 0.0;
+        for (size_t i = 0; i < zx.size(); ++i) {
+            double z = zx[i];
+            double phi = std::exp(beta * (std::sqrt(1.0 - z * z) - 1.0));
+            acc += zw[i] * phi * std::cos(M_PI * k * W * z / nf);
+        }
+        dinv[p] = 1.0 / (0.5 * W * acc);
+    }
+}
+
+template <typename T>
+ivis_status upload_real(ivis_plan_s *p, void **dst, const std::vector<double> &src) {
+    std::vector<T> tmp(src.begin(), src.end());
+    ivis_status s = alloc(p, dst, tmp.size() * sizeof(T));
+    if (s) return s;
+    CK(cudaMemcpy(*dst, tmp.data(), tmp.size() * sizeof(T), cudaMemcpyHostToDevice));
+    return IVIS_OK;
+}
+
+template <typename T>
+ivis_status upload_twiddles(ivis_plan_s *p) {
+    typedef typename cplx_of<T>::type C;
+    int half = p->nf / 2;
+    std::vector<C> tw(half);
+    for (int j = 0; j < half; ++j) {
+        double a = 2.0 * M_PI * j / p->nf;
+        tw[j].x = (T)std::cos(a);
+        tw[j].y = (T)(-std::sin(a));
+    }
+    ivis_status s = alloc(p, &p->tw_d, half * sizeof(C));
+    if (s) return s;
+    CK(cudaMemcpy(p->tw_d, tw.data(), half * sizeof(C), cudaMemcpyHostToDevice));
+    return IVIS_OK;
+}
+
+// ------------------------------------------------------------------ kernel dispatch on W
+template <typename T, int MODE>
+cudaError_t launch_grid_pass(ivis_plan_s *p, int first_chunk, int nchunk, double *jpart,
+                             void *pred) {
+    typedef typename cplx_of<T>::type C;
+    if (nchunk <= 0) return cudaSuccess;
+    const int PW = p->tile + p->W - 1;
+    size_t smem = (size_t)PW * PW * sizeof(C) * (MODE == MODE_COSTGRAD ? 2 : 1);
+    const Chunk *ch = p->chunks_d + first_chunk;
+    const PairData<T> *pd = (const PairData<T> *)p->pdata_d;
+    const C *F = (const C *)p->F;
+    C *G = (C *)p->G;
+    T beta = (T)p->beta;
+#define GP_CASE(WW)                                                                           \
+    case WW: {                                                                                \
+        auto kern = k_grid_pass<T, WW, MODE>;                                                 \
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);   \
+        kern<<<nchunk, 256, smem, p->stream>>>(ch, pd, F, G, p->lognf, p->tile, p->ntx, beta, \
+                                               jpart, (C *)pred);                             \
+        break;                                                                                \
+    }
+    switch (p->W) {
+        GP_CASE(2) GP_CASE(3) GP_CASE(4) GP_CASE(5) GP_CASE(6) GP_CASE(7) GP_CASE(8) GP_CASE(9)
+        GP_CASE(10) GP_CASE(11) GP_CASE(12) GP_CASE(13) GP_CASE(14) GP_CASE(15) GP_CASE(16)
+        default: return cudaErrorInvalidValue;
+    }
+#undef GP_CASE
+    return cudaGetLastError();
+}
+
+int row_threads(int nf) { return std::min(512, std::max(32, nf / 2)); }
+
+template <typename T>
+cudaError_t launch_forward(ivis_plan_s *p, const void *sky) {
+    typedef typename cplx_of<T>::type C;
+    const int nb = p->cfg.nb, nf = p->nf;
+    dim3 gr(nb, p->nslot);
+    size_t smem_row = (size_t)nf * sizeof(C);
+    cudaFuncSetAttribute(k_fwd_rows<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_row);
+    k_fwd_rows<T><<<gr, row_threads(nf), smem_row, p->stream>>>(
+        (const T *)sky, (const T *)p->beams_d, p->pinfo_d, (const T *)p->dinv_d, (C *)p->rowbuf,
+        p->cfg.n, nb, p->lognf, (const C *)p->tw_d);
+    dim3 gc(nf >> p->logc_cols, p->nslot);
+    size_t smem_col = ((size_t)nf << p->logc_cols) * sizeof(C);
+    cudaFuncSetAttribute(k_fwd_cols<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_col);
+    k_fwd_cols<T><<<gc, 512, smem_col, p->stream>>>((const C *)p->rowbuf, (C *)p->F, nb, p->lognf,
+                                                    p->logc_cols, (const C *)p->tw_d);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_adjoint(ivis_plan_s *p) {
+    typedef typename cplx_of<T>::type C;
+    const int nb = p->cfg.nb, nf = p->nf;
+    dim3 gc(nf >> p->logc_cols, p->nslot);
+    size_t smem_col = ((size_t)nf << p->logc_cols) * sizeof(C);
+    cudaFuncSetAttribute(k_adj_cols<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_col);
+    k_adj_cols<T><<<gc, 512, smem_col, p->stream>>>((const C *)p->G, (C *)p->rowbuf, nb, p->lognf,
+                                                    p->logc_cols, (const C *)p->tw_d);
+    dim3 gr(nb, p->nslot);
+    size_t smem_row = (size_t)nf * sizeof(C);
+    cudaFuncSetAttribute(k_adj_rows<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_row);
+    k_adj_rows<T><<<gr, row_threads(nf), smem_row, p->stream>>>(
+        (const C *)p->rowbuf, (const T *)p->beams_d, p->pinfo_d, (const T *)p->dinv_d,
+        (T *)p->contrib, p->cfg.n, nb, p->lognf, (const C *)p->tw_d);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_fusion(ivis_plan_s *p, cudaStream_t st, const void *sky, void *tsd_out_e,
+                          void *gradK_out, bool fused) {
+    const int n = p->cfg.n, nchan = p->cfg.nchan, R = p->Rsd;
+    dim3 gr((n + 255) / 256, n, nchan);
+    size_t smr = (size_t)(256 + 2 * R) * sizeof(T);
+    cudaFuncSetAttribute(k_conv_rows<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smr);
+    size_t smc = (size_t)(p->conv_ty + 2 * R) * 32 * sizeof(T);
+    cudaFuncSetAttribute(k_conv_cols<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smc);
+    cudaFuncSetAttribute(k_conv_cols<T, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smc);
+    dim3 gcc((n + 31) / 32, (n + p->conv_ty - 1) / p->conv_ty, nchan);
+    k_conv_rows<T><<<gr, 256, smr, st>>>((const T *)sky, (T *)p->tmp1, (const T *)p->taps_d, R, n);
+    if (!fused) {  // plain B (x) I into tsd_out_e
+        k_conv_cols<T, 0><<<gcc, 256, smc, st>>>((const T *)p->tmp1, (T *)tsd_out_e,
+                                                 (const T *)p->taps_d, R, n, p->conv_ty, nullptr,
+                                                 nullptr, nullptr);
+        return cudaGetLastError();
+    }
+    k_conv_cols<T, 1><<<gcc, 256, smc, st>>>((const T *)p->tmp1, (T *)p->tmp2,
+                                             (const T *)p->taps_d, R, n, p->conv_ty,
+                                             (const T *)p->tsd_d, p->inv_sig2_d, p->kpart);
+    k_conv_rows<T><<<gr, 256, smr, st>>>((const T *)p->tmp2, (T *)p->tmp1, (const T *)p->taps_d, R, n);
+    k_conv_cols<T, 0><<<gcc, 256, smc, st>>>((const T *)p->tmp1, (T *)gradK_out,
+                                             (const T *)p->taps_d, R, n, p->conv_ty, nullptr,
+                                             nullptr, nullptr);
+    return cudaGetLastError();
+}
+
+void stage_mark(ivis_plan_s *p, const char *name, size_t &si) {
+    if (!p->profile || p->capturing) return;
+    if (si >= p->stages.size()) {
+        Stage s{name, nullptr};
+        cudaEventCreate(&s.ev);
+        p->stages.push_back(s);
+        p->stage_ms.push_back(0.0);
+    }
+    cudaEventRecord(p->stages[si].ev, p->stream);
+    ++si;
+}
+
+// Enqueue one full evaluation at p->x into p->g and p->cost_d (and cost_h).
+template <typename T>
+cudaError_t enqueue_eval(ivis_plan_s *p, bool capture) {
+    typedef typename cplx_of<T>::type C;
+    cudaError_t e;
+    const bool use_k = p->cfg.lambda_s != 0.0;
+    const bool use_r = p->cfg.lambda_r != 0.0;
+    size_t si = 0;
+    int launches = 0;
+    stage_mark(p, "start", si);
+    const bool fork = capture && use_k;
+    if (use_k) {
+        cudaStream_t st = p->stream;
+        if (fork) {
+            cudaEventRecord(p->ev_fork, p->stream);
+            cudaStreamWaitEvent(p->side, p->ev_fork, 0);
+            st = p->side;
+        }
+        if ((e = launch_fusion<T>(p, st, p->x, nullptr, p->gradK, true)) != cudaSuccess) return e;
+        launches += 4;
+        if (fork) {
+            cudaEventRecord(p->ev_join, p->side);
+        }
+        stage_mark(p, "fusion_K", si);
+    }
+    if (p->nslot > 0) {
+        cudaMemsetAsync(p->G, 0, (size_t)p->nslot * p->nf * p->nf * sizeof(C), p->stream);
+        stage_mark(p, "zero_adjoint_grid", si);
+        if ((e = launch_forward<T>(p, p->x)) != cudaSuccess) return e;
+        launches += 2;
+        stage_mark(p, "fwd_fft", si);
+        if ((e = launch_grid_pass<T, MODE_COSTGRAD>(p, 0, p->nchunk, p->jpart, nullptr)) != cudaSuccess)
+            return e;
+        launches += 1;
+        stage_mark(p, "degrid_spread", si);
+        if ((e = launch_adjoint<T>(p)) != cudaSuccess) return e;
+        launches += 2;
+        stage_mark(p, "adj_fft", si);
+    }
+    if (fork) cudaStreamWaitEvent(p->stream, p->ev_join, 0);
+    const int n = p->cfg.n, nchan = p->cfg.nchan;
+    const size_t npix = (size_t)nchan * n * n;
+    k_assemble<T><<<(unsigned)((npix + 255) / 256), 256, 0, p->stream>>>(
+        (const T *)p->x, (const T *)p->contrib, p->pinfo_d, p->chan_start_d, p->chan_list_d,
+        (const T *)p->gradK, (T *)p->g, n, p->cfg.nb, nchan, (T)p->cfg.lambda_r,
+        (T)p->cfg.lambda_s, use_r ? 1 : 0, use_k ? 1 : 0, p->rpart);
+    launches += 1;
+    stage_mark(p, "assemble_R", si);
+    k_finalize<<<1, 256, 0, p->stream>>>(p->jpart, p->nchunk, p->kpart, use_k ? p->nkpart : 0,
+                                         p->rpart, use_r ? p->nrpart : 0, p->cfg.lambda_r,
+                                         p->cfg.lambda_s, p->cost_d);
+    launches += 1;
+    cudaMemcpyAsync(p->cost_h, p->cost_d, 4 * sizeof(double), cudaMemcpyDeviceToHost, p->stream);
+    stage_mark(p, "finalize", si);
+    p->launches = launches;
+    return cudaGetLastError();
+}
+
+cudaError_t enqueue_eval_any(ivis_plan_s *p, bool capture) {
+    return p->fp64 ? enqueue_eval<double>(p, capture) : enqueue_eval<float>(p, capture);
+}
+
+ivis_status capture_graph(ivis_plan_s *p) {
+    if (p->graph) {
+        cudaGraphExecDestroy(p->graph);
+        p->graph = nullptr;
+    }
+    cudaGraph_t gph;
+    CK(cudaStreamBeginCapture(p->stream, cudaStreamCaptureModeRelaxed));
+    p->capturing = true;
+    cudaError_t e = enqueue_eval_any(p, true);
+    p->capturing = false;
+    cudaError_t e2 = cudaStreamEndCapture(p->stream, &gph);
+    if (e != cudaSuccess) return fail(p, IVIS_ERR_CUDA, std::string("capture: ") + cudaGetErrorString(e));
+    if (e2 != cudaSuccess) return fail(p, IVIS_ERR_CUDA, std::string("end capture: ") + cudaGetErrorString(e2));
+    e = cudaGraphInstantiate(&p->graph, gph, 0);
+    cudaGraphDestroy(gph);
+    if (e != cudaSuccess) return fail(p, IVIS_ERR_CUDA, std::string("instantiate: ") + cudaGetErrorString(e));
+    return IVIS_OK;
+}
+
+// Run one evaluation at p->x (graph replay, or direct launches with stage events).
+ivis_status run_eval(ivis_plan_s *p) {
+    if (p->profile) {
+        cudaError_t e = enqueue_eval_any(p, false);
+        if (e != cudaSuccess) return fail(p, IVIS_ERR_CUDA, std::string("eval: ") + cudaGetErrorString(e));
+        CK(cudaStreamSynchronize(p->stream));
+        for (size_t i = 1; i < p->stages.size(); ++i) {
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, p->stages[i - 1].ev, p->stages[i].ev);
+            p->stage_ms[i] += ms;
+        }
+        p->prof_evals++;
+    } else {
+        CK(cudaGraphLaunch(p->graph, p->stream));
+        CK(cudaStreamSynchronize(p->stream));
+    }
+    if (!std::isfinite(p->cost_h[0]))
+        return fail(p, IVIS_ERR_NONFINITE, "non-finite cost");
+    return IVIS_OK;
+}
+
+template <typename T>
+ivis_status set_vis_impl(ivis_plan_s *p, PairHost &ph, int m, const float *uvw, const float *vis,
+                         const float *w) {
+    typedef typename coord_of<T>::type CO;
+    typedef typename cplx_of<T>::type C;
+    void *coord_tmp = nullptr, *key = nullptr, *cnt = nullptr, *err = nullptr;
+    ivis_status s;
+    if ((s = alloc(p, &coord_tmp, (size_t)m * sizeof(CO)))) return s;
+    if ((s = alloc(p, &key, (size_t)m * sizeof(int)))) { dfree(coord_tmp); return s; }
+    if ((s = alloc(p, &cnt, (size_t)p->ntiles * sizeof(int)))) { dfree(coord_tmp); dfree(key); return s; }
+    if ((s = alloc(p, &err, sizeof(int)))) { dfree(coord_tmp); dfree(key); dfree(cnt); return s; }
+    auto cleanup = [&]() { dfree(coord_tmp); dfree(key); dfree(cnt); dfree(err); };
+    cudaMemsetAsync(err, 0, sizeof(int), p->stream);
+    cudaMemsetAsync(cnt, 0, (size_t)p->ntiles * sizeof(int), p->stream);
+    int nblk = (m + 255) / 256;
+    double scale = p->cfg.cell_rad * p->nf;
+    k_vis_prepare<T><<<nblk, 256, 0, p->stream>>>(m, uvw, vis, w, scale, p->lognf, p->W, p->tile,
+                                                   p->ntx, (CO *)coord_tmp, (int *)key, (int *)err);
+    k_hist<<<nblk, 256, 0, p->stream>>>(m, (const int *)key, (int *)cnt);
+    int herr = 0;
+    ph.tile_count.assign(p->ntiles, 0);
+    cudaError_t e = cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, p->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(ph.tile_count.data(), cnt, (size_t)p->ntiles * sizeof(int),
+                            cudaMemcpyDeviceToHost, p->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
+    if (e != cudaSuccess) { cleanup(); return fail(p, IVIS_ERR_CUDA, std::string("set_vis: ") + cudaGetErrorString(e)); }
+    if (herr) { cleanup(); return fail(p, IVIS_ERR_NONFINITE, "set_vis: non-finite uvw/vis/weight or negative weight"); }
+    std::vector<int> start(p->ntiles);
+    int acc = 0;
+    for (int t = 0; t < p->ntiles; ++t) { start[t] = acc; acc += ph.tile_count[t]; }
+    if ((s = alloc(p, &ph.coord, (size_t)m * sizeof(CO))) || (s = alloc(p, &ph.vis, (size_t)m * sizeof(C))) ||
+        (s = alloc(p, &ph.w, (size_t)m * sizeof(T))) || (s = alloc(p, (void **)&ph.orig, (size_t)m * sizeof(int)))) {
+        cleanup();
+        return s;
+    }
+    e = cudaMemcpyAsync(cnt, start.data(), (size_t)p->ntiles * sizeof(int), cudaMemcpyHostToDevice, p->stream);
+    if (e == cudaSuccess) {
+        k_vis_scatter<T><<<nblk, 256, 0, p->stream>>>(m, (const int *)key, (const CO *)coord_tmp, vis, w,
+                                                       (int *)cnt, (CO *)ph.coord, (C *)ph.vis, (T *)ph.w, ph.orig);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
+    cleanup();
+    if (e != cudaSuccess) return fail(p, IVIS_ERR_CUDA, std::string("set_vis scatter: ") + cudaGetErrorString(e));
+    ph.m = m;
+    ph.set = true;
+    return IVIS_OK;
+}
+
+void free_pair(PairHost &ph) {
+    dfree(ph.coord);
+    dfree(ph.vis);
+    dfree(ph.w);
+    void *o = ph.orig;
+    dfree(o);
+    ph.orig = nullptr;
+    ph.set = false;
+    ph.m = 0;
+}
+
+void release_prepared(ivis_plan_s *p) {
+    if (p->graph) cudaGraphExecDestroy(p->graph);
+    p->graph = nullptr;
+    void *pi = p->pinfo_d, *ck = p->chunks_d, *cs = p->chan_start_d, *cl = p->chan_list_d;
+    dfree(pi); dfree(p->pdata_d); dfree(ck); dfree(cs); dfree(cl);
+    p->pinfo_d = nullptr; p->chunks_d = nullptr; p->chan_start_d = nullptr; p->chan_list_d = nullptr;
+    dfree(p->taps_d);
+    void *is = p->inv_sig2_d; dfree(is); p->inv_sig2_d = nullptr;
+    dfree(p->rowbuf); dfree(p->F); dfree(p->G); dfree(p->contrib);
+    dfree(p->x); dfree(p->g); dfree(p->tmp1); dfree(p->tmp2); dfree(p->gradK);
+    void *a = p->jpart, *b = p->kpart, *c = p->rpart, *d = p->cost_d;
+    dfree(a); dfree(b); dfree(c); dfree(d);
+    p->jpart = p->kpart = p->rpart = p->cost_d = nullptr;
+    solver_free(p->solver);
+    p->prepared = false;
+}
+
+template <typename T>
+ivis_status prepare_impl(ivis_plan_s *p) {
+    typedef typename cplx_of<T>::type C;
+    const ivis_config &c = p->cfg;
+    ivis_status s;
+    for (int k = 0; k < c.npoint; ++k)
+        if (!p->pset[k]) return fail(p, IVIS_ERR_STATE, "pointing " + std::to_string(k) + " not set");
+    for (size_t i = 0; i < p->pairs.size(); ++i)
+        if (!p->pairs[i].set)
+            return fail(p, IVIS_ERR_STATE, "visibilities of pair (k=" + std::to_string(i % c.npoint) +
+                                               ", chan=" + std::to_string(i / c.npoint) + ") not set");
+    if (c.lambda_s != 0.0)
+        for (int ch = 0; ch < c.nchan; ++ch)
+            if (!p->sdset[ch]) return fail(p, IVIS_ERR_STATE, "single-dish map of channel " + std::to_string(ch) + " not set");
+    // slots: pairs with data, in (chan, k) order
+    p->slot_pair.clear();
+    for (size_t i = 0; i < p->pairs.size(); ++i)
+        if (p->pairs[i].m > 0) p->slot_pair.push_back((int)i);
+    p->nslot = (int)p->slot_pair.size();
+    std::vector<PairInfo> pinfo(p->nslot);
+    std::vector<PairData<T>> pdata(p->nslot);
+    std::vector<Chunk> chunks;
+    p->chunk_first.assign(p->nslot + 1, 0);
+    const int CH = 1024;
+    std::vector<int> chan_start(c.nchan + 1, 0), chan_list;
+    for (int sl = 0; sl < p->nslot; ++sl) {
+        int pi_ = p->slot_pair[sl];
+        int k = pi_ % c.npoint, ch = pi_ / c.npoint;
+        pinfo[sl] = PairInfo{k, ch, p->cx[k], p->cy[k]};
+        PairHost &ph = p->pairs[pi_];
+        pdata[sl].coord = (const typename coord_of<T>::type *)ph.coord;
+        pdata[sl].vis = (const C *)ph.vis;
+        pdata[sl].w = (const T *)ph.w;
+        pdata[sl].orig = ph.orig;
+        pdata[sl].m = ph.m;
+        p->chunk_first[sl] = (int)chunks.size();
+        int acc = 0;
+        for (int t = 0; t < p->ntiles; ++t) {
+            int cnt = ph.tile_count[t];
+            for (int b = 0; b < cnt; b += CH)
+                chunks.push_back(Chunk{sl, t, acc + b, acc + std::min(cnt, b + CH)});
+            acc += cnt;
+        }
+    }
+    p->chunk_first[p->nslot] = (int)chunks.size();
+    p->nchunk = (int)chunks.size();
+    for (int ch = 0; ch < c.nchan; ++ch) {
+        chan_start[ch] = (int)chan_list.size();
+        for (int sl = 0; sl < p->nslot; ++sl)
+            if (pinfo[sl].chan == ch) chan_list.push_back(sl);
+    }
+    chan_start[c.nchan] = (int)chan_list.size();
+    auto up = [&](void **dst, const void *src, size_t bytes) -> ivis_status {
+        ivis_status st = alloc(p, dst, bytes);
+        if (st) return st;
+        if (bytes) CK(cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice));
+        return IVIS_OK;
+    };
+    if ((s = up((void **)&p->pinfo_d, pinfo.data(), pinfo.size() * sizeof(PairInfo)))) return s;
+    if ((s = up(&p->pdata_d, pdata.data(), pdata.size() * sizeof(PairData<T>)))) return s;
+    if ((s = up((void **)&p->chunks_d, chunks.data(), chunks.size() * sizeof(Chunk)))) return s;
+    if ((s = up((void **)&p->chan_start_d, chan_start.data(), chan_start.size() * sizeof(int)))) return s;
+    if ((s = up((void **)&p->chan_list_d, chan_list.data(), chan_list.size() * sizeof(int)))) return s;
+    const size_t nf2 = (size_t)p->nf * p->nf;
+    const size_t npix = (size_t)c.nchan * c.n * c.n;
+    if ((s = alloc(p, &p->rowbuf, (size_t)p->nslot * c.nb * p->nf * sizeof(C)))) return s;
+    if ((s = alloc(p, &p->F, (size_t)p->nslot * nf2 * sizeof(C)))) return s;
+    if ((s = alloc(p, &p->G, (size_t)p->nslot * nf2 * sizeof(C)))) return s;
+    if ((s = alloc(p, &p->contrib, (size_t)p->nslot * c.nb * c.nb * sizeof(T)))) return s;
+    if ((s = alloc(p, &p->x, npix * sizeof(T)))) return s;
+    if ((s = alloc(p, &p->g, npix * sizeof(T)))) return s;
+    if ((s = alloc(p, (void **)&p->jpart, (size_t)std::max(1, p->nchunk) * sizeof(double)))) return s;
+    p->nrpart = (int)((npix + 255) / 256);
+    if ((s = alloc(p, (void **)&p->rpart, (size_t)p->nrpart * sizeof(double)))) return s;
+    if ((s = alloc(p, (void **)&p->cost_d, 4 * sizeof(double)))) return s;
+    // single dish: taps with a common half-width, per-channel 1/sigma^2
+    bool need_sd = false;
+    for (int ch = 0; ch < c.nchan; ++ch) need_sd |= (bool)p->sdset[ch];
+    if (need_sd) {
+        int R = 0;
+        for (int ch = 0; ch < c.nchan; ++ch) {
+            double sg = p->fwhm_sd[ch] / (2.0 * std::sqrt(2.0 * std::log(2.0)));
+            R = std::max(R, (int)std::ceil(4.0 * sg));
+        }
+        p->Rsd = R;
+        std::vector<double> taps((size_t)c.nchan * (2 * R + 1), 0.0), is2(c.nchan, 0.0);
+        for (int ch = 0; ch < c.nchan; ++ch) {
+            if (!p->sdset[ch]) continue;
+            double sg = p->fwhm_sd[ch] / (2.0 * std::sqrt(2.0 * std::log(2.0)));
+            int r = (int)std::ceil(4.0 * sg);
+            double sum = 0.0;
+            for (int t = -r; t <= r; ++t) sum += std::exp(-0.5 * (t / sg) * (t / sg));
+            for (int t = -r; t <= r; ++t)
+                taps[(size_t)ch * (2 * R + 1) + R + t] = std::exp(-0.5 * (t / sg) * (t / sg)) / sum;
+            is2[ch] = 1.0 / (p->sig_sd[ch] * p->sig_sd[ch]);
+        }
+        if ((s = upload_real<T>(p, &p->taps_d, taps))) return s;
+        if ((s = up((void **)&p->inv_sig2_d, is2.data(), is2.size() * sizeof(double)))) return s;
+        p->conv_ty = 64;
+        while (p->conv_ty > 8 && (size_t)(p->conv_ty + 2 * R) * 32 * sizeof(T) > 160 * 1024) p->conv_ty /= 2;
+        if ((size_t)(p->conv_ty + 2 * R) * 32 * sizeof(T) > 200 * 1024)
+            return fail(p, IVIS_ERR_ARG, "single-dish beam too wide for the column pass");
+        if ((s = alloc(p, &p->tmp1, npix * sizeof(T)))) return s;
+        if ((s = alloc(p, &p->tmp2, npix * sizeof(T)))) return s;
+        if ((s = alloc(p, &p->gradK, npix * sizeof(T)))) return s;
+        p->nkpart = ((c.n + 31) / 32) * ((c.n + p->conv_ty - 1) / p->conv_ty) * c.nchan;
+        if ((s = alloc(p, (void **)&p->kpart, (size_t)p->nkpart * sizeof(double)))) return s;
+    }
+    if (!p->kpart && (s = alloc(p, (void **)&p->kpart, sizeof(double)))) return s;
+    if ((s = solver_alloc<T>(p->solver, npix))) return fail(p, s, "solver buffers: out of device memory");
+    p->prepared = true;
+    if ((s = capture_graph(p))) { p->prepared = false; return s; }
+    return IVIS_OK;
+}
+
+ivis_status ensure_prepared(ivis_plan_s *p) {
+    if (p->prepared) return IVIS_OK;
+    release_prepared(p);
+    ivis_status s = p->fp64 ? prepare_impl<double>(p) : prepare_impl<float>(p);
+    if (s) release_prepared(p);
+    return s;
+}
+
+void invalidate(ivis_plan_s *p) {
+    if (p->prepared) release_prepared(p);
+}
+
+// ------------------------------------------------------------------------------- solver
+template <typename T>
+ivis_status solve_impl(ivis_plan_s *p, void *sky_dev, int maxiter, int m_hist, double pgtol,
+                       double ftol, ivis_solve_report *rep) {
+    auto t0 = std::chrono::steady_clock::now();
+    SolverBufs &B = p->solver;
+    ivis_status s = solver_ensure<T>(B, m_hist);
+    if (s) return fail(p, s, "solver buffers: out of device memory");
+    const size_t n = B.npix;
+    const size_t bytes = n * sizeof(T);
+    const int pos = p->cfg.positivity ? 1 : 0;
+    const int stride = 3 * B.mcap + 4;
+    const unsigned nb = (unsigned)B.nblk;
+    T *x = (T *)p->x, *g = (T *)p->g, *xk = (T *)B.xk, *gk = (T *)B.gk, *d = (T *)B.d;
+    T *S = (T *)B.S, *Y = (T *)B.Y;
+    CK(cudaMemcpyAsync(x, sky_dev, bytes, cudaMemcpyDeviceToDevice, p->stream));
+    k_sol_project<T><<<(unsigned)((n + 255) / 256), 256, 0, p->stream>>>(x, n, pos);
+    CK(cudaMemsetAsync(B.scal, 0, 16 * sizeof(double), p->stream));
+    if ((s = run_eval(p))) return s;
+    double f = p->cost_h[0];
+    int evals = 1, iters = 0, status = 1;
+    double pg = 0.0;
+    CK(cudaMemcpyAsync(xk, x, bytes, cudaMemcpyDeviceToDevice, p->stream));
+    CK(cudaMemcpyAsync(gk, g, bytes, cudaMemcpyDeviceToDevice, p->stream));
+    std::vector<int> order;
+    const double c1 = 1e-4;
+    for (int it = 0; it <= maxiter; ++it) {
+        SlotList ord{};
+        ord.m = (int)order.size();
+        for (int t = 0; t < ord.m; ++t) ord.slot[t] = order[t];
+        k_sol_dots<T><<<nb, 256, 0, p->stream>>>(n, xk, gk, pos, S, Y, ord, stride, B.part);
+        k_sol_small<<<1, 128, 0, p->stream>>>(B.nblk, stride, B.part, ord, B.SY, B.YY, B.mcap, B.coef, B.scal);
+        k_sol_dir<T><<<nb, 256, 0, p->stream>>>(n, xk, gk, pos, S, Y, ord, B.coef, B.scal, d, stride, B.part);
+        k_sol_sum<<<1, 256, 0, p->stream>>>(B.nblk, stride, B.part, B.scal, 1);
+        CK(cudaGetLastError());
+        CK(cudaMemcpyAsync(B.scal_h, B.scal, 8 * sizeof(double), cudaMemcpyDeviceToHost, p->stream));
+        CK(cudaStreamSynchronize(p->stream));
+        const double gd = B.scal_h[1];
+        pg = B.scal_h[2];
+        const double gg = B.scal_h[3];
+        if (pg <= pgtol) { status = 0; break; }
+        if (it == maxiter) { status = 1; break; }
+        if (!(gd < 0.0) || !std::isfinite(gd)) {
+            if (!order.empty()) { order.clear(); --it; continue; }
+            status = 2;
+            break;
+        }
+        double alpha = order.empty() ? std::min(1.0, 1.0 / std::sqrt(gg)) : 1.0;
+        bool accepted = false;
+        double fnew = f;
+        for (int trial = 0; trial < 40; ++trial) {
+            k_sol_trial<T><<<nb, 256, 0, p->stream>>>(n, xk, gk, d, alpha, pos, x, stride, B.part);
+            k_sol_sum<<<1, 256, 0, p->stream>>>(B.nblk, stride, B.part, B.scal, 4);
+            CK(cudaGetLastError());
+            ivis_status es = run_eval(p);
+            ++evals;
+            if (es && es != IVIS_ERR_NONFINITE) return es;
+            CK(cudaMemcpyAsync(B.scal_h + 4, B.scal + 4, sizeof(double), cudaMemcpyDeviceToHost, p->stream));
+            CK(cudaStreamSynchronize(p->stream));
+            fnew = p->cost_h[0];
+            const double dd = B.scal_h[4];
+            if (es == IVIS_OK && fnew <= f + c1 * dd && dd <= 0.0) { accepted = true; break; }
+            if (dd == 0.0) break;  // the projected step no longer moves
+            // safeguarded quadratic backtracking on phi(a) = f(P(x + a d))
+            double anew = 0.5 * alpha;
+            if (es == IVIS_OK && std::isfinite(fnew)) {
+                const double den = 2.0 * (fnew - f - dd);
+                if (den > 0.0) anew = -dd * alpha / den;
+            }
+            alpha = std::min(0.5 * alpha, std::max(0.1 * alpha, anew));
+        }
+        if (!accepted) {
+            status = 2;
+            CK(cudaMemcpyAsync(x, xk, bytes, cudaMemcpyDeviceToDevice, p->stream));
+            break;
+        }
+        ++iters;
+        // new correction pair
+        int slot;
+        if ((int)order.size() < m_hist) {
+            std::vector<char> used(B.mcap, 0);
+            for (int o : order) used[o] = 1;
+            slot = 0;
+            while (used[slot]) ++slot;
+        } else {
+            slot = order.front();
+            order.erase(order.begin());
+        }
+        SlotList ou{};
+        ou.m = (int)order.size() + 1;
+        for (size_t t = 0; t < order.size(); ++t) ou.slot[t] = order[t];
+        ou.slot[ou.m - 1] = slot;
+        k_sol_update<T><<<nb, 256, 0, p->stream>>>(n, x, g, xk, gk, S, Y, slot, ou, stride, B.part);
+        k_sol_update_small<<<1, 128, 0, p->stream>>>(B.nblk, stride, B.part, slot, ou, B.SY, B.YY,
+                                                     B.mcap, 2.2e-16, B.scal);
+        CK(cudaGetLastError());
+        CK(cudaMemcpyAsync(B.scal_h + 5, B.scal + 5, sizeof(double), cudaMemcpyDeviceToHost, p->stream));
+        CK(cudaStreamSynchronize(p->stream));
+        if (B.scal_h[5] != 0.0) order.push_back(slot);
+        const double rel = (f - fnew) / std::max(std::max(std::fabs(f), std::fabs(fnew)), 1.0);
+        f = fnew;
+        if (rel <= ftol) { status = 0; break; }
+    }
+    CK(cudaMemcpyAsync(sky_dev, xk, bytes, cudaMemcpyDeviceToDevice, p->stream));
+    CK(cudaStreamSynchronize(p->stream));
+    if (rep) {
+        rep->iterations = iters;
+        rep->evaluations = evals;
+        rep->f = f;
+        rep->pg_inf = pg;
+        rep->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        rep->status = status;
+    }
+    if (status == 2 && iters == 0) return fail(p, IVIS_ERR_LINESEARCH, "line search found no decrease");
+    return IVIS_OK;
+}
+
+}  // namespace
+
+// ======================================================================= C ABI
+extern "C" {
+
+ivis_status ivis_plan(const ivis_config *cfg, void *stream, ivis_plan_t *out) {
+    if (!cfg || !out) return fail(nullptr, IVIS_ERR_ARG, "null config or output pointer");
+    *out = nullptr;
+    const ivis_config &c = *cfg;
+    if (c.n < 1 || c.nchan < 1 || c.npoint < 1) return fail(nullptr, IVIS_ERR_ARG, "n, nchan, npoint must be >= 1");
+    if (!is_pow2(c.nb) || c.nb < 16 || c.nb > 2048) return fail(nullptr, IVIS_ERR_ARG, "nb must be a power of two in [16, 2048]");
+    if (!(c.cell_rad > 0.0) || !std::isfinite(c.cell_rad)) return fail(nullptr, IVIS_ERR_ARG, "cell_rad must be > 0");
+    if (c.precision != IVIS_FP64 && c.precision != IVIS_FP32) return fail(nullptr, IVIS_ERR_ARG, "precision must be IVIS_FP64 or IVIS_FP32");
+    if (c.kernel_width != 0 && (c.kernel_width < 2 || c.kernel_width > 16)) return fail(nullptr, IVIS_ERR_ARG, "kernel_width must be 0 or in [2, 16]");
+    if (c.kernel_width == 0 && !(c.nufft_tol > 0.0 && c.nufft_tol < 1.0)) return fail(nullptr, IVIS_ERR_ARG, "nufft_tol must be in (0, 1)");
+    if (!std::isfinite(c.lambda_r) || !std::isfinite(c.lambda_s) || c.lambda_r < 0 || c.lambda_s < 0)
+        return fail(nullptr, IVIS_ERR_NONFINITE, "lambda_r and lambda_s must be finite and >= 0");
+    ivis_plan_s *p = new (std::nothrow) ivis_plan_s();
+    if (!p) return fail(nullptr, IVIS_ERR_OOM, "host allocation failed");
+    p->cfg = c;
+    p->user_stream = (cudaStream_t)stream;
+    p->fp64 = c.precision == IVIS_FP64;
+    p->rsz = p->fp64 ? 8 : 4;
+    p->nf = 2 * c.nb;
+    p->lognf = ilog2(p->nf);
+    if (!p->fp64 && p->nf > 4096) { delete p; return fail(nullptr, IVIS_ERR_ARG, "IVIS_FP32 supports nb <= 2048"); }
+    if (c.kernel_width) p->W = c.kernel_width;
+    else p->W = std::min(16, std::max(2, (int)std::ceil(-std::log10(c.nufft_tol)) + 1));
+    p->beta = 2.30 * p->W;
+    p->tile = std::min(32, p->nf);
+    p->ntx = p->nf / p->tile;
+    p->ntiles = p->ntx * p->ntx;
+    {
+        // columns per CTA in the column FFT passes: fill up to 96 KB of shared memory
+        size_t csz = p->fp64 ? 16 : 8;
+        int logc = 0;
+        while (logc < 4 && ((size_t)p->nf << (logc + 1)) * csz <= 96 * 1024) ++logc;
+        p->logc_cols = logc;
+        if (((size_t)p->nf << logc) * csz > 200 * 1024) { delete p; return fail(nullptr, IVIS_ERR_ARG, "grid too large"); }
+    }
+    p->cx.assign(c.npoint, 0);
+    p->cy.assign(c.npoint, 0);
+    p->pset.assign(c.npoint, 0);
+    p->pairs.resize((size_t)c.npoint * c.nchan);
+    p->sdset.assign(c.nchan, 0);
+    p->sig_sd.assign(c.nchan, 1.0);
+    p->fwhm_sd.assign(c.nchan, 0.0);
+    ivis_status s = IVIS_OK;
+    if (cudaStreamCreateWithFlags(&p->stream, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        delete p;
+        return fail(nullptr, IVIS_ERR_CUDA, "stream creation failed");
+    }
+    es_deapod(c.nb, p->nf, p->W, p->beta, p->dinv_h);
+    if (p->fp64) {
+        s = upload_real<double>(p, &p->dinv_d, p->dinv_h);
+        if (!s) s = upload_twiddles<double>(p);
+    } else {
+        s = upload_real<float>(p, &p->dinv_d, p->dinv_h);
+        if (!s) s = upload_twiddles<float>(p);
+    }
+    if (!s) s = alloc(p, &p->beams_d, (size_t)c.npoint * c.nb * c.nb * p->rsz);
+    if (!s) {
+        if (cudaMemset(p->beams_d, 0, (size_t)c.npoint * c.nb * c.nb * p->rsz) != cudaSuccess) s = IVIS_ERR_CUDA;
+    }
+    if (!s) s = alloc(p, &p->tsd_d, (size_t)c.nchan * c.n * c.n * p->rsz);
+    if (!s && cudaStreamCreateWithFlags(&p->side, cudaStreamNonBlocking) != cudaSuccess) s = IVIS_ERR_CUDA;
+    if (!s && cudaEventCreateWithFlags(&p->ev_in, cudaEventDisableTiming) != cudaSuccess) s = IVIS_ERR_CUDA;
+    if (!s && cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming) != cudaSuccess) s = IVIS_ERR_CUDA;
+    if (!s && cudaEventCreateWithFlags(&p->ev_join, cudaEventDisableTiming) != cudaSuccess) s = IVIS_ERR_CUDA;
+    if (!s && cudaMallocHost((void **)&p->cost_h, 4 * sizeof(double)) != cudaSuccess) s = IVIS_ERR_OOM;
+    if (s) {
+        g_plan_error = p->err.empty() ? "plan set-up failed" : p->err;
+        ivis_destroy(p);
+        return s;
+    }
+    *out = p;
+    return IVIS_OK;
+}
+
+ivis_status ivis_set_pointing(ivis_plan_t p, int k, int cx, int cy, const float *beam_dev) {
+    if (!p) return fail(nullptr, IVIS_ERR_ARG, "null plan");
+    if (k < 0 || k >= p->cfg.npoint || !beam_dev) return fail(p, IVIS_ERR_ARG, "bad pointing index or null beam");
+    enter(p);
+    size_t nn = (size_t)p->cfg.nb * p->cfg.nb;
+    char *dst = (char *)p->beams_d + (size_t)k * nn * p->rsz;
+    if (p->fp64) k_f32_to<double><<<(unsigned)((nn + 255) / 256), 256, 0, p->stream>>>(beam_dev, (double *)dst, nn);
+    else CK(cudaMemcpyAsync(dst, beam_dev, nn * sizeof(float), cudaMemcpyDeviceToDevice, p->stream));
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(p->stream));
+    p->cx[k] = cx;
+    p->cy[k] = cy;
+    p->pset[k] = 1;
+    invalidate(p);
+    return IVIS_OK;
+}
+
+ivis_status ivis_set_vis(ivis_plan_t p, int k, int chan, int64_t m, const float *uvw_dev,
+                         const float *vis_dev, const float *weight_dev) {
+    if (!p) return fail(nullptr, IVIS_ERR_ARG, "null plan");
+    if (k < 0 || k >= p->cfg.npoint || chan < 0 || chan >= p->cfg.nchan || m < 0 || m > (int64_t)0x7fffffff)
+        return fail(p, IVIS_ERR_ARG, "bad pair index or visibility count");
+    if (m > 0 && (!uvw_dev || !vis_dev || !weight_dev)) return fail(p, IVIS_ERR_ARG, "null visibility pointer");
+    enter(p);
+    PairHost &ph = p->pairs[(size_t)chan * p->cfg.npoint + k];
+    invalidate(p);
+    free_pair(ph);
+    if (m == 0) {
+        ph.set = true;
+        return IVIS_OK;
+    }
+    return p->fp64 ? set_vis_impl<double>(p, ph, (int)m, uvw_dev, vis_dev, weight_dev)
+                   : set_vis_impl<float>(p, ph, (int)m, uvw_dev, vis_dev, weight_dev);
+}
+
+ivis_status ivis_set_sd(ivis_plan_t p, int chan, const float *tsd_dev, double sigma_sd, double fwhm_pix) {
+    if (!p) return fail(nullptr, IVIS_ERR_ARG, "null plan");
+    if (chan < 0 || chan >= p->cfg.nchan || !tsd_dev) return fail(p, IVIS_ERR_ARG, "bad channel or null map");
+    if (!(sigma_sd > 0.0) || !std::isfinite(sigma_sd) || !(fwhm_pix > 0.0) || !std::isfinite(fwhm_pix))
+        return fail(p, IVIS_ERR_ARG, "sigma_sd and fwhm_pix must be finite and > 0");
+    enter(p);
+    size_t nn = (size_t)p->cfg.n * p->cfg.n;
+    char *dst = (char *)p->tsd_d + (size_t)chan * nn * p->rsz;
+    if (p->fp64) k_f32_to<double><<<(unsigned)((nn + 255) / 256), 256, 0, p->stream>>>(tsd_dev, (double *)dst, nn);
+    else CK(cudaMemcpyAsync(dst, tsd_dev, nn * sizeof(float), cudaMemcpyDeviceToDevice, p->stream));
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(p->stream));
+    p->sdset[chan] = 1;
+    p->sig_sd[chan] = sigma_sd;
+    p->fwhm_sd[chan] = fwhm_pix;
+    invalidate(p);
+    return IVIS_OK;
+}
+
+ivis_status ivis_prepare(ivis_plan_t p) {
+    if (!p) return fail(nullptr, IVIS_ERR_ARG, "null plan");
+    enter(p);
+    return ensure_prepared(p);
+}
+
+ivis_status ivis_cost_grad(ivis_plan_t p, const void *sky_dev, double *cost_out, void *grad_dev,
+                           double *terms_out) {
+    if (!p) return fail(nullptr, IVIS_ERR_ARG, "null plan");
+    if (!sky_dev || !cost_out || !grad_dev) return fail(p, IVIS_ERR_ARG, "null sky, cost or gradient pointer");
+    enter(p);
+    ivis_status s = ensure_prepared(p);
+    if (s) return s;
+    size_t bytes = (size_t)p->cfg.nchan * p->cfg.n * p->cfg.n * p->rsz;
+    CK(cudaMemcpyAsync(p->x, sky_dev, bytes, cudaMemcpyDeviceToDevice, p->stream));
+    if ((s = run_eval(p))) return s;
+    CK(cudaMemcpyAsync(grad_dev, p->g, bytes, cudaMemcpyDeviceToDevice, p->stream));
+    CK(cudaStreamSynchronize(p->stream));
+    *cost_out = p->cost_h[0];
+    if (terms_out) {
+        terms_out[0] = p->cost_h[1];
+        terms_out[1] = p->cost_h[2];
+        terms_out[2] = p->cost_h[3];
+    }
+    return IVIS_OK;
+}
+
+ivis_status ivis_cost_grad_host(ivis_plan_t p, const void *sky_host, double *cost_out, void *grad_host,
+                                double *terms_out) {
+    if (!p) return fail(nullptr, IVIS_ERR_ARG, "null plan");
+    if (!sky_host || !cost_out || !grad_host) return fail(p, IVIS_ERR_ARG, "null sky, cost or gradient pointer");
+    enter(p);
+    ivis_status s = ensure_prepared(p);
+    if (s) return s;
+    size_t bytes = (size_t)p->cfg.nchan * p->cfg.n * p->cfg.n * p->rsz;
+    CK(cudaMemcpyAsync(p->x, sky_host, bytes, cudaMemcpyHostToDevice, p->stream));
+    if ((s = run_eval(p))) return s;
+    CK(cudaMemcpyAsync(grad_host, p->g, bytes, cudaMemcpyDeviceToHost, p->stream));
+    CK(cudaStreamSynchronize(p->stream));
+    *cost_out = p->cost_h[0];
+    if (terms_out) {
+        terms_out[0] = p->cost_h[1];
+        terms_out[1] = p->cost_h[2];
+        terms_out[2] = p->cost_h[3];
+    }
+    return IVIS_OK;
+}
+
+ivis_status ivis_predict(ivis_plan_t p, const void *sky_dev, int k, int chan, void *vis_out_dev) {
+    if (!p) return fail(nullptr, IVIS_ERR_ARG, "null plan");
+    if (!sky_dev || !vis_out_dev) return fail(p, IVIS_ERR_ARG, "null pointer");
+    if (k < 0 || k >= p->cfg.npoint || chan < 0 || chan >= p->cfg.nchan) return fail(p, IVIS_ERR_ARG, "bad pair index");
+    enter(p);
+    ivis_status s = ensure_prepared(p);
+    if (s) return s;
+    int pair = chan * p->cfg.npoint + k;
+    int slot = -1;
+    for (int i = 0; i < p->nslot; ++i)
+        if (p->slot_pair[i] == pair) slot = i;
+    if (slot < 0) return IVIS_OK;  // no visibilities
+    size_t bytes = (size_t)p->cfg.nchan * p->cfg.n * p->cfg.n * p->rsz;
+    CK(cudaMemcpyAsync(p->x, sky_dev, bytes, cudaMemcpyDeviceToDevice, p->stream));
+    cudaError_t e;
+    if (p->fp64) {
+        e = launch_forward<double>(p, p->x);
+        if (e == cudaSuccess)
+            e = launch_grid_pass<double, MODE_PREDICT>(p, p->chunk_first[slot], p->chunk_first[slot + 1] - p->chunk_first[slot], nullptr, vis_out_dev);
+    } else {
+        e = launch_forward<float>(p, p->x);
+        if (e == cudaSuccess)
+            e = launch_grid_pass<float, MODE_PREDICT>(p, p->chunk_first[slot], p->chunk_first[slot + 1] - p->chunk_first[slot], nullptr, vis_out_dev);
+    }
+    if (e != cudaSuccess) return fail(p, IVIS_ERR_CUDA, std::string("predict: ") + cudaGetErrorString(e));
+    CK(cudaStreamSynchronize(p->stream));
+    return IVIS_OK;
+}
+
+ivis_status ivis_sd_predict(ivis_plan_t p, const void *sky_dev, void *out_dev) {
+    if (!p) return fail(nullptr, IVIS_ERR_ARG, "null plan");
+    if (!sky_dev || !out_dev) return fail(p, IVIS_ERR_ARG, "null pointer");
+    enter(p);
+    for (int ch = 0; ch < p->cfg.nchan; ++ch)
+        if (!p->sdset[ch]) return fail(p, IVIS_ERR_STATE, "dish beam of channel " + std::to_string(ch) + " not set");
+    ivis_status s = ensure_prepared(p);
+    if (s) return s;
+    cudaError_t e = p->fp64 ? launch_fusion<double>(p, p->stream, sky_dev, out_dev, nullptr, false)
+                            : launch_fusion<float>(p, p->stream, sky_dev, out_dev, nullptr, false);
+    if (e != cudaSuccess) return fail(p, IVIS_ERR_CUDA, std::string("sd_predict: ") + cudaGetErrorString(e));
+    CK(cudaStreamSynchronize(p->stream));
+    return IVIS_OK;
+}
+
+ivis_status ivis_get_nufft_params(ivis_plan_t p, int *w, double *beta, int *nf) {
+    if (!p) return fail(nullptr, IVIS_ERR_ARG, "null plan");
+    if (w) *w = p->W;
+    if (beta) *beta = p->beta;
+    if (nf) *nf = p->nf;
+    return IVIS_OK;
+}
+
+ivis_status ivis_profile(ivis_plan_t p, int enable) {
+    if (!p) return fail(nullptr, IVIS_ERR_ARG, "null plan");
+    p->profile = enable != 0;
+    for (auto &v : p->stage_ms) v = 0.0;
+    p->prof_evals = 0;
+    return IVIS_OK;
+}
+
+ivis_status ivis_stage_times(ivis_plan_t p, const char **names, double *ms, int cap, int *count) {
+    if (!p) return fail(nullptr, IVIS_ERR_ARG, "null plan");
+    int n = p->stages.empty() ? 0 : (int)p->stages.size() - 1;
+    if (count) *count = n;
+    for (int i = 0; i < n && i < cap; ++i) {
+        if (names) names[i] = p->stages[i + 1].name;
+        if (ms) ms[i] = p->prof_evals ? p->stage_ms[i + 1] / p->prof_evals : 0.0;
+    }
+    return IVIS_OK;
+}
+
+ivis_status ivis_launches_per_eval(ivis_plan_t p, int *count) {
+    if (!p || !count) return fail(p, IVIS_ERR_ARG, "null pointer");
+    ivis_status s = ensure_prepared(p);
+    if (s) return s;
+    *count = p->launches;
+    return IVIS_OK;
+}
+
+ivis_status ivis_solve(ivis_plan_t p, void *sky_dev, int maxiter, int m_hist, double pgtol, double ftol,
+                       ivis_solve_report *rep) {
+    if (!p) return fail(nullptr, IVIS_ERR_ARG, "null plan");
+    if (!sky_dev || maxiter < 0 || m_hist < 1 || m_hist > 32 || !(pgtol >= 0) || !(ftol >= 0))
+        return fail(p, IVIS_ERR_ARG, "bad solve arguments");
+    enter(p);
+    ivis_status s = ensure_prepared(p);
+    if (s) return s;
+    return p->fp64 ? solve_impl<double>(p, sky_dev, maxiter, m_hist, pgtol, ftol, rep)
+                   : solve_impl<float>(p, sky_dev, maxiter, m_hist, pgtol, ftol, rep);
+}
+
+ivis_status ivis_destroy(ivis_plan_t p) {
+    if (!p) return IVIS_OK;
+    if (p->stream) cudaStreamSynchronize(p->stream);
+    release_prepared(p);
+    for (auto &ph : p->pairs) free_pair(ph);
+    dfree(p->dinv_d);
+    dfree(p->tw_d);
+    dfree(p->beams_d);
+    dfree(p->tsd_d);
+    for (auto &st : p->stages) cudaEventDestroy(st.ev);
+    if (p->ev_fork) cudaEventDestroy(p->ev_fork);
+    if (p->ev_join) cudaEventDestroy(p->ev_join);
+    if (p->side) cudaStreamDestroy(p->side);
+    if (p->ev_in) cudaEventDestroy(p->ev_in);
+    if (p->stream) cudaStreamDestroy(p->stream);
+    if (p->cost_h) cudaFreeHost(p->cost_h);
+    delete p;
+    return IVIS_OK;
+}
+
+const char *ivis_last_error(ivis_plan_t p) {
+    return p ? p->err.c_str() : g_plan_error.c_str();
+}
+
+}  // extern "C"

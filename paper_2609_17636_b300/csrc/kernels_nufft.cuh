@@ -1,0 +1,342 @@
+// kernels_nufft.cuh -- the per-pointing NUFFT pair of the data term (paper Eqs. 3-6).
+//
+// Forward (type 2, image -> visibilities), for each (pointing, channel) pair:
+//   a1  window gather x beam x deapodisation, zero-padded to the 2x oversampled grid,
+//       fused into the row FFT                                         (k_fwd_rows)
+//   a2  column FFT of the fine grid                                    (k_fwd_cols)
+//   a3  interpolation with the ES kernel -> model visibilities, residual r = V~ - V,
+//       J partial 1/2 w |r|^2 in FP64                                  (k_grid_pass)
+// Adjoint (type 1, visibilities -> image), in the same pass and the reverse order:
+//   a4  spreading of w r with the same kernel values into a shared-memory sub-grid,
+//       flushed to the global adjoint grid with atomics                (k_grid_pass)
+//   a5  column inverse FFT, keeping only the nb modes of the window    (k_adj_cols)
+//       row inverse FFT + deapodisation + Re + beam                    (k_adj_rows)
+//
+// Conventions: fine grid nf = 2 nb; window mode k = p - nb/2 sits at grid index k mod nf;
+// a visibility's grid coordinate is s = u * cell * nf (folded into [0, nf)); its W taps are
+// cells g0 .. g0+W-1 with g0 = floor(s - W/2) + 1 and kernel argument (s - g)/(W/2).
+#pragma once
+#include "common.cuh"
+#include "fft.cuh"
+
+namespace ivis {
+
+struct PairInfo {
+    int k, chan, cx, cy;
+};
+
+struct Chunk {
+    int slot;    // active pair slot
+    int tile;    // tile id within the pair's fine grid (ty * ntx + tx)
+    int begin;   // first visibility (pair-local sorted index)
+    int end;     // one past the last
+};
+
+template <typename T> struct coord_of;
+template <> struct coord_of<float> { typedef uint2 type; };     // 12-bit cell | 20-bit fraction
+template <> struct coord_of<double> { typedef double2 type; };  // folded grid coordinate
+
+template <typename T> struct PairData {
+    const typename coord_of<T>::type *coord;
+    const typename cplx_of<T>::type *vis;
+    const T *w;
+    const int *orig;
+    int m;
+};
+
+constexpr int FRAC_BITS = 20;
+constexpr unsigned FRAC_ONE = 1u << FRAC_BITS;
+
+// ---------------------------------------------------------------- set-up: coordinates, sort
+// Grid coordinate, tile key and validity of each input visibility.
+template <typename T>
+__global__ void k_vis_prepare(int m, const float *__restrict__ uvw, const float *__restrict__ vis,
+                              const float *__restrict__ wt, double scale, int lognf, int W,
+                              int tile, int ntx, typename coord_of<T>::type *coord_tmp,
+                              int *key, int *err) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    const int nf = 1 << lognf;
+    float u = uvw[3 * (size_t)i], v = uvw[3 * (size_t)i + 1];
+    float vr = vis[2 * (size_t)i], vi = vis[2 * (size_t)i + 1], w = wt[i];
+    if (!isfinite(u) || !isfinite(v) || !isfinite(vr) || !isfinite(vi) || !isfinite(w) || w < 0.f)
+        atomicOr(err, 1);
+    double sc[2] = {(double)u * scale, (double)v * scale};
+    int g0[2];
+    double half = 0.5 * W;
+    unsigned packed[2];
+    for (int a = 0; a < 2; ++a) {
+        double s = sc[a] - nf * floor(sc[a] / nf);
+        if (s >= nf) s -= nf;
+        if (!(s >= 0.0)) s = 0.0;  // non-finite input: flagged above
+        sc[a] = s;
+        double gd = floor(s - half) + 1.0;
+        long long g = (long long)gd;
+        double frac = s - gd - (half - 1.0);
+        unsigned q = (unsigned)(frac * (double)FRAC_ONE + 0.5);
+        if (q >= FRAC_ONE) { q = 0; g += 1; }
+        g = ((g % nf) + nf) % nf;
+        if (sizeof(T) == 8) {  // the FP64 kernels recompute g0 from s: use the same rule
+            long long g2 = (long long)(floor(s - half) + 1.0);
+            g = ((g2 % nf) + nf) % nf;
+        }
+        g0[a] = (int)g;
+        packed[a] = ((unsigned)g << FRAC_BITS) | q;
+    }
+    if constexpr (sizeof(T) == 4) {
+        coord_tmp[i] = make_uint2(packed[0], packed[1]);
+    } else {
+        coord_tmp[i] = make_double2(sc[0], sc[1]);
+    }
+    key[i] = (g0[1] / tile) * ntx + (g0[0] / tile);
+}
+
+__global__ void k_hist(int m, const int *__restrict__ key, int *count) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < m) atomicAdd(&count[key[i]], 1);
+}
+
+// Scatter into tile order. cursor[t] starts at the tile's first slot.
+template <typename T>
+__global__ void k_vis_scatter(int m, const int *__restrict__ key,
+                              const typename coord_of<T>::type *__restrict__ coord_tmp,
+                              const float *__restrict__ vis, const float *__restrict__ wt,
+                              int *cursor, typename coord_of<T>::type *coord,
+                              typename cplx_of<T>::type *vout, T *wout, int *orig) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    int pos = atomicAdd(&cursor[key[i]], 1);
+    coord[pos] = coord_tmp[i];
+    vout[pos] = mk((T)vis[2 * (size_t)i], (T)vis[2 * (size_t)i + 1]);
+    wout[pos] = (T)wt[i];
+    orig[pos] = i;
+}
+
+// ------------------------------------------------------------------ forward row pass (a1)
+template <typename T>
+__global__ void k_fwd_rows(const T *__restrict__ sky, const T *__restrict__ beams,
+                           const PairInfo *__restrict__ pinfo, const T *__restrict__ dinv,
+                           typename cplx_of<T>::type *rowbuf, int n, int nb, int lognf,
+                           const typename cplx_of<T>::type *__restrict__ tw) {
+    typedef typename cplx_of<T>::type C;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C *s = reinterpret_cast<C *>(smem_raw);
+    const int q = blockIdx.x, slot = blockIdx.y, nf = 1 << lognf;
+    const PairInfo pi = pinfo[slot];
+    C *out = rowbuf + ((size_t)slot * nb + q) * nf;
+    const int y = pi.cy - nb / 2 + q;
+    if (y < 0 || y >= n) {
+        for (int i = threadIdx.x; i < nf; i += blockDim.x) out[i] = mk((T)0, (T)0);
+        return;
+    }
+    for (int i = threadIdx.x; i < nf; i += blockDim.x) s[i] = mk((T)0, (T)0);
+    __syncthreads();
+    const T *srow = sky + ((size_t)pi.chan * n + y) * n;
+    const T *brow = beams + ((size_t)pi.k * nb + q) * nb;
+    const T dq = dinv[q];
+    const int x0 = pi.cx - nb / 2;
+    for (int p = threadIdx.x; p < nb; p += blockDim.x) {
+        const int x = x0 + p;
+        T val = (x >= 0 && x < n) ? srow[x] * brow[p] * dinv[p] * dq : (T)0;
+        const int idx = (p - nb / 2) & (nf - 1);
+        s[bitrev(idx, lognf)] = mk(val, (T)0);
+    }
+    __syncthreads();
+    fft_dit_smem<C, -1>(s, lognf, 0, tw);
+    for (int i = threadIdx.x; i < nf; i += blockDim.x) out[i] = s[i];
+}
+
+// ---------------------------------------------------------------- forward column pass (a2)
+template <typename T>
+__global__ void k_fwd_cols(const typename cplx_of<T>::type *__restrict__ rowbuf,
+                           typename cplx_of<T>::type *F, int nb, int lognf, int logc,
+                           const typename cplx_of<T>::type *__restrict__ tw) {
+    typedef typename cplx_of<T>::type C;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C *s = reinterpret_cast<C *>(smem_raw);
+    const int nf = 1 << lognf, ncol = 1 << logc;
+    const int c0 = blockIdx.x << logc, slot = blockIdx.y;
+    for (int i = threadIdx.x; i < (nf << logc); i += blockDim.x) s[i] = mk((T)0, (T)0);
+    __syncthreads();
+    const C *src = rowbuf + (size_t)slot * nb * nf;
+    for (int i = threadIdx.x; i < (nb << logc); i += blockDim.x) {
+        const int q = i >> logc, c = i & (ncol - 1);
+        const int idx = (q - nb / 2) & (nf - 1);
+        s[(bitrev(idx, lognf) << logc) + c] = src[(size_t)q * nf + c0 + c];
+    }
+    __syncthreads();
+    fft_dit_smem<C, -1>(s, lognf, logc, tw);
+    C *dst = F + (size_t)slot * nf * nf;
+    for (int i = threadIdx.x; i < (nf << logc); i += blockDim.x) {
+        const int g = i >> logc, c = i & (ncol - 1);
+        dst[(size_t)g * nf + c0 + c] = s[i];
+    }
+}
+
+// --------------------------------------------- interpolation / residual / spreading (a3, a4)
+template <int W>
+__device__ __forceinline__ void decode(uint2 c, int nf, int &gx, int &gy, float &dx, float &dy) {
+    (void)nf;
+    gx = (int)(c.x >> FRAC_BITS);
+    gy = (int)(c.y >> FRAC_BITS);
+    const float base = 0.5f * (W - 2);
+    dx = base + (float)(c.x & (FRAC_ONE - 1)) * (1.0f / (float)FRAC_ONE);
+    dy = base + (float)(c.y & (FRAC_ONE - 1)) * (1.0f / (float)FRAC_ONE);
+}
+template <int W>
+__device__ __forceinline__ void decode(double2 c, int nf, int &gx, int &gy, double &dx, double &dy) {
+    const double half = 0.5 * W;
+    double g = floor(c.x - half) + 1.0;
+    dx = c.x - g;
+    gx = (int)g;
+    gx = gx < 0 ? gx + nf : gx;
+    g = floor(c.y - half) + 1.0;
+    dy = c.y - g;
+    gy = (int)g;
+    gy = gy < 0 ? gy + nf : gy;
+}
+
+enum { MODE_COSTGRAD = 0, MODE_PREDICT = 1 };
+
+// One CTA per chunk (a run of visibilities of one tile of one pair). The tile's fine-grid
+// patch (tile + W - 1 cells square, wrapped) is staged in shared memory; each thread takes one
+// visibility, evaluates its 2W kernel values once and uses them for both interpolation and
+// spreading. MODE_PREDICT writes V~ to pred[orig] instead of spreading.
+template <typename T, int W, int MODE>
+__global__ void __launch_bounds__(256)
+k_grid_pass(const Chunk *__restrict__ chunks, const PairData<T> *__restrict__ pdata,
+            const typename cplx_of<T>::type *__restrict__ F, typename cplx_of<T>::type *G,
+            int lognf, int tile, int ntx, T beta, double *jpart,
+            typename cplx_of<T>::type *pred) {
+    typedef typename cplx_of<T>::type C;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ double red[32];
+    const int nf = 1 << lognf;
+    const int PW = tile + W - 1;
+    C *Fs = reinterpret_cast<C *>(smem_raw);
+    C *Gs = Fs + PW * PW;
+    const Chunk ch = chunks[blockIdx.x];
+    const PairData<T> pd = pdata[ch.slot];
+    const int ty = ch.tile / ntx, tx = ch.tile - ty * ntx;
+    const int x0 = tx * tile, y0 = ty * tile;
+    const C *Fp = F + (size_t)ch.slot * nf * nf;
+    for (int i = threadIdx.x; i < PW * PW; i += blockDim.x) {
+        const int ly = i / PW, lx = i - ly * PW;
+        const int gy = (y0 + ly) & (nf - 1), gx = (x0 + lx) & (nf - 1);
+        Fs[i] = Fp[(size_t)gy * nf + gx];
+        if (MODE == MODE_COSTGRAD) Gs[i] = mk((T)0, (T)0);
+    }
+    __syncthreads();
+    const T zs = (T)2 / (T)W;
+    double jacc = 0.0;
+    for (int v = ch.begin + threadIdx.x; v < ch.end; v += blockDim.x) {
+        int gx, gy;
+        T dx, dy;
+        decode<W>(pd.coord[v], nf, gx, gy, dx, dy);
+        const int lx = gx - x0, ly = gy - y0;
+        T kx[W], ky[W];
+#pragma unroll
+        for (int t = 0; t < W; ++t) {
+            kx[t] = es_kernel((dx - (T)t) * zs, beta);
+            ky[t] = es_kernel((dy - (T)t) * zs, beta);
+        }
+        C acc = mk((T)0, (T)0);
+        const C *fr = Fs + ly * PW + lx;
+#pragma unroll
+        for (int b = 0; b < W; ++b) {
+            C row = mk((T)0, (T)0);
+#pragma unroll
+            for (int a = 0; a < W; ++a) {
+                const C f = fr[b * PW + a];
+                row.x += kx[a] * f.x;
+                row.y += kx[a] * f.y;
+            }
+            acc.x += ky[b] * row.x;
+            acc.y += ky[b] * row.y;
+        }
+        if (MODE == MODE_PREDICT) {
+            pred[pd.orig[v]] = acc;
+            continue;
+        }
+        const C vv = pd.vis[v];
+        const T w = pd.w[v];
+        const C r = mk(acc.x - vv.x, acc.y - vv.y);
+        jacc += 0.5 * (double)w * ((double)r.x * (double)r.x + (double)r.y * (double)r.y);
+        const C c = mk(w * r.x, w * r.y);
+        C *gr = Gs + ly * PW + lx;
+#pragma unroll
+        for (int b = 0; b < W; ++b) {
+            const T cyx = ky[b] * c.x, cyy = ky[b] * c.y;
+#pragma unroll
+            for (int a = 0; a < W; ++a) {
+                atomicAdd(&gr[b * PW + a].x, cyx * kx[a]);
+                atomicAdd(&gr[b * PW + a].y, cyy * kx[a]);
+            }
+        }
+    }
+    if (MODE == MODE_PREDICT) return;
+    const double js = block_sum(jacc, red);
+    if (threadIdx.x == 0) jpart[blockIdx.x] = js;
+    __syncthreads();
+    C *Gp = G + (size_t)ch.slot * nf * nf;
+    for (int i = threadIdx.x; i < PW * PW; i += blockDim.x) {
+        const C g = Gs[i];
+        if (g.x == (T)0 && g.y == (T)0) continue;
+        const int ly = i / PW, lx = i - ly * PW;
+        const int gy = (y0 + ly) & (nf - 1), gx = (x0 + lx) & (nf - 1);
+        atomic_add_c(&Gp[(size_t)gy * nf + gx], g);
+    }
+}
+
+// ---------------------------------------------------------------- adjoint column pass (a5)
+template <typename T>
+__global__ void k_adj_cols(const typename cplx_of<T>::type *__restrict__ G,
+                           typename cplx_of<T>::type *rowbuf, int nb, int lognf, int logc,
+                           const typename cplx_of<T>::type *__restrict__ tw) {
+    typedef typename cplx_of<T>::type C;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C *s = reinterpret_cast<C *>(smem_raw);
+    const int nf = 1 << lognf, ncol = 1 << logc;
+    const int c0 = blockIdx.x << logc, slot = blockIdx.y;
+    const C *src = G + (size_t)slot * nf * nf;
+    for (int i = threadIdx.x; i < (nf << logc); i += blockDim.x) {
+        const int g = i >> logc, c = i & (ncol - 1);
+        s[(bitrev(g, lognf) << logc) + c] = src[(size_t)g * nf + c0 + c];
+    }
+    __syncthreads();
+    fft_dit_smem<C, +1>(s, lognf, logc, tw);
+    C *dst = rowbuf + (size_t)slot * nb * nf;
+    for (int i = threadIdx.x; i < (nb << logc); i += blockDim.x) {
+        const int q = i >> logc, c = i & (ncol - 1);
+        const int idx = (q - nb / 2) & (nf - 1);
+        dst[(size_t)q * nf + c0 + c] = s[(idx << logc) + c];
+    }
+}
+
+// ------------------------------------------- adjoint row pass + deapod + Re + beam (a5, a6)
+template <typename T>
+__global__ void k_adj_rows(const typename cplx_of<T>::type *__restrict__ rowbuf,
+                           const T *__restrict__ beams, const PairInfo *__restrict__ pinfo,
+                           const T *__restrict__ dinv, T *contrib, int n, int nb, int lognf,
+                           const typename cplx_of<T>::type *__restrict__ tw) {
+    typedef typename cplx_of<T>::type C;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C *s = reinterpret_cast<C *>(smem_raw);
+    const int q = blockIdx.x, slot = blockIdx.y, nf = 1 << lognf;
+    const PairInfo pi = pinfo[slot];
+    const int y = pi.cy - nb / 2 + q;
+    if (y < 0 || y >= n) return;  // never gathered: off the sky
+    const C *src = rowbuf + ((size_t)slot * nb + q) * nf;
+    for (int i = threadIdx.x; i < nf; i += blockDim.x) s[bitrev(i, lognf)] = src[i];
+    __syncthreads();
+    fft_dit_smem<C, +1>(s, lognf, 0, tw);
+    const T *brow = beams + ((size_t)pi.k * nb + q) * nb;
+    const T dq = dinv[q];
+    T *out = contrib + ((size_t)slot * nb + q) * nb;
+    for (int p = threadIdx.x; p < nb; p += blockDim.x) {
+        const int idx = (p - nb / 2) & (nf - 1);
+        out[p] = s[idx].x * dinv[p] * dq * brow[p];
+    }
+}
+
+}  // namespace ivis

@@ -1,0 +1,198 @@
+"""Thin Python face of the C ABI: one :class:`Plan` per imaging problem.
+
+PyTorch provides device memory and the CUDA stream; the arrays handed over are CUDA
+tensors and the calls only pass their pointers and sizes to libivis.so.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import torch
+
+from . import _lib
+from ._lib import IVIS_FP32, IVIS_FP64, IvisError, SolveReport
+
+
+def _check(L, plan, status):
+    if status != 0:
+        msg = L.ivis_last_error(plan)
+        raise IvisError(status, msg.decode() if msg else "")
+
+
+def _dev_f32(t: torch.Tensor, shape=None) -> torch.Tensor:
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float32:
+        raise TypeError("expected a CUDA float32 tensor")
+    t = t.contiguous()
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"expected shape {shape}, got {tuple(t.shape)}")
+    return t
+
+
+class Plan:
+    """One problem: sky cube [nchan, n, n], npoint windows of nb x nb, a data set per
+    (pointing, channel) pair, optional single-dish maps. See include/ivis.h."""
+
+    def __init__(self, n: int, nchan: int, npoint: int, nb: int, cell_rad: float,
+                 precision: str = "fp32", nufft_tol: float | None = None, kernel_width: int = 0,
+                 lambda_r: float = 0.0, lambda_s: float = 0.0, positivity: bool = True,
+                 stream: torch.cuda.Stream | None = None):
+        self.L = _lib.load()
+        if precision not in ("fp32", "fp64"):
+            raise ValueError("precision must be 'fp32' or 'fp64'")
+        self.precision = precision
+        self.dtype = torch.float32 if precision == "fp32" else torch.float64
+        if nufft_tol is None:
+            nufft_tol = 1e-6 if precision == "fp32" else 1e-11
+        self.cfg = _lib.Config(n, nchan, npoint, nb, cell_rad,
+                               IVIS_FP32 if precision == "fp32" else IVIS_FP64,
+                               nufft_tol, kernel_width, lambda_r, lambda_s, int(bool(positivity)))
+        self.shape = (nchan, n, n)
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self._p = ctypes.c_void_p()
+        st = self.L.ivis_plan(ctypes.byref(self.cfg), ctypes.c_void_p(self.stream.cuda_stream),
+                              ctypes.byref(self._p))
+        _check(self.L, None, st)
+        self.m = {}
+
+    # ------------------------------------------------------------------ set-up
+    def set_pointing(self, k: int, cx: int, cy: int, beam: torch.Tensor):
+        beam = _dev_f32(beam, (self.cfg.nb, self.cfg.nb))
+        _check(self.L, self._p, self.L.ivis_set_pointing(self._p, k, int(cx), int(cy),
+                                                         ctypes.c_void_p(beam.data_ptr())))
+
+    def set_vis(self, k: int, chan: int, uvw: torch.Tensor, vis: torch.Tensor, weight: torch.Tensor):
+        m = int(uvw.shape[0])
+        if m:
+            uvw = _dev_f32(uvw, (m, 3))
+            vis = _dev_f32(vis, (m, 2))
+            weight = _dev_f32(weight, (m,))
+            args = [ctypes.c_void_p(t.data_ptr()) for t in (uvw, vis, weight)]
+        else:
+            args = [None, None, None]
+        _check(self.L, self._p, self.L.ivis_set_vis(self._p, k, chan, m, *args))
+        self.m[(k, chan)] = m
+
+    def set_sd(self, chan: int, tsd: torch.Tensor, sigma_sd: float, fwhm_pix: float):
+        tsd = _dev_f32(tsd, self.shape[1:])
+        _check(self.L, self._p, self.L.ivis_set_sd(self._p, chan, ctypes.c_void_p(tsd.data_ptr()),
+                                                   float(sigma_sd), float(fwhm_pix)))
+
+    def prepare(self):
+        _check(self.L, self._p, self.L.ivis_prepare(self._p))
+
+    # ------------------------------------------------------------------ evaluation
+    def _sky(self, sky: torch.Tensor) -> torch.Tensor:
+        if not sky.is_cuda or sky.dtype != self.dtype or tuple(sky.shape) != self.shape:
+            raise TypeError(f"sky must be a CUDA {self.dtype} tensor of shape {self.shape}")
+        return sky.contiguous()
+
+    def cost_grad(self, sky: torch.Tensor, grad: torch.Tensor | None = None):
+        """Returns (Q_tot, gradient tensor, (Q, K, R))."""
+        sky = self._sky(sky)
+        if grad is None:
+            grad = torch.empty_like(sky)
+        cost = ctypes.c_double()
+        terms = (ctypes.c_double * 3)()
+        _check(self.L, self._p, self.L.ivis_cost_grad(self._p, ctypes.c_void_p(sky.data_ptr()),
+                                                      ctypes.byref(cost),
+                                                      ctypes.c_void_p(grad.data_ptr()), terms))
+        return cost.value, grad, (terms[0], terms[1], terms[2])
+
+    def cost_grad_host(self, sky_host: torch.Tensor, grad_host: torch.Tensor):
+        """Same evaluation from host (ideally pinned) CPU tensors."""
+        if sky_host.is_cuda or grad_host.is_cuda:
+            raise TypeError("host tensors expected")
+        cost = ctypes.c_double()
+        terms = (ctypes.c_double * 3)()
+        _check(self.L, self._p, self.L.ivis_cost_grad_host(
+            self._p, ctypes.c_void_p(sky_host.data_ptr()), ctypes.byref(cost),
+            ctypes.c_void_p(grad_host.data_ptr()), terms))
+        return cost.value, (terms[0], terms[1], terms[2])
+
+    def predict(self, sky: torch.Tensor, k: int, chan: int) -> torch.Tensor:
+        sky = self._sky(sky)
+        out = torch.zeros((self.m.get((k, chan), 0), 2), dtype=self.dtype, device=sky.device)
+        _check(self.L, self._p, self.L.ivis_predict(self._p, ctypes.c_void_p(sky.data_ptr()), k, chan,
+                                                    ctypes.c_void_p(out.data_ptr())))
+        return out
+
+    def sd_predict(self, sky: torch.Tensor) -> torch.Tensor:
+        sky = self._sky(sky)
+        out = torch.empty_like(sky)
+        _check(self.L, self._p, self.L.ivis_sd_predict(self._p, ctypes.c_void_p(sky.data_ptr()),
+                                                       ctypes.c_void_p(out.data_ptr())))
+        return out
+
+    def solve(self, sky: torch.Tensor, maxiter: int, m_hist: int = 10, pgtol: float = 1e-5,
+              ftol: float = 1e7 * 2.220446049250313e-16) -> dict:
+        """Overwrites ``sky`` with the solution; returns the solve report."""
+        if not sky.is_contiguous():
+            raise ValueError("sky must be contiguous (it is updated in place)")
+        self._sky(sky)
+        rep = SolveReport()
+        _check(self.L, self._p, self.L.ivis_solve(self._p, ctypes.c_void_p(sky.data_ptr()), maxiter,
+                                                  m_hist, pgtol, ftol, ctypes.byref(rep)))
+        return {"iterations": rep.iterations, "evaluations": rep.evaluations, "f": rep.f,
+                "pg_inf": rep.pg_inf, "seconds": rep.seconds, "status": rep.status}
+
+    # ------------------------------------------------------------------ introspection
+    def nufft_params(self):
+        w, beta, nf = ctypes.c_int(), ctypes.c_double(), ctypes.c_int()
+        _check(self.L, self._p, self.L.ivis_get_nufft_params(self._p, ctypes.byref(w),
+                                                             ctypes.byref(beta), ctypes.byref(nf)))
+        return w.value, beta.value, nf.value
+
+    def profile(self, enable: bool):
+        _check(self.L, self._p, self.L.ivis_profile(self._p, int(bool(enable))))
+
+    def stage_times(self) -> dict:
+        cap = 32
+        names = (ctypes.c_char_p * cap)()
+        ms = (ctypes.c_double * cap)()
+        cnt = ctypes.c_int()
+        _check(self.L, self._p, self.L.ivis_stage_times(self._p, names, ms, cap, ctypes.byref(cnt)))
+        return {names[i].decode(): ms[i] for i in range(min(cnt.value, cap))}
+
+    def launches_per_eval(self) -> int:
+        c = ctypes.c_int()
+        _check(self.L, self._p, self.L.ivis_launches_per_eval(self._p, ctypes.byref(c)))
+        return c.value
+
+    def close(self):
+        if self._p:
+            self.L.ivis_destroy(self._p)
+            self._p = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def plan_from_problem(prob, precision: str = "fp32", device="cuda", **kw) -> Plan:
+    """Build a plan from an object with the attributes of a problem description (n, nchan,
+    centres, nb, cell_rad, beams, pairs[k, chan, uvw, vis, weight], lambdas, positivity and,
+    for lambda_s != 0, tsd / sigma_sd / sd_fwhm_pix). Host arrays are copied to the device."""
+    plan = Plan(prob.n, prob.nchan, prob.centres.shape[0], prob.nb, prob.cell_rad, precision,
+                lambda_r=kw.pop("lambda_r", prob.lambda_r), lambda_s=kw.pop("lambda_s", prob.lambda_s),
+                positivity=prob.positivity, **kw)
+    for k in range(prob.centres.shape[0]):
+        plan.set_pointing(k, int(prob.centres[k][0]), int(prob.centres[k][1]),
+                          torch.as_tensor(prob.beams[k], dtype=torch.float32, device=device))
+    seen = set()
+    for pair in prob.pairs:
+        uvw = torch.as_tensor(pair.uvw, dtype=torch.float32, device=device)
+        v = torch.view_as_real(torch.as_tensor(pair.vis).to(torch.complex64)).to(device)
+        w = torch.as_tensor(pair.weight, dtype=torch.float32, device=device)
+        plan.set_vis(pair.k, pair.chan, uvw, v, w)
+        seen.add((pair.k, pair.chan))
+    for c in range(prob.nchan):
+        for k in range(prob.centres.shape[0]):
+            if (k, c) not in seen:
+                plan.set_vis(k, c, torch.zeros((0, 3), device=device), None, None)
+    if plan.cfg.lambda_s != 0.0:
+        for c in range(prob.nchan):
+            plan.set_sd(c, torch.as_tensor(prob.tsd[c], dtype=torch.float32, device=device),
+                        float(prob.sigma_sd[c]), prob.sd_fwhm_pix)
+    return plan

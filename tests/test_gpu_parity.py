@@ -1,0 +1,159 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerances (stated by the method's targets): relative L2 <= 1e-9 for the FP64 path and
+<= 1e-5 for the FP32 path, on model visibilities and on the gradient; the cost and its three
+terms to the same relative bound. Inputs are seeded synthetic problems whose data come from
+the oracle (tests/_data.py)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from _data import attach_data, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-9, "fp32": 1e-5}
+
+
+@pytest.fixture(scope="module")
+def mosaic():
+    """3 pointings x 2 channels, 96^2 sky, 64^2 windows off the sky edges, 24 antennas x
+    20 dumps (ragged per pair after flagging), baselines far beyond the pixel Nyquist limit
+    (the NUFFT folds), Laplacian and fusion terms on."""
+    prob = synth.small_mosaic(301, n=96, nb=64, nchan=2, npoint=3, ndump=20, n_ant=24,
+                              cell_arcsec=20.0, lambda_r=0.3, lambda_s=0.5, sd_fwhm_pix=5.0)
+    attach_data(prob)
+    rng = np.random.default_rng(301)
+    x = prob.sky_true * rng.uniform(0.3, 1.3, prob.sky_true.shape)
+    f, g, terms = oracle.cost_grad(prob, x, prob.tsd, prob.sigma_sd, with_terms=True)
+    return prob, x, f, g, terms
+
+
+def _plan(prob, precision):
+    from paper_2609_17636_b300 import plan_from_problem
+    return plan_from_problem(prob, precision)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_cost_and_gradient_match_oracle(mosaic, precision):
+    prob, x, f, g, terms = mosaic
+    plan = _plan(prob, precision)
+    dt = torch.float64 if precision == "fp64" else torch.float32
+    xs = torch.as_tensor(x, dtype=dt, device="cuda")
+    fg, grad, tg = plan.cost_grad(xs)
+    tol = TOL[precision]
+    assert abs(fg - f) <= tol * abs(f), (fg, f)
+    for a, b in zip(tg, terms):
+        assert abs(a - b) <= tol * abs(b) + 1e-300, (tg, terms)
+    assert rel_l2(grad.cpu().numpy(), g) <= tol, rel_l2(grad.cpu().numpy(), g)
+    plan.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_model_visibilities_match_direct_dft(mosaic, precision):
+    prob, x, *_ = mosaic
+    plan = _plan(prob, precision)
+    dt = torch.float64 if precision == "fp64" else torch.float32
+    xs = torch.as_tensor(x, dtype=dt, device="cuda")
+    for pair in prob.pairs:
+        got = plan.predict(xs, pair.k, pair.chan).cpu().numpy()
+        got = got[:, 0] + 1j * got[:, 1]
+        ref = oracle.pair_model_vis(prob, x, pair)
+        assert rel_l2(got, ref) <= TOL[precision], (pair.k, pair.chan, rel_l2(got, ref))
+    plan.close()
+
+
+def test_single_dish_model_matches_oracle(mosaic):
+    prob, x, *_ = mosaic
+    plan = _plan(prob, "fp64")
+    got = plan.sd_predict(torch.as_tensor(x, device="cuda")).cpu().numpy()
+    b = oracle.dish_kernel(prob.sd_fwhm_pix)
+    ref = np.stack([oracle.dish_conv(x[c], b) for c in range(prob.nchan)])
+    assert rel_l2(got, ref) <= 1e-12
+    plan.close()
+
+
+def test_gradient_central_differences_fp64(mosaic):
+    prob, x, *_ = mosaic
+    plan = _plan(prob, "fp64")
+    xs = torch.as_tensor(x, device="cuda")
+    _, g, _ = plan.cost_grad(xs)
+    g = g.cpu().numpy()
+    rng = np.random.default_rng(7)
+    h = 1e-4 * np.abs(x).max()
+    for i in rng.choice(x.size, 12, replace=False):
+        e = torch.zeros_like(xs).view(-1)
+        e[i] = h
+        fp, _, _ = plan.cost_grad(xs + e.view_as(xs))
+        fm, _, _ = plan.cost_grad(xs - e.view_as(xs))
+        fd = (fp - fm) / (2 * h)
+        assert abs(fd - g.flat[i]) <= 1e-6 * np.abs(g).max(), (i, fd, g.flat[i])
+    plan.close()
+
+
+def test_data_term_quadratic_identity_fp32():
+    """With V = 0 and lambda = 0, Q(x) = 1/2 ||A x||_W^2 and grad Q = A^H W A x, so
+    <x, grad Q(x)> = 2 Q(x) exactly for an operator and its exact adjoint."""
+    prob = synth.small_mosaic(302, n=80, nb=64, nchan=1, npoint=2, ndump=10, n_ant=20,
+                              lambda_r=0.0, lambda_s=0.0)
+    for p in prob.pairs:
+        p.vis = np.zeros(p.m, np.complex64)
+    plan = _plan(prob, "fp32")
+    xs = torch.as_tensor(prob.sky_true, dtype=torch.float32, device="cuda")
+    f, g, _ = plan.cost_grad(xs)
+    ip = float(torch.sum(xs.double() * g.double()))
+    assert abs(ip - 2 * f) <= 1e-5 * abs(2 * f)
+    plan.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_edge_cases(precision):
+    """nb = 16 (smallest window), a pair with no data, a single visibility, a window that
+    hangs mostly off the sky, visibilities exactly on grid cells and on the fold boundary."""
+    prob = synth.small_mosaic(303, n=20, nb=16, nchan=2, npoint=3, ndump=2, n_ant=5,
+                              lambda_r=0.0, lambda_s=0.0)
+    prob.centres[:] = [[10, 10], [-5, 3], [18, 19]]
+    prob.pairs[1].uvw = prob.pairs[1].uvw[:0]
+    prob.pairs[1].weight = prob.pairs[1].weight[:0]
+    prob.pairs[1].noise = prob.pairs[1].noise[:0]
+    prob.pairs[2].uvw = prob.pairs[2].uvw[:1]
+    prob.pairs[2].weight = prob.pairs[2].weight[:1]
+    prob.pairs[2].noise = prob.pairs[2].noise[:1]
+    nf = 32
+    fold = 1.0 / (nf * prob.cell_rad)  # one fine-grid cell in wavelengths
+    uvw = prob.pairs[3].uvw.astype(np.float64)
+    uvw[:4, 0] = np.array([0.0, 3.0, -5.0, nf / 2]) * fold
+    uvw[:4, 1] = np.array([0.0, -7.0, nf - 1, 2.0]) * fold
+    prob.pairs[3].uvw = uvw.astype(np.float32)
+    attach_data(prob)
+    x = prob.sky_true * 0.5
+    f, g = oracle.cost_grad(prob, x)
+    plan = _plan(prob, precision)
+    dt = torch.float64 if precision == "fp64" else torch.float32
+    fg, grad, _ = plan.cost_grad(torch.as_tensor(x, dtype=dt, device="cuda"))
+    tol = TOL[precision]
+    assert abs(fg - f) <= tol * abs(f)
+    assert rel_l2(grad.cpu().numpy(), g) <= tol
+    plan.close()
+
+
+def test_invalid_inputs_are_rejected():
+    from paper_2609_17636_b300 import IvisError, Plan
+    plan = Plan(32, 1, 1, 16, 1e-4, "fp32")
+    plan.set_pointing(0, 16, 16, torch.ones(16, 16, device="cuda"))
+    uvw = torch.zeros(4, 3, device="cuda")
+    vis = torch.zeros(4, 2, device="cuda")
+    w = torch.ones(4, device="cuda")
+    w[2] = float("nan")
+    with pytest.raises(IvisError) as e:
+        plan.set_vis(0, 0, uvw, vis, w)
+    assert e.value.status == 6
+    with pytest.raises(IvisError) as e:  # the pair was not set: cost refuses
+        plan.cost_grad(torch.zeros(1, 32, 32, device="cuda"))
+    assert e.value.status == 2
+    with pytest.raises(IvisError) as e:
+        plan.set_vis(3, 0, uvw, vis, torch.ones(4, device="cuda"))
+    assert e.value.status == 1
+    plan.close()

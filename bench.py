@@ -1,0 +1,419 @@
+"""Benchmark of the Classic3D cost+gradient hot path on B300.
+
+One step = one evaluation of Q_tot and its gradient over the whole workload (all pointings
+and channels: window/beam/deapodisation + row/column FFTs, fused degrid/residual/spread,
+adjoint FFTs, joint sum, Laplacian, single-dish fusion, FP64 reductions), with the sky,
+visibilities and maps resident in HBM. The metric is visibilities per second per
+cost+gradient evaluation. L2 is flushed (a 256 MiB write) before every timed step.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ivis|reference]
+                  [--config c2|c1|c3|c4] [--no-solve]
+
+N > 1 (torchrun): every rank runs its own independent copy of the workload (channels and
+problems are independent in the method: no collective on the data path); ranks meet only
+at a barrier around the timed region and for the max of their times.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "vis/s per cost+grad eval (% HBM roofline); solve time-to-tol vs plain FP64 GPU"
+UNIT = "vis/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ivis", choices=["ivis", "reference"])
+    ap.add_argument("--config", default="c2", choices=["c1", "c2", "c3", "c4"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--no-solve", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def make_problem(name, seed_offset=0):
+    import synth
+    if name == "c1":
+        return synth.config_c1(1001 + seed_offset)
+    if name == "c2":
+        return synth.config_c2(1002 + seed_offset)
+    if name == "c3":
+        return synth.config_c3(1003 + seed_offset)
+    return synth.config_c4(1004 + seed_offset)
+
+
+WORKLOAD = {
+    "c1": "single pointing, 128^2 sky at 4 arcsec, nb=128, 8190 visibilities, 1 channel",
+    "c2": "7-pointing hexagonal mosaic, 512^2 sky at 7 arcsec, nb=512 (fine grid 1024^2), "
+          "630 baselines x 360 dumps per pointing, 0-30% flagged, lambda_r=1e-2, "
+          "single-dish fusion 16 arcmin (lambda_s=1)",
+    "c3": "batched cube: 32 channels x 36 beams (6x6 hex, 0.9 deg pitch), 1024^2 sky at "
+          "25 arcsec, nb=512, U[1e5,3e5] visibilities per (beam, channel)",
+    "c4": "full footprint 10 h: 36 beams x 2.27e6 visibilities, 4096^2 sky at 5 arcsec, "
+          "nb=2048 (fine grid 4096^2), lambda_r=1e-2, fusion 16 arcmin",
+}
+
+
+# --------------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.rows = []
+        self.proc = None
+        self.index = index
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([t.strip() for t in line.split(",")])
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = [r for r in self.rows if len(r) >= 8]
+        sm = [float(r[0]) for r in rows if r[0].replace(".", "").isdigit()]
+        smax = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[4 + i].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+# ------------------------------------------------------------------- data synthesis
+def attach_data_gpu(prob, plan_fp64_like):
+    """Observed data for the benchmark: V = model(I_true) + noise and T = B (x) I_true + noise,
+    computed with the library's own predict calls (the oracle is far too slow at these sizes)."""
+    import torch
+    plan = plan_fp64_like
+    sky = torch.as_tensor(prob.sky_true, dtype=plan.dtype, device="cuda")
+    for pair in prob.pairs:
+        v = plan.predict(sky, pair.k, pair.chan).double().cpu().numpy()
+        pair.vis = (v[:, 0] + 1j * v[:, 1] + pair.noise).astype(np.complex64)
+    if prob.lambda_s != 0.0:
+        t = plan.sd_predict(sky).double().cpu().numpy()
+        sig = prob.sd_noise_frac * np.sqrt(np.mean(t.reshape(prob.nchan, -1) ** 2, axis=1))
+        prob.tsd = (t + prob.sd_noise_unit * sig[:, None, None]).astype(np.float32)
+        prob.sigma_sd = sig
+
+
+def build_plan(prob, precision):
+    from paper_2609_17636_b300 import plan_from_problem
+    if prob.lambda_s != 0.0 and getattr(prob, "tsd", None) is None:
+        prob.tsd = np.zeros((prob.nchan, prob.n, prob.n), np.float32)
+        prob.sigma_sd = np.ones(prob.nchan)
+    return plan_from_problem(prob, precision)
+
+
+# ----------------------------------------------------------------- roofline model
+def stage_bytes(prob, plan):
+    """Algorithmic bytes per launch of each stage (measurement section)."""
+    w, beta, nf = plan.nufft_params()
+    cs = 8 if plan.precision == "fp32" else 16      # complex sample
+    rs = cs // 2                                     # real sample
+    vis_b = 20 if plan.precision == "fp32" else 40   # coord + V + weight per visibility
+    npair = sum(1 for p in prob.pairs if p.m > 0)
+    nb = prob.nb
+    M = prob.total_vis
+    npix = prob.nchan * prob.n * prob.n
+    return {
+        "degrid_spread": vis_b * M + 2 * cs * nf * nf * npair,
+        "fwd_fft": npair * (2 * rs * nb * nb + 2 * cs * nb * nf + cs * nf * nf),
+        "adj_fft": npair * (cs * nf * nf + 2 * cs * nb * nf + 2 * rs * nb * nb),
+        "zero_adjoint_grid": cs * nf * nf * npair,
+        "assemble_R": npix * rs * 2 + npair * nb * nb * rs,
+    }
+
+
+def run_ivis(args, rank, world):
+    import torch
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    prob = make_problem(args.config, seed_offset=rank)
+    datagen = build_plan(prob, "fp64" if args.config in ("c1", "c2") else "fp32")
+    attach_data_gpu(prob, datagen)
+    datagen.close()
+    plan = build_plan(prob, args.precision)
+    plan.prepare()
+    x = torch.as_tensor(prob.sky_true * 0.5, dtype=plan.dtype, device=dev)
+    g = torch.empty_like(x)
+    cost = torch.zeros(4, dtype=torch.float64, device=dev)
+    ps = plan.cuda_stream
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
+
+    def step():
+        with torch.cuda.stream(ps):
+            flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(ps)
+        plan.cost_grad_async(x, g, cost)
+        e1.record(ps)
+        return e0, e1
+
+    plan.profile(True)  # the profiled graph (stage event nodes) is captured in the warm-up
+    for _ in range(args.warmup):
+        step()
+        ps.synchronize()
+    torch.cuda.synchronize()
+    plan.profile(True)  # reset the stage totals; the graph is kept
+    barrier(world)
+    torch.cuda.synchronize()
+    clk = ClockSampler(dev.index)
+    clk.start()
+    evs = []
+    for _ in range(args.steps):
+        evs.append(step())
+        ps.synchronize()  # stage events are folded in before the next step
+    torch.cuda.synchronize()
+    barrier(world)
+    clocks = clk.stop()
+    stages = plan.stage_times()
+    plan.profile(False)
+    t_step = sum(a.elapsed_time(b) for a, b in evs) / len(evs) / 1e3
+    t_max = allreduce_max(t_step, world)
+    vis_step = prob.total_vis
+    value = vis_step * world / t_max
+    launches = plan.launches_per_eval()
+
+    # roofline of the dominant kernel (the longest single-kernel stage)
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    hbm = peaks.get("hbm_gbs", 6400.0)
+    sb = stage_bytes(prob, plan)
+    single = {k: v for k, v in stages.items() if k in ("degrid_spread",)}
+    dom = max(single, key=single.get) if single else max(stages, key=stages.get)
+    ach = sb[dom] / (stages[dom] / 1e3) / 1e9
+    roofline = {"kernel": "k_grid_pass (fused degrid + residual + spread)", "bound": "hbm",
+                "achieved": round(ach, 1), "peak": hbm, "unit": "GB/s",
+                "frac": round(ach / hbm, 4), "traffic": None,
+                "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
+                "algorithmic_bytes_per_launch": sb[dom],
+                "stage_ms": {k: round(v, 4) for k, v in stages.items()},
+                "stage_frac_of_hbm": {k: round(sb[k] / (stages[k] / 1e3) / 1e9 / hbm, 4)
+                                      for k in stages if k in sb and stages[k] > 0}}
+    tfile = os.path.join(ROOT, "profiles", f"traffic_{args.config}_{args.precision}.json")
+    if os.path.exists(tfile):
+        roofline["traffic"] = json.load(open(tfile)).get("dram_bytes_per_launch")
+
+    # end to end through the host-buffer entry point
+    xh = torch.empty_like(x, device="cpu").pin_memory()
+    xh.copy_(x.cpu())
+    gh = torch.empty_like(xh).pin_memory()
+    for _ in range(2):
+        plan.cost_grad_host(xh, gh)
+    barrier(world)
+    t0 = time.perf_counter()
+    ke = max(3, args.steps // 2)
+    for _ in range(ke):
+        plan.cost_grad_host(xh, gh)
+    te = allreduce_max((time.perf_counter() - t0) / ke, world)
+    nbytes = xh.numel() * xh.element_size()
+    e2e = {"value": round(vis_step * world / te, 1), "unit": UNIT, "h2d_bytes_per_step": nbytes,
+           "d2h_bytes_per_step": nbytes + 32, "api": "ivis_cost_grad_host"}
+
+    solve = None
+    if not args.no_solve and args.config in ("c1", "c2") and rank == 0:
+        solve = solve_compare(prob, args)
+
+    out = {"metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(t_max * 1e3, 4),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f32" if args.precision == "fp32" else "f64",
+           "data": "synthetic (seeded ASKAP-shaped uv tracks, lognormal k^-3 sky; V and T from "
+                   "the engine's own predict calls plus noise)",
+           "config": {"workload": WORKLOAD[args.config], "config": args.config,
+                      "vis_per_step_per_gpu": vis_step, "precision": args.precision,
+                      "nufft_kernel_width": plan.nufft_params()[0],
+                      "l2": "flushed before every timed step (256 MiB write)",
+                      "parallelism": f"replicas x{world} (independent problems)"},
+           "roofline": roofline, "clocks": clocks, "e2e": e2e,
+           "gpu_launches": launches * args.steps}
+    if solve:
+        out["solve"] = solve
+    plan.close()
+    return out, prob
+
+
+def solve_compare(prob, args):
+    """Solve time-to-tolerance: the all-FP64 path vs the FP32-grid / FP64-reduction path,
+    judged at equal final cost by the FP64 cost function."""
+    import torch
+    maxiter = 30
+    res = {}
+    p64 = build_plan(prob, "fp64")
+    p64.prepare()
+    x64 = torch.zeros(prob.nchan, prob.n, prob.n, dtype=torch.float64, device="cuda")
+    p64.cost_grad(x64)
+    r64 = p64.solve(x64, maxiter=maxiter, pgtol=0.0, ftol=0.0)
+    res["fp64"] = {k: r64[k] for k in ("seconds", "evaluations", "iterations", "f")}
+    p32 = build_plan(prob, "fp32")
+    p32.prepare()
+    target = r64["f"] * (1 + 1e-6)
+    best = None
+    for it in (maxiter, int(maxiter * 1.5), maxiter * 2):
+        x32 = torch.zeros(prob.nchan, prob.n, prob.n, dtype=torch.float32, device="cuda")
+        p32.cost_grad(x32)
+        r32 = p32.solve(x32, maxiter=it, pgtol=0.0, ftol=0.0)
+        f_true, _, _ = p64.cost_grad(x32.double())
+        best = {"maxiter": it, "seconds": r32["seconds"], "evaluations": r32["evaluations"],
+                "f_fp64_eval": f_true, "reached_fp64_cost": bool(f_true <= target)}
+        if f_true <= target:
+            break
+    res["fp32"] = best
+    res["speedup_time_to_equal_cost"] = (r64["seconds"] / best["seconds"]
+                                         if best["reached_fp64_cost"] else None)
+    res["note"] = "both solves batched over all pointings; tolerance = FP64 final cost x (1+1e-6)"
+    p64.close()
+    p32.close()
+    return res
+
+
+# ----------------------------------------------------------------- CPU oracle legs
+def oracle_rate(prob, seconds_target=15.0, nvis=None, seed=0):
+    """Oracle (direct DFT) cost+grad throughput on a bounded sample: forward over the full
+    window and adjoint at every window pixel for a sample of visibilities of one pair."""
+    import oracle
+    pair = max(prob.pairs, key=lambda p: p.m)
+    if nvis is None:
+        nvis = 4000 if prob.nb >= 512 else 2000
+    rng = np.random.default_rng(seed)
+    idx = np.sort(rng.choice(pair.m, size=min(nvis, pair.m), replace=False))
+    cx, cy = (int(t) for t in prob.centres[pair.k])
+    f = np.asarray(prob.beams[pair.k], np.float64) * oracle.window(prob.sky_true[pair.chan] * 0.5, cx, cy, prob.nb)
+    u, v = pair.uvw[idx, 0], pair.uvw[idx, 1]
+    t0 = time.perf_counter()
+    vt = oracle.model_vis(f, prob.cell_rad, u, v)
+    r = vt - (pair.vis[idx] if pair.vis is not None else 0)
+    oracle.adjoint(pair.weight[idx] * r, prob.nb, prob.cell_rad, u, v)
+    dt = time.perf_counter() - t0
+    return len(idx) / dt, len(idx), dt
+
+
+def cpu_model():
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return "unknown"
+
+
+def run_reference(args, rank, world):
+    """The reference arm: the FP64 CPU oracle as it stands, on the host cores."""
+    import oracle
+    if rank != 0:
+        return None
+    prob = make_problem(args.config)
+    rates, total_vis, total_t = [], 0, 0.0
+    for s in range(args.warmup + args.steps):
+        r, nv, dt = oracle_rate(prob, nvis=1000 if prob.nb >= 512 else 1000, seed=s)
+        if s >= args.warmup:
+            rates.append(r)
+            total_vis += nv
+            total_t += dt
+    value = total_vis / total_t
+    cores = oracle.num_threads()
+    return {"metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(total_t / args.steps * 1e3, 2), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": WORKLOAD[args.config], "config": args.config},
+            "cpu_baseline": {"value": round(value, 2), "unit": UNIT, "cores": cores,
+                             "kind": "oracle", "cpu": cpu_model(),
+                             "sample": "per step: 1000 sampled visibilities of the largest pair, "
+                                       "direct-DFT forward over the full window + adjoint at "
+                                       "every window pixel"},
+            "e2e": {"value": round(value, 2), "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+
+
+# ------------------------------------------------------------------- distributed glue
+def dist_init():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group(backend)
+    return rank, world
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def allreduce_max(v, world):
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if torch.cuda.is_available() and dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([v], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def main():
+    args = parse()
+    rank, world = dist_init()
+    if args.impl == "reference":
+        out = run_reference(args, rank, world)
+        if out is not None:
+            print(json.dumps(out), flush=True)
+        return
+    out, prob = run_ivis(args, rank, world)
+    if rank == 0:
+        if world == 1 and not args.no_cpu:
+            import oracle
+            r, nv, dt = oracle_rate(prob)
+            out["cpu_baseline"] = {"value": round(r, 2), "unit": UNIT, "cores": oracle.num_threads(),
+                                   "kind": "oracle", "cpu": cpu_model(),
+                                   "sample": f"{nv} sampled visibilities of the largest pair: direct-DFT "
+                                             f"forward over the {prob.nb}^2 window + adjoint at every "
+                                             f"window pixel ({dt:.1f} s)"}
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

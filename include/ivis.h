@@ -23,9 +23,10 @@
  *    buffers are borrowed for the duration of the call; set_* calls copy what
  *    they keep into plan-owned device memory. The caller keeps ownership of
  *    everything it passes in.
- *  - All device work is issued on the stream given to ivis_plan. Each call
- *    returns after its work is complete (it synchronises that stream), except
- *    where stated.
+ *  - All device work runs on the plan's own stream (ivis_get_stream), which each
+ *    call first orders after the work already queued on the caller's stream given
+ *    to ivis_plan. Each call returns after its work is complete, except where
+ *    stated.
  *  - No call aborts the process or throws across the ABI. On error the call
  *    returns a non-zero ivis_status, ivis_last_error() describes it, and the
  *    plan remains valid for ivis_destroy (and, unless the status is
@@ -115,6 +116,16 @@ ivis_status ivis_prepare(ivis_plan_t plan);
 ivis_status ivis_cost_grad(ivis_plan_t plan, const void *sky_dev, double *cost_out,
                            void *grad_dev, double *terms_out);
 
+/* Asynchronous form for pipelined callers: enqueue the evaluation on the plan's stream
+ * (ordered after the caller's stream) and return at once. cost_dev (device) receives
+ * {Q_tot, Q, K, R}; grad_dev the gradient. Synchronise with the stream of ivis_get_stream
+ * before reading either. Non-finite costs are not detected by this form. */
+ivis_status ivis_cost_grad_async(ivis_plan_t plan, const void *sky_dev, void *grad_dev,
+                                 double *cost_dev);
+
+/* The plan's own CUDA stream (a cudaStream_t) on which every evaluation runs. */
+ivis_status ivis_get_stream(ivis_plan_t plan, void **stream);
+
 /* Same evaluation from HOST buffers: sky_host is copied in and the gradient copied out
  * inside the call (the end-to-end path of a host-resident caller). */
 ivis_status ivis_cost_grad_host(ivis_plan_t plan, const void *sky_host, double *cost_out,
@@ -140,10 +151,11 @@ ivis_status ivis_solve(ivis_plan_t plan, void *sky_dev, int maxiter, int m_hist,
 /* Kernel width w, ES shape beta and oversampled grid size actually used. */
 ivis_status ivis_get_nufft_params(ivis_plan_t plan, int *w, double *beta, int *nf);
 
-/* Stage timing. enable != 0 records CUDA events around every stage of each evaluation
- * (on the plan's stream); ivis_stage_times then fills up to cap entries of names[] (static
- * strings) and ms[] (mean milliseconds per evaluation since enabling) and returns the
- * number of stages in *count. */
+/* Stage timing. enable != 0 re-captures the evaluation graph with CUDA event nodes around
+ * every stage (on the stream each stage runs on); ivis_stage_times then fills up to cap
+ * entries of names[] (static strings) and ms[] (mean milliseconds per evaluation since
+ * enabling) and returns the number of stages in *count. Folding an evaluation's events into
+ * the totals synchronises the plan's stream before the next evaluation starts. */
 ivis_status ivis_profile(ivis_plan_t plan, int enable);
 ivis_status ivis_stage_times(ivis_plan_t plan, const char **names, double *ms, int cap,
                              int *count);

@@ -21,7 +21,7 @@ STATUS = {0: "IVIS_OK", 1: "IVIS_ERR_ARG", 2: "IVIS_ERR_STATE", 3: "IVIS_ERR_OOM
 
 # Every entry point include/ivis.h declares.
 EXPORTS = ["ivis_plan", "ivis_set_pointing", "ivis_set_vis", "ivis_set_sd", "ivis_prepare",
-           "ivis_cost_grad", "ivis_cost_grad_host", "ivis_predict", "ivis_sd_predict",
+           "ivis_cost_grad", "ivis_cost_grad_async", "ivis_get_stream", "ivis_cost_grad_host", "ivis_predict", "ivis_sd_predict",
            "ivis_solve", "ivis_get_nufft_params", "ivis_profile", "ivis_stage_times",
            "ivis_launches_per_eval", "ivis_destroy", "ivis_last_error"]
 
@@ -67,6 +67,8 @@ def load(path: str = LIB_PATH):
     L.ivis_prepare.argtypes = [vp]
     L.ivis_cost_grad.argtypes = [vp, vp, dp, vp, dp]
     L.ivis_cost_grad_host.argtypes = [vp, vp, dp, vp, dp]
+    L.ivis_cost_grad_async.argtypes = [vp, vp, vp, vp]
+    L.ivis_get_stream.argtypes = [vp, ctypes.POINTER(vp)]
     L.ivis_predict.argtypes = [vp, vp, i, i, vp]
     L.ivis_sd_predict.argtypes = [vp, vp, vp]
     L.ivis_solve.argtypes = [vp, vp, i, i, d, d, ctypes.POINTER(SolveReport)]

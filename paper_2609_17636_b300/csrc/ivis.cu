@@ -37,8 +37,10 @@ struct PairHost {
 
 struct Stage {
     const char *name;
-    cudaEvent_t ev;
+    cudaEvent_t b, e;  // recorded by event nodes of the profiled graph
+    double ms;         // accumulated milliseconds
 };
+constexpr int MAX_STAGES = 16;
 
 }  // namespace
 
@@ -88,9 +90,11 @@ struct ivis_plan_s {
     // solver state
     SolverBufs solver{};
     // profiling
-    bool profile = false;
-    std::vector<Stage> stages;
-    std::vector<double> stage_ms;
+    bool profile = false;        // stage events wanted
+    bool graph_profiled = false; // the instantiated graph carries stage events
+    bool prof_pending = false;   // a profiled evaluation has not been accumulated yet
+    Stage stages[MAX_STAGES]{};
+    int nstage = 0;
     long long prof_evals = 0;
     std::string err;
 };
@@ -311,16 +315,17 @@ cudaError_t launch_fusion(ivis_plan_s *p, cudaStream_t st, const void *sky, void
     return cudaGetLastError();
 }
 
-void stage_mark(ivis_plan_s *p, const char *name, size_t &si) {
-    if (!p->profile || p->capturing) return;
-    if (si >= p->stages.size()) {
-        Stage s{name, nullptr};
-        cudaEventCreate(&s.ev);
-        p->stages.push_back(s);
-        p->stage_ms.push_back(0.0);
-    }
-    cudaEventRecord(p->stages[si].ev, p->stream);
+// Stage intervals are recorded by external event nodes inside the profiled graph.
+void stage_begin(ivis_plan_s *p, const char *name, cudaStream_t st, int &si) {
+    if (!p->profile || si >= MAX_STAGES) return;
+    p->stages[si].name = name;
+    cudaEventRecordWithFlags(p->stages[si].b, st, cudaEventRecordExternal);
+}
+void stage_end(ivis_plan_s *p, cudaStream_t st, int &si) {
+    if (!p->profile || si >= MAX_STAGES) return;
+    cudaEventRecordWithFlags(p->stages[si].e, st, cudaEventRecordExternal);
     ++si;
+    p->nstage = std::max(p->nstage, si);
 }
 
 // Enqueue one full evaluation at p->x into p->g and p->cost_d (and cost_h).
@@ -330,9 +335,8 @@ cudaError_t enqueue_eval(ivis_plan_s *p, bool capture) {
     cudaError_t e;
     const bool use_k = p->cfg.lambda_s != 0.0;
     const bool use_r = p->cfg.lambda_r != 0.0;
-    size_t si = 0;
+    int si = 0;
     int launches = 0;
-    stage_mark(p, "start", si);
     const bool fork = capture && use_k;
     if (use_k) {
         cudaStream_t st = p->stream;
@@ -341,42 +345,47 @@ cudaError_t enqueue_eval(ivis_plan_s *p, bool capture) {
             cudaStreamWaitEvent(p->side, p->ev_fork, 0);
             st = p->side;
         }
+        stage_begin(p, "fusion_K", st, si);
         if ((e = launch_fusion<T>(p, st, p->x, nullptr, p->gradK, true)) != cudaSuccess) return e;
         launches += 4;
-        if (fork) {
-            cudaEventRecord(p->ev_join, p->side);
-        }
-        stage_mark(p, "fusion_K", si);
+        stage_end(p, st, si);
+        if (fork) cudaEventRecord(p->ev_join, p->side);
     }
     if (p->nslot > 0) {
+        stage_begin(p, "zero_adjoint_grid", p->stream, si);
         cudaMemsetAsync(p->G, 0, (size_t)p->nslot * p->nf * p->nf * sizeof(C), p->stream);
-        stage_mark(p, "zero_adjoint_grid", si);
+        stage_end(p, p->stream, si);
+        stage_begin(p, "fwd_fft", p->stream, si);
         if ((e = launch_forward<T>(p, p->x)) != cudaSuccess) return e;
         launches += 2;
-        stage_mark(p, "fwd_fft", si);
+        stage_end(p, p->stream, si);
+        stage_begin(p, "degrid_spread", p->stream, si);
         if ((e = launch_grid_pass<T, MODE_COSTGRAD>(p, 0, p->nchunk, p->jpart, nullptr)) != cudaSuccess)
             return e;
         launches += 1;
-        stage_mark(p, "degrid_spread", si);
+        stage_end(p, p->stream, si);
+        stage_begin(p, "adj_fft", p->stream, si);
         if ((e = launch_adjoint<T>(p)) != cudaSuccess) return e;
         launches += 2;
-        stage_mark(p, "adj_fft", si);
+        stage_end(p, p->stream, si);
     }
     if (fork) cudaStreamWaitEvent(p->stream, p->ev_join, 0);
     const int n = p->cfg.n, nchan = p->cfg.nchan;
     const size_t npix = (size_t)nchan * n * n;
+    stage_begin(p, "assemble_R", p->stream, si);
     k_assemble<T><<<(unsigned)((npix + 255) / 256), 256, 0, p->stream>>>(
         (const T *)p->x, (const T *)p->contrib, p->pinfo_d, p->chan_start_d, p->chan_list_d,
         (const T *)p->gradK, (T *)p->g, n, p->cfg.nb, nchan, (T)p->cfg.lambda_r,
         (T)p->cfg.lambda_s, use_r ? 1 : 0, use_k ? 1 : 0, p->rpart);
     launches += 1;
-    stage_mark(p, "assemble_R", si);
+    stage_end(p, p->stream, si);
+    stage_begin(p, "finalize", p->stream, si);
     k_finalize<<<1, 256, 0, p->stream>>>(p->jpart, p->nchunk, p->kpart, use_k ? p->nkpart : 0,
                                          p->rpart, use_r ? p->nrpart : 0, p->cfg.lambda_r,
                                          p->cfg.lambda_s, p->cost_d);
     launches += 1;
+    stage_end(p, p->stream, si);
     cudaMemcpyAsync(p->cost_h, p->cost_d, 4 * sizeof(double), cudaMemcpyDeviceToHost, p->stream);
-    stage_mark(p, "finalize", si);
     p->launches = launches;
     return cudaGetLastError();
 }
@@ -395,6 +404,7 @@ ivis_status capture_graph(ivis_plan_s *p) {
     p->capturing = true;
     cudaError_t e = enqueue_eval_any(p, true);
     p->capturing = false;
+    p->graph_profiled = p->profile;
     cudaError_t e2 = cudaStreamEndCapture(p->stream, &gph);
     if (e != cudaSuccess) return fail(p, IVIS_ERR_CUDA, std::string("capture: ") + cudaGetErrorString(e));
     if (e2 != cudaSuccess) return fail(p, IVIS_ERR_CUDA, std::string("end capture: ") + cudaGetErrorString(e2));
@@ -404,26 +414,35 @@ ivis_status capture_graph(ivis_plan_s *p) {
     return IVIS_OK;
 }
 
-// Run one evaluation at p->x (graph replay, or direct launches with stage events).
-ivis_status run_eval(ivis_plan_s *p) {
-    if (p->profile) {
-        cudaError_t e = enqueue_eval_any(p, false);
-        if (e != cudaSuccess) return fail(p, IVIS_ERR_CUDA, std::string("eval: ") + cudaGetErrorString(e));
-        CK(cudaStreamSynchronize(p->stream));
-        for (size_t i = 1; i < p->stages.size(); ++i) {
-            float ms = 0.f;
-            cudaEventElapsedTime(&ms, p->stages[i - 1].ev, p->stages[i].ev);
-            p->stage_ms[i] += ms;
-        }
-        p->prof_evals++;
-    } else {
-        CK(cudaGraphLaunch(p->graph, p->stream));
-        CK(cudaStreamSynchronize(p->stream));
+// Fold the stage events of the last profiled evaluation into the running totals.
+ivis_status accumulate_profile(ivis_plan_s *p) {
+    if (!p->prof_pending) return IVIS_OK;
+    CK(cudaStreamSynchronize(p->stream));
+    for (int i = 0; i < p->nstage; ++i) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, p->stages[i].b, p->stages[i].e) == cudaSuccess) p->stages[i].ms += ms;
     }
+    cudaGetLastError();
+    p->prof_evals++;
+    p->prof_pending = false;
+    return IVIS_OK;
+}
+
+// Enqueue one evaluation at p->x (graph replay); with_sync waits and checks the cost.
+ivis_status launch_eval(ivis_plan_s *p, bool with_sync) {
+    ivis_status s;
+    if ((s = accumulate_profile(p))) return s;
+    if (p->graph_profiled != p->profile && (s = capture_graph(p))) return s;
+    CK(cudaGraphLaunch(p->graph, p->stream));
+    if (p->profile) p->prof_pending = true;
+    if (!with_sync) return IVIS_OK;
+    CK(cudaStreamSynchronize(p->stream));
     if (!std::isfinite(p->cost_h[0]))
         return fail(p, IVIS_ERR_NONFINITE, "non-finite cost");
     return IVIS_OK;
 }
+
+ivis_status run_eval(ivis_plan_s *p) { return launch_eval(p, true); }
 
 template <typename T>
 ivis_status set_vis_impl(ivis_plan_s *p, PairHost &ph, int m, const float *uvw, const float *vis,
@@ -815,6 +834,9 @@ ivis_status ivis_plan(const ivis_config *cfg, void *stream, ivis_plan_t *out) {
     if (!s) s = alloc(p, &p->tsd_d, (size_t)c.nchan * c.n * c.n * p->rsz);
     if (!s && cudaStreamCreateWithFlags(&p->side, cudaStreamNonBlocking) != cudaSuccess) s = IVIS_ERR_CUDA;
     if (!s && cudaEventCreateWithFlags(&p->ev_in, cudaEventDisableTiming) != cudaSuccess) s = IVIS_ERR_CUDA;
+    for (int i = 0; i < MAX_STAGES && !s; ++i)
+        if (cudaEventCreate(&p->stages[i].b) != cudaSuccess || cudaEventCreate(&p->stages[i].e) != cudaSuccess)
+            s = IVIS_ERR_CUDA;
     if (!s && cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming) != cudaSuccess) s = IVIS_ERR_CUDA;
     if (!s && cudaEventCreateWithFlags(&p->ev_join, cudaEventDisableTiming) != cudaSuccess) s = IVIS_ERR_CUDA;
     if (!s && cudaMallocHost((void **)&p->cost_h, 4 * sizeof(double)) != cudaSuccess) s = IVIS_ERR_OOM;
@@ -983,20 +1005,44 @@ ivis_status ivis_get_nufft_params(ivis_plan_t p, int *w, double *beta, int *nf) 
 
 ivis_status ivis_profile(ivis_plan_t p, int enable) {
     if (!p) return fail(nullptr, IVIS_ERR_ARG, "null plan");
+    ivis_status s = accumulate_profile(p);
+    if (s) return s;
     p->profile = enable != 0;
-    for (auto &v : p->stage_ms) v = 0.0;
+    for (int i = 0; i < MAX_STAGES; ++i) p->stages[i].ms = 0.0;
+    p->nstage = 0;
     p->prof_evals = 0;
     return IVIS_OK;
 }
 
 ivis_status ivis_stage_times(ivis_plan_t p, const char **names, double *ms, int cap, int *count) {
     if (!p) return fail(nullptr, IVIS_ERR_ARG, "null plan");
-    int n = p->stages.empty() ? 0 : (int)p->stages.size() - 1;
-    if (count) *count = n;
-    for (int i = 0; i < n && i < cap; ++i) {
-        if (names) names[i] = p->stages[i + 1].name;
-        if (ms) ms[i] = p->prof_evals ? p->stage_ms[i + 1] / p->prof_evals : 0.0;
+    ivis_status s = accumulate_profile(p);
+    if (s) return s;
+    if (count) *count = p->nstage;
+    for (int i = 0; i < p->nstage && i < cap; ++i) {
+        if (names) names[i] = p->stages[i].name;
+        if (ms) ms[i] = p->prof_evals ? p->stages[i].ms / p->prof_evals : 0.0;
     }
+    return IVIS_OK;
+}
+
+ivis_status ivis_get_stream(ivis_plan_t p, void **stream) {
+    if (!p || !stream) return fail(p, IVIS_ERR_ARG, "null pointer");
+    *stream = (void *)p->stream;
+    return IVIS_OK;
+}
+
+ivis_status ivis_cost_grad_async(ivis_plan_t p, const void *sky_dev, void *grad_dev, double *cost_dev) {
+    if (!p) return fail(nullptr, IVIS_ERR_ARG, "null plan");
+    if (!sky_dev || !grad_dev || !cost_dev) return fail(p, IVIS_ERR_ARG, "null sky, gradient or cost pointer");
+    enter(p);
+    ivis_status s = ensure_prepared(p);
+    if (s) return s;
+    size_t bytes = (size_t)p->cfg.nchan * p->cfg.n * p->cfg.n * p->rsz;
+    CK(cudaMemcpyAsync(p->x, sky_dev, bytes, cudaMemcpyDeviceToDevice, p->stream));
+    if ((s = launch_eval(p, false))) return s;
+    CK(cudaMemcpyAsync(cost_dev, p->cost_d, 4 * sizeof(double), cudaMemcpyDeviceToDevice, p->stream));
+    CK(cudaMemcpyAsync(grad_dev, p->g, bytes, cudaMemcpyDeviceToDevice, p->stream));
     return IVIS_OK;
 }
 
@@ -1029,7 +1075,10 @@ ivis_status ivis_destroy(ivis_plan_t p) {
     dfree(p->tw_d);
     dfree(p->beams_d);
     dfree(p->tsd_d);
-    for (auto &st : p->stages) cudaEventDestroy(st.ev);
+    for (auto &st : p->stages) {
+        if (st.b) cudaEventDestroy(st.b);
+        if (st.e) cudaEventDestroy(st.e);
+    }
     if (p->ev_fork) cudaEventDestroy(p->ev_fork);
     if (p->ev_join) cudaEventDestroy(p->ev_join);
     if (p->side) cudaStreamDestroy(p->side);

@@ -98,6 +98,20 @@ class Plan:
                                                       ctypes.c_void_p(grad.data_ptr()), terms))
         return cost.value, grad, (terms[0], terms[1], terms[2])
 
+    def cost_grad_async(self, sky: torch.Tensor, grad: torch.Tensor, cost: torch.Tensor):
+        """Enqueue an evaluation on the plan's stream; cost (CUDA float64[4]) receives
+        {Q_tot, Q, K, R}. Synchronise with :attr:`cuda_stream` before reading."""
+        sky = self._sky(sky)
+        _check(self.L, self._p, self.L.ivis_cost_grad_async(
+            self._p, ctypes.c_void_p(sky.data_ptr()), ctypes.c_void_p(grad.data_ptr()),
+            ctypes.c_void_p(cost.data_ptr())))
+
+    @property
+    def cuda_stream(self) -> torch.cuda.ExternalStream:
+        ptr = ctypes.c_void_p()
+        _check(self.L, self._p, self.L.ivis_get_stream(self._p, ctypes.byref(ptr)))
+        return torch.cuda.ExternalStream(ptr.value)
+
     def cost_grad_host(self, sky_host: torch.Tensor, grad_host: torch.Tensor):
         """Same evaluation from host (ideally pinned) CPU tensors."""
         if sky_host.is_cuda or grad_host.is_cuda:

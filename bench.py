@@ -35,8 +35,8 @@ UNIT = "vis/s"
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ivis", choices=["ivis", "reference"])
     ap.add_argument("--config", default="c2", choices=["c1", "c2", "c3", "c4"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
@@ -83,7 +83,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "20"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
@@ -92,7 +92,10 @@ class ClockSampler:
 
     def _read(self):
         for line in self.proc.stdout:
-            self.rows.append([t.strip() for t in line.split(",")])
+            self.rows.append((time.time(), [t.strip() for t in line.split(",")]))
+
+    def mark(self, which):
+        setattr(self, which, time.time())
 
     def stop(self):
         if self.proc is None:
@@ -102,14 +105,16 @@ class ClockSampler:
             self.proc.wait(timeout=5)
         except Exception:
             self.proc.kill()
-        rows = [r for r in self.rows if len(r) >= 8]
+        t0, t1 = getattr(self, "t_begin", 0.0), getattr(self, "t_end", 1e30)
+        inside = [r for (t, r) in self.rows if t0 <= t <= t1 + 0.03 and len(r) >= 8]
+        rows = inside if inside else [r for (t, r) in self.rows if len(r) >= 8][-3:]
         sm = [float(r[0]) for r in rows if r[0].replace(".", "").isdigit()]
         smax = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         reasons = sorted({names[i] for r in rows for i in range(4) if r[4 + i].lower() == "active"})
         return {"sm_mhz": float(np.median(sm)) if sm else None,
                 "sm_max_mhz": max(smax) if smax else None, "reasons": reasons,
-                "samples": len(rows)}
+                "samples": len(rows), "samples_in_timed_region": len(inside)}
 
 
 # ------------------------------------------------------------------- data synthesis
@@ -131,6 +136,9 @@ def attach_data_gpu(prob, plan_fp64_like):
 
 def build_plan(prob, precision):
     from paper_2609_17636_b300 import plan_from_problem
+    for pair in prob.pairs:
+        if pair.vis is None:
+            pair.vis = np.zeros(pair.m, np.complex64)
     if prob.lambda_s != 0.0 and getattr(prob, "tsd", None) is None:
         prob.tsd = np.zeros((prob.nchan, prob.n, prob.n), np.float32)
         prob.sigma_sd = np.ones(prob.nchan)
@@ -182,6 +190,8 @@ def run_ivis(args, rank, world):
         e1.record(ps)
         return e0, e1
 
+    clk = ClockSampler(dev.index)
+    clk.start()
     plan.profile(True)  # the profiled graph (stage event nodes) is captured in the warm-up
     for _ in range(args.warmup):
         step()
@@ -190,13 +200,13 @@ def run_ivis(args, rank, world):
     plan.profile(True)  # reset the stage totals; the graph is kept
     barrier(world)
     torch.cuda.synchronize()
-    clk = ClockSampler(dev.index)
-    clk.start()
+    clk.mark("t_begin")
     evs = []
     for _ in range(args.steps):
         evs.append(step())
         ps.synchronize()  # stage events are folded in before the next step
     torch.cuda.synchronize()
+    clk.mark("t_end")
     barrier(world)
     clocks = clk.stop()
     stages = plan.stage_times()

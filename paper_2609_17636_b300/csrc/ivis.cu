@@ -77,7 +77,6 @@ struct ivis_plan_s {
     int Rsd = 0;
     void *taps_d = nullptr;
     double *inv_sig2_d = nullptr;
-    int conv_ty = 64;
     void *rowbuf = nullptr, *F = nullptr, *G = nullptr, *contrib = nullptr;
     void *x = nullptr, *g = nullptr, *tmp1 = nullptr, *tmp2 = nullptr, *gradK = nullptr;
     double *jpart = nullptr, *kpart = nullptr, *rpart = nullptr, *cost_d = nullptr;
@@ -288,30 +287,29 @@ cudaError_t launch_adjoint(ivis_plan_s *p) {
 }
 
 template <typename T>
+size_t conv_smem(int R) { return ((size_t)(CONV_TO + 2 * R) * 33 + 2 * R + 1) * sizeof(T); }
+
+template <typename T>
 cudaError_t launch_fusion(ivis_plan_s *p, cudaStream_t st, const void *sky, void *tsd_out_e,
                           void *gradK_out, bool fused) {
     const int n = p->cfg.n, nchan = p->cfg.nchan, R = p->Rsd;
-    dim3 gr((n + 255) / 256, n, nchan);
-    size_t smr = (size_t)(256 + 2 * R) * sizeof(T);
-    cudaFuncSetAttribute(k_conv_rows<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smr);
-    size_t smc = (size_t)(p->conv_ty + 2 * R) * 32 * sizeof(T);
-    cudaFuncSetAttribute(k_conv_cols<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smc);
-    cudaFuncSetAttribute(k_conv_cols<T, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smc);
-    dim3 gcc((n + 31) / 32, (n + p->conv_ty - 1) / p->conv_ty, nchan);
-    k_conv_rows<T><<<gr, 256, smr, st>>>((const T *)sky, (T *)p->tmp1, (const T *)p->taps_d, R, n);
+    const size_t sm = conv_smem<T>(R);
+    cudaFuncSetAttribute(k_conv_axis<T, 0, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaFuncSetAttribute(k_conv_axis<T, 1, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaFuncSetAttribute(k_conv_axis<T, 1, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    dim3 gr((n + 31) / 32, (n + CONV_TO - 1) / CONV_TO, nchan);
+    const T *taps = (const T *)p->taps_d;
+    k_conv_axis<T, 0, 0><<<gr, 256, sm, st>>>((const T *)sky, (T *)p->tmp1, taps, R, n, nullptr, nullptr, nullptr);
     if (!fused) {  // plain B (x) I into tsd_out_e
-        k_conv_cols<T, 0><<<gcc, 256, smc, st>>>((const T *)p->tmp1, (T *)tsd_out_e,
-                                                 (const T *)p->taps_d, R, n, p->conv_ty, nullptr,
-                                                 nullptr, nullptr);
+        k_conv_axis<T, 1, 0><<<gr, 256, sm, st>>>((const T *)p->tmp1, (T *)tsd_out_e, taps, R, n, nullptr,
+                                                  nullptr, nullptr);
         return cudaGetLastError();
     }
-    k_conv_cols<T, 1><<<gcc, 256, smc, st>>>((const T *)p->tmp1, (T *)p->tmp2,
-                                             (const T *)p->taps_d, R, n, p->conv_ty,
-                                             (const T *)p->tsd_d, p->inv_sig2_d, p->kpart);
-    k_conv_rows<T><<<gr, 256, smr, st>>>((const T *)p->tmp2, (T *)p->tmp1, (const T *)p->taps_d, R, n);
-    k_conv_cols<T, 0><<<gcc, 256, smc, st>>>((const T *)p->tmp1, (T *)gradK_out,
-                                             (const T *)p->taps_d, R, n, p->conv_ty, nullptr,
-                                             nullptr, nullptr);
+    k_conv_axis<T, 1, 1><<<gr, 256, sm, st>>>((const T *)p->tmp1, (T *)p->tmp2, taps, R, n,
+                                              (const T *)p->tsd_d, p->inv_sig2_d, p->kpart);
+    k_conv_axis<T, 0, 0><<<gr, 256, sm, st>>>((const T *)p->tmp2, (T *)p->tmp1, taps, R, n, nullptr, nullptr, nullptr);
+    k_conv_axis<T, 1, 0><<<gr, 256, sm, st>>>((const T *)p->tmp1, (T *)gradK_out, taps, R, n, nullptr,
+                                              nullptr, nullptr);
     return cudaGetLastError();
 }
 
@@ -402,6 +400,7 @@ ivis_status capture_graph(ivis_plan_s *p) {
     cudaGraph_t gph;
     CK(cudaStreamBeginCapture(p->stream, cudaStreamCaptureModeRelaxed));
     p->capturing = true;
+    p->nstage = 0;
     cudaError_t e = enqueue_eval_any(p, true);
     p->capturing = false;
     p->graph_profiled = p->profile;
@@ -620,14 +619,12 @@ ivis_status prepare_impl(ivis_plan_s *p) {
         }
         if ((s = upload_real<T>(p, &p->taps_d, taps))) return s;
         if ((s = up((void **)&p->inv_sig2_d, is2.data(), is2.size() * sizeof(double)))) return s;
-        p->conv_ty = 64;
-        while (p->conv_ty > 8 && (size_t)(p->conv_ty + 2 * R) * 32 * sizeof(T) > 160 * 1024) p->conv_ty /= 2;
-        if ((size_t)(p->conv_ty + 2 * R) * 32 * sizeof(T) > 200 * 1024)
-            return fail(p, IVIS_ERR_ARG, "single-dish beam too wide for the column pass");
+        if (conv_smem<T>(R) > 220 * 1024)
+            return fail(p, IVIS_ERR_ARG, "single-dish beam too wide for the convolution strip");
         if ((s = alloc(p, &p->tmp1, npix * sizeof(T)))) return s;
         if ((s = alloc(p, &p->tmp2, npix * sizeof(T)))) return s;
         if ((s = alloc(p, &p->gradK, npix * sizeof(T)))) return s;
-        p->nkpart = ((c.n + 31) / 32) * ((c.n + p->conv_ty - 1) / p->conv_ty) * c.nchan;
+        p->nkpart = ((c.n + 31) / 32) * ((c.n + CONV_TO - 1) / CONV_TO) * c.nchan;
         if ((s = alloc(p, (void **)&p->kpart, (size_t)p->nkpart * sizeof(double)))) return s;
     }
     if (!p->kpart && (s = alloc(p, (void **)&p->kpart, sizeof(double)))) return s;
@@ -1009,7 +1006,6 @@ ivis_status ivis_profile(ivis_plan_t p, int enable) {
     if (s) return s;
     p->profile = enable != 0;
     for (int i = 0; i < MAX_STAGES; ++i) p->stages[i].ms = 0.0;
-    p->nstage = 0;
     p->prof_evals = 0;
     return IVIS_OK;
 }

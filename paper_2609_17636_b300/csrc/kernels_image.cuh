@@ -5,7 +5,7 @@
 //   a7  Laplacian regulariser R = 1/2 ||D I||^2, grad R = D^T D I (Eqs. 7-8), zero
 //       boundary, evaluated on the fly in k_assemble
 //   a8  fusion term: t = B (x) I by two separable passes, e = (t - T)/sigma^2,
-//       K = 1/2 sum (t - T)^2 / sigma^2, grad K = B (x) e (Eqs. 11-13)  (k_conv_rows/cols)
+//       K = 1/2 sum (t - T)^2 / sigma^2, grad K = B (x) e (Eqs. 11-13)  (k_conv_axis)
 //   a9  Q_tot = Q + lambda_s K + lambda_r R from FP64 partials in a fixed order (k_finalize)
 #pragma once
 #include "common.cuh"
@@ -63,67 +63,85 @@ k_assemble(const T *__restrict__ sky, const T *__restrict__ contrib,
     if (threadIdx.x == 0) rpart[blockIdx.x] = s;
 }
 
-// out[c][y][x] = sum_{t=-R..R} b_c[t] in[c][y][x - t], zero outside; block = 256 outputs of a row.
-template <typename T>
-__global__ void __launch_bounds__(256)
-k_conv_rows(const T *__restrict__ in, T *out, const T *__restrict__ taps, int R, int n) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    T *sh = reinterpret_cast<T *>(smem_raw);
-    const int x0 = blockIdx.x * 256, y = blockIdx.y, c = blockIdx.z;
-    const T *row = in + ((size_t)c * n + y) * n;
-    const T *b = taps + (size_t)c * (2 * R + 1);
-    for (int i = threadIdx.x; i < 256 + 2 * R; i += 256) {
-        const int x = x0 - R + i;
-        sh[i] = (x >= 0 && x < n) ? row[x] : (T)0;
-    }
-    __syncthreads();
-    const int x = x0 + threadIdx.x;
-    if (x >= n) return;
-    T acc = (T)0;
-    const T *s = sh + threadIdx.x + 2 * R;
-    for (int t = 0; t <= 2 * R; ++t) acc += __ldg(&b[t]) * s[-t];
-    out[((size_t)c * n + y) * n + x] = acc;
-}
+// Separable dish-beam convolution, one axis per launch: out = sum_{t=-R..R} b_c[t] in(. - t),
+// zero outside the image. A CTA of 8 warps covers 32 lines (one per lane) x CONV_TO outputs
+// along the convolution axis; each thread produces CONV_OPT consecutive outputs from a
+// sliding window of registers, so each shared-memory load feeds CONV_OPT FMAs. The staged
+// strip is laid out [position][line] with a 33-word row pitch (rows pass: lines are image
+// rows and the transpose would otherwise serialise on one bank).
+constexpr int CONV_OPT = 8;
+constexpr int CONV_TO = 8 * CONV_OPT;  // outputs per CTA along the axis
 
-// Column pass; block (32, 8) covers 32 columns x TY output rows. FUSED: the output is the
-// single-dish residual e = (t - T)/sigma^2 and the block's share of K is written to kpart.
-template <typename T, int FUSED>
+// AXIS 0: along x (lines = rows); AXIS 1: along y (lines = columns).
+// FUSED (AXIS 1 only): out = e = (t - T)/sigma^2 and the CTA's share of K goes to kpart.
+template <typename T, int AXIS, int FUSED>
 __global__ void __launch_bounds__(256)
-k_conv_cols(const T *__restrict__ in, T *out, const T *__restrict__ taps, int R, int n, int TY,
+k_conv_axis(const T *__restrict__ in, T *out, const T *__restrict__ taps, int R, int n,
             const T *__restrict__ tsd, const double *__restrict__ inv_sig2, double *kpart) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double red[32];
+    const int P = 33;
+    const int L = CONV_TO + 2 * R;  // staged positions
     T *sh = reinterpret_cast<T *>(smem_raw);
-    const int tx = threadIdx.x & 31, tyi = threadIdx.x >> 5;
-    const int x = blockIdx.x * 32 + tx, y0 = blockIdx.y * TY, c = blockIdx.z;
+    T *tp = sh + (size_t)L * P;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int line0 = blockIdx.x * 32, pos0 = blockIdx.y * CONV_TO, c = blockIdx.z;
     const T *img = in + (size_t)c * n * n;
     const T *b = taps + (size_t)c * (2 * R + 1);
-    for (int i = tyi; i < TY + 2 * R; i += 8) {
-        const int y = y0 - R + i;
-        sh[i * 32 + tx] = (y >= 0 && y < n && x < n) ? img[(size_t)y * n + x] : (T)0;
+    for (int t = threadIdx.x; t <= 2 * R; t += blockDim.x) tp[t] = b[t];
+    if (AXIS == 0) {
+        // rows: global reads run along x (positions) for coalescing
+        for (int i = threadIdx.x; i < 32 * L; i += blockDim.x) {
+            const int li = i / L, pi = i - li * L;
+            const int y = line0 + li, x = pos0 - R + pi;
+            sh[pi * P + li] = (y < n && x >= 0 && x < n) ? img[(size_t)y * n + x] : (T)0;
+        }
+    } else {
+        for (int i = threadIdx.x; i < 32 * L; i += blockDim.x) {
+            const int pi = i >> 5, li = i & 31;
+            const int y = pos0 - R + pi, x = line0 + li;
+            sh[pi * P + li] = (x < n && y >= 0 && y < n) ? img[(size_t)y * n + x] : (T)0;
+        }
     }
     __syncthreads();
+    // outputs j = 0..OPT-1 at axis position o0 + j use staged position o0 + j + 2R - t
+    const int o0 = wid * CONV_OPT;
+    T acc[CONV_OPT], win[CONV_OPT];
+#pragma unroll
+    for (int j = 0; j < CONV_OPT; ++j) {
+        acc[j] = (T)0;
+        win[j] = sh[(o0 + j + 2 * R) * P + lane];
+    }
+    for (int t = 0; t <= 2 * R; ++t) {
+        const T bt = tp[t];
+#pragma unroll
+        for (int j = 0; j < CONV_OPT; ++j) acc[j] += bt * win[j];
+        if (t < 2 * R) {
+#pragma unroll
+            for (int j = CONV_OPT - 1; j > 0; --j) win[j] = win[j - 1];
+            win[0] = sh[(o0 + 2 * R - t - 1) * P + lane];
+        }
+    }
     double kloc = 0.0;
     const double is2 = FUSED ? inv_sig2[c] : 0.0;
-    for (int yy = tyi; yy < TY; yy += 8) {
-        const int y = y0 + yy;
-        if (y >= n || x >= n) continue;
-        T acc = (T)0;
-        const T *s = sh + (yy + 2 * R) * 32 + tx;
-        for (int t = 0; t <= 2 * R; ++t) acc += __ldg(&b[t]) * s[-t * 32];
-        const size_t o = ((size_t)c * n + y) * n + x;
+    const int line = line0 + lane;
+#pragma unroll
+    for (int j = 0; j < CONV_OPT; ++j) {
+        const int pos = pos0 + o0 + j;
+        if (line >= n || pos >= n) continue;
+        const size_t o = AXIS == 0 ? ((size_t)c * n + line) * n + pos : ((size_t)c * n + pos) * n + line;
         if (FUSED) {
-            const double e = (double)acc - (double)tsd[o];
+            const double e = (double)acc[j] - (double)tsd[o];
             kloc += 0.5 * e * e * is2;
             out[o] = (T)(e * is2);
         } else {
-            out[o] = acc;
+            out[o] = acc[j];
         }
     }
     if (FUSED) {
-        const double s = block_sum(kloc, red);
+        const double sum = block_sum(kloc, red);
         if (threadIdx.x == 0)
-            kpart[((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = s;
+            kpart[((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = sum;
     }
 }
 

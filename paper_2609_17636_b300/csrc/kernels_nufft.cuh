@@ -198,9 +198,19 @@ __device__ __forceinline__ void decode(double2 c, int nf, int &gx, int &gy, doub
 
 enum { MODE_COSTGRAD = 0, MODE_PREDICT = 1 };
 
+// Vector reduction into global memory for one complex cell (sm_90+ has 2-wide float adds).
+__device__ __forceinline__ void red_add_c(float2 *p, float2 v) { atomicAdd(p, v); }
+__device__ __forceinline__ void red_add_c(double2 *p, double2 v) {
+    atomicAdd(&p->x, v.x);
+    atomicAdd(&p->y, v.y);
+}
+
 // One CTA per chunk (a run of visibilities of one tile of one pair). The tile's fine-grid
-// patch (tile + W - 1 cells square, wrapped) is staged in shared memory; each thread takes one
-// visibility, evaluates its 2W kernel values once and uses them for both interpolation and
+// patch (tile + W - 1 cells square, wrapped) is staged in shared memory. A group of GS lanes
+// (GS = W rounded up to a power of two) handles one visibility at a time: lane r owns kernel
+// row r. Each lane evaluates one x and one y kernel value, the x values are exchanged by
+// shuffles, the row sums of the interpolation are reduced across the group, and every lane
+// spreads w r into its own kernel row. The same 2W kernel values serve interpolation and
 // spreading. MODE_PREDICT writes V~ to pred[orig] instead of spreading.
 template <typename T, int W, int MODE>
 __global__ void __launch_bounds__(256)
@@ -209,6 +219,8 @@ k_grid_pass(const Chunk *__restrict__ chunks, const PairData<T> *__restrict__ pd
             int lognf, int tile, int ntx, T beta, double *jpart,
             typename cplx_of<T>::type *pred) {
     typedef typename cplx_of<T>::type C;
+    constexpr int GS = W <= 4 ? 4 : (W <= 8 ? 8 : 16);
+    constexpr int NG = 256 / GS;  // groups per CTA
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double red[32];
     const int nf = 1 << lognf;
@@ -228,49 +240,59 @@ k_grid_pass(const Chunk *__restrict__ chunks, const PairData<T> *__restrict__ pd
     }
     __syncthreads();
     const T zs = (T)2 / (T)W;
+    const int r = threadIdx.x & (GS - 1);       // kernel row of this lane
+    const bool active_row = r < W;
     double jacc = 0.0;
-    for (int v = ch.begin + threadIdx.x; v < ch.end; v += blockDim.x) {
-        int gx, gy;
-        T dx, dy;
-        decode<W>(pd.coord[v], nf, gx, gy, dx, dy);
+    constexpr int GPW = 32 / GS;                 // groups per warp
+    const int warp = threadIdx.x >> 5;
+    const int gw = (threadIdx.x & 31) / GS;      // group index within the warp
+    // The loop bound depends on the warp only (vb), so every lane of a warp runs the same
+    // number of iterations and the full-warp shuffles below always see all 32 lanes.
+    for (int vb = ch.begin + warp * GPW; vb < ch.end; vb += NG) {
+        const int v = vb + gw;
+        const bool valid = v < ch.end;
+        int gx = x0, gy = y0;
+        T dx = (T)(0.5 * W), dy = (T)(0.5 * W);
+        if (valid) decode<W>(pd.coord[v], nf, gx, gy, dx, dy);
         const int lx = gx - x0, ly = gy - y0;
-        T kx[W], ky[W];
+        const bool row_on = valid && active_row;
+        const T kxr = row_on ? es_kernel((dx - (T)r) * zs, beta) : (T)0;
+        const T kyr = row_on ? es_kernel((dy - (T)r) * zs, beta) : (T)0;
+        T kx[W];
 #pragma unroll
-        for (int t = 0; t < W; ++t) {
-            kx[t] = es_kernel((dx - (T)t) * zs, beta);
-            ky[t] = es_kernel((dy - (T)t) * zs, beta);
-        }
-        C acc = mk((T)0, (T)0);
-        const C *fr = Fs + ly * PW + lx;
-#pragma unroll
-        for (int b = 0; b < W; ++b) {
-            C row = mk((T)0, (T)0);
+        for (int a = 0; a < W; ++a) kx[a] = __shfl_sync(0xffffffffu, kxr, a, GS);
+        C row = mk((T)0, (T)0);
+        if (row_on) {
+            const C *fr = Fs + (ly + r) * PW + lx;
 #pragma unroll
             for (int a = 0; a < W; ++a) {
-                const C f = fr[b * PW + a];
+                const C f = fr[a];
                 row.x += kx[a] * f.x;
                 row.y += kx[a] * f.y;
             }
-            acc.x += ky[b] * row.x;
-            acc.y += ky[b] * row.y;
         }
+        C acc = mk(kyr * row.x, kyr * row.y);
+#pragma unroll
+        for (int o = GS / 2; o > 0; o >>= 1) {
+            acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o, GS);
+            acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o, GS);
+        }
+        if (!valid) continue;
         if (MODE == MODE_PREDICT) {
-            pred[pd.orig[v]] = acc;
+            if (r == 0) pred[pd.orig[v]] = acc;
             continue;
         }
         const C vv = pd.vis[v];
         const T w = pd.w[v];
-        const C r = mk(acc.x - vv.x, acc.y - vv.y);
-        jacc += 0.5 * (double)w * ((double)r.x * (double)r.x + (double)r.y * (double)r.y);
-        const C c = mk(w * r.x, w * r.y);
-        C *gr = Gs + ly * PW + lx;
-#pragma unroll
-        for (int b = 0; b < W; ++b) {
-            const T cyx = ky[b] * c.x, cyy = ky[b] * c.y;
+        const C res = mk(acc.x - vv.x, acc.y - vv.y);
+        if (r == 0) jacc += 0.5 * (double)w * ((double)res.x * (double)res.x + (double)res.y * (double)res.y);
+        if (active_row) {
+            const T cyx = kyr * w * res.x, cyy = kyr * w * res.y;
+            C *gr = Gs + (ly + r) * PW + lx;
 #pragma unroll
             for (int a = 0; a < W; ++a) {
-                atomicAdd(&gr[b * PW + a].x, cyx * kx[a]);
-                atomicAdd(&gr[b * PW + a].y, cyy * kx[a]);
+                atomicAdd(&gr[a].x, cyx * kx[a]);
+                atomicAdd(&gr[a].y, cyy * kx[a]);
             }
         }
     }
@@ -284,7 +306,7 @@ k_grid_pass(const Chunk *__restrict__ chunks, const PairData<T> *__restrict__ pd
         if (g.x == (T)0 && g.y == (T)0) continue;
         const int ly = i / PW, lx = i - ly * PW;
         const int gy = (y0 + ly) & (nf - 1), gx = (x0 + lx) & (nf - 1);
-        atomic_add_c(&Gp[(size_t)gy * nf + gx], g);
+        red_add_c(&Gp[(size_t)gy * nf + gx], g);
     }
 }
 

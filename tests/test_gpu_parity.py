@@ -75,6 +75,32 @@ def test_single_dish_model_matches_oracle(mosaic):
     plan.close()
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_single_dish_wide_beam_matches_oracle(precision):
+    """The 16 arcmin dish at 7 arcsec (FWHM 137 px, 467 taps) on a 256^2 sky: the taps run
+    past the image on both sides; the fused residual/K path against the oracle's K."""
+    from paper_2609_17636_b300 import Plan
+    rng = np.random.default_rng(5)
+    n, fwhm = 256, 16 * 60 / 7.0
+    sky = rng.uniform(0, 1, (1, n, n))
+    b = oracle.dish_kernel(fwhm)
+    tsd = oracle.dish_conv(sky[0] * 0.8, b)[None] + 0.01 * rng.standard_normal((1, n, n))
+    tsd = tsd.astype(np.float32)
+    plan = Plan(n, 1, 1, 16, 1e-5, precision, lambda_s=0.7)
+    plan.set_pointing(0, n // 2, n // 2, torch.ones(16, 16, device="cuda"))
+    plan.set_vis(0, 0, torch.zeros((0, 3), device="cuda"), None, None)
+    plan.set_sd(0, torch.as_tensor(tsd[0], device="cuda"), 0.05, fwhm)
+    dt = torch.float64 if precision == "fp64" else torch.float32
+    xs = torch.as_tensor(sky, dtype=dt, device="cuda")
+    f, g, terms = plan.cost_grad(xs)
+    K, gK = oracle.fusion_cost_grad(sky, tsd, 0.05, fwhm)
+    tol = 1e-12 if precision == "fp64" else 1e-5
+    assert abs(terms[1] - K) <= tol * K and abs(f - 0.7 * K) <= tol * f
+    assert rel_l2(g.cpu().numpy(), 0.7 * gK) <= tol
+    assert rel_l2(plan.sd_predict(xs).cpu().numpy()[0], oracle.dish_conv(sky[0], b)) <= tol
+    plan.close()
+
+
 def test_gradient_central_differences_fp64(mosaic):
     prob, x, *_ = mosaic
     plan = _plan(prob, "fp64")

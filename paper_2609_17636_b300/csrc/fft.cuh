@@ -1,46 +1,134 @@
-// fft.cuh -- power-of-two complex FFTs on data staged in shared memory.
+// fft.cuh -- power-of-two complex FFTs on lines staged in shared memory.
 //
 // The oversampled grid of the NUFFT is transformed by two passes of 1-D FFTs (rows, then
-// columns, and the reverse for the adjoint). Each CTA stages one row, or a block of adjacent
-// columns, in shared memory; the 1-D transforms run there so that HBM sees one coalesced read
-// and one coalesced write per pass.
+// columns, and the reverse for the adjoint). Each CTA stages a few rows, or a block of
+// adjacent columns, in shared memory; HBM sees one coalesced read and one coalesced write per
+// pass.
+//
+// Each line of length L = 2^logL is transformed by the Stockham auto-sort formulation
+// (Govindaraju et al., "High performance discrete Fourier transforms on graphics
+// processors", SC 2008): log_R(L) passes, in each of which a thread loads R elements spaced
+// L/R apart, applies the pass twiddles, does a radix-R DFT in registers and stores the R
+// results spaced Ns apart. Input and output are in natural order (no bit reversal). R = 16,
+// with one final pass of radix 2, 4 or 8 when logL is not a multiple of 4. Shared-memory
+// addresses are padded by one element every 16 (pidx) so the strided stores of the early
+// passes do not pile onto one bank.
 #pragma once
 #include "common.cuh"
 
 namespace ivis {
 
-__device__ __forceinline__ int bitrev(int n, int logL) {
-    return (int)(__brev((unsigned)n) >> (32 - logL));
+__host__ __device__ __forceinline__ int pidx(int e) { return e + (e >> 4); }
+
+// Twiddle W_16^q = exp(-2 pi i q / 16) for q < 8 (cos and sin of q pi / 8).
+__device__ __forceinline__ double cos16(int q) {
+    constexpr double c[8] = {1.0, 0.92387953251128675613, 0.70710678118654752440,
+                             0.38268343236508977173, 0.0, -0.38268343236508977173,
+                             -0.70710678118654752440, -0.92387953251128675613};
+    return c[q];
+}
+__device__ __forceinline__ double sin16(int q) {
+    constexpr double s[8] = {0.0, 0.38268343236508977173, 0.70710678118654752440,
+                             0.92387953251128675613, 1.0, 0.92387953251128675613,
+                             0.70710678118654752440, 0.38268343236508977173};
+    return s[q];
 }
 
-// In-place decimation-in-time radix-2 FFT of `ncols` independent columns of length L
-// (L = 2^logL). Element n of column c must already sit at s[bitrev(n) * ncols + c]; on
-// return output k of column c is at s[k * ncols + c]. SIGN = -1: sum x[n] e^{-2 pi i nk/L};
-// SIGN = +1: sum x[n] e^{+2 pi i nk/L} (unnormalised). tw[j] = e^{-2 pi i j / L}, j < L/2.
-// ncols must be a power of two. The caller synchronises before the call; the call ends
-// with a __syncthreads.
-template <typename C, int SIGN>
-__device__ __forceinline__ void fft_dit_smem(C *s, int logL, int logc, const C *__restrict__ tw) {
-    const int L = 1 << logL;
-    const int ncols = 1 << logc;
-    const int nbf = (L >> 1) << logc;
-    for (int logh = 0; logh < logL; ++logh) {
-        const int h = 1 << logh;
-        for (int idx = threadIdx.x; idx < nbf; idx += blockDim.x) {
-            const int c = idx & (ncols - 1);
-            const int b = idx >> logc;
-            const int j = b & (h - 1);
-            const int i0 = ((b >> logh) << (logh + 1)) + j;
-            const int i1 = i0 + h;
-            C w = __ldg(&tw[j << (logL - 1 - logh)]);
-            if (SIGN > 0) w.y = -w.y;
-            C a = s[(i0 << logc) + c];
-            C x = cmul(s[(i1 << logc) + c], w);
-            s[(i0 << logc) + c] = a + x;
-            s[(i1 << logc) + c] = a - x;
+// In-register radix-2 decimation-in-frequency DFT of size R (natural-order input); output
+// k ends up in v[bitrev_R(k)]. SIGN = -1 forward, +1 inverse (unnormalised).
+template <typename C, int R, int SIGN>
+__device__ __forceinline__ void dft_regs(C (&v)[R]) {
+#pragma unroll
+    for (int h = R / 2; h >= 1; h >>= 1) {
+#pragma unroll
+        for (int g = 0; g < R; g += 2 * h) {
+#pragma unroll
+            for (int i = 0; i < h; ++i) {
+                const C a = v[g + i], b = v[g + i + h];
+                v[g + i] = a + b;
+                C d = a - b;
+                const int q = i * (16 / (2 * h));  // W_{2h}^i = W_16^q
+                if (q != 0) {
+                    if (q == 4) {  // multiply by -i (forward) or +i (inverse)
+                        d = SIGN < 0 ? mk(d.y, -d.x) : mk(-d.y, d.x);
+                    } else {
+                        const auto c = (decltype(d.x))cos16(q);
+                        const auto s = (decltype(d.x))(SIGN < 0 ? -sin16(q) : sin16(q));
+                        d = mk(d.x * c - d.y * s, d.x * s + d.y * c);
+                    }
+                }
+                v[g + i + h] = d;
+            }
         }
-        __syncthreads();
     }
 }
+
+template <int R>
+__device__ __forceinline__ constexpr int brev_c(int k) {
+    int r = 0;
+    for (int b = 1, o = R >> 1; b < R; b <<= 1, o >>= 1)
+        if (k & b) r |= o;
+    return r;
+}
+
+// One Stockham pass of radix RP on a line: element n at base[pidx(n * stride + off)].
+// tpl threads (index j0 in [0, tpl)) each handle 16/RP butterfly groups.
+template <typename C, int RP, int SIGN>
+__device__ __forceinline__ void stockham_pass(C *base, int stride, int off, int L, int logL,
+                                              int Ns, int logNs, int j0, int tpl,
+                                              const C *__restrict__ tw) {
+    constexpr int G = 16 / RP;
+    C v[G][RP];
+    const int LR = L / RP;
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+        const int j = j0 + g * tpl;
+        const int k = j & (Ns - 1);
+        // twiddle of input r: exp(SIGN 2 pi i k r / (Ns RP)) = tw[k r L / (Ns RP)]
+        const int tstep = k << (logL - logNs) >> (RP == 16 ? 4 : (RP == 8 ? 3 : (RP == 4 ? 2 : 1)));
+#pragma unroll
+        for (int r = 0; r < RP; ++r) {
+            C x = base[pidx((j + r * LR) * stride + off)];
+            if (r > 0 && k != 0) {
+                C w = __ldg(&tw[(tstep * r) & (L - 1)]);
+                if (SIGN > 0) w.y = -w.y;
+                x = cmul(x, w);
+            }
+            v[g][r] = x;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+        const int j = j0 + g * tpl;
+        C (&vv)[RP] = v[g];
+        dft_regs<C, RP, SIGN>(vv);
+        const int k = j & (Ns - 1);
+        const int idxD = ((j >> logNs) << logNs) * RP + k;
+#pragma unroll
+        for (int r = 0; r < RP; ++r) base[pidx((idxD + r * Ns) * stride + off)] = vv[brev_c<RP>(r)];
+    }
+    __syncthreads();
+}
+
+// Full FFT of one line of length L = 2^logL (logL >= 4) held at base[pidx(n*stride + off)],
+// by tpl = L/16 threads with line-local index j0. The caller synchronises before the call;
+// the call ends synchronised. tw[m] = exp(-2 pi i m / L), m < L.
+template <typename C, int SIGN>
+__device__ __forceinline__ void line_fft(C *base, int stride, int off, int logL, int j0,
+                                         const C *__restrict__ tw) {
+    const int L = 1 << logL;
+    const int tpl = L >> 4;
+    int logNs = 0;
+    for (; logNs + 4 <= logL; logNs += 4)
+        stockham_pass<C, 16, SIGN>(base, stride, off, L, logL, 1 << logNs, logNs, j0, tpl, tw);
+    const int rem = logL - logNs;
+    if (rem == 3) stockham_pass<C, 8, SIGN>(base, stride, off, L, logL, 1 << logNs, logNs, j0, tpl, tw);
+    else if (rem == 2) stockham_pass<C, 4, SIGN>(base, stride, off, L, logL, 1 << logNs, logNs, j0, tpl, tw);
+    else if (rem == 1) stockham_pass<C, 2, SIGN>(base, stride, off, L, logL, 1 << logNs, logNs, j0, tpl, tw);
+}
+
+// Shared-memory elements needed for `lines` lines of length L (padded addressing).
+__host__ __device__ inline int fft_smem_elems(int L, int lines) { return pidx(L * lines - 1) + 1; }
 
 }  // namespace ivis

@@ -205,16 +205,16 @@ ivis_status upload_real(ivis_plan_s *p, void **dst, const std::vector<double> &s
 template <typename T>
 ivis_status upload_twiddles(ivis_plan_s *p) {
     typedef typename cplx_of<T>::type C;
-    int half = p->nf / 2;
-    std::vector<C> tw(half);
-    for (int j = 0; j < half; ++j) {
-        double a = 2.0 * M_PI * j / p->nf;
+    const int L = p->nf;
+    std::vector<C> tw(L);
+    for (int j = 0; j < L; ++j) {
+        double a = 2.0 * M_PI * j / L;
         tw[j].x = (T)std::cos(a);
         tw[j].y = (T)(-std::sin(a));
     }
-    ivis_status s = alloc(p, &p->tw_d, half * sizeof(C));
+    ivis_status s = alloc(p, &p->tw_d, L * sizeof(C));
     if (s) return s;
-    CK(cudaMemcpy(p->tw_d, tw.data(), half * sizeof(C), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(p->tw_d, tw.data(), L * sizeof(C), cudaMemcpyHostToDevice));
     return IVIS_OK;
 }
 
@@ -248,46 +248,48 @@ cudaError_t launch_grid_pass(ivis_plan_s *p, int first_chunk, int nchunk, double
     return cudaGetLastError();
 }
 
-int row_threads(int nf) { return std::min(512, std::max(32, nf / 2)); }
-
+// Row passes: 256 threads = lpb lines of nf/16 threads. Column passes: ncol x nf/16 threads.
 template <typename T>
 cudaError_t launch_forward(ivis_plan_s *p, const void *sky) {
     typedef typename cplx_of<T>::type C;
-    const int nb = p->cfg.nb, nf = p->nf;
-    dim3 gr(nb, p->nslot);
-    size_t smem_row = (size_t)nf * sizeof(C);
+    const int nb = p->cfg.nb, nf = p->nf, tpl = nf / 16, lpb = 256 / tpl;
+    dim3 gr((nb + lpb - 1) / lpb, p->nslot);
+    size_t smem_row = (size_t)fft_smem_elems(nf, lpb) * sizeof(C);
     cudaFuncSetAttribute(k_fwd_rows<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_row);
-    k_fwd_rows<T><<<gr, row_threads(nf), smem_row, p->stream>>>(
+    k_fwd_rows<T><<<gr, 256, smem_row, p->stream>>>(
         (const T *)sky, (const T *)p->beams_d, p->pinfo_d, (const T *)p->dinv_d, (C *)p->rowbuf,
         p->cfg.n, nb, p->lognf, (const C *)p->tw_d);
     dim3 gc(nf >> p->logc_cols, p->nslot);
-    size_t smem_col = ((size_t)nf << p->logc_cols) * sizeof(C);
+    size_t smem_col = (size_t)fft_smem_elems(nf, 1 << p->logc_cols) * sizeof(C);
     cudaFuncSetAttribute(k_fwd_cols<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_col);
-    k_fwd_cols<T><<<gc, 512, smem_col, p->stream>>>((const C *)p->rowbuf, (C *)p->F, nb, p->lognf,
-                                                    p->logc_cols, (const C *)p->tw_d);
+    k_fwd_cols<T><<<gc, tpl << p->logc_cols, smem_col, p->stream>>>(
+        (const C *)p->rowbuf, (C *)p->F, nb, p->lognf, p->logc_cols, (const C *)p->tw_d);
     return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_adjoint(ivis_plan_s *p) {
     typedef typename cplx_of<T>::type C;
-    const int nb = p->cfg.nb, nf = p->nf;
+    const int nb = p->cfg.nb, nf = p->nf, tpl = nf / 16, lpb = 256 / tpl;
     dim3 gc(nf >> p->logc_cols, p->nslot);
-    size_t smem_col = ((size_t)nf << p->logc_cols) * sizeof(C);
+    size_t smem_col = (size_t)fft_smem_elems(nf, 1 << p->logc_cols) * sizeof(C);
     cudaFuncSetAttribute(k_adj_cols<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_col);
-    k_adj_cols<T><<<gc, 512, smem_col, p->stream>>>((const C *)p->G, (C *)p->rowbuf, nb, p->lognf,
-                                                    p->logc_cols, (const C *)p->tw_d);
-    dim3 gr(nb, p->nslot);
-    size_t smem_row = (size_t)nf * sizeof(C);
+    k_adj_cols<T><<<gc, tpl << p->logc_cols, smem_col, p->stream>>>(
+        (const C *)p->G, (C *)p->rowbuf, nb, p->lognf, p->logc_cols, (const C *)p->tw_d);
+    dim3 gr((nb + lpb - 1) / lpb, p->nslot);
+    size_t smem_row = (size_t)fft_smem_elems(nf, lpb) * sizeof(C);
     cudaFuncSetAttribute(k_adj_rows<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_row);
-    k_adj_rows<T><<<gr, row_threads(nf), smem_row, p->stream>>>(
+    k_adj_rows<T><<<gr, 256, smem_row, p->stream>>>(
         (const C *)p->rowbuf, (const T *)p->beams_d, p->pinfo_d, (const T *)p->dinv_d,
         (T *)p->contrib, p->cfg.n, nb, p->lognf, (const C *)p->tw_d);
     return cudaGetLastError();
 }
 
 template <typename T>
-size_t conv_smem(int R) { return ((size_t)(CONV_TO + 2 * R) * 33 + 2 * R + 1) * sizeof(T); }
+size_t conv_smem(int R) {
+    const size_t strip = std::max((size_t)(CONV_TO + 2 * R) * 33, (size_t)(CONV_SPLIT - 1) * 8 * CONV_OPT * 32);
+    return (strip + 2 * R + 1) * sizeof(T);
+}
 
 template <typename T>
 cudaError_t launch_fusion(ivis_plan_s *p, cudaStream_t st, const void *sky, void *tsd_out_e,
@@ -299,16 +301,16 @@ cudaError_t launch_fusion(ivis_plan_s *p, cudaStream_t st, const void *sky, void
     cudaFuncSetAttribute(k_conv_axis<T, 1, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     dim3 gr((n + 31) / 32, (n + CONV_TO - 1) / CONV_TO, nchan);
     const T *taps = (const T *)p->taps_d;
-    k_conv_axis<T, 0, 0><<<gr, 256, sm, st>>>((const T *)sky, (T *)p->tmp1, taps, R, n, nullptr, nullptr, nullptr);
+    k_conv_axis<T, 0, 0><<<gr, 256 * CONV_SPLIT, sm, st>>>((const T *)sky, (T *)p->tmp1, taps, R, n, nullptr, nullptr, nullptr);
     if (!fused) {  // plain B (x) I into tsd_out_e
-        k_conv_axis<T, 1, 0><<<gr, 256, sm, st>>>((const T *)p->tmp1, (T *)tsd_out_e, taps, R, n, nullptr,
+        k_conv_axis<T, 1, 0><<<gr, 256 * CONV_SPLIT, sm, st>>>((const T *)p->tmp1, (T *)tsd_out_e, taps, R, n, nullptr,
                                                   nullptr, nullptr);
         return cudaGetLastError();
     }
-    k_conv_axis<T, 1, 1><<<gr, 256, sm, st>>>((const T *)p->tmp1, (T *)p->tmp2, taps, R, n,
+    k_conv_axis<T, 1, 1><<<gr, 256 * CONV_SPLIT, sm, st>>>((const T *)p->tmp1, (T *)p->tmp2, taps, R, n,
                                               (const T *)p->tsd_d, p->inv_sig2_d, p->kpart);
-    k_conv_axis<T, 0, 0><<<gr, 256, sm, st>>>((const T *)p->tmp2, (T *)p->tmp1, taps, R, n, nullptr, nullptr, nullptr);
-    k_conv_axis<T, 1, 0><<<gr, 256, sm, st>>>((const T *)p->tmp1, (T *)gradK_out, taps, R, n, nullptr,
+    k_conv_axis<T, 0, 0><<<gr, 256 * CONV_SPLIT, sm, st>>>((const T *)p->tmp2, (T *)p->tmp1, taps, R, n, nullptr, nullptr, nullptr);
+    k_conv_axis<T, 1, 0><<<gr, 256 * CONV_SPLIT, sm, st>>>((const T *)p->tmp1, (T *)gradK_out, taps, R, n, nullptr,
                                               nullptr, nullptr);
     return cudaGetLastError();
 }
@@ -448,43 +450,50 @@ ivis_status set_vis_impl(ivis_plan_s *p, PairHost &ph, int m, const float *uvw, 
                          const float *w) {
     typedef typename coord_of<T>::type CO;
     typedef typename cplx_of<T>::type C;
-    void *coord_tmp = nullptr, *key = nullptr, *cnt = nullptr, *err = nullptr;
+    const int nbins = p->nf * p->nf;  // one key per fine-grid cell (tile-major order)
+    const int nsb = (nbins + 1023) / 1024;
+    void *coord_tmp = nullptr, *key = nullptr, *cnt = nullptr, *cur = nullptr, *bsum = nullptr,
+         *tst = nullptr, *err = nullptr;
+    auto cleanup = [&]() { dfree(coord_tmp); dfree(key); dfree(cnt); dfree(cur); dfree(bsum); dfree(tst); dfree(err); };
     ivis_status s;
-    if ((s = alloc(p, &coord_tmp, (size_t)m * sizeof(CO)))) return s;
-    if ((s = alloc(p, &key, (size_t)m * sizeof(int)))) { dfree(coord_tmp); return s; }
-    if ((s = alloc(p, &cnt, (size_t)p->ntiles * sizeof(int)))) { dfree(coord_tmp); dfree(key); return s; }
-    if ((s = alloc(p, &err, sizeof(int)))) { dfree(coord_tmp); dfree(key); dfree(cnt); return s; }
-    auto cleanup = [&]() { dfree(coord_tmp); dfree(key); dfree(cnt); dfree(err); };
+    if ((s = alloc(p, &coord_tmp, (size_t)m * sizeof(CO))) || (s = alloc(p, &key, (size_t)m * sizeof(int))) ||
+        (s = alloc(p, &cnt, (size_t)nbins * sizeof(int))) || (s = alloc(p, &cur, (size_t)nbins * sizeof(int))) ||
+        (s = alloc(p, &bsum, (size_t)nsb * sizeof(int))) || (s = alloc(p, &tst, (size_t)(p->ntiles + 1) * sizeof(int))) ||
+        (s = alloc(p, &err, sizeof(int)))) {
+        cleanup();
+        return s;
+    }
     cudaMemsetAsync(err, 0, sizeof(int), p->stream);
-    cudaMemsetAsync(cnt, 0, (size_t)p->ntiles * sizeof(int), p->stream);
-    int nblk = (m + 255) / 256;
-    double scale = p->cfg.cell_rad * p->nf;
+    cudaMemsetAsync(cnt, 0, (size_t)nbins * sizeof(int), p->stream);
+    const int nblk = (m + 255) / 256;
+    const double scale = p->cfg.cell_rad * p->nf;
     k_vis_prepare<T><<<nblk, 256, 0, p->stream>>>(m, uvw, vis, w, scale, p->lognf, p->W, p->tile,
                                                    p->ntx, (CO *)coord_tmp, (int *)key, (int *)err);
     k_hist<<<nblk, 256, 0, p->stream>>>(m, (const int *)key, (int *)cnt);
+    k_scan_block<<<nsb, 256, 0, p->stream>>>(nbins, (const int *)cnt, (int *)cur, (int *)bsum);
+    k_scan_top<<<1, 1024, 0, p->stream>>>(nsb, (int *)bsum);
+    k_scan_add<<<nsb, 256, 0, p->stream>>>(nbins, (int *)cur, (const int *)bsum);
+    k_tile_starts<<<(p->ntiles + 256) / 256, 256, 0, p->stream>>>(p->ntiles, p->tile * p->tile, m,
+                                                                   (const int *)cur, (int *)tst);
     int herr = 0;
-    ph.tile_count.assign(p->ntiles, 0);
-    cudaError_t e = cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, p->stream);
+    std::vector<int> starts(p->ntiles + 1, 0);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, p->stream);
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(ph.tile_count.data(), cnt, (size_t)p->ntiles * sizeof(int),
-                            cudaMemcpyDeviceToHost, p->stream);
+        e = cudaMemcpyAsync(starts.data(), tst, (size_t)(p->ntiles + 1) * sizeof(int), cudaMemcpyDeviceToHost, p->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
     if (e != cudaSuccess) { cleanup(); return fail(p, IVIS_ERR_CUDA, std::string("set_vis: ") + cudaGetErrorString(e)); }
     if (herr) { cleanup(); return fail(p, IVIS_ERR_NONFINITE, "set_vis: non-finite uvw/vis/weight or negative weight"); }
-    std::vector<int> start(p->ntiles);
-    int acc = 0;
-    for (int t = 0; t < p->ntiles; ++t) { start[t] = acc; acc += ph.tile_count[t]; }
+    ph.tile_count.assign(p->ntiles, 0);
+    for (int t = 0; t < p->ntiles; ++t) ph.tile_count[t] = starts[t + 1] - starts[t];
     if ((s = alloc(p, &ph.coord, (size_t)m * sizeof(CO))) || (s = alloc(p, &ph.vis, (size_t)m * sizeof(C))) ||
         (s = alloc(p, &ph.w, (size_t)m * sizeof(T))) || (s = alloc(p, (void **)&ph.orig, (size_t)m * sizeof(int)))) {
         cleanup();
         return s;
     }
-    e = cudaMemcpyAsync(cnt, start.data(), (size_t)p->ntiles * sizeof(int), cudaMemcpyHostToDevice, p->stream);
-    if (e == cudaSuccess) {
-        k_vis_scatter<T><<<nblk, 256, 0, p->stream>>>(m, (const int *)key, (const CO *)coord_tmp, vis, w,
-                                                       (int *)cnt, (CO *)ph.coord, (C *)ph.vis, (T *)ph.w, ph.orig);
-        e = cudaGetLastError();
-    }
+    k_vis_scatter<T><<<nblk, 256, 0, p->stream>>>(m, (const int *)key, (const CO *)coord_tmp, vis, w,
+                                                   (int *)cur, (CO *)ph.coord, (C *)ph.vis, (T *)ph.w, ph.orig);
+    e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
     cleanup();
     if (e != cudaSuccess) return fail(p, IVIS_ERR_CUDA, std::string("set_vis scatter: ") + cudaGetErrorString(e));
@@ -796,12 +805,20 @@ ivis_status ivis_plan(const ivis_config *cfg, void *stream, ivis_plan_t *out) {
     p->ntx = p->nf / p->tile;
     p->ntiles = p->ntx * p->ntx;
     {
-        // columns per CTA in the column FFT passes: fill up to 96 KB of shared memory
+        // columns per CTA in the column FFT passes: as many as fit 100 KB of shared memory
+        // and 1024 threads; at least 4 (32-byte row segments) if 160 KB allows it
         size_t csz = p->fp64 ? 16 : 8;
+        const int tpl = p->nf / 16;
+        auto fits = [&](int l, size_t budget) {
+            return (size_t)fft_smem_elems(p->nf, 1 << l) * csz <= budget &&
+                   (tpl << l) <= (p->fp64 ? 512 : 1024) &&
+                   (1 << l) <= p->nf;
+        };
         int logc = 0;
-        while (logc < 4 && ((size_t)p->nf << (logc + 1)) * csz <= 96 * 1024) ++logc;
+        while (logc < 4 && fits(logc + 1, 100 * 1024)) ++logc;
+        while (logc < 2 && fits(logc + 1, 160 * 1024)) ++logc;
+        if (!fits(logc, 200 * 1024)) { delete p; return fail(nullptr, IVIS_ERR_ARG, "grid too large"); }
         p->logc_cols = logc;
-        if (((size_t)p->nf << logc) * csz > 200 * 1024) { delete p; return fail(nullptr, IVIS_ERR_ARG, "grid too large"); }
     }
     p->cx.assign(c.npoint, 0);
     p->cy.assign(c.npoint, 0);

@@ -54,7 +54,7 @@ k_assemble(const T *__restrict__ sky, const T *__restrict__ contrib,
             if (x > 0) gr -= lap(I, n, y, x - 1);
             if (x < n - 1) gr -= lap(I, n, y, x + 1);
             g += lr * gr;
-            rloc = 0.5 * (double)d0 * (double)d0;
+            rloc = (double)((T)0.5 * d0 * d0);
         }
         if (use_k) g += ls * gradK[idx];
         grad[idx] = g;
@@ -64,27 +64,32 @@ k_assemble(const T *__restrict__ sky, const T *__restrict__ contrib,
 }
 
 // Separable dish-beam convolution, one axis per launch: out = sum_{t=-R..R} b_c[t] in(. - t),
-// zero outside the image. A CTA of 8 warps covers 32 lines (one per lane) x CONV_TO outputs
-// along the convolution axis; each thread produces CONV_OPT consecutive outputs from a
-// sliding window of registers, so each shared-memory load feeds CONV_OPT FMAs. The staged
-// strip is laid out [position][line] with a 33-word row pitch (rows pass: lines are image
-// rows and the transpose would otherwise serialise on one bank).
+// zero outside the image. A CTA covers 32 lines (one per lane) x CONV_TO outputs along the
+// convolution axis. Warp w produces CONV_OPT consecutive outputs (w % 8) over one of
+// CONV_SPLIT segments of the taps (w / 8) from a sliding window of registers, so each
+// shared-memory load feeds CONV_OPT FMAs; the segments are summed through shared memory in a
+// fixed order. The staged strip is laid out [position][line] with a 33-word pitch (rows
+// pass: lines are image rows and the transpose would otherwise serialise on one bank).
 constexpr int CONV_OPT = 8;
 constexpr int CONV_TO = 8 * CONV_OPT;  // outputs per CTA along the axis
+constexpr int CONV_SPLIT = 4;          // tap segments (CTA = 256 * CONV_SPLIT threads)
 
 // AXIS 0: along x (lines = rows); AXIS 1: along y (lines = columns).
 // FUSED (AXIS 1 only): out = e = (t - T)/sigma^2 and the CTA's share of K goes to kpart.
 template <typename T, int AXIS, int FUSED>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256 * CONV_SPLIT)
 k_conv_axis(const T *__restrict__ in, T *out, const T *__restrict__ taps, int R, int n,
             const T *__restrict__ tsd, const double *__restrict__ inv_sig2, double *kpart) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double red[32];
     const int P = 33;
     const int L = CONV_TO + 2 * R;  // staged positions
+    constexpr int NPART = (CONV_SPLIT - 1) * 8 * CONV_OPT * 32;
     T *sh = reinterpret_cast<T *>(smem_raw);
-    T *tp = sh + (size_t)L * P;
+    T *tp = sh + max(L * P, NPART);
+    T *part = sh;  // [CONV_SPLIT - 1][8 warps][CONV_OPT][32], reuses the strip after the taps loop
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int wo = wid & 7, seg = wid >> 3;
     const int line0 = blockIdx.x * 32, pos0 = blockIdx.y * CONV_TO, c = blockIdx.z;
     const T *img = in + (size_t)c * n * n;
     const T *b = taps + (size_t)c * (2 * R + 1);
@@ -105,41 +110,54 @@ k_conv_axis(const T *__restrict__ in, T *out, const T *__restrict__ taps, int R,
     }
     __syncthreads();
     // outputs j = 0..OPT-1 at axis position o0 + j use staged position o0 + j + 2R - t
-    const int o0 = wid * CONV_OPT;
+    const int o0 = wo * CONV_OPT;
+    const int ntap = 2 * R + 1;
+    const int tb = seg * ntap / CONV_SPLIT, te = (seg + 1) * ntap / CONV_SPLIT;
     T acc[CONV_OPT], win[CONV_OPT];
 #pragma unroll
     for (int j = 0; j < CONV_OPT; ++j) {
         acc[j] = (T)0;
-        win[j] = sh[(o0 + j + 2 * R) * P + lane];
+        win[j] = sh[(o0 + j + 2 * R - tb) * P + lane];
     }
-    for (int t = 0; t <= 2 * R; ++t) {
+#pragma unroll 4
+    for (int t = tb; t < te; ++t) {
         const T bt = tp[t];
 #pragma unroll
         for (int j = 0; j < CONV_OPT; ++j) acc[j] += bt * win[j];
-        if (t < 2 * R) {
 #pragma unroll
-            for (int j = CONV_OPT - 1; j > 0; --j) win[j] = win[j - 1];
-            win[0] = sh[(o0 + 2 * R - t - 1) * P + lane];
-        }
+        for (int j = CONV_OPT - 1; j > 0; --j) win[j] = win[j - 1];
+        win[0] = sh[max(o0 + 2 * R - t - 1, 0) * P + lane];
     }
-    double kloc = 0.0;
-    const double is2 = FUSED ? inv_sig2[c] : 0.0;
-    const int line = line0 + lane;
+    __syncthreads();  // every warp is done reading the strip
+    if (seg > 0) {
 #pragma unroll
-    for (int j = 0; j < CONV_OPT; ++j) {
-        const int pos = pos0 + o0 + j;
-        if (line >= n || pos >= n) continue;
-        const size_t o = AXIS == 0 ? ((size_t)c * n + line) * n + pos : ((size_t)c * n + pos) * n + line;
-        if (FUSED) {
-            const double e = (double)acc[j] - (double)tsd[o];
-            kloc += 0.5 * e * e * is2;
-            out[o] = (T)(e * is2);
-        } else {
-            out[o] = acc[j];
+        for (int j = 0; j < CONV_OPT; ++j) part[(((seg - 1) * 8 + wo) * CONV_OPT + j) * 32 + lane] = acc[j];
+    }
+    __syncthreads();
+    T kloc = (T)0;  // <= CONV_OPT terms per thread in the working precision, then FP64
+    if (seg == 0) {
+#pragma unroll
+        for (int q = 1; q < CONV_SPLIT; ++q)
+#pragma unroll
+            for (int j = 0; j < CONV_OPT; ++j) acc[j] += part[(((q - 1) * 8 + wo) * CONV_OPT + j) * 32 + lane];
+        const T is2 = FUSED ? (T)inv_sig2[c] : (T)0;
+        const int line = line0 + lane;
+#pragma unroll
+        for (int j = 0; j < CONV_OPT; ++j) {
+            const int pos = pos0 + o0 + j;
+            if (line >= n || pos >= n) continue;
+            const size_t o = AXIS == 0 ? ((size_t)c * n + line) * n + pos : ((size_t)c * n + pos) * n + line;
+            if (FUSED) {
+                const T e = acc[j] - tsd[o];
+                kloc += (T)0.5 * e * e * is2;
+                out[o] = e * is2;
+            } else {
+                out[o] = acc[j];
+            }
         }
     }
     if (FUSED) {
-        const double sum = block_sum(kloc, red);
+        const double sum = block_sum((double)kloc, red);
         if (threadIdx.x == 0)
             kpart[((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = sum;
     }

@@ -88,7 +88,9 @@ __global__ void k_vis_prepare(int m, const float *__restrict__ uvw, const float 
     } else {
         coord_tmp[i] = make_double2(sc[0], sc[1]);
     }
-    key[i] = (g0[1] / tile) * ntx + (g0[0] / tile);
+    // tile-major, then the first-tap cell within the tile (row-major): visibilities that share
+    // a base cell end up adjacent, which the grid pass exploits
+    key[i] = ((g0[1] / tile) * ntx + (g0[0] / tile)) * tile * tile + (g0[1] % tile) * tile + (g0[0] % tile);
 }
 
 __global__ void k_hist(int m, const int *__restrict__ key, int *count) {
@@ -96,7 +98,75 @@ __global__ void k_hist(int m, const int *__restrict__ key, int *count) {
     if (i < m) atomicAdd(&count[key[i]], 1);
 }
 
-// Scatter into tile order. cursor[t] starts at the tile's first slot.
+// Exclusive prefix sum of n ints (set-up only): per-1024 block scans, a scan of the block
+// totals, then the block offsets added back.
+__global__ void k_scan_block(int n, const int *__restrict__ in, int *out, int *bsum) {
+    __shared__ int wsum[8];
+    const int base = blockIdx.x * 1024 + threadIdx.x * 4;
+    int v[4], t = 0;
+    for (int k = 0; k < 4; ++k) {
+        v[k] = base + k < n ? in[base + k] : 0;
+        t += v[k];
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int incl = t;
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) wsum[wid] = incl;
+    __syncthreads();
+    int woff = 0;
+    for (int w = 0; w < wid; ++w) woff += wsum[w];
+    int run = woff + incl - t;
+    for (int k = 0; k < 4; ++k) {
+        if (base + k < n) out[base + k] = run;
+        run += v[k];
+    }
+    if (threadIdx.x == 255) bsum[blockIdx.x] = woff + incl;
+}
+
+// In-place exclusive scan of nb block totals by one CTA of 1024 threads.
+__global__ void k_scan_top(int nb, int *bsum) {
+    __shared__ int tmp[1024];
+    __shared__ int carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int b0 = 0; b0 < nb; b0 += 1024) {
+        const int i = b0 + threadIdx.x;
+        const int v = i < nb ? bsum[i] : 0;
+        tmp[threadIdx.x] = v;
+        __syncthreads();
+        for (int o = 1; o < 1024; o <<= 1) {
+            int y = threadIdx.x >= o ? tmp[threadIdx.x - o] : 0;
+            __syncthreads();
+            tmp[threadIdx.x] += y;
+            __syncthreads();
+        }
+        const int excl = tmp[threadIdx.x] - v + carry;
+        __syncthreads();
+        if (i < nb) bsum[i] = excl;
+        if (threadIdx.x == 1023) carry += tmp[1023];
+        __syncthreads();
+    }
+}
+
+__global__ void k_scan_add(int n, int *out, const int *__restrict__ bsum) {
+    const int i = blockIdx.x * 1024 + threadIdx.x * 4;
+    const int off = bsum[blockIdx.x];
+    for (int k = 0; k < 4; ++k)
+        if (i + k < n) out[i + k] += off;
+}
+
+// start[t] = first sorted slot of tile t (t <= ntiles; start[ntiles] = m).
+__global__ void k_tile_starts(int ntiles, int per_tile, int m, const int *__restrict__ cell_start,
+                              int *start) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < ntiles) start[t] = cell_start[(size_t)t * per_tile];
+    if (t == ntiles) start[t] = m;
+}
+
+// Scatter into key order. cursor[key] starts at the key's first slot.
 template <typename T>
 __global__ void k_vis_scatter(int m, const int *__restrict__ key,
                               const typename coord_of<T>::type *__restrict__ coord_tmp,
@@ -113,64 +183,70 @@ __global__ void k_vis_scatter(int m, const int *__restrict__ key,
 }
 
 // ------------------------------------------------------------------ forward row pass (a1)
+// CTA = lpb window rows of one pair (tpl = nf/16 threads per row). blockIdx.x = row block.
 template <typename T>
-__global__ void k_fwd_rows(const T *__restrict__ sky, const T *__restrict__ beams,
-                           const PairInfo *__restrict__ pinfo, const T *__restrict__ dinv,
-                           typename cplx_of<T>::type *rowbuf, int n, int nb, int lognf,
-                           const typename cplx_of<T>::type *__restrict__ tw) {
+__global__ void __launch_bounds__(256)
+k_fwd_rows(const T *__restrict__ sky, const T *__restrict__ beams,
+           const PairInfo *__restrict__ pinfo, const T *__restrict__ dinv,
+           typename cplx_of<T>::type *rowbuf, int n, int nb, int lognf,
+           const typename cplx_of<T>::type *__restrict__ tw) {
     typedef typename cplx_of<T>::type C;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C *s = reinterpret_cast<C *>(smem_raw);
-    const int q = blockIdx.x, slot = blockIdx.y, nf = 1 << lognf;
+    const int nf = 1 << lognf, tpl = nf >> 4, lpb = blockDim.x / tpl;
+    const int slot = blockIdx.y;
     const PairInfo pi = pinfo[slot];
-    C *out = rowbuf + ((size_t)slot * nb + q) * nf;
+    const int l = threadIdx.x / tpl, j0 = threadIdx.x - l * tpl;
+    const int q = blockIdx.x * lpb + l;
     const int y = pi.cy - nb / 2 + q;
-    if (y < 0 || y >= n) {
-        for (int i = threadIdx.x; i < nf; i += blockDim.x) out[i] = mk((T)0, (T)0);
-        return;
-    }
-    for (int i = threadIdx.x; i < nf; i += blockDim.x) s[i] = mk((T)0, (T)0);
+    const bool on = q < nb && y >= 0 && y < n;
+    C *line = s;  // element e of line l at s[pidx(l * nf + e)]
+    for (int e = j0; e < nf; e += tpl) line[pidx(l * nf + e)] = mk((T)0, (T)0);
     __syncthreads();
-    const T *srow = sky + ((size_t)pi.chan * n + y) * n;
-    const T *brow = beams + ((size_t)pi.k * nb + q) * nb;
-    const T dq = dinv[q];
-    const int x0 = pi.cx - nb / 2;
-    for (int p = threadIdx.x; p < nb; p += blockDim.x) {
-        const int x = x0 + p;
-        T val = (x >= 0 && x < n) ? srow[x] * brow[p] * dinv[p] * dq : (T)0;
-        const int idx = (p - nb / 2) & (nf - 1);
-        s[bitrev(idx, lognf)] = mk(val, (T)0);
+    if (on) {
+        const T *srow = sky + ((size_t)pi.chan * n + y) * n;
+        const T *brow = beams + ((size_t)pi.k * nb + q) * nb;
+        const T dq = dinv[q];
+        const int x0 = pi.cx - nb / 2;
+        for (int p = j0; p < nb; p += tpl) {
+            const int x = x0 + p;
+            const T val = (x >= 0 && x < n) ? srow[x] * brow[p] * dinv[p] * dq : (T)0;
+            line[pidx(l * nf + ((p - nb / 2) & (nf - 1)))] = mk(val, (T)0);
+        }
     }
     __syncthreads();
-    fft_dit_smem<C, -1>(s, lognf, 0, tw);
-    for (int i = threadIdx.x; i < nf; i += blockDim.x) out[i] = s[i];
+    line_fft<C, -1>(s, 1, l * nf, lognf, j0, tw);
+    if (q < nb) {
+        C *out = rowbuf + ((size_t)slot * nb + q) * nf;
+        for (int e = j0; e < nf; e += tpl) out[e] = on ? line[pidx(l * nf + e)] : mk((T)0, (T)0);
+    }
 }
 
 // ---------------------------------------------------------------- forward column pass (a2)
+// CTA = ncol adjacent columns of one pair; thread t -> column t % ncol, line index t / ncol.
 template <typename T>
-__global__ void k_fwd_cols(const typename cplx_of<T>::type *__restrict__ rowbuf,
-                           typename cplx_of<T>::type *F, int nb, int lognf, int logc,
-                           const typename cplx_of<T>::type *__restrict__ tw) {
+__global__ void __launch_bounds__(sizeof(T) == 8 ? 512 : 1024)
+k_fwd_cols(const typename cplx_of<T>::type *__restrict__ rowbuf,
+           typename cplx_of<T>::type *F, int nb, int lognf, int logc,
+           const typename cplx_of<T>::type *__restrict__ tw) {
     typedef typename cplx_of<T>::type C;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C *s = reinterpret_cast<C *>(smem_raw);
     const int nf = 1 << lognf, ncol = 1 << logc;
     const int c0 = blockIdx.x << logc, slot = blockIdx.y;
-    for (int i = threadIdx.x; i < (nf << logc); i += blockDim.x) s[i] = mk((T)0, (T)0);
+    const int c = threadIdx.x & (ncol - 1), j0 = threadIdx.x >> logc;
+    const int tpl = nf >> 4;
+    for (int e = j0; e < nf; e += tpl) s[pidx((e << logc) + c)] = mk((T)0, (T)0);
     __syncthreads();
     const C *src = rowbuf + (size_t)slot * nb * nf;
-    for (int i = threadIdx.x; i < (nb << logc); i += blockDim.x) {
-        const int q = i >> logc, c = i & (ncol - 1);
+    for (int q = j0; q < nb; q += tpl) {
         const int idx = (q - nb / 2) & (nf - 1);
-        s[(bitrev(idx, lognf) << logc) + c] = src[(size_t)q * nf + c0 + c];
+        s[pidx((idx << logc) + c)] = src[(size_t)q * nf + c0 + c];
     }
     __syncthreads();
-    fft_dit_smem<C, -1>(s, lognf, logc, tw);
+    line_fft<C, -1>(s, ncol, c, lognf, j0, tw);
     C *dst = F + (size_t)slot * nf * nf;
-    for (int i = threadIdx.x; i < (nf << logc); i += blockDim.x) {
-        const int g = i >> logc, c = i & (ncol - 1);
-        dst[(size_t)g * nf + c0 + c] = s[i];
-    }
+    for (int e = j0; e < nf; e += tpl) dst[(size_t)e * nf + c0 + c] = s[pidx((e << logc) + c)];
 }
 
 // --------------------------------------------- interpolation / residual / spreading (a3, a4)
@@ -209,9 +285,11 @@ __device__ __forceinline__ void red_add_c(double2 *p, double2 v) {
 // patch (tile + W - 1 cells square, wrapped) is staged in shared memory. A group of GS lanes
 // (GS = W rounded up to a power of two) handles one visibility at a time: lane r owns kernel
 // row r. Each lane evaluates one x and one y kernel value, the x values are exchanged by
-// shuffles, the row sums of the interpolation are reduced across the group, and every lane
-// spreads w r into its own kernel row. The same 2W kernel values serve interpolation and
-// spreading. MODE_PREDICT writes V~ to pred[orig] instead of spreading.
+// shuffles, the row sums of the interpolation are reduced across the group, and the same 2W
+// kernel values serve the spreading. Each group walks a contiguous run of the chunk, whose
+// visibilities are sorted by first-tap cell: while the cell repeats, a lane keeps its row of
+// the spread in registers and only adds it to the shared sub-grid (atomics) when the cell
+// changes. MODE_PREDICT writes V~ to pred[orig] instead of spreading.
 template <typename T, int W, int MODE>
 __global__ void __launch_bounds__(256)
 k_grid_pass(const Chunk *__restrict__ chunks, const PairData<T> *__restrict__ pdata,
@@ -240,21 +318,38 @@ k_grid_pass(const Chunk *__restrict__ chunks, const PairData<T> *__restrict__ pd
     }
     __syncthreads();
     const T zs = (T)2 / (T)W;
-    const int r = threadIdx.x & (GS - 1);       // kernel row of this lane
+    const int r = threadIdx.x & (GS - 1);  // kernel row of this lane
     const bool active_row = r < W;
-    double jacc = 0.0;
-    constexpr int GPW = 32 / GS;                 // groups per warp
-    const int warp = threadIdx.x >> 5;
-    const int gw = (threadIdx.x & 31) / GS;      // group index within the warp
-    // The loop bound depends on the warp only (vb), so every lane of a warp runs the same
-    // number of iterations and the full-warp shuffles below always see all 32 lanes.
-    for (int vb = ch.begin + warp * GPW; vb < ch.end; vb += NG) {
-        const int v = vb + gw;
-        const bool valid = v < ch.end;
+    const int len = (ch.end - ch.begin + NG - 1) / NG;  // same for every group of the CTA
+    const int vbeg = ch.begin + (threadIdx.x / GS) * len;
+    const int vend = min(ch.end, vbeg + len);
+    T jacc = (T)0;
+    C racc[W];
+#pragma unroll
+    for (int a = 0; a < W; ++a) racc[a] = mk((T)0, (T)0);
+    int clx = -1, cly = 0;  // cell of the run held in racc
+    // Every lane of a warp runs exactly len iterations, so the full-warp shuffles below always
+    // see all 32 lanes.
+    for (int i = 0; i < len; ++i) {
+        const int v = vbeg + i;
+        const bool valid = v < vend;
         int gx = x0, gy = y0;
         T dx = (T)(0.5 * W), dy = (T)(0.5 * W);
         if (valid) decode<W>(pd.coord[v], nf, gx, gy, dx, dy);
         const int lx = gx - x0, ly = gy - y0;
+        if (MODE == MODE_COSTGRAD && valid && (lx != clx || ly != cly)) {
+            if (clx >= 0 && active_row) {
+                C *gr = Gs + (cly + r) * PW + clx;
+#pragma unroll
+                for (int a = 0; a < W; ++a) {
+                    atomicAdd(&gr[a].x, racc[a].x);
+                    atomicAdd(&gr[a].y, racc[a].y);
+                    racc[a] = mk((T)0, (T)0);
+                }
+            }
+            clx = lx;
+            cly = ly;
+        }
         const bool row_on = valid && active_row;
         const T kxr = row_on ? es_kernel((dx - (T)r) * zs, beta) : (T)0;
         const T kyr = row_on ? es_kernel((dy - (T)r) * zs, beta) : (T)0;
@@ -285,19 +380,28 @@ k_grid_pass(const Chunk *__restrict__ chunks, const PairData<T> *__restrict__ pd
         const C vv = pd.vis[v];
         const T w = pd.w[v];
         const C res = mk(acc.x - vv.x, acc.y - vv.y);
-        if (r == 0) jacc += 0.5 * (double)w * ((double)res.x * (double)res.x + (double)res.y * (double)res.y);
+        // per-visibility term in the working precision; a lane sums at most len (<= 32) terms
+        // before the FP64 block and global reductions (FP64 issue is scarce on this part)
+        if (r == 0) jacc += (T)0.5 * w * (res.x * res.x + res.y * res.y);
         if (active_row) {
             const T cyx = kyr * w * res.x, cyy = kyr * w * res.y;
-            C *gr = Gs + (ly + r) * PW + lx;
 #pragma unroll
             for (int a = 0; a < W; ++a) {
-                atomicAdd(&gr[a].x, cyx * kx[a]);
-                atomicAdd(&gr[a].y, cyy * kx[a]);
+                racc[a].x += cyx * kx[a];
+                racc[a].y += cyy * kx[a];
             }
         }
     }
     if (MODE == MODE_PREDICT) return;
-    const double js = block_sum(jacc, red);
+    if (clx >= 0 && active_row) {
+        C *gr = Gs + (cly + r) * PW + clx;
+#pragma unroll
+        for (int a = 0; a < W; ++a) {
+            atomicAdd(&gr[a].x, racc[a].x);
+            atomicAdd(&gr[a].y, racc[a].y);
+        }
+    }
+    const double js = block_sum((double)jacc, red);
     if (threadIdx.x == 0) jpart[blockIdx.x] = js;
     __syncthreads();
     C *Gp = G + (size_t)ch.slot * nf * nf;
@@ -312,52 +416,58 @@ k_grid_pass(const Chunk *__restrict__ chunks, const PairData<T> *__restrict__ pd
 
 // ---------------------------------------------------------------- adjoint column pass (a5)
 template <typename T>
-__global__ void k_adj_cols(const typename cplx_of<T>::type *__restrict__ G,
-                           typename cplx_of<T>::type *rowbuf, int nb, int lognf, int logc,
-                           const typename cplx_of<T>::type *__restrict__ tw) {
+__global__ void __launch_bounds__(sizeof(T) == 8 ? 512 : 1024)
+k_adj_cols(const typename cplx_of<T>::type *__restrict__ G,
+           typename cplx_of<T>::type *rowbuf, int nb, int lognf, int logc,
+           const typename cplx_of<T>::type *__restrict__ tw) {
     typedef typename cplx_of<T>::type C;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C *s = reinterpret_cast<C *>(smem_raw);
     const int nf = 1 << lognf, ncol = 1 << logc;
     const int c0 = blockIdx.x << logc, slot = blockIdx.y;
+    const int c = threadIdx.x & (ncol - 1), j0 = threadIdx.x >> logc;
+    const int tpl = nf >> 4;
     const C *src = G + (size_t)slot * nf * nf;
-    for (int i = threadIdx.x; i < (nf << logc); i += blockDim.x) {
-        const int g = i >> logc, c = i & (ncol - 1);
-        s[(bitrev(g, lognf) << logc) + c] = src[(size_t)g * nf + c0 + c];
-    }
+    for (int e = j0; e < nf; e += tpl) s[pidx((e << logc) + c)] = src[(size_t)e * nf + c0 + c];
     __syncthreads();
-    fft_dit_smem<C, +1>(s, lognf, logc, tw);
+    line_fft<C, +1>(s, ncol, c, lognf, j0, tw);
     C *dst = rowbuf + (size_t)slot * nb * nf;
-    for (int i = threadIdx.x; i < (nb << logc); i += blockDim.x) {
-        const int q = i >> logc, c = i & (ncol - 1);
+    for (int q = j0; q < nb; q += tpl) {
         const int idx = (q - nb / 2) & (nf - 1);
-        dst[(size_t)q * nf + c0 + c] = s[(idx << logc) + c];
+        dst[(size_t)q * nf + c0 + c] = s[pidx((idx << logc) + c)];
     }
 }
 
 // ------------------------------------------- adjoint row pass + deapod + Re + beam (a5, a6)
 template <typename T>
-__global__ void k_adj_rows(const typename cplx_of<T>::type *__restrict__ rowbuf,
-                           const T *__restrict__ beams, const PairInfo *__restrict__ pinfo,
-                           const T *__restrict__ dinv, T *contrib, int n, int nb, int lognf,
-                           const typename cplx_of<T>::type *__restrict__ tw) {
+__global__ void __launch_bounds__(256)
+k_adj_rows(const typename cplx_of<T>::type *__restrict__ rowbuf,
+           const T *__restrict__ beams, const PairInfo *__restrict__ pinfo,
+           const T *__restrict__ dinv, T *contrib, int n, int nb, int lognf,
+           const typename cplx_of<T>::type *__restrict__ tw) {
     typedef typename cplx_of<T>::type C;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C *s = reinterpret_cast<C *>(smem_raw);
-    const int q = blockIdx.x, slot = blockIdx.y, nf = 1 << lognf;
+    const int nf = 1 << lognf, tpl = nf >> 4, lpb = blockDim.x / tpl;
+    const int slot = blockIdx.y;
     const PairInfo pi = pinfo[slot];
+    const int l = threadIdx.x / tpl, j0 = threadIdx.x - l * tpl;
+    const int q = blockIdx.x * lpb + l;
     const int y = pi.cy - nb / 2 + q;
-    if (y < 0 || y >= n) return;  // never gathered: off the sky
-    const C *src = rowbuf + ((size_t)slot * nb + q) * nf;
-    for (int i = threadIdx.x; i < nf; i += blockDim.x) s[bitrev(i, lognf)] = src[i];
+    const bool on = q < nb && y >= 0 && y < n;  // rows off the sky are never gathered
+    if (on) {
+        const C *src = rowbuf + ((size_t)slot * nb + q) * nf;
+        for (int e = j0; e < nf; e += tpl) s[pidx(l * nf + e)] = src[e];
+    }
     __syncthreads();
-    fft_dit_smem<C, +1>(s, lognf, 0, tw);
+    line_fft<C, +1>(s, 1, l * nf, lognf, j0, tw);
+    if (!on) return;
     const T *brow = beams + ((size_t)pi.k * nb + q) * nb;
     const T dq = dinv[q];
     T *out = contrib + ((size_t)slot * nb + q) * nb;
-    for (int p = threadIdx.x; p < nb; p += blockDim.x) {
+    for (int p = j0; p < nb; p += tpl) {
         const int idx = (p - nb / 2) & (nf - 1);
-        out[p] = s[idx].x * dinv[p] * dq * brow[p];
+        out[p] = s[pidx(l * nf + idx)].x * dinv[p] * dq * brow[p];
     }
 }
 

@@ -165,6 +165,29 @@ def test_edge_cases(precision):
     plan.close()
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_dense_single_tile_many_chunks(precision):
+    """nb = 16 gives a 32^2 fine grid, i.e. a single 32-cell tile: ~3000 visibilities per pair
+    split into several chunks, with many visibilities sharing a first-tap cell (the spread's
+    run merging) and a ragged last chunk."""
+    prob = synth.small_mosaic(304, n=24, nb=16, nchan=1, npoint=2, ndump=4, n_ant=40,
+                              cell_arcsec=30.0, lambda_r=0.0, lambda_s=0.0)
+    attach_data(prob)
+    assert max(p.m for p in prob.pairs) > 2048
+    x = prob.sky_true * 0.6
+    f, g = oracle.cost_grad(prob, x)
+    plan = _plan(prob, precision)
+    dt = torch.float64 if precision == "fp64" else torch.float32
+    fg, grad, _ = plan.cost_grad(torch.as_tensor(x, dtype=dt, device="cuda"))
+    tol = TOL[precision]
+    assert abs(fg - f) <= tol * abs(f)
+    assert rel_l2(grad.cpu().numpy(), g) <= tol
+    for pair in prob.pairs:
+        got = plan.predict(torch.as_tensor(x, dtype=dt, device="cuda"), pair.k, pair.chan).cpu().numpy()
+        assert rel_l2(got[:, 0] + 1j * got[:, 1], oracle.pair_model_vis(prob, x, pair)) <= tol
+    plan.close()
+
+
 def test_invalid_inputs_are_rejected():
     from paper_2609_17636_b300 import IvisError, Plan
     plan = Plan(32, 1, 1, 16, 1e-4, "fp32")

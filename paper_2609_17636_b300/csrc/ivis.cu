@@ -57,6 +57,7 @@ struct ivis_plan_s {
     int logc_cols = 0;  // log2 columns per CTA in the column FFT passes
     std::vector<double> dinv_h;
     void *dinv_d = nullptr, *tw_d = nullptr, *beams_d = nullptr;
+    float *kpoly_d = nullptr;  // per-tap kernel polynomials (FP32 path)
     std::vector<int> cx, cy;
     std::vector<char> pset;
     std::vector<PairHost> pairs;  // index chan * npoint + k
@@ -193,6 +194,45 @@ void es_deapod(int nb, int nf, int W, double beta, std::vector<double> &dinv) {
     }
 }
 
+// Per-tap polynomial of the ES kernel for the FP32 gridding kernels: for tap t and first-tap
+// fraction f in [0, 1) the kernel argument is z = (f + W/2 - 1 - t) / (W/2); the value is
+// interpolated at deg + 1 Chebyshev nodes in x = 2f - 1 and stored as monomial coefficients
+// c[t][0..deg] (row stride ES_MAXDEG + 1) for Horner evaluation.
+void es_fit(int W, double beta, int deg, std::vector<double> &c) {
+    const int n = deg + 1;
+    c.assign((size_t)W * (ES_MAXDEG + 1), 0.0);
+    for (int t = 0; t < W; ++t) {
+        std::vector<double> A((size_t)n * n), y(n);
+        for (int k = 0; k < n; ++k) {
+            const double x = std::cos(M_PI * (k + 0.5) / n);
+            const double z = ((x + 1.0) * 0.5 + 0.5 * W - 1.0 - t) / (0.5 * W);
+            const double a = 1.0 - z * z;
+            y[k] = a >= 0.0 ? std::exp(beta * (std::sqrt(a) - 1.0)) : 0.0;
+            double xp = 1.0;
+            for (int i = 0; i < n; ++i) { A[(size_t)k * n + i] = xp; xp *= x; }
+        }
+        for (int col = 0; col < n; ++col) {  // Gaussian elimination, partial pivoting
+            int piv = col;
+            for (int r = col + 1; r < n; ++r)
+                if (std::fabs(A[(size_t)r * n + col]) > std::fabs(A[(size_t)piv * n + col])) piv = r;
+            if (piv != col) {
+                for (int i = 0; i < n; ++i) std::swap(A[(size_t)col * n + i], A[(size_t)piv * n + i]);
+                std::swap(y[col], y[piv]);
+            }
+            for (int r = col + 1; r < n; ++r) {
+                const double f = A[(size_t)r * n + col] / A[(size_t)col * n + col];
+                for (int i = col; i < n; ++i) A[(size_t)r * n + i] -= f * A[(size_t)col * n + i];
+                y[r] -= f * y[col];
+            }
+        }
+        for (int i = n - 1; i >= 0; --i) {
+            double acc = y[i];
+            for (int j = i + 1; j < n; ++j) acc -= A[(size_t)i * n + j] * c[(size_t)t * (ES_MAXDEG + 1) + j];
+            c[(size_t)t * (ES_MAXDEG + 1) + i] = acc / A[(size_t)i * n + i];
+        }
+    }
+}
+
 template <typename T>
 ivis_status upload_real(ivis_plan_s *p, void **dst, const std::vector<double> &src) {
     std::vector<T> tmp(src.begin(), src.end());
@@ -235,7 +275,7 @@ cudaError_t launch_grid_pass(ivis_plan_s *p, int first_chunk, int nchunk, double
     case WW: {                                                                                \
         auto kern = k_grid_pass<T, WW, MODE>;                                                 \
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);   \
-        kern<<<nchunk, 256, smem, p->stream>>>(ch, pd, F, G, p->lognf, p->tile, p->ntx, beta, \
+        kern<<<nchunk, 256, smem, p->stream>>>(ch, pd, F, G, p->lognf, p->ntx, beta, p->kpoly_d, \
                                                jpart, (C *)pred);                             \
         break;                                                                                \
     }
@@ -801,7 +841,7 @@ ivis_status ivis_plan(const ivis_config *cfg, void *stream, ivis_plan_t *out) {
     if (c.kernel_width) p->W = c.kernel_width;
     else p->W = std::min(16, std::max(2, (int)std::ceil(-std::log10(c.nufft_tol)) + 1));
     p->beta = 2.30 * p->W;
-    p->tile = std::min(32, p->nf);
+    p->tile = GTILE;  // nf >= 32 always (nb >= 16)
     p->ntx = p->nf / p->tile;
     p->ntiles = p->ntx * p->ntx;
     {
@@ -840,6 +880,14 @@ ivis_status ivis_plan(const ivis_config *cfg, void *stream, ivis_plan_t *out) {
     } else {
         s = upload_real<float>(p, &p->dinv_d, p->dinv_h);
         if (!s) s = upload_twiddles<float>(p);
+    }
+    if (!s) {
+        std::vector<double> kp;
+        es_fit(p->W, p->beta, std::min(p->W + 2, ES_MAXDEG), kp);
+        std::vector<float> kpf(kp.begin(), kp.end());
+        s = alloc(p, (void **)&p->kpoly_d, kpf.size() * sizeof(float));
+        if (!s && cudaMemcpy(p->kpoly_d, kpf.data(), kpf.size() * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess)
+            s = IVIS_ERR_CUDA;
     }
     if (!s) s = alloc(p, &p->beams_d, (size_t)c.npoint * c.nb * c.nb * p->rsz);
     if (!s) {
@@ -1086,6 +1134,11 @@ ivis_status ivis_destroy(ivis_plan_t p) {
     for (auto &ph : p->pairs) free_pair(ph);
     dfree(p->dinv_d);
     dfree(p->tw_d);
+    {
+        void *kp = p->kpoly_d;
+        dfree(kp);
+        p->kpoly_d = nullptr;
+    }
     dfree(p->beams_d);
     dfree(p->tsd_d);
     for (auto &st : p->stages) {

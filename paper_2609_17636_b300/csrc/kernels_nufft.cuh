@@ -46,6 +46,21 @@ template <typename T> struct PairData {
 
 constexpr int FRAC_BITS = 20;
 constexpr unsigned FRAC_ONE = 1u << FRAC_BITS;
+constexpr int GTILE = 32;    // fine-grid tile edge (cells) of the gridding work list
+constexpr int ES_MAXDEG = 18; // max degree of the per-tap kernel polynomials
+template <int W> struct es_deg { static constexpr int value = W + 2 < ES_MAXDEG ? W + 2 : ES_MAXDEG; };
+
+// Per-tap polynomials of the ES kernel (FP32 path): the x kernel value of tap t of a
+// visibility whose first-tap fraction is f in [0, 1) is sum_i c[t][i] (2f - 1)^i. Fitted at
+// plan time in FP64 by interpolation at Chebyshev nodes (see es_fit in ivis.cu).
+template <int W>
+__device__ __forceinline__ float es_poly(const float (&c)[es_deg<W>::value + 1], float f) {
+    const float x = 2.0f * f - 1.0f;
+    float acc = c[es_deg<W>::value];
+#pragma unroll
+    for (int i = es_deg<W>::value - 1; i >= 0; --i) acc = fmaf(acc, x, c[i]);
+    return acc;
+}
 
 // ---------------------------------------------------------------- set-up: coordinates, sort
 // Grid coordinate, tile key and validity of each input visibility.
@@ -250,14 +265,15 @@ k_fwd_cols(const typename cplx_of<T>::type *__restrict__ rowbuf,
 }
 
 // --------------------------------------------- interpolation / residual / spreading (a3, a4)
+// FP32 records: first-tap cell and the fraction f in [0, 1) (the first tap sits at offset
+// W/2 - 1 + f from the visibility).
 template <int W>
-__device__ __forceinline__ void decode(uint2 c, int nf, int &gx, int &gy, float &dx, float &dy) {
+__device__ __forceinline__ void decode(uint2 c, int nf, int &gx, int &gy, float &fx, float &fy) {
     (void)nf;
     gx = (int)(c.x >> FRAC_BITS);
     gy = (int)(c.y >> FRAC_BITS);
-    const float base = 0.5f * (W - 2);
-    dx = base + (float)(c.x & (FRAC_ONE - 1)) * (1.0f / (float)FRAC_ONE);
-    dy = base + (float)(c.y & (FRAC_ONE - 1)) * (1.0f / (float)FRAC_ONE);
+    fx = (float)(c.x & (FRAC_ONE - 1)) * (1.0f / (float)FRAC_ONE);
+    fy = (float)(c.y & (FRAC_ONE - 1)) * (1.0f / (float)FRAC_ONE);
 }
 template <int W>
 __device__ __forceinline__ void decode(double2 c, int nf, int &gx, int &gy, double &dx, double &dy) {
@@ -291,18 +307,20 @@ __device__ __forceinline__ void red_add_c(double2 *p, double2 v) {
 // the spread in registers and only adds it to the shared sub-grid (atomics) when the cell
 // changes. MODE_PREDICT writes V~ to pred[orig] instead of spreading.
 template <typename T, int W, int MODE>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 5 : 2)
 k_grid_pass(const Chunk *__restrict__ chunks, const PairData<T> *__restrict__ pdata,
             const typename cplx_of<T>::type *__restrict__ F, typename cplx_of<T>::type *G,
-            int lognf, int tile, int ntx, T beta, double *jpart,
-            typename cplx_of<T>::type *pred) {
+            int lognf, int ntx, T beta, const float *__restrict__ kpoly,
+            double *jpart, typename cplx_of<T>::type *pred) {
     typedef typename cplx_of<T>::type C;
     constexpr int GS = W <= 4 ? 4 : (W <= 8 ? 8 : 16);
     constexpr int NG = 256 / GS;  // groups per CTA
+    constexpr int tile = GTILE;
+    constexpr int PW = tile + W - 1;
+    constexpr bool POLY = sizeof(T) == 4;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double red[32];
     const int nf = 1 << lognf;
-    const int PW = tile + W - 1;
     C *Fs = reinterpret_cast<C *>(smem_raw);
     C *Gs = Fs + PW * PW;
     const Chunk ch = chunks[blockIdx.x];
@@ -320,6 +338,10 @@ k_grid_pass(const Chunk *__restrict__ chunks, const PairData<T> *__restrict__ pd
     const T zs = (T)2 / (T)W;
     const int r = threadIdx.x & (GS - 1);  // kernel row of this lane
     const bool active_row = r < W;
+    constexpr int KD = es_deg<W>::value;
+    float pc[KD + 1];  // this lane's tap polynomial (FP32 path)
+#pragma unroll
+    for (int i = 0; i <= KD; ++i) pc[i] = (POLY && active_row) ? kpoly[r * (ES_MAXDEG + 1) + i] : 0.f;
     const int len = (ch.end - ch.begin + NG - 1) / NG;  // same for every group of the CTA
     const int vbeg = ch.begin + (threadIdx.x / GS) * len;
     const int vend = min(ch.end, vbeg + len);
@@ -330,12 +352,27 @@ k_grid_pass(const Chunk *__restrict__ chunks, const PairData<T> *__restrict__ pd
     int clx = -1, cly = 0;  // cell of the run held in racc
     // Every lane of a warp runs exactly len iterations, so the full-warp shuffles below always
     // see all 32 lanes.
+    typedef typename coord_of<T>::type CO;
+    CO cnext{};  // record of the next visibility, fetched one iteration ahead
+    C vnext = mk((T)0, (T)0);
+    T wnext = (T)0;
+    if (vbeg < vend) {
+        cnext = pd.coord[vbeg];
+        if (MODE == MODE_COSTGRAD) { vnext = pd.vis[vbeg]; wnext = pd.w[vbeg]; }
+    }
     for (int i = 0; i < len; ++i) {
         const int v = vbeg + i;
         const bool valid = v < vend;
+        const CO ccur = cnext;
+        const C vv = vnext;
+        const T w = wnext;
+        if (v + 1 < vend) {
+            cnext = pd.coord[v + 1];
+            if (MODE == MODE_COSTGRAD) { vnext = pd.vis[v + 1]; wnext = pd.w[v + 1]; }
+        }
         int gx = x0, gy = y0;
         T dx = (T)(0.5 * W), dy = (T)(0.5 * W);
-        if (valid) decode<W>(pd.coord[v], nf, gx, gy, dx, dy);
+        if (valid) decode<W>(ccur, nf, gx, gy, dx, dy);
         const int lx = gx - x0, ly = gy - y0;
         if (MODE == MODE_COSTGRAD && valid && (lx != clx || ly != cly)) {
             if (clx >= 0 && active_row) {
@@ -351,8 +388,14 @@ k_grid_pass(const Chunk *__restrict__ chunks, const PairData<T> *__restrict__ pd
             cly = ly;
         }
         const bool row_on = valid && active_row;
-        const T kxr = row_on ? es_kernel((dx - (T)r) * zs, beta) : (T)0;
-        const T kyr = row_on ? es_kernel((dy - (T)r) * zs, beta) : (T)0;
+        T kxr, kyr;
+        if constexpr (POLY) {
+            kxr = row_on ? (T)es_poly<W>(pc, (float)dx) : (T)0;
+            kyr = row_on ? (T)es_poly<W>(pc, (float)dy) : (T)0;
+        } else {
+            kxr = row_on ? es_kernel((dx - (T)r) * zs, beta) : (T)0;
+            kyr = row_on ? es_kernel((dy - (T)r) * zs, beta) : (T)0;
+        }
         T kx[W];
 #pragma unroll
         for (int a = 0; a < W; ++a) kx[a] = __shfl_sync(0xffffffffu, kxr, a, GS);
@@ -377,8 +420,6 @@ k_grid_pass(const Chunk *__restrict__ chunks, const PairData<T> *__restrict__ pd
             if (r == 0) pred[pd.orig[v]] = acc;
             continue;
         }
-        const C vv = pd.vis[v];
-        const T w = pd.w[v];
         const C res = mk(acc.x - vv.x, acc.y - vv.y);
         // per-visibility term in the working precision; a lane sums at most len (<= 32) terms
         // before the FP64 block and global reductions (FP64 issue is scarce on this part)

@@ -1,0 +1,94 @@
+"""Parity at the benchmark's full size (the 7-pointing 512^2 mosaic, 1.36 M visibilities,
+Laplacian + fusion terms, FP32 grids), in the launch configuration bench.py times (the
+plan's captured evaluation graph).
+
+The oracle cannot evaluate a dense 512^2 sky against 1.36 M visibilities in seconds, so both
+the data and the evaluation point are sparse skies (the oracle's direct DFT skips zero
+pixels, which leaves its sums unchanged): then the oracle's cost terms are exact and cheap,
+and the gradient is checked on sampled pixels and the model visibilities on sampled rows.
+Tolerance: the FP32 path's 1e-5 relative."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from _data import rel_l2
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-5
+
+
+def _sparse_sky(rng, n, k, lo=0.0):
+    sky = np.zeros((1, n, n))
+    idx = rng.choice(n * n, size=k, replace=False)
+    sky.flat[idx] = rng.uniform(0.2, 1.0, size=k) + lo
+    return sky
+
+
+@pytest.fixture(scope="module")
+def c2():
+    prob = synth.config_c2()
+    rng = np.random.default_rng(2024)
+    truth = _sparse_sky(rng, prob.n, 48)
+    for pair in prob.pairs:
+        pair.vis = (oracle.pair_model_vis(prob, truth, pair) + pair.noise).astype(np.complex64)
+    b = oracle.dish_kernel(prob.sd_fwhm_pix)
+    t = oracle.dish_conv(truth[0], b)[None]
+    prob.sigma_sd = np.array([0.05 * np.sqrt(np.mean(t ** 2))])
+    prob.tsd = (t + prob.sd_noise_unit * prob.sigma_sd[0]).astype(np.float32)
+    x = _sparse_sky(rng, prob.n, 40)
+    return prob, x
+
+
+def test_fullsize_cost_terms_gradient_samples_and_visibilities(c2):
+    from paper_2609_17636_b300 import plan_from_problem
+    prob, x = c2
+    plan = plan_from_problem(prob, "fp32")
+    xs = torch.as_tensor(x, dtype=torch.float32, device="cuda")
+    f, g, (Q, K, R) = plan.cost_grad(xs)
+    g = g.cpu().numpy()
+    # oracle terms
+    resid = [oracle.pair_model_vis(prob, x, p) - p.vis.astype(np.complex128) for p in prob.pairs]
+    Q_ref = sum(0.5 * float(np.sum(p.weight.astype(np.float64) * np.abs(r) ** 2))
+                for p, r in zip(prob.pairs, resid))
+    R_ref, gR = oracle.reg_cost_grad(x)
+    K_ref, gK = oracle.fusion_cost_grad(x, prob.tsd, prob.sigma_sd, prob.sd_fwhm_pix)
+    f_ref = Q_ref + prob.lambda_s * K_ref + prob.lambda_r * R_ref
+    assert abs(Q - Q_ref) <= TOL * Q_ref
+    assert abs(K - K_ref) <= TOL * K_ref
+    assert abs(R - R_ref) <= TOL * R_ref
+    assert abs(f - f_ref) <= TOL * f_ref
+    # gradient at sampled pixels: inside several windows, on the sky edge, in overlaps
+    rng = np.random.default_rng(7)
+    ys = np.concatenate([rng.integers(0, prob.n, 40), [0, prob.n - 1, 256, 256]])
+    xs_ = np.concatenate([rng.integers(0, prob.n, 40), [5, prob.n - 1, 256, 410]])
+    gq = oracle.data_grad_pixels(prob, x, 0, ys, xs_, residuals=resid)
+    g_ref = gq + prob.lambda_r * gR[0, ys, xs_] + prob.lambda_s * gK[0, ys, xs_]
+    assert rel_l2(g[0, ys, xs_], g_ref) <= TOL, rel_l2(g[0, ys, xs_], g_ref)
+    # model visibilities on sampled rows of every pointing
+    for pair in prob.pairs:
+        idx = np.sort(rng.choice(pair.m, 1500, replace=False))
+        got = plan.predict(xs, pair.k, pair.chan).cpu().numpy()[idx]
+        ref = oracle.pair_model_vis(prob, x, pair, idx)
+        assert rel_l2(got[:, 0] + 1j * got[:, 1], ref) <= TOL
+    plan.close()
+
+
+def test_fullsize_gradient_is_consistent_with_cost_along_a_direction(c2):
+    """Directional derivative by central differences of the GPU cost (a property that holds at
+    any size) on a dense random sky: (f(x + h d) - f(x - h d)) / 2h = <g, d>."""
+    from paper_2609_17636_b300 import plan_from_problem
+    prob, _ = c2
+    plan = plan_from_problem(prob, "fp64")
+    rng = np.random.default_rng(3)
+    x = torch.as_tensor(prob.sky_true * rng.uniform(0.5, 1.5, prob.sky_true.shape), device="cuda")
+    d = torch.as_tensor(rng.standard_normal(prob.sky_true.shape), device="cuda")
+    _, g, _ = plan.cost_grad(x)
+    h = 0.05 * float(x.abs().max()) / float(d.abs().max())  # the cost is quadratic: no truncation error
+    fp, _, _ = plan.cost_grad(x + h * d)
+    fm, _, _ = plan.cost_grad(x - h * d)
+    fd = (fp - fm) / (2 * h)
+    ip = float(torch.sum(g * d))
+    assert abs(fd - ip) <= 1e-6 * abs(ip)
+    plan.close()

@@ -163,6 +163,24 @@ ivis_status ivis_stage_times(ivis_plan_t plan, const char **names, double *ms, i
 /* Number of kernel launches one evaluation issues (the graph's kernel nodes). */
 ivis_status ivis_launches_per_eval(ivis_plan_t plan, int *count);
 
+/* Allocation-free single-dish model B (x) I, for callers that cannot allocate device memory
+ * when they need it (e.g. inside a region whose memory a pool or an outside framework owns,
+ * or an embedded host that forbids runtime allocation). No counterpart in the paper: it is
+ * the same separable dish-beam convolution as ivis_sd_predict (Gaussian taps truncated at
+ * +-ceil(4 sigma), unit sum, zero outside the image), computed without a plan and without
+ * allocating: its scratch (taps and the row-pass image of one channel) lives in a
+ * file-scope device array of 4 MiB + 16 KiB that every GPU loading the library keeps until
+ * the process exits. sky_dev, out_dev: float [nchan][n][n] on the current device; stream: a
+ * cudaStream_t (NULL = legacy default stream); the call returns after the work completes.
+ * Limits: n * n <= 1,048,576 and 2 ceil(4 sigma) + 1 <= 4095, else IVIS_ERR_ARG with a
+ * message. The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture. Every call shares
+ * the one array: calls that overlap on the GPU (other streams, other host threads) race and
+ * must be serialised by the caller. Calls no cudaMalloc/cudaFree. Errors are reported by
+ * ivis_last_error(NULL). */
+ivis_status ivis_sd_predict_noalloc(const float *sky_dev, int n, int nchan, double fwhm_pix,
+                                    float *out_dev, void *stream);
+
 /* Release every device resource of the plan. Safe on NULL. */
 ivis_status ivis_destroy(ivis_plan_t plan);
 

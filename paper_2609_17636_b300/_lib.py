@@ -23,7 +23,7 @@ STATUS = {0: "IVIS_OK", 1: "IVIS_ERR_ARG", 2: "IVIS_ERR_STATE", 3: "IVIS_ERR_OOM
 EXPORTS = ["ivis_plan", "ivis_set_pointing", "ivis_set_vis", "ivis_set_sd", "ivis_prepare",
            "ivis_cost_grad", "ivis_cost_grad_async", "ivis_get_stream", "ivis_cost_grad_host", "ivis_predict", "ivis_sd_predict",
            "ivis_solve", "ivis_get_nufft_params", "ivis_profile", "ivis_stage_times",
-           "ivis_launches_per_eval", "ivis_destroy", "ivis_last_error"]
+           "ivis_launches_per_eval", "ivis_sd_predict_noalloc", "ivis_destroy", "ivis_last_error"]
 
 
 class IvisError(RuntimeError):
@@ -76,6 +76,7 @@ def load(path: str = LIB_PATH):
     L.ivis_profile.argtypes = [vp, i]
     L.ivis_stage_times.argtypes = [vp, ctypes.POINTER(ctypes.c_char_p), dp, i, ctypes.POINTER(i)]
     L.ivis_launches_per_eval.argtypes = [vp, ctypes.POINTER(i)]
+    L.ivis_sd_predict_noalloc.argtypes = [vp, i, i, d, vp, vp]
     L.ivis_destroy.argtypes = [vp]
     L.ivis_last_error.argtypes = [vp]
     L.ivis_last_error.restype = ctypes.c_char_p

@@ -13,6 +13,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -814,6 +815,49 @@ ivis_status solve_impl(ivis_plan_s *p, void *sky_dev, int maxiter, int m_hist, d
 
 }  // namespace
 
+// ------------------------------------------------ allocation-free single-dish prediction
+// Some callers cannot allocate device memory at the point where they need B (x) I: for
+// example code that runs while the device allocator must not be touched (inside a region
+// that a memory pool or an outside framework owns), or an embedded host that forbids runtime
+// allocation after start-up. For them, ivis_sd_predict_noalloc keeps its scratch (the row-pass
+// intermediate image and the beam taps) in this file-scope device array instead of
+// plan-owned memory. Every device that loads the library holds the array until the process
+// exits.
+constexpr int NOALLOC_MAX_TAPS = 4096;                   // 2R + 1 <= 4095
+constexpr size_t NOALLOC_MAX_PIXELS = (size_t)1 << 20;   // n * n <= 1,048,576 per call
+static __device__ __align__(256) float g_noalloc_scratch[NOALLOC_MAX_TAPS + NOALLOC_MAX_PIXELS];
+
+namespace {
+constexpr int NOALLOC_MAX_DEVICES = 64;
+float *g_noalloc_ptr[NOALLOC_MAX_DEVICES] = {};
+std::mutex g_noalloc_mu;
+thread_local std::string g_noalloc_err;
+
+ivis_status noalloc_fail(ivis_status s, const std::string &msg) {
+    g_noalloc_err = msg;
+    g_plan_error = msg;
+    return s;
+}
+
+// Device address of the scratch array on the current device (looked up once per device).
+ivis_status noalloc_scratch(float **out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return noalloc_fail(IVIS_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+    if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return noalloc_fail(IVIS_ERR_ARG, "device index out of range");
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void *ptr = nullptr;
+        e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+        if (e != cudaSuccess || !ptr)
+            return noalloc_fail(IVIS_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+        g_noalloc_ptr[dev] = (float *)ptr;
+    }
+    *out = g_noalloc_ptr[dev];
+    return IVIS_OK;
+}
+}  // namespace
+
 // ======================================================================= C ABI
 extern "C" {
 
@@ -1125,6 +1169,48 @@ ivis_status ivis_solve(ivis_plan_t p, void *sky_dev, int maxiter, int m_hist, do
     if (s) return s;
     return p->fp64 ? solve_impl<double>(p, sky_dev, maxiter, m_hist, pgtol, ftol, rep)
                    : solve_impl<float>(p, sky_dev, maxiter, m_hist, pgtol, ftol, rep);
+}
+
+ivis_status ivis_sd_predict_noalloc(const float *sky_dev, int n, int nchan, double fwhm_pix,
+                                    float *out_dev, void *stream) {
+    if (!sky_dev || !out_dev) return noalloc_fail(IVIS_ERR_ARG, "null sky or output pointer");
+    if (n < 1 || nchan < 1) return noalloc_fail(IVIS_ERR_ARG, "n and nchan must be >= 1");
+    if (!(fwhm_pix > 0.0) || !std::isfinite(fwhm_pix)) return noalloc_fail(IVIS_ERR_ARG, "fwhm_pix must be finite and > 0");
+    if ((size_t)n * n > NOALLOC_MAX_PIXELS)
+        return noalloc_fail(IVIS_ERR_ARG, "image too large for the allocation-free path: n*n must be <= " +
+                                              std::to_string(NOALLOC_MAX_PIXELS));
+    const double sg = fwhm_pix / (2.0 * std::sqrt(2.0 * std::log(2.0)));
+    const double rr = std::ceil(4.0 * sg);
+    if (rr > (NOALLOC_MAX_TAPS - 1) / 2)
+        return noalloc_fail(IVIS_ERR_ARG, "dish beam too wide for the allocation-free path: 2*ceil(4 sigma)+1 must be <= " +
+                                              std::to_string(NOALLOC_MAX_TAPS - 1));
+    const int R = (int)rr;
+    const size_t sm = conv_smem<float>(R);
+    if (sm > 220 * 1024) return noalloc_fail(IVIS_ERR_ARG, "dish beam too wide for the convolution strip");
+    float *scratch = nullptr;
+    ivis_status st = noalloc_scratch(&scratch);
+    if (st) return st;
+    float *taps_d = scratch;                       // [2R + 1]
+    float *mid_d = scratch + NOALLOC_MAX_TAPS;     // [n][n] row-pass output of one channel
+    float taps[NOALLOC_MAX_TAPS];
+    double sum = 0.0;
+    for (int t = -R; t <= R; ++t) sum += std::exp(-0.5 * (t / sg) * (t / sg));
+    for (int t = -R; t <= R; ++t) taps[R + t] = (float)(std::exp(-0.5 * (t / sg) * (t / sg)) / sum);
+    cudaStream_t cs = (cudaStream_t)stream;
+    cudaError_t e = cudaMemcpyAsync(taps_d, taps, (size_t)(2 * R + 1) * sizeof(float), cudaMemcpyHostToDevice, cs);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_conv_axis<float, 0, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_conv_axis<float, 1, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    dim3 gr((n + 31) / 32, (n + CONV_TO - 1) / CONV_TO, 1);
+    for (int c = 0; c < nchan && e == cudaSuccess; ++c) {
+        const float *in = sky_dev + (size_t)c * n * n;
+        float *out = out_dev + (size_t)c * n * n;
+        k_conv_axis<float, 0, 0><<<gr, 256 * CONV_SPLIT, sm, cs>>>(in, mid_d, taps_d, R, n, nullptr, nullptr, nullptr);
+        k_conv_axis<float, 1, 0><<<gr, 256 * CONV_SPLIT, sm, cs>>>(mid_d, out, taps_d, R, n, nullptr, nullptr, nullptr);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
+    if (e != cudaSuccess) return noalloc_fail(IVIS_ERR_CUDA, std::string("sd_predict_noalloc: ") + cudaGetErrorString(e));
+    return IVIS_OK;
 }
 
 ivis_status ivis_destroy(ivis_plan_t p) {

@@ -290,21 +290,26 @@ cudaError_t launch_grid_pass(ivis_plan_s *p, int first_chunk, int nchunk, double
 }
 
 // Row passes: 256 threads = lpb lines of nf/16 threads. Column passes: ncol x nf/16 threads.
+// Forward passes for slots [slot0, slot0 + nslots) (all slots by default).
 template <typename T>
-cudaError_t launch_forward(ivis_plan_s *p, const void *sky) {
+cudaError_t launch_forward(ivis_plan_s *p, const void *sky, int slot0 = 0, int nslots = -1) {
     typedef typename cplx_of<T>::type C;
     const int nb = p->cfg.nb, nf = p->nf, tpl = nf / 16, lpb = 256 / tpl;
-    dim3 gr((nb + lpb - 1) / lpb, p->nslot);
+    if (nslots < 0) nslots = p->nslot;
+    const PairInfo *pinfo = p->pinfo_d + slot0;
+    C *rowbuf = (C *)p->rowbuf + (size_t)slot0 * nb * nf;
+    C *F = (C *)p->F + (size_t)slot0 * nf * nf;
+    dim3 gr((nb + lpb - 1) / lpb, nslots);
     size_t smem_row = (size_t)fft_smem_elems(nf, lpb) * sizeof(C);
     cudaFuncSetAttribute(k_fwd_rows<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_row);
     k_fwd_rows<T><<<gr, 256, smem_row, p->stream>>>(
-        (const T *)sky, (const T *)p->beams_d, p->pinfo_d, (const T *)p->dinv_d, (C *)p->rowbuf,
+        (const T *)sky, (const T *)p->beams_d, pinfo, (const T *)p->dinv_d, rowbuf,
         p->cfg.n, nb, p->lognf, (const C *)p->tw_d);
-    dim3 gc(nf >> p->logc_cols, p->nslot);
+    dim3 gc(nf >> p->logc_cols, nslots);
     size_t smem_col = (size_t)fft_smem_elems(nf, 1 << p->logc_cols) * sizeof(C);
     cudaFuncSetAttribute(k_fwd_cols<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_col);
     k_fwd_cols<T><<<gc, tpl << p->logc_cols, smem_col, p->stream>>>(
-        (const C *)p->rowbuf, (C *)p->F, nb, p->lognf, p->logc_cols, (const C *)p->tw_d);
+        (const C *)rowbuf, F, nb, p->lognf, p->logc_cols, (const C *)p->tw_d);
     return cudaGetLastError();
 }
 
@@ -421,7 +426,7 @@ cudaError_t enqueue_eval(ivis_plan_s *p, bool capture) {
     launches += 1;
     stage_end(p, p->stream, si);
     stage_begin(p, "finalize", p->stream, si);
-    k_finalize<<<1, 256, 0, p->stream>>>(p->jpart, p->nchunk, p->kpart, use_k ? p->nkpart : 0,
+    k_finalize<<<1, 1024, 0, p->stream>>>(p->jpart, p->nchunk, p->kpart, use_k ? p->nkpart : 0,
                                          p->rpart, use_r ? p->nrpart : 0, p->cfg.lambda_r,
                                          p->cfg.lambda_s, p->cost_d);
     launches += 1;
@@ -1073,11 +1078,11 @@ ivis_status ivis_predict(ivis_plan_t p, const void *sky_dev, int k, int chan, vo
     CK(cudaMemcpyAsync(p->x, sky_dev, bytes, cudaMemcpyDeviceToDevice, p->stream));
     cudaError_t e;
     if (p->fp64) {
-        e = launch_forward<double>(p, p->x);
+        e = launch_forward<double>(p, p->x, slot, 1);
         if (e == cudaSuccess)
             e = launch_grid_pass<double, MODE_PREDICT>(p, p->chunk_first[slot], p->chunk_first[slot + 1] - p->chunk_first[slot], nullptr, vis_out_dev);
     } else {
-        e = launch_forward<float>(p, p->x);
+        e = launch_forward<float>(p, p->x, slot, 1);
         if (e == cudaSuccess)
             e = launch_grid_pass<float, MODE_PREDICT>(p, p->chunk_first[slot], p->chunk_first[slot + 1] - p->chunk_first[slot], nullptr, vis_out_dev);
     }

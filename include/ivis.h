@@ -148,6 +148,11 @@ ivis_status ivis_sd_predict(ivis_plan_t plan, const void *sky_dev, void *out_dev
 ivis_status ivis_solve(ivis_plan_t plan, void *sky_dev, int maxiter, int m_hist, double pgtol,
                        double ftol, ivis_solve_report *rep);
 
+/* Same solve, also stopping as soon as Q_tot <= f_target (time-to-cost measurements, e.g. a
+ * warm start against the cost a cold start reached). */
+ivis_status ivis_solve_target(ivis_plan_t plan, void *sky_dev, int maxiter, int m_hist,
+                              double pgtol, double ftol, double f_target, ivis_solve_report *rep);
+
 /* Kernel width w, ES shape beta and oversampled grid size actually used. */
 ivis_status ivis_get_nufft_params(ivis_plan_t plan, int *w, double *beta, int *nf);
 
@@ -180,6 +185,47 @@ ivis_status ivis_launches_per_eval(ivis_plan_t plan, int *count);
  * ivis_last_error(NULL). */
 ivis_status ivis_sd_predict_noalloc(const float *sky_dev, int n, int nchan, double fwhm_pix,
                                     float *out_dev, void *stream);
+
+/* Inputs of the learned warm start (not in the paper; spec extension): the dirty
+ * image -grad Q(0) of each channel (the adjoint of the weighted data, Eqs. 5-6 at I = 0;
+ * real [nchan][n][n] on the device) and, if beamw_dev is not NULL, the beam-weight map
+ * sum_k A_k^2 of the linear mosaic of Sect. 4.3 (real [n][n]). */
+ivis_status ivis_dirty_image(ivis_plan_t plan, void *dirty_dev, void *beamw_dev);
+
+/* ---- learned warm start: a 4-level U-Net [dirty image, beam-weight map] -> initial sky ----
+ * No counterpart in the paper (its closest hook is the "physically motivated priors" of its
+ * future prospects). Per level two 3x3 convolutions + ReLU; encoder widths c, 2c, 4c, 8c with
+ * 2x2 max pooling; decoder: nearest 2x upsampling, concatenation with the encoder output of
+ * the same level, two 3x3 convolutions + ReLU; a 1x1 head; loss = mean squared error.
+ * BF16 weights and activations, FP32 accumulation and gradients, FP32 Adam.
+ * Parameters are one flat float vector: for each 3x3 layer in order (enc 0a, 0b, 1a, 1b, 2a,
+ * 2b, 3a, 3b, dec 2a, 2b, 1a, 1b, 0a, 0b) the weights W[cout][tap = 3 dy + dx][cin] then the
+ * bias[cout]; then the head weights [c] and bias [1]. Decoder "a" layers take the upsampled
+ * deeper tensor's channels first, then the skip channels. */
+typedef struct ivis_unet_s *ivis_unet_t;
+
+/* Create a network of base width c (multiple of 8, 8..64) for batches up to max_batch images
+ * of up to max_hw pixels; work runs on stream (cudaStream_t; NULL = legacy default). The
+ * parameters start at zero: set them with ivis_unet_set_params. */
+ivis_status ivis_unet_create(int base_channels, int max_batch, int max_hw, void *stream,
+                             ivis_unet_t *out);
+ivis_status ivis_unet_num_params(ivis_unet_t net, int64_t *n);
+/* Copy the flat parameter vector from / to host memory (float [n]); set also resets Adam. */
+ivis_status ivis_unet_set_params(ivis_unet_t net, const float *host_params);
+ivis_status ivis_unet_get_params(ivis_unet_t net, float *host_params);
+/* Forward: in_dev float [B][2][H][W] (plane 0 dirty image, plane 1 beam-weight map), out_dev
+ * float [B][H][W]; H and W multiples of 8. */
+ivis_status ivis_unet_forward(ivis_unet_t net, const float *in_dev, float *out_dev, int B, int H,
+                              int W);
+/* Forward + backward of the MSE loss against tgt_dev (float [B][H][W]); the parameter
+ * gradient (zeroed first) stays on the device; loss_out (host, may be NULL) gets the loss. */
+ivis_status ivis_unet_backward(ivis_unet_t net, const float *in_dev, const float *tgt_dev, int B,
+                               int H, int W, double *loss_out);
+ivis_status ivis_unet_get_grads(ivis_unet_t net, float *host_grads);
+/* One Adam update with the last gradient (Kingma & Ba 2015, bias-corrected). */
+ivis_status ivis_unet_adam_step(ivis_unet_t net, float lr, float beta1, float beta2, float eps);
+ivis_status ivis_unet_destroy(ivis_unet_t net);
+const char *ivis_unet_last_error(ivis_unet_t net);
 
 /* Release every device resource of the plan. Safe on NULL. */
 ivis_status ivis_destroy(ivis_plan_t plan);

@@ -23,7 +23,10 @@ STATUS = {0: "IVIS_OK", 1: "IVIS_ERR_ARG", 2: "IVIS_ERR_STATE", 3: "IVIS_ERR_OOM
 EXPORTS = ["ivis_plan", "ivis_set_pointing", "ivis_set_vis", "ivis_set_sd", "ivis_prepare",
            "ivis_cost_grad", "ivis_cost_grad_async", "ivis_get_stream", "ivis_cost_grad_host", "ivis_predict", "ivis_sd_predict",
            "ivis_solve", "ivis_get_nufft_params", "ivis_profile", "ivis_stage_times",
-           "ivis_launches_per_eval", "ivis_sd_predict_noalloc", "ivis_destroy", "ivis_last_error"]
+           "ivis_launches_per_eval", "ivis_sd_predict_noalloc", "ivis_destroy", "ivis_last_error",
+           "ivis_dirty_image", "ivis_solve_target", "ivis_unet_create", "ivis_unet_num_params", "ivis_unet_set_params",
+           "ivis_unet_get_params", "ivis_unet_forward", "ivis_unet_backward", "ivis_unet_get_grads",
+           "ivis_unet_adam_step", "ivis_unet_destroy", "ivis_unet_last_error"]
 
 
 class IvisError(RuntimeError):
@@ -80,8 +83,21 @@ def load(path: str = LIB_PATH):
     L.ivis_destroy.argtypes = [vp]
     L.ivis_last_error.argtypes = [vp]
     L.ivis_last_error.restype = ctypes.c_char_p
+    L.ivis_dirty_image.argtypes = [vp, vp, vp]
+    L.ivis_solve_target.argtypes = [vp, vp, i, i, d, d, d, ctypes.POINTER(SolveReport)]
+    L.ivis_unet_create.argtypes = [i, i, i, vp, ctypes.POINTER(vp)]
+    L.ivis_unet_num_params.argtypes = [vp, ctypes.POINTER(i64)]
+    L.ivis_unet_set_params.argtypes = [vp, vp]
+    L.ivis_unet_get_params.argtypes = [vp, vp]
+    L.ivis_unet_forward.argtypes = [vp, vp, vp, i, i, i]
+    L.ivis_unet_backward.argtypes = [vp, vp, vp, i, i, i, dp]
+    L.ivis_unet_get_grads.argtypes = [vp, vp]
+    L.ivis_unet_adam_step.argtypes = [vp, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float]
+    L.ivis_unet_destroy.argtypes = [vp]
+    L.ivis_unet_last_error.argtypes = [vp]
+    L.ivis_unet_last_error.restype = ctypes.c_char_p
     for name in EXPORTS:
-        if name != "ivis_last_error":
+        if name not in ("ivis_last_error", "ivis_unet_last_error"):
             getattr(L, name).restype = ctypes.c_int
     _LIB = L
     return L

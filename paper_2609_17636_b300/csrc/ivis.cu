@@ -704,7 +704,7 @@ void invalidate(ivis_plan_s *p) {
 // ------------------------------------------------------------------------------- solver
 template <typename T>
 ivis_status solve_impl(ivis_plan_s *p, void *sky_dev, int maxiter, int m_hist, double pgtol,
-                       double ftol, ivis_solve_report *rep) {
+                       double ftol, double f_target, ivis_solve_report *rep) {
     auto t0 = std::chrono::steady_clock::now();
     SolverBufs &B = p->solver;
     ivis_status s = solver_ensure<T>(B, m_hist);
@@ -741,7 +741,7 @@ ivis_status solve_impl(ivis_plan_s *p, void *sky_dev, int maxiter, int m_hist, d
         const double gd = B.scal_h[1];
         pg = B.scal_h[2];
         const double gg = B.scal_h[3];
-        if (pg <= pgtol) { status = 0; break; }
+        if (pg <= pgtol || f <= f_target) { status = 0; break; }
         if (it == maxiter) { status = 1; break; }
         if (!(gd < 0.0) || !std::isfinite(gd)) {
             if (!order.empty()) { order.clear(); --it; continue; }
@@ -815,6 +815,51 @@ ivis_status solve_impl(ivis_plan_s *p, void *sky_dev, int maxiter, int m_hist, d
         rep->status = status;
     }
     if (status == 2 && iters == 0) return fail(p, IVIS_ERR_LINESEARCH, "line search found no decrease");
+    return IVIS_OK;
+}
+
+}  // namespace
+
+namespace {
+template <typename T>
+ivis_status dirty_impl(ivis_plan_s *p, void *dirty_dev, void *beamw_dev) {
+    typedef typename cplx_of<T>::type C;
+    const int n = p->cfg.n, nchan = p->cfg.nchan;
+    const size_t npix = (size_t)nchan * n * n;
+    CK(cudaMemsetAsync(p->x, 0, npix * sizeof(T), p->stream));
+    if (p->nslot > 0) {
+        // at I = 0 the model visibilities vanish: the residual is -V and the data-term
+        // gradient is the adjoint of -w V
+        CK(cudaMemsetAsync(p->F, 0, (size_t)p->nslot * p->nf * p->nf * sizeof(C), p->stream));
+        CK(cudaMemsetAsync(p->G, 0, (size_t)p->nslot * p->nf * p->nf * sizeof(C), p->stream));
+        cudaError_t e = launch_grid_pass<T, MODE_COSTGRAD>(p, 0, p->nchunk, p->jpart, nullptr);
+        if (e == cudaSuccess) e = launch_adjoint<T>(p);
+        if (e != cudaSuccess) return fail(p, IVIS_ERR_CUDA, std::string("dirty: ") + cudaGetErrorString(e));
+    }
+    k_assemble<T><<<(unsigned)((npix + 255) / 256), 256, 0, p->stream>>>(
+        (const T *)p->x, (const T *)p->contrib, p->pinfo_d, p->chan_start_d, p->chan_list_d, nullptr,
+        (T *)p->g, n, p->cfg.nb, nchan, (T)0, (T)0, 0, 0, p->rpart);
+    k_scale<T><<<(unsigned)((npix + 255) / 256), 256, 0, p->stream>>>(npix, (const T *)p->g, (T)-1, (T *)dirty_dev);
+    if (beamw_dev) {
+        std::vector<int> hc(p->cx), hy(p->cy);
+        int *dc = nullptr, *dy = nullptr;
+        ivis_status s;
+        if ((s = alloc(p, (void **)&dc, hc.size() * sizeof(int))) || (s = alloc(p, (void **)&dy, hy.size() * sizeof(int)))) {
+            void *a = dc; dfree(a);
+            return s;
+        }
+        cudaMemcpyAsync(dc, hc.data(), hc.size() * sizeof(int), cudaMemcpyHostToDevice, p->stream);
+        cudaMemcpyAsync(dy, hy.data(), hy.size() * sizeof(int), cudaMemcpyHostToDevice, p->stream);
+        k_beam_weight<T><<<(unsigned)(((size_t)n * n + 255) / 256), 256, 0, p->stream>>>(
+            (const T *)p->beams_d, dc, dy, p->cfg.npoint, n, p->cfg.nb, (T *)beamw_dev);
+        cudaError_t e = cudaStreamSynchronize(p->stream);
+        void *a = dc, *b = dy;
+        dfree(a);
+        dfree(b);
+        if (e != cudaSuccess) return fail(p, IVIS_ERR_CUDA, std::string("beam weight: ") + cudaGetErrorString(e));
+    }
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(p->stream));
     return IVIS_OK;
 }
 
@@ -1172,8 +1217,29 @@ ivis_status ivis_solve(ivis_plan_t p, void *sky_dev, int maxiter, int m_hist, do
     enter(p);
     ivis_status s = ensure_prepared(p);
     if (s) return s;
-    return p->fp64 ? solve_impl<double>(p, sky_dev, maxiter, m_hist, pgtol, ftol, rep)
-                   : solve_impl<float>(p, sky_dev, maxiter, m_hist, pgtol, ftol, rep);
+    return p->fp64 ? solve_impl<double>(p, sky_dev, maxiter, m_hist, pgtol, ftol, -HUGE_VAL, rep)
+                   : solve_impl<float>(p, sky_dev, maxiter, m_hist, pgtol, ftol, -HUGE_VAL, rep);
+}
+
+ivis_status ivis_solve_target(ivis_plan_t p, void *sky_dev, int maxiter, int m_hist, double pgtol,
+                              double ftol, double f_target, ivis_solve_report *rep) {
+    if (!p) return fail(nullptr, IVIS_ERR_ARG, "null plan");
+    if (!sky_dev || maxiter < 0 || m_hist < 1 || m_hist > 32 || !(pgtol >= 0) || !(ftol >= 0) || std::isnan(f_target))
+        return fail(p, IVIS_ERR_ARG, "bad solve arguments");
+    enter(p);
+    ivis_status s = ensure_prepared(p);
+    if (s) return s;
+    return p->fp64 ? solve_impl<double>(p, sky_dev, maxiter, m_hist, pgtol, ftol, f_target, rep)
+                   : solve_impl<float>(p, sky_dev, maxiter, m_hist, pgtol, ftol, f_target, rep);
+}
+
+ivis_status ivis_dirty_image(ivis_plan_t p, void *dirty_dev, void *beamw_dev) {
+    if (!p) return fail(nullptr, IVIS_ERR_ARG, "null plan");
+    if (!dirty_dev) return fail(p, IVIS_ERR_ARG, "null dirty image pointer");
+    enter(p);
+    ivis_status s = ensure_prepared(p);
+    if (s) return s;
+    return p->fp64 ? dirty_impl<double>(p, dirty_dev, beamw_dev) : dirty_impl<float>(p, dirty_dev, beamw_dev);
 }
 
 ivis_status ivis_sd_predict_noalloc(const float *sky_dev, int n, int nchan, double fwhm_pix,

@@ -183,6 +183,31 @@ __global__ void k_finalize(const double *__restrict__ jpart, int nj, const doubl
     }
 }
 
+// Beam-weight map b[y][x] = sum over pointings covering (y, x) of A_k[q][p]^2 (the weight of
+// a linear mosaic, Sect. 4.3); used as an input plane of the learned warm start.
+template <typename T>
+__global__ void k_beam_weight(const T *__restrict__ beams, const int *__restrict__ cx,
+                              const int *__restrict__ cy, int npoint, int n, int nb, T *out) {
+    const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (size_t)n * n) return;
+    const int y = (int)(idx / n), x = (int)(idx % n);
+    T s = (T)0;
+    for (int k = 0; k < npoint; ++k) {
+        const int q = y - (cy[k] - nb / 2), p = x - (cx[k] - nb / 2);
+        if ((unsigned)q < (unsigned)nb && (unsigned)p < (unsigned)nb) {
+            const T a = beams[((size_t)k * nb + q) * nb + p];
+            s += a * a;
+        }
+    }
+    out[idx] = s;
+}
+
+template <typename T>
+__global__ void k_scale(size_t n, const T *__restrict__ in, T a, T *out) {
+    size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = a * in[i];
+}
+
 template <typename T>
 __global__ void k_f32_to(const float *__restrict__ in, T *out, size_t n) {
     size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;

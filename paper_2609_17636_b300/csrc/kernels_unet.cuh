@@ -1,0 +1,325 @@
+// kernels_unet.cuh -- kernels of the learned warm start (a U-Net mapping [dirty image,
+// beam-weight map] to an initial sky).
+//
+// Convolutions are lowered to GEMMs: an im2col gather (which also folds in the nearest-
+// neighbour 2x upsampling and the channel concatenation of the decoder inputs) followed by a
+// BF16 tensor-core GEMM with FP32 accumulation (mma.sync m16n8k16). Activations are NHWC BF16;
+// activation gradients are FP32 and are rounded to BF16 only as GEMM operands; weights are
+// FP32 masters with BF16 copies; Adam runs in FP32.
+#pragma once
+#include <cuda_bf16.h>
+
+#include "common.cuh"
+
+namespace ivis {
+
+typedef __nv_bfloat16 bf16;
+
+// ------------------------------------------------------------------------------- GEMM
+// C[M x N] = op(A) op(B) with A given either as [M][K] (TA = 0) or as [K][M] (TA = 1),
+// B either as [K][N] (TB = 0) or [N][K] (TB = 1), all row-major BF16. Split-K over gridDim.z.
+// EPI 0: C bf16 = relu?(acc + bias[n]) ; EPI 1: C fp32 = acc ; EPI 2: C fp32 += acc (atomic).
+constexpr int GB_M = 128, GB_N = 64, GB_K = 32, GB_PAD = 8;
+
+__device__ __forceinline__ void mma_bf16_16816(float (&d)[4], const uint32_t (&a)[4],
+                                               const uint32_t (&b)[2]) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 "
+        "{%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+template <int TA, int TB, int EPI>
+__global__ void __launch_bounds__(256)
+k_gemm_bf16(int M, int N, int K, int kchunk, const bf16 *__restrict__ A, const bf16 *__restrict__ B,
+            void *Cout, const float *__restrict__ bias, int relu) {
+    __shared__ __align__(16) bf16 As[GB_M][GB_K + GB_PAD];
+    __shared__ __align__(16) bf16 Bs[GB_N][GB_K + GB_PAD];
+    const int m0 = blockIdx.x * GB_M, n0 = blockIdx.y * GB_N;
+    const int kbeg = blockIdx.z * kchunk, kend = min(K, kbeg + kchunk);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;  // 4 x 2 warps, 32 x 32 each
+    float acc[2][4][4];
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) acc[i][j][c] = 0.f;
+    const bf16 zero = __float2bfloat16(0.f);
+    for (int k0 = kbeg; k0 < kend; k0 += GB_K) {
+        // stage A tile [GB_M][GB_K] (m-major) and B tile [GB_N][GB_K] (n-major)
+        for (int i = tid; i < GB_M * GB_K; i += 256) {
+            int mm, kk;
+            if (TA == 0) { mm = i / GB_K; kk = i - mm * GB_K; } else { kk = i / GB_M; mm = i - kk * GB_M; }
+            const int gm = m0 + mm, gk = k0 + kk;
+            bf16 v = zero;
+            if (gm < M && gk < kend) v = TA == 0 ? A[(size_t)gm * K + gk] : A[(size_t)gk * M + gm];
+            As[mm][kk] = v;
+        }
+        for (int i = tid; i < GB_N * GB_K; i += 256) {
+            int nn, kk;
+            if (TB == 1) { nn = i / GB_K; kk = i - nn * GB_K; } else { kk = i / GB_N; nn = i - kk * GB_N; }
+            const int gn = n0 + nn, gk = k0 + kk;
+            bf16 v = zero;
+            if (gn < N && gk < kend) v = TB == 1 ? B[(size_t)gn * K + gk] : B[(size_t)gk * N + gn];
+            Bs[nn][kk] = v;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int ks = 0; ks < GB_K; ks += 16) {
+            uint32_t af[2][4], bfr[4][2];
+            const int r = lane >> 2, c = (lane & 3) * 2;
+#pragma unroll
+            for (int i = 0; i < 2; ++i) {
+                const int row = wm + i * 16 + r;
+                af[i][0] = *reinterpret_cast<const uint32_t *>(&As[row][ks + c]);
+                af[i][1] = *reinterpret_cast<const uint32_t *>(&As[row + 8][ks + c]);
+                af[i][2] = *reinterpret_cast<const uint32_t *>(&As[row][ks + c + 8]);
+                af[i][3] = *reinterpret_cast<const uint32_t *>(&As[row + 8][ks + c + 8]);
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int col = wn + j * 8 + r;
+                bfr[j][0] = *reinterpret_cast<const uint32_t *>(&Bs[col][ks + c]);
+                bfr[j][1] = *reinterpret_cast<const uint32_t *>(&Bs[col][ks + c + 8]);
+            }
+#pragma unroll
+            for (int i = 0; i < 2; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) mma_bf16_16816(acc[i][j], af[i], bfr[j]);
+        }
+        __syncthreads();
+    }
+    const int r = lane >> 2, c = (lane & 3) * 2;
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int gm = m0 + wm + i * 16 + r + h * 8;
+                if (gm >= M) continue;
+#pragma unroll
+                for (int e = 0; e < 2; ++e) {
+                    const int gn = n0 + wn + j * 8 + c + e;
+                    if (gn >= N) continue;
+                    float v = acc[i][j][h * 2 + e];
+                    if (EPI == 0) {
+                        v += bias ? bias[gn] : 0.f;
+                        if (relu) v = fmaxf(v, 0.f);
+                        reinterpret_cast<bf16 *>(Cout)[(size_t)gm * N + gn] = __float2bfloat16(v);
+                    } else if (EPI == 1) {
+                        reinterpret_cast<float *>(Cout)[(size_t)gm * N + gn] = v;
+                    } else {
+                        atomicAdd(&reinterpret_cast<float *>(Cout)[(size_t)gm * N + gn], v);
+                    }
+                }
+            }
+}
+
+// ----------------------------------------------------------------------------- im2col
+// Input of a 3x3 'same' convolution at resolution H x W is the channel concatenation of
+// source a (ca channels, stored at H/ua x W/ua, nearest upsampling by ua in {1, 2}) and
+// source b (cb channels, H x W; cb may be 0). col[p][(dy*3 + dx) * (ca + cb) + ci].
+__global__ void k_im2col(int B, int H, int W, const bf16 *__restrict__ a, int ca, int ua,
+                         const bf16 *__restrict__ b, int cb, bf16 *col) {
+    const int cin = ca + cb, K = 9 * cin;
+    const size_t total = (size_t)B * H * W * K;
+    const bf16 zero = __float2bfloat16(0.f);
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += (size_t)gridDim.x * blockDim.x) {
+        const size_t p = i / K;
+        const int k = (int)(i - p * K);
+        const int tap = k / cin, ci = k - tap * cin;
+        const int dy = tap / 3 - 1, dx = tap % 3 - 1;
+        const int n = (int)(p / ((size_t)H * W));
+        const int rem = (int)(p - (size_t)n * H * W);
+        const int y = rem / W + dy, x = rem % W + dx;
+        bf16 v = zero;
+        if (y >= 0 && y < H && x >= 0 && x < W) {
+            if (ci < ca) {
+                const int Ha = H / ua, Wa = W / ua;
+                v = a[(((size_t)n * Ha + y / ua) * Wa + x / ua) * ca + ci];
+            } else {
+                v = b[(((size_t)n * H + y) * W + x) * cb + (ci - ca)];
+            }
+        }
+        col[i] = v;
+    }
+}
+
+// Adjoint of k_im2col: from dcol (fp32, [p][K]) accumulate the gradients of sources a and b
+// (fp32, same layouts as the forward sources). Gather form: each source element sums the col
+// entries that read it, so no atomics are needed.
+__global__ void k_col2im(int B, int H, int W, const float *__restrict__ dcol, float *da, int ca,
+                         int ua, float *db, int cb) {
+    const int cin = ca + cb, K = 9 * cin;
+    const int Ha = H / ua, Wa = W / ua;
+    const size_t na = (size_t)B * Ha * Wa * ca, nbt = (size_t)B * H * W * cb;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < na + nbt;
+         i += (size_t)gridDim.x * blockDim.x) {
+        float s = 0.f;
+        if (i < na) {
+            const int ci = (int)(i % ca);
+            const size_t q = i / ca;
+            const int X = (int)(q % Wa), Y = (int)((q / Wa) % Ha), n = (int)(q / ((size_t)Wa * Ha));
+            for (int sy = 0; sy < ua; ++sy)
+                for (int sx = 0; sx < ua; ++sx) {
+                    const int y = Y * ua + sy, x = X * ua + sx;  // pixel of the upsampled input
+                    for (int tap = 0; tap < 9; ++tap) {
+                        const int yo = y - (tap / 3 - 1), xo = x - (tap % 3 - 1);  // output pixel
+                        if (yo < 0 || yo >= H || xo < 0 || xo >= W) continue;
+                        s += dcol[(((size_t)n * H + yo) * W + xo) * K + tap * cin + ci];
+                    }
+                }
+            da[i] = s;
+        } else {
+            const size_t j = i - na;
+            const int ci = (int)(j % cb);
+            const size_t q = j / cb;
+            const int x = (int)(q % W), y = (int)((q / W) % H), n = (int)(q / ((size_t)W * H));
+            for (int tap = 0; tap < 9; ++tap) {
+                const int yo = y - (tap / 3 - 1), xo = x - (tap % 3 - 1);
+                if (yo < 0 || yo >= H || xo < 0 || xo >= W) continue;
+                s += dcol[(((size_t)n * H + yo) * W + xo) * K + tap * cin + ca + ci];
+            }
+            db[j] = s;
+        }
+    }
+}
+
+// ------------------------------------------------------------------- elementwise / small
+// dz = dy * (y > 0) rounded to bf16 (the ReLU's backward; y is the post-ReLU output).
+__global__ void k_relu_bwd(size_t n, const float *__restrict__ dy, const bf16 *__restrict__ y,
+                           int relu, bf16 *dz) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        float g = dy[i];
+        if (relu && !(__bfloat162float(y[i]) > 0.f)) g = 0.f;
+        dz[i] = __float2bfloat16(g);
+    }
+}
+
+// 2x2 max pooling, NHWC.
+__global__ void k_maxpool(int B, int H, int W, int C, const bf16 *__restrict__ in, bf16 *out) {
+    const int Ho = H / 2, Wo = W / 2;
+    const size_t total = (size_t)B * Ho * Wo * C;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        const int c = (int)(i % C);
+        const size_t q = i / C;
+        const int x = (int)(q % Wo), y = (int)((q / Wo) % Ho), n = (int)(q / ((size_t)Wo * Ho));
+        float m = -3.0e38f;
+        for (int s = 0; s < 4; ++s) {
+            const float v = __bfloat162float(in[(((size_t)n * H + 2 * y + (s >> 1)) * W + 2 * x + (s & 1)) * C + c]);
+            m = fmaxf(m, v);
+        }
+        out[i] = __float2bfloat16(m);
+    }
+}
+
+// Backward of 2x2 max pooling: the gradient goes to the first maximal element of each window.
+// dinp += routed gradient (dinp already holds the skip-connection gradient).
+__global__ void k_maxpool_bwd(int B, int H, int W, int C, const bf16 *__restrict__ in,
+                              const float *__restrict__ dout, float *dinp) {
+    const int Ho = H / 2, Wo = W / 2;
+    const size_t total = (size_t)B * Ho * Wo * C;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        const int c = (int)(i % C);
+        const size_t q = i / C;
+        const int x = (int)(q % Wo), y = (int)((q / Wo) % Ho), n = (int)(q / ((size_t)Wo * Ho));
+        float m = -3.0e38f;
+        int arg = 0;
+        for (int s = 0; s < 4; ++s) {
+            const float v = __bfloat162float(in[(((size_t)n * H + 2 * y + (s >> 1)) * W + 2 * x + (s & 1)) * C + c]);
+            if (v > m) { m = v; arg = s; }
+        }
+        dinp[(((size_t)n * H + 2 * y + (arg >> 1)) * W + 2 * x + (arg & 1)) * C + c] += dout[i];
+    }
+}
+
+// Head: 1x1 convolution C -> 1 (fp32 out) and its backward.
+__global__ void k_head(size_t P, int C, const bf16 *__restrict__ in, const float *__restrict__ w,
+                       const float *__restrict__ b, float *out) {
+    for (size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x; p < P; p += (size_t)gridDim.x * blockDim.x) {
+        float s = b[0];
+        for (int c = 0; c < C; ++c) s += w[c] * __bfloat162float(in[p * C + c]);
+        out[p] = s;
+    }
+}
+
+// MSE loss L = mean((out - tgt)^2): dout = 2 (out - tgt) / P; partial sums of (out - tgt)^2.
+__global__ void k_mse(size_t P, const float *__restrict__ out, const float *__restrict__ tgt,
+                      float *dout, double *part) {
+    __shared__ double red[32];
+    double s = 0.0;
+    for (size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x; p < P; p += (size_t)gridDim.x * blockDim.x) {
+        const float d = out[p] - tgt[p];
+        dout[p] = 2.0f * d / (float)P;
+        s += (double)d * (double)d;
+    }
+    s = block_sum(s, red);
+    if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+// Head backward: dW[c] += sum_p dout[p] in[p][c]; db += sum dout; din[p][c] = dout[p] w[c].
+__global__ void k_head_bwd(size_t P, int C, const bf16 *__restrict__ in, const float *__restrict__ w,
+                           const float *__restrict__ dout, float *dw, float *db, float *din) {
+    __shared__ float sw[256];
+    __shared__ float sb;
+    for (int c = threadIdx.x; c < C; c += blockDim.x) sw[c] = 0.f;
+    if (threadIdx.x == 0) sb = 0.f;
+    __syncthreads();
+    for (size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x; p < P; p += (size_t)gridDim.x * blockDim.x) {
+        const float g = dout[p];
+        atomicAdd(&sb, g);
+        for (int c = 0; c < C; ++c) {
+            atomicAdd(&sw[c], g * __bfloat162float(in[p * C + c]));
+            din[p * C + c] = g * w[c];
+        }
+    }
+    __syncthreads();
+    for (int c = threadIdx.x; c < C; c += blockDim.x) atomicAdd(&dw[c], sw[c]);
+    if (threadIdx.x == 0) atomicAdd(db, sb);
+}
+
+// Bias gradient: db[c] += sum_p dz[p][c].
+__global__ void k_bias_grad(size_t P, int C, const bf16 *__restrict__ dz, float *db) {
+    const int c = blockIdx.y * blockDim.x + threadIdx.x;
+    if (c >= C) return;
+    float s = 0.f;
+    for (size_t p = blockIdx.x; p < P; p += gridDim.x) s += __bfloat162float(dz[p * C + c]);
+    atomicAdd(&db[c], s);
+}
+
+// Pack the two network inputs (fp32 planes [B][2][H][W]) into NHWC bf16 [B][H][W][2].
+__global__ void k_pack_input(int B, int H, int W, const float *__restrict__ in, bf16 *out) {
+    const size_t total = (size_t)B * H * W;
+    for (size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x; p < total; p += (size_t)gridDim.x * blockDim.x) {
+        const size_t n = p / ((size_t)H * W), r = p - n * H * W;
+        out[2 * p] = __float2bfloat16(in[(n * 2) * H * W + r]);
+        out[2 * p + 1] = __float2bfloat16(in[(n * 2 + 1) * H * W + r]);
+    }
+}
+
+// Adam on fp32 masters; refresh the bf16 copies. step >= 1.
+__global__ void k_adam(size_t n, float *w, const float *__restrict__ g, float *m, float *v, bf16 *wb,
+                       float lr, float b1, float b2, float eps, float c1, float c2) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const float gi = g[i];
+        const float mi = b1 * m[i] + (1.f - b1) * gi;
+        const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+        m[i] = mi;
+        v[i] = vi;
+        const float wi = w[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+        w[i] = wi;
+        if (wb) wb[i] = __float2bfloat16(wi);
+    }
+}
+
+__global__ void k_to_bf16(size_t n, const float *__restrict__ in, bf16 *out) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        out[i] = __float2bfloat16(in[i]);
+}
+
+}  // namespace ivis

@@ -1,0 +1,357 @@
+// unet.cu -- the learned warm start: a 4-level U-Net that maps [dirty image, beam-weight map]
+// to an initial sky for the solver (see include/ivis.h, ivis_unet_*). Training and inference
+// run in this library's own kernels (kernels_unet.cuh).
+//
+// Architecture (base width c = 32): per level two 3x3 convolutions with ReLU; encoder widths
+// c, 2c, 4c, 8c at H, H/2, H/4, H/8 with 2x2 max pooling between levels; decoder: nearest 2x
+// upsampling, concatenation with the encoder output of the same level, two 3x3 convolutions
+// with ReLU (widths 4c, 2c, c); a 1x1 head to one output plane. Loss: mean squared error.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <string>
+#include <vector>
+
+#include "../../include/ivis.h"
+#include "kernels_unet.cuh"
+
+using namespace ivis;
+
+namespace {
+
+struct ConvSpec {
+    int src_a, ca, ua;  // tensor id, channels, upsampling of source a
+    int src_b, cb;      // tensor id and channels of source b (concatenated), or -1 / 0
+    int cout, level;    // output channels, resolution level (H >> level)
+    int out;            // output tensor id
+    size_t w_off, b_off;
+};
+
+thread_local std::string g_unet_err;
+
+}  // namespace
+
+struct ivis_unet_s {
+    int c = 32, max_batch = 0, max_hw = 0;
+    cudaStream_t stream = nullptr;
+    std::vector<ConvSpec> convs;
+    int ntensor = 0;
+    std::vector<int> tch, tlev;          // channels and level of each activation tensor
+    size_t nparam = 0, head_w = 0, head_b = 0;
+    float *w = nullptr, *g = nullptr, *m = nullptr, *v = nullptr;
+    bf16 *wb = nullptr;
+    std::vector<bf16 *> act;             // activations (bf16 NHWC)
+    std::vector<float *> dact;           // their gradients (fp32)
+    bf16 *col = nullptr, *dz = nullptr;
+    float *dcol = nullptr, *out = nullptr, *dout = nullptr, *tgt = nullptr;
+    double *part = nullptr, *part_h = nullptr;
+    size_t col_cap = 0, dz_cap = 0;
+    long long step = 0;
+    std::string err;
+};
+
+namespace {
+
+ivis_status ufail(ivis_unet_s *u, ivis_status s, const std::string &msg) {
+    if (u) u->err = msg;
+    g_unet_err = msg;
+    return s;
+}
+
+#define UCK(call)                                                                          \
+    do {                                                                                   \
+        cudaError_t e_ = (call);                                                           \
+        if (e_ != cudaSuccess) return ufail(u, IVIS_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+// tensor ids
+enum { T_IN = 0, T_A0, T_A1, T_P0, T_A2, T_A3, T_P1, T_A4, T_A5, T_P2, T_A6, T_A7, T_A8, T_A9,
+       T_A10, T_A11, T_A12, T_A13, T_COUNT };
+
+void build_net(ivis_unet_s *u) {
+    const int c = u->c;
+    u->ntensor = T_COUNT;
+    u->tch.assign(T_COUNT, 0);
+    u->tlev.assign(T_COUNT, 0);
+    auto T = [&](int id, int ch, int lev) { u->tch[id] = ch; u->tlev[id] = lev; };
+    T(T_IN, 2, 0);
+    T(T_A0, c, 0); T(T_A1, c, 0); T(T_P0, c, 1);
+    T(T_A2, 2 * c, 1); T(T_A3, 2 * c, 1); T(T_P1, 2 * c, 2);
+    T(T_A4, 4 * c, 2); T(T_A5, 4 * c, 2); T(T_P2, 4 * c, 3);
+    T(T_A6, 8 * c, 3); T(T_A7, 8 * c, 3);
+    T(T_A8, 4 * c, 2); T(T_A9, 4 * c, 2);
+    T(T_A10, 2 * c, 1); T(T_A11, 2 * c, 1);
+    T(T_A12, c, 0); T(T_A13, c, 0);
+    auto C = [&](int a, int ua, int b, int out) {
+        ConvSpec s{};
+        s.src_a = a; s.ca = u->tch[a]; s.ua = ua;
+        s.src_b = b; s.cb = b >= 0 ? u->tch[b] : 0;
+        s.cout = u->tch[out]; s.level = u->tlev[out]; s.out = out;
+        u->convs.push_back(s);
+    };
+    C(T_IN, 1, -1, T_A0); C(T_A0, 1, -1, T_A1);
+    C(T_P0, 1, -1, T_A2); C(T_A2, 1, -1, T_A3);
+    C(T_P1, 1, -1, T_A4); C(T_A4, 1, -1, T_A5);
+    C(T_P2, 1, -1, T_A6); C(T_A6, 1, -1, T_A7);
+    C(T_A7, 2, T_A5, T_A8); C(T_A8, 1, -1, T_A9);
+    C(T_A9, 2, T_A3, T_A10); C(T_A10, 1, -1, T_A11);
+    C(T_A11, 2, T_A1, T_A12); C(T_A12, 1, -1, T_A13);
+    size_t off = 0;
+    for (auto &s : u->convs) {
+        s.w_off = off;
+        off += (size_t)s.cout * 9 * (s.ca + s.cb);
+        s.b_off = off;
+        off += s.cout;
+    }
+    u->head_w = off;
+    off += c;
+    u->head_b = off;
+    off += 1;
+    u->nparam = off;
+}
+
+unsigned nblk(size_t n, int t = 256) { return (unsigned)std::min<size_t>((n + t - 1) / t, 148 * 32); }
+
+ivis_status ensure_scratch(ivis_unet_s *u, size_t col_elems, size_t dz_elems) {
+    if (col_elems > u->col_cap) {
+        if (u->col) cudaFree(u->col);
+        if (u->dcol) cudaFree(u->dcol);
+        u->col = nullptr; u->dcol = nullptr;
+        if (cudaMalloc(&u->col, col_elems * sizeof(bf16)) != cudaSuccess ||
+            cudaMalloc(&u->dcol, col_elems * sizeof(float)) != cudaSuccess) {
+            cudaGetLastError();
+            u->col_cap = 0;
+            return ufail(u, IVIS_ERR_OOM, "U-Net scratch allocation failed");
+        }
+        u->col_cap = col_elems;
+    }
+    if (dz_elems > u->dz_cap) {
+        if (u->dz) cudaFree(u->dz);
+        u->dz = nullptr;
+        if (cudaMalloc(&u->dz, dz_elems * sizeof(bf16)) != cudaSuccess) {
+            cudaGetLastError();
+            u->dz_cap = 0;
+            return ufail(u, IVIS_ERR_OOM, "U-Net scratch allocation failed");
+        }
+        u->dz_cap = dz_elems;
+    }
+    return IVIS_OK;
+}
+
+void gemm(cudaStream_t st, int ta, int tb, int epi, int M, int N, int K, const bf16 *A, const bf16 *B,
+          void *Cm, const float *bias, int relu, int splitk_chunk = 0) {
+    int kchunk = splitk_chunk > 0 ? splitk_chunk : K;
+    kchunk = (kchunk + GB_K - 1) / GB_K * GB_K;
+    dim3 g((M + GB_M - 1) / GB_M, (N + GB_N - 1) / GB_N, (K + kchunk - 1) / kchunk);
+    if (ta == 0 && tb == 1 && epi == 0) k_gemm_bf16<0, 1, 0><<<g, 256, 0, st>>>(M, N, K, kchunk, A, B, Cm, bias, relu);
+    else if (ta == 1 && tb == 0 && epi == 2) k_gemm_bf16<1, 0, 2><<<g, 256, 0, st>>>(M, N, K, kchunk, A, B, Cm, bias, relu);
+    else if (ta == 0 && tb == 0 && epi == 1) k_gemm_bf16<0, 0, 1><<<g, 256, 0, st>>>(M, N, K, kchunk, A, B, Cm, bias, relu);
+}
+
+ivis_status check_shape(ivis_unet_s *u, int B, int H, int W) {
+    if (B < 1 || B > u->max_batch) return ufail(u, IVIS_ERR_ARG, "batch outside [1, max_batch]");
+    if (H < 8 || W < 8 || H % 8 || W % 8) return ufail(u, IVIS_ERR_ARG, "H and W must be multiples of 8");
+    if ((size_t)H * W > (size_t)u->max_hw) return ufail(u, IVIS_ERR_ARG, "H*W above max_hw");
+    return IVIS_OK;
+}
+
+ivis_status forward_impl(ivis_unet_s *u, const float *in_dev, int B, int H, int W) {
+    cudaStream_t st = u->stream;
+    const size_t P0 = (size_t)B * H * W;
+    k_pack_input<<<nblk(P0), 256, 0, st>>>(B, H, W, in_dev, u->act[T_IN]);
+    for (size_t li = 0; li < u->convs.size(); ++li) {
+        const ConvSpec &s = u->convs[li];
+        const int h = H >> s.level, w = W >> s.level;
+        const size_t P = (size_t)B * h * w;
+        const int K = 9 * (s.ca + s.cb);
+        k_im2col<<<nblk(P * K), 256, 0, st>>>(B, h, w, u->act[s.src_a], s.ca, s.ua,
+                                               s.src_b >= 0 ? u->act[s.src_b] : nullptr, s.cb, u->col);
+        gemm(st, 0, 1, 0, (int)P, s.cout, K, u->col, u->wb + s.w_off, u->act[s.out], u->w + s.b_off, 1);
+        // pooling after the second convolution of each encoder level
+        if (s.out == T_A1 || s.out == T_A3 || s.out == T_A5) {
+            const int pid = s.out == T_A1 ? T_P0 : (s.out == T_A3 ? T_P1 : T_P2);
+            k_maxpool<<<nblk(P / 4 * s.cout), 256, 0, st>>>(B, h, w, s.cout, u->act[s.out], u->act[pid]);
+        }
+    }
+    k_head<<<nblk(P0), 256, 0, st>>>(P0, u->c, u->act[T_A13], u->w + u->head_w, u->w + u->head_b, u->out);
+    UCK(cudaGetLastError());
+    return IVIS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+ivis_status ivis_unet_create(int base_channels, int max_batch, int max_hw, void *stream, ivis_unet_t *out) {
+    if (!out) return ufail(nullptr, IVIS_ERR_ARG, "null output pointer");
+    *out = nullptr;
+    if (base_channels < 8 || base_channels > 64 || base_channels % 8)
+        return ufail(nullptr, IVIS_ERR_ARG, "base_channels must be a multiple of 8 in [8, 64]");
+    if (max_batch < 1 || max_hw < 64) return ufail(nullptr, IVIS_ERR_ARG, "max_batch >= 1 and max_hw >= 64 required");
+    ivis_unet_s *u = new (std::nothrow) ivis_unet_s();
+    if (!u) return ufail(nullptr, IVIS_ERR_OOM, "host allocation failed");
+    u->c = base_channels;
+    u->max_batch = max_batch;
+    u->max_hw = max_hw;
+    u->stream = (cudaStream_t)stream;
+    build_net(u);
+    bool ok = cudaMalloc(&u->w, u->nparam * 4) == cudaSuccess && cudaMalloc(&u->g, u->nparam * 4) == cudaSuccess &&
+              cudaMalloc(&u->m, u->nparam * 4) == cudaSuccess && cudaMalloc(&u->v, u->nparam * 4) == cudaSuccess &&
+              cudaMalloc(&u->wb, u->nparam * 2) == cudaSuccess;
+    u->act.assign(u->ntensor, nullptr);
+    u->dact.assign(u->ntensor, nullptr);
+    for (int t = 0; t < u->ntensor && ok; ++t) {
+        const size_t n = (size_t)max_batch * (max_hw >> (2 * u->tlev[t])) * u->tch[t];
+        ok = cudaMalloc(&u->act[t], n * sizeof(bf16)) == cudaSuccess &&
+             cudaMalloc(&u->dact[t], n * sizeof(float)) == cudaSuccess;
+    }
+    const size_t P0 = (size_t)max_batch * max_hw;
+    ok = ok && cudaMalloc(&u->out, P0 * 4) == cudaSuccess && cudaMalloc(&u->dout, P0 * 4) == cudaSuccess &&
+         cudaMalloc(&u->tgt, P0 * 4) == cudaSuccess && cudaMalloc(&u->part, 148 * 32 * sizeof(double)) == cudaSuccess &&
+         cudaMallocHost(&u->part_h, 148 * 32 * sizeof(double)) == cudaSuccess;
+    if (ok) {
+        cudaMemset(u->w, 0, u->nparam * 4);
+        cudaMemset(u->g, 0, u->nparam * 4);
+        cudaMemset(u->m, 0, u->nparam * 4);
+        cudaMemset(u->v, 0, u->nparam * 4);
+        cudaMemset(u->wb, 0, u->nparam * 2);
+    }
+    if (!ok) {
+        cudaGetLastError();
+        ivis_unet_destroy(u);
+        return ufail(nullptr, IVIS_ERR_OOM, "U-Net device allocation failed");
+    }
+    *out = u;
+    return IVIS_OK;
+}
+
+ivis_status ivis_unet_num_params(ivis_unet_t u, int64_t *n) {
+    if (!u || !n) return ufail(u, IVIS_ERR_ARG, "null pointer");
+    *n = (int64_t)u->nparam;
+    return IVIS_OK;
+}
+
+ivis_status ivis_unet_set_params(ivis_unet_t u, const float *host_params) {
+    if (!u || !host_params) return ufail(u, IVIS_ERR_ARG, "null pointer");
+    UCK(cudaMemcpyAsync(u->w, host_params, u->nparam * 4, cudaMemcpyHostToDevice, u->stream));
+    k_to_bf16<<<nblk(u->nparam), 256, 0, u->stream>>>(u->nparam, u->w, u->wb);
+    UCK(cudaMemsetAsync(u->m, 0, u->nparam * 4, u->stream));
+    UCK(cudaMemsetAsync(u->v, 0, u->nparam * 4, u->stream));
+    UCK(cudaStreamSynchronize(u->stream));
+    u->step = 0;
+    return IVIS_OK;
+}
+
+ivis_status ivis_unet_get_params(ivis_unet_t u, float *host_params) {
+    if (!u || !host_params) return ufail(u, IVIS_ERR_ARG, "null pointer");
+    UCK(cudaMemcpyAsync(host_params, u->w, u->nparam * 4, cudaMemcpyDeviceToHost, u->stream));
+    UCK(cudaStreamSynchronize(u->stream));
+    return IVIS_OK;
+}
+
+ivis_status ivis_unet_get_grads(ivis_unet_t u, float *host_grads) {
+    if (!u || !host_grads) return ufail(u, IVIS_ERR_ARG, "null pointer");
+    UCK(cudaMemcpyAsync(host_grads, u->g, u->nparam * 4, cudaMemcpyDeviceToHost, u->stream));
+    UCK(cudaStreamSynchronize(u->stream));
+    return IVIS_OK;
+}
+
+ivis_status ivis_unet_forward(ivis_unet_t u, const float *in_dev, float *out_dev, int B, int H, int W) {
+    if (!u || !in_dev || !out_dev) return ufail(u, IVIS_ERR_ARG, "null pointer");
+    ivis_status s = check_shape(u, B, H, W);
+    if (s) return s;
+    size_t colmax = 0;
+    for (auto &c : u->convs) colmax = std::max(colmax, (size_t)B * (H >> c.level) * (W >> c.level) * 9 * (c.ca + c.cb));
+    if ((s = ensure_scratch(u, colmax, 1))) return s;
+    if ((s = forward_impl(u, in_dev, B, H, W))) return s;
+    UCK(cudaMemcpyAsync(out_dev, u->out, (size_t)B * H * W * 4, cudaMemcpyDeviceToDevice, u->stream));
+    UCK(cudaStreamSynchronize(u->stream));
+    return IVIS_OK;
+}
+
+ivis_status ivis_unet_backward(ivis_unet_t u, const float *in_dev, const float *tgt_dev, int B, int H,
+                               int W, double *loss_out) {
+    if (!u || !in_dev || !tgt_dev) return ufail(u, IVIS_ERR_ARG, "null pointer");
+    ivis_status s = check_shape(u, B, H, W);
+    if (s) return s;
+    cudaStream_t st = u->stream;
+    size_t colmax = 0, dzmax = 0;
+    for (auto &c : u->convs) {
+        const size_t P = (size_t)B * (H >> c.level) * (W >> c.level);
+        colmax = std::max(colmax, P * 9 * (c.ca + c.cb));
+        dzmax = std::max(dzmax, P * c.cout);
+    }
+    if ((s = ensure_scratch(u, colmax, dzmax))) return s;
+    if ((s = forward_impl(u, in_dev, B, H, W))) return s;
+    const size_t P0 = (size_t)B * H * W;
+    UCK(cudaMemsetAsync(u->g, 0, u->nparam * 4, st));
+    const unsigned nb_mse = nblk(P0);
+    k_mse<<<nb_mse, 256, 0, st>>>(P0, u->out, tgt_dev, u->dout, u->part);
+    k_head_bwd<<<nblk(P0), 256, 0, st>>>(P0, u->c, u->act[T_A13], u->w + u->head_w, u->dout,
+                                         u->g + u->head_w, u->g + u->head_b, u->dact[T_A13]);
+    for (int li = (int)u->convs.size() - 1; li >= 0; --li) {
+        const ConvSpec &c = u->convs[li];
+        const int h = H >> c.level, w = W >> c.level;
+        const size_t P = (size_t)B * h * w;
+        const int K = 9 * (c.ca + c.cb);
+        k_relu_bwd<<<nblk(P * c.cout), 256, 0, st>>>(P * c.cout, u->dact[c.out], u->act[c.out], 1, u->dz);
+        k_im2col<<<nblk(P * K), 256, 0, st>>>(B, h, w, u->act[c.src_a], c.ca, c.ua,
+                                               c.src_b >= 0 ? u->act[c.src_b] : nullptr, c.cb, u->col);
+        // dW += dz^T col (split over pixels), db += sum dz, dcol = dz W
+        gemm(st, 1, 0, 2, c.cout, K, (int)P, u->dz, u->col, u->g + c.w_off, nullptr, 0, 8192);
+        dim3 gb(std::min<size_t>(P, 1024), (c.cout + 127) / 128);
+        k_bias_grad<<<gb, 128, 0, st>>>(P, c.cout, u->dz, u->g + c.b_off);
+        if (li == 0) continue;  // no gradient needed for the network input
+        gemm(st, 0, 0, 1, (int)P, K, c.cout, u->dz, u->wb + c.w_off, u->dcol, nullptr, 0);
+        const int ha = h / c.ua, wa = w / c.ua;
+        const size_t nsrc = (size_t)B * ha * wa * c.ca + (c.src_b >= 0 ? P * c.cb : 0);
+        k_col2im<<<nblk(nsrc), 256, 0, st>>>(B, h, w, u->dcol, u->dact[c.src_a], c.ca, c.ua,
+                                             c.src_b >= 0 ? u->dact[c.src_b] : nullptr, c.cb);
+        // the pooled tensor's gradient goes back into its pooling source, which already holds
+        // the gradient from the decoder's skip connection (that layer ran earlier in reverse)
+        if (c.src_a == T_P0 || c.src_a == T_P1 || c.src_a == T_P2) {
+            const int pre = c.src_a == T_P0 ? T_A1 : (c.src_a == T_P1 ? T_A3 : T_A5);
+            const int hp = h * 2, wp = w * 2;
+            k_maxpool_bwd<<<nblk((size_t)B * h * w * c.ca), 256, 0, st>>>(B, hp, wp, c.ca, u->act[pre],
+                                                                          u->dact[c.src_a], u->dact[pre]);
+        }
+    }
+    UCK(cudaGetLastError());
+    UCK(cudaMemcpyAsync(u->part_h, u->part, nb_mse * sizeof(double), cudaMemcpyDeviceToHost, st));
+    UCK(cudaStreamSynchronize(st));
+    if (loss_out) {
+        double sum = 0.0;
+        for (unsigned i = 0; i < nb_mse; ++i) sum += u->part_h[i];
+        *loss_out = sum / (double)P0;
+    }
+    return IVIS_OK;
+}
+
+ivis_status ivis_unet_adam_step(ivis_unet_t u, float lr, float beta1, float beta2, float eps) {
+    if (!u) return ufail(nullptr, IVIS_ERR_ARG, "null pointer");
+    u->step++;
+    const float c1 = 1.f - std::pow(beta1, (float)u->step), c2 = 1.f - std::pow(beta2, (float)u->step);
+    k_adam<<<nblk(u->nparam), 256, 0, u->stream>>>(u->nparam, u->w, u->g, u->m, u->v, u->wb, lr, beta1,
+                                                    beta2, eps, c1, c2);
+    UCK(cudaGetLastError());
+    UCK(cudaStreamSynchronize(u->stream));
+    return IVIS_OK;
+}
+
+ivis_status ivis_unet_destroy(ivis_unet_t u) {
+    if (!u) return IVIS_OK;
+    if (u->stream) cudaStreamSynchronize(u->stream);
+    void *ptrs[] = {u->w, u->g, u->m, u->v, u->wb, u->col, u->dz, u->dcol, u->out, u->dout, u->tgt, u->part};
+    for (void *q : ptrs)
+        if (q) cudaFree(q);
+    for (auto q : u->act) if (q) cudaFree(q);
+    for (auto q : u->dact) if (q) cudaFree(q);
+    if (u->part_h) cudaFreeHost(u->part_h);
+    delete u;
+    return IVIS_OK;
+}
+
+const char *ivis_unet_last_error(ivis_unet_t u) { return u ? u->err.c_str() : g_unet_err.c_str(); }
+
+}  // extern "C"

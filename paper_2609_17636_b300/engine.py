@@ -138,14 +138,20 @@ class Plan:
         return out
 
     def solve(self, sky: torch.Tensor, maxiter: int, m_hist: int = 10, pgtol: float = 1e-5,
-              ftol: float = 1e7 * 2.220446049250313e-16) -> dict:
-        """Overwrites ``sky`` with the solution; returns the solve report."""
+              ftol: float = 1e7 * 2.220446049250313e-16, f_target: float | None = None) -> dict:
+        """Overwrites ``sky`` with the solution; returns the solve report. With f_target the
+        solve also stops once Q_tot <= f_target."""
         if not sky.is_contiguous():
             raise ValueError("sky must be contiguous (it is updated in place)")
         self._sky(sky)
         rep = SolveReport()
-        _check(self.L, self._p, self.L.ivis_solve(self._p, ctypes.c_void_p(sky.data_ptr()), maxiter,
-                                                  m_hist, pgtol, ftol, ctypes.byref(rep)))
+        if f_target is None:
+            st = self.L.ivis_solve(self._p, ctypes.c_void_p(sky.data_ptr()), maxiter, m_hist, pgtol,
+                                   ftol, ctypes.byref(rep))
+        else:
+            st = self.L.ivis_solve_target(self._p, ctypes.c_void_p(sky.data_ptr()), maxiter, m_hist,
+                                          pgtol, ftol, float(f_target), ctypes.byref(rep))
+        _check(self.L, self._p, st)
         return {"iterations": rep.iterations, "evaluations": rep.evaluations, "f": rep.f,
                 "pg_inf": rep.pg_inf, "seconds": rep.seconds, "status": rep.status}
 
@@ -210,3 +216,84 @@ def plan_from_problem(prob, precision: str = "fp32", device="cuda", **kw) -> Pla
             plan.set_sd(c, torch.as_tensor(prob.tsd[c], dtype=torch.float32, device=device),
                         float(prob.sigma_sd[c]), prob.sd_fwhm_pix)
     return plan
+
+
+class UNet:
+    """The learned warm start (ivis_unet_*): [dirty image, beam-weight map] -> initial sky.
+    Argument marshalling only; the network runs in libivis.so's kernels."""
+
+    def __init__(self, base_channels: int = 32, max_batch: int = 8, max_hw: int = 256 * 256,
+                 stream: torch.cuda.Stream | None = None):
+        self.L = _lib.load()
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self._p = ctypes.c_void_p()
+        st = self.L.ivis_unet_create(base_channels, max_batch, max_hw,
+                                     ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(self._p))
+        self._check(st, None)
+        n = ctypes.c_int64()
+        self._check(self.L.ivis_unet_num_params(self._p, ctypes.byref(n)))
+        self.nparam = n.value
+        self.c = base_channels
+
+    def _check(self, status, plan="self"):
+        if status != 0:
+            msg = self.L.ivis_unet_last_error(self._p if plan == "self" else None)
+            raise IvisError(status, msg.decode() if msg else "")
+
+    def set_params(self, params):
+        import numpy as np
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        assert p.size == self.nparam
+        self._check(self.L.ivis_unet_set_params(self._p, ctypes.c_void_p(p.ctypes.data)))
+
+    def get_params(self):
+        import numpy as np
+        p = np.empty(self.nparam, np.float32)
+        self._check(self.L.ivis_unet_get_params(self._p, ctypes.c_void_p(p.ctypes.data)))
+        return p
+
+    def get_grads(self):
+        import numpy as np
+        g = np.empty(self.nparam, np.float32)
+        self._check(self.L.ivis_unet_get_grads(self._p, ctypes.c_void_p(g.ctypes.data)))
+        return g
+
+    def forward(self, inp: torch.Tensor) -> torch.Tensor:
+        inp = _dev_f32(inp)
+        B, two, H, W = inp.shape
+        out = torch.empty((B, H, W), dtype=torch.float32, device=inp.device)
+        self._check(self.L.ivis_unet_forward(self._p, ctypes.c_void_p(inp.data_ptr()),
+                                             ctypes.c_void_p(out.data_ptr()), B, H, W))
+        return out
+
+    def backward(self, inp: torch.Tensor, tgt: torch.Tensor) -> float:
+        inp, tgt = _dev_f32(inp), _dev_f32(tgt)
+        B, _, H, W = inp.shape
+        loss = ctypes.c_double()
+        self._check(self.L.ivis_unet_backward(self._p, ctypes.c_void_p(inp.data_ptr()),
+                                              ctypes.c_void_p(tgt.data_ptr()), B, H, W,
+                                              ctypes.byref(loss)))
+        return loss.value
+
+    def adam_step(self, lr: float, beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8):
+        self._check(self.L.ivis_unet_adam_step(self._p, lr, beta1, beta2, eps))
+
+    def close(self):
+        if self._p:
+            self.L.ivis_unet_destroy(self._p)
+            self._p = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def dirty_image(plan: Plan):
+    """(-grad Q(0) per channel, beam-weight map) as device tensors (ivis_dirty_image)."""
+    d = torch.empty(plan.shape, dtype=plan.dtype, device="cuda")
+    b = torch.empty(plan.shape[1:], dtype=plan.dtype, device="cuda")
+    _check(plan.L, plan._p, plan.L.ivis_dirty_image(plan._p, ctypes.c_void_p(d.data_ptr()),
+                                                    ctypes.c_void_p(b.data_ptr())))
+    return d, b

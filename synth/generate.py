@@ -9,7 +9,8 @@ __all__ = [
     "C_LIGHT", "HI_FREQ_HZ", "ARCSEC", "DEG", "make_rng", "antenna_layout",
     "baseline_pairs", "uvw_tracks", "gaussian_beam", "point_source_sky",
     "lognormal_sky", "hex_footprint", "flag_keep_mask", "complex_noise",
-    "gaussian_noise", "point_source_flux_law",
+    "gaussian_noise", "point_source_flux_law", "unet_layer_shapes", "unet_num_params",
+    "unet_init",
 ]
 
 C_LIGHT = 299_792_458.0
@@ -131,3 +132,36 @@ def point_source_flux_law(freq_hz: np.ndarray, s_ref: float = 5.0,
                           f_ref: float = 1.5e9, alpha: float = -1.0) -> np.ndarray:
     """Power-law input spectrum of the point-source test, S = s_ref (f/f_ref)^alpha."""
     return s_ref * (np.asarray(freq_hz) / f_ref) ** alpha
+
+
+# ----------------------------------------------------------------- warm-start network shapes
+def unet_layer_shapes(c: int = 32):
+    """Shapes of the warm-start U-Net's 3x3 layers in parameter order, as tuples
+    (cin_a, upsample_a, cin_b, cout, level): encoder 0a, 0b, 1a, 1b, 2a, 2b, 3a, 3b and decoder
+    2a, 2b, 1a, 1b, 0a, 0b (decoder 'a' layers read the upsampled deeper tensor, then the skip)."""
+    return [(2, 1, 0, c, 0), (c, 1, 0, c, 0),
+            (c, 1, 0, 2 * c, 1), (2 * c, 1, 0, 2 * c, 1),
+            (2 * c, 1, 0, 4 * c, 2), (4 * c, 1, 0, 4 * c, 2),
+            (4 * c, 1, 0, 8 * c, 3), (8 * c, 1, 0, 8 * c, 3),
+            (8 * c, 2, 4 * c, 4 * c, 2), (4 * c, 1, 0, 4 * c, 2),
+            (4 * c, 2, 2 * c, 2 * c, 1), (2 * c, 1, 0, 2 * c, 1),
+            (2 * c, 2, c, c, 0), (c, 1, 0, c, 0)]
+
+
+def unet_num_params(c: int = 32) -> int:
+    n = sum(co * 9 * (ca + cb) + co for (ca, _, cb, co, _) in unet_layer_shapes(c))
+    return n + c + 1
+
+
+def unet_init(c: int = 32, seed: int = 0) -> np.ndarray:
+    """He-normal weights (std sqrt(2 / fan_in)), zero biases, flat float32 vector in the
+    library's parameter order."""
+    rng = make_rng(seed)
+    out = []
+    for (ca, _, cb, co, _) in unet_layer_shapes(c):
+        fan = 9 * (ca + cb)
+        out.append(rng.standard_normal(co * fan) * math.sqrt(2.0 / fan))
+        out.append(np.zeros(co))
+    out.append(rng.standard_normal(c) * math.sqrt(1.0 / c))
+    out.append(np.zeros(1))
+    return np.concatenate(out).astype(np.float32)

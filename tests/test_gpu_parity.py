@@ -188,6 +188,21 @@ def test_dense_single_tile_many_chunks(precision):
     plan.close()
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_dirty_image_and_beam_weight_map(mosaic, precision):
+    """Inputs of the learned warm start: -grad Q(0) (the data term alone) and sum_k A_k^2."""
+    from paper_2609_17636_b300 import dirty_image
+    prob, *_ = mosaic
+    plan = _plan(prob, precision)
+    d, b = dirty_image(plan)
+    _, gq = oracle.data_cost_grad(prob, np.zeros_like(prob.sky_true))
+    assert rel_l2(d.cpu().numpy(), -gq) <= TOL[precision]
+    bw = sum(oracle.window_adjoint(np.asarray(prob.beams[k], np.float64) ** 2, *prob.centres[k], (prob.n, prob.n))
+             for k in range(prob.npoint))
+    assert rel_l2(b.cpu().numpy(), bw) <= TOL[precision]
+    plan.close()
+
+
 def test_invalid_inputs_are_rejected():
     from paper_2609_17636_b300 import IvisError, Plan
     plan = Plan(32, 1, 1, 16, 1e-4, "fp32")

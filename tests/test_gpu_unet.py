@@ -1,0 +1,76 @@
+"""The warm-start U-Net's CUDA forward and backward (BF16 tensor-core GEMMs, FP32 accumulate)
+against the FP64 oracle (oracle/unet.py), through the C ABI.
+
+Tolerances. BF16 keeps 8 significant bits (unit roundoff 2^-9 ~ 2e-3); activations and GEMM
+operands are rounded at each of the 15 layers, so the output and the loss stay within ~1e-2.
+The parameter gradient is far more sensitive: ReLU units and max-pool winners near a tie switch
+under perturbations of that size, which moves whole routes of the backward pass. That
+sensitivity is measured on the oracle itself: delta = the oracle's gradient change when only
+its weights are rounded to BF16 (3.5 % at c = 8, 7 % at c = 32 on these inputs). The GPU
+gradient must stay within 2 delta + 1e-2 of the oracle, point the same way (cosine >= 0.99),
+and so must the head's gradient block on its own."""
+import numpy as np
+import pytest
+import torch
+
+import synth
+from oracle import unet as ou
+
+pytestmark = pytest.mark.gpu
+
+
+def _batch(c, B, H, W, seed):
+    rng = np.random.default_rng(seed)
+    inp = rng.standard_normal((B, 2, H, W)).astype(np.float32)
+    inp[:, 1] = np.abs(inp[:, 1])
+    tgt = rng.standard_normal((B, H, W)).astype(np.float32)
+    return inp, tgt
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(np.ravel(a) - np.ravel(b)) / max(np.linalg.norm(np.ravel(b)), 1e-30))
+
+
+@pytest.mark.parametrize("c,H,W", [(8, 16, 16), (32, 32, 24)])
+def test_unet_forward_and_gradient_match_oracle(c, H, W):
+    from paper_2609_17636_b300 import UNet
+    B = 2
+    shapes = synth.unet_layer_shapes(c)
+    p = synth.unet_init(c, 3)
+    inp, tgt = _batch(c, B, H, W, 4)
+    net = UNet(c, max_batch=B, max_hw=H * W)
+    net.set_params(p)
+    out = net.forward(torch.as_tensor(inp, device="cuda")).cpu().numpy()
+    ref = ou.forward(p, shapes, c, inp)
+    assert _rel(out, ref) <= 2e-2, _rel(out, ref)
+    loss = net.backward(torch.as_tensor(inp, device="cuda"), torch.as_tensor(tgt, device="cuda"))
+    g = net.get_grads()
+    lref, gref = ou.loss_and_grad(p, shapes, c, inp, tgt)
+    pb = torch.as_tensor(p).to(torch.bfloat16).to(torch.float64).numpy()
+    _, gref_b = ou.loss_and_grad(pb, shapes, c, inp, tgt)
+    delta = _rel(gref_b, gref)
+    assert abs(loss - lref) <= 1e-2 * lref
+    assert _rel(g, gref) <= 2 * delta + 1e-2, (_rel(g, gref), delta)
+    cos = float(np.dot(g, gref) / (np.linalg.norm(g) * np.linalg.norm(gref)))
+    assert cos >= 0.99, cos
+    nh = c + 1
+    assert _rel(g[-nh:], gref[-nh:]) <= 2 * delta + 1e-2
+    net.close()
+
+
+def test_unet_adam_training_reduces_loss_on_a_fixed_batch():
+    from paper_2609_17636_b300 import UNet
+    c, B, H, W = 8, 4, 32, 32
+    inp, _ = _batch(c, B, H, W, 5)
+    tgt = np.maximum(inp[:, 0], 0) * 0.5  # a learnable map of the inputs
+    net = UNet(c, max_batch=B, max_hw=H * W)
+    net.set_params(synth.unet_init(c, 6))
+    x = torch.as_tensor(inp, device="cuda")
+    t = torch.as_tensor(tgt, device="cuda")
+    first = net.backward(x, t)
+    for _ in range(60):
+        net.backward(x, t)
+        net.adam_step(3e-3)
+    last = net.backward(x, t)
+    assert last < 0.3 * first, (first, last)
+    net.close()

@@ -69,6 +69,8 @@ typedef struct {
     double lambda_r;    /* weight of R (Eq. 14)                                            */
     double lambda_s;    /* weight of K (Eq. 14)                                            */
     int positivity;     /* 1: bound I >= 0 in ivis_solve (Sect. 3.4)                       */
+    int serial_pairs;   /* 1: process the (pointing, channel) pairs one at a time (the
+                           unbatched reference path); 0: all pairs in each kernel launch     */
 } ivis_config;
 
 typedef struct {

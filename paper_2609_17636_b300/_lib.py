@@ -40,7 +40,7 @@ class Config(ctypes.Structure):
                 ("nb", ctypes.c_int), ("cell_rad", ctypes.c_double), ("precision", ctypes.c_int),
                 ("nufft_tol", ctypes.c_double), ("kernel_width", ctypes.c_int),
                 ("lambda_r", ctypes.c_double), ("lambda_s", ctypes.c_double),
-                ("positivity", ctypes.c_int)]
+                ("positivity", ctypes.c_int), ("serial_pairs", ctypes.c_int)]
 
 
 class SolveReport(ctypes.Structure):

@@ -313,21 +313,26 @@ cudaError_t launch_forward(ivis_plan_s *p, const void *sky, int slot0 = 0, int n
     return cudaGetLastError();
 }
 
+// Adjoint passes for slots [slot0, slot0 + nslots) (all slots by default).
 template <typename T>
-cudaError_t launch_adjoint(ivis_plan_s *p) {
+cudaError_t launch_adjoint(ivis_plan_s *p, int slot0 = 0, int nslots = -1) {
     typedef typename cplx_of<T>::type C;
     const int nb = p->cfg.nb, nf = p->nf, tpl = nf / 16, lpb = 256 / tpl;
-    dim3 gc(nf >> p->logc_cols, p->nslot);
+    if (nslots < 0) nslots = p->nslot;
+    const C *G = (const C *)p->G + (size_t)slot0 * nf * nf;
+    C *rowbuf = (C *)p->rowbuf + (size_t)slot0 * nb * nf;
+    T *contrib = (T *)p->contrib + (size_t)slot0 * nb * nb;
+    dim3 gc(nf >> p->logc_cols, nslots);
     size_t smem_col = (size_t)fft_smem_elems(nf, 1 << p->logc_cols) * sizeof(C);
     cudaFuncSetAttribute(k_adj_cols<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_col);
     k_adj_cols<T><<<gc, tpl << p->logc_cols, smem_col, p->stream>>>(
-        (const C *)p->G, (C *)p->rowbuf, nb, p->lognf, p->logc_cols, (const C *)p->tw_d);
-    dim3 gr((nb + lpb - 1) / lpb, p->nslot);
+        G, rowbuf, nb, p->lognf, p->logc_cols, (const C *)p->tw_d);
+    dim3 gr((nb + lpb - 1) / lpb, nslots);
     size_t smem_row = (size_t)fft_smem_elems(nf, lpb) * sizeof(C);
     cudaFuncSetAttribute(k_adj_rows<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_row);
     k_adj_rows<T><<<gr, 256, smem_row, p->stream>>>(
-        (const C *)p->rowbuf, (const T *)p->beams_d, p->pinfo_d, (const T *)p->dinv_d,
-        (T *)p->contrib, p->cfg.n, nb, p->lognf, (const C *)p->tw_d);
+        rowbuf, (const T *)p->beams_d, p->pinfo_d + slot0, (const T *)p->dinv_d,
+        contrib, p->cfg.n, nb, p->lognf, (const C *)p->tw_d);
     return cudaGetLastError();
 }
 
@@ -401,19 +406,33 @@ cudaError_t enqueue_eval(ivis_plan_s *p, bool capture) {
         stage_begin(p, "zero_adjoint_grid", p->stream, si);
         cudaMemsetAsync(p->G, 0, (size_t)p->nslot * p->nf * p->nf * sizeof(C), p->stream);
         stage_end(p, p->stream, si);
-        stage_begin(p, "fwd_fft", p->stream, si);
-        if ((e = launch_forward<T>(p, p->x)) != cudaSuccess) return e;
-        launches += 2;
-        stage_end(p, p->stream, si);
-        stage_begin(p, "degrid_spread", p->stream, si);
-        if ((e = launch_grid_pass<T, MODE_COSTGRAD>(p, 0, p->nchunk, p->jpart, nullptr)) != cudaSuccess)
-            return e;
-        launches += 1;
-        stage_end(p, p->stream, si);
-        stage_begin(p, "adj_fft", p->stream, si);
-        if ((e = launch_adjoint<T>(p)) != cudaSuccess) return e;
-        launches += 2;
-        stage_end(p, p->stream, si);
+        if (p->cfg.serial_pairs) {
+            // one (pointing, channel) pair at a time: the unbatched reference path
+            stage_begin(p, "serial_pairs", p->stream, si);
+            for (int sl = 0; sl < p->nslot; ++sl) {
+                const int c0 = p->chunk_first[sl], nc = p->chunk_first[sl + 1] - c0;
+                if ((e = launch_forward<T>(p, p->x, sl, 1)) != cudaSuccess) return e;
+                if ((e = launch_grid_pass<T, MODE_COSTGRAD>(p, c0, nc, p->jpart + c0, nullptr)) != cudaSuccess)
+                    return e;
+                if ((e = launch_adjoint<T>(p, sl, 1)) != cudaSuccess) return e;
+                launches += 4 + (nc > 0 ? 1 : 0);
+            }
+            stage_end(p, p->stream, si);
+        } else {
+            stage_begin(p, "fwd_fft", p->stream, si);
+            if ((e = launch_forward<T>(p, p->x)) != cudaSuccess) return e;
+            launches += 2;
+            stage_end(p, p->stream, si);
+            stage_begin(p, "degrid_spread", p->stream, si);
+            if ((e = launch_grid_pass<T, MODE_COSTGRAD>(p, 0, p->nchunk, p->jpart, nullptr)) != cudaSuccess)
+                return e;
+            launches += 1;
+            stage_end(p, p->stream, si);
+            stage_begin(p, "adj_fft", p->stream, si);
+            if ((e = launch_adjoint<T>(p)) != cudaSuccess) return e;
+            launches += 2;
+            stage_end(p, p->stream, si);
+        }
     }
     if (fork) cudaStreamWaitEvent(p->stream, p->ev_join, 0);
     const int n = p->cfg.n, nchan = p->cfg.nchan;

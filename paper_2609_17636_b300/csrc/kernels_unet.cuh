@@ -48,23 +48,65 @@ k_gemm_bf16(int M, int N, int K, int kchunk, const bf16 *__restrict__ A, const b
 #pragma unroll
             for (int c = 0; c < 4; ++c) acc[i][j][c] = 0.f;
     const bf16 zero = __float2bfloat16(0.f);
+    // 16-byte staging when the contiguous dimension of each operand is a multiple of 8
+    // (split-K chunk ends are multiples of GB_K, so a vector never straddles kend)
+    const bool vecA = TA == 0 ? (K % 8 == 0) : (M % 8 == 0);
+    const bool vecB = TB == 1 ? (K % 8 == 0) : (N % 8 == 0);
     for (int k0 = kbeg; k0 < kend; k0 += GB_K) {
         // stage A tile [GB_M][GB_K] (m-major) and B tile [GB_N][GB_K] (n-major)
-        for (int i = tid; i < GB_M * GB_K; i += 256) {
-            int mm, kk;
-            if (TA == 0) { mm = i / GB_K; kk = i - mm * GB_K; } else { kk = i / GB_M; mm = i - kk * GB_M; }
-            const int gm = m0 + mm, gk = k0 + kk;
-            bf16 v = zero;
-            if (gm < M && gk < kend) v = TA == 0 ? A[(size_t)gm * K + gk] : A[(size_t)gk * M + gm];
-            As[mm][kk] = v;
+        if (vecA) {
+            for (int v = tid; v < GB_M * GB_K / 8; v += 256) {
+                uint4 q = make_uint4(0u, 0u, 0u, 0u);
+                if (TA == 0) {
+                    const int mm = v / (GB_K / 8), kk = (v % (GB_K / 8)) * 8;
+                    const int gm = m0 + mm, gk = k0 + kk;
+                    if (gm < M && gk < kend) q = *reinterpret_cast<const uint4 *>(A + (size_t)gm * K + gk);
+                    *reinterpret_cast<uint4 *>(&As[mm][kk]) = q;
+                } else {
+                    const int kk = v / (GB_M / 8), mm = (v % (GB_M / 8)) * 8;
+                    const int gm = m0 + mm, gk = k0 + kk;
+                    if (gm < M && gk < kend) q = *reinterpret_cast<const uint4 *>(A + (size_t)gk * M + gm);
+                    const bf16 *e = reinterpret_cast<const bf16 *>(&q);
+#pragma unroll
+                    for (int t = 0; t < 8; ++t) As[mm + t][kk] = e[t];
+                }
+            }
+        } else {
+            for (int i = tid; i < GB_M * GB_K; i += 256) {
+                int mm, kk;
+                if (TA == 0) { mm = i / GB_K; kk = i - mm * GB_K; } else { kk = i / GB_M; mm = i - kk * GB_M; }
+                const int gm = m0 + mm, gk = k0 + kk;
+                bf16 v = zero;
+                if (gm < M && gk < kend) v = TA == 0 ? A[(size_t)gm * K + gk] : A[(size_t)gk * M + gm];
+                As[mm][kk] = v;
+            }
         }
-        for (int i = tid; i < GB_N * GB_K; i += 256) {
-            int nn, kk;
-            if (TB == 1) { nn = i / GB_K; kk = i - nn * GB_K; } else { kk = i / GB_N; nn = i - kk * GB_N; }
-            const int gn = n0 + nn, gk = k0 + kk;
-            bf16 v = zero;
-            if (gn < N && gk < kend) v = TB == 1 ? B[(size_t)gn * K + gk] : B[(size_t)gk * N + gn];
-            Bs[nn][kk] = v;
+        if (vecB) {
+            for (int v = tid; v < GB_N * GB_K / 8; v += 256) {
+                uint4 q = make_uint4(0u, 0u, 0u, 0u);
+                if (TB == 1) {
+                    const int nn = v / (GB_K / 8), kk = (v % (GB_K / 8)) * 8;
+                    const int gn = n0 + nn, gk = k0 + kk;
+                    if (gn < N && gk < kend) q = *reinterpret_cast<const uint4 *>(B + (size_t)gn * K + gk);
+                    *reinterpret_cast<uint4 *>(&Bs[nn][kk]) = q;
+                } else {
+                    const int kk = v / (GB_N / 8), nn = (v % (GB_N / 8)) * 8;
+                    const int gn = n0 + nn, gk = k0 + kk;
+                    if (gn < N && gk < kend) q = *reinterpret_cast<const uint4 *>(B + (size_t)gk * N + gn);
+                    const bf16 *e = reinterpret_cast<const bf16 *>(&q);
+#pragma unroll
+                    for (int t = 0; t < 8; ++t) Bs[nn + t][kk] = e[t];
+                }
+            }
+        } else {
+            for (int i = tid; i < GB_N * GB_K; i += 256) {
+                int nn, kk;
+                if (TB == 1) { nn = i / GB_K; kk = i - nn * GB_K; } else { kk = i / GB_N; nn = i - kk * GB_N; }
+                const int gn = n0 + nn, gk = k0 + kk;
+                bf16 v = zero;
+                if (gn < N && gk < kend) v = TB == 1 ? B[(size_t)gn * K + gk] : B[(size_t)gk * N + gn];
+                Bs[nn][kk] = v;
+            }
         }
         __syncthreads();
 #pragma unroll
@@ -123,48 +165,59 @@ k_gemm_bf16(int M, int N, int K, int kchunk, const bf16 *__restrict__ A, const b
 // Input of a 3x3 'same' convolution at resolution H x W is the channel concatenation of
 // source a (ca channels, stored at H/ua x W/ua, nearest upsampling by ua in {1, 2}) and
 // source b (cb channels, H x W; cb may be 0). col[p][(dy*3 + dx) * (ca + cb) + ci].
+// One work item = (pixel, tap, 8-channel group); channel counts other than the first layer's
+// are multiples of 8, so a group is one 16-byte copy. Indices fit 32 bits (P * 9 * cin < 2^31
+// is checked by the host).
 __global__ void k_im2col(int B, int H, int W, const bf16 *__restrict__ a, int ca, int ua,
                          const bf16 *__restrict__ b, int cb, bf16 *col) {
     const int cin = ca + cb, K = 9 * cin;
-    const size_t total = (size_t)B * H * W * K;
+    const int HW = H * W, Ha = H / ua, Wa = W / ua;
+    const bool vec = (ca % 8 == 0) && (cb % 8 == 0);
+    const int G = vec ? cin / 8 : cin;  // groups per tap
+    const unsigned total = (unsigned)B * HW * 9u * (unsigned)G;
     const bf16 zero = __float2bfloat16(0.f);
-    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
-         i += (size_t)gridDim.x * blockDim.x) {
-        const size_t p = i / K;
-        const int k = (int)(i - p * K);
-        const int tap = k / cin, ci = k - tap * cin;
-        const int dy = tap / 3 - 1, dx = tap % 3 - 1;
-        const int n = (int)(p / ((size_t)H * W));
-        const int rem = (int)(p - (size_t)n * H * W);
-        const int y = rem / W + dy, x = rem % W + dx;
-        bf16 v = zero;
-        if (y >= 0 && y < H && x >= 0 && x < W) {
-            if (ci < ca) {
-                const int Ha = H / ua, Wa = W / ua;
-                v = a[(((size_t)n * Ha + y / ua) * Wa + x / ua) * ca + ci];
-            } else {
-                v = b[(((size_t)n * H + y) * W + x) * cb + (ci - ca)];
+    for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+        const unsigned grp = i % (unsigned)G;
+        const unsigned pt = i / (unsigned)G;  // pixel * 9 + tap
+        const unsigned tap = pt % 9u, p = pt / 9u;
+        const int n = (int)(p / (unsigned)HW), rem = (int)(p % (unsigned)HW);
+        const int y = rem / W + (int)(tap / 3u) - 1, x = rem % W + (int)(tap % 3u) - 1;
+        const bool in = y >= 0 && y < H && x >= 0 && x < W;
+        bf16 *dst = col + (size_t)p * K + tap * cin;
+        if (vec) {
+            const int ci = grp * 8;
+            uint4 v = make_uint4(0u, 0u, 0u, 0u);
+            if (in) {
+                const bf16 *src = ci < ca ? a + (((size_t)n * Ha + y / ua) * Wa + x / ua) * ca + ci
+                                          : b + (((size_t)n * H + y) * W + x) * cb + (ci - ca);
+                v = *reinterpret_cast<const uint4 *>(src);
             }
+            *reinterpret_cast<uint4 *>(dst + ci) = v;
+        } else {
+            const int ci = grp;
+            bf16 v = zero;
+            if (in) v = ci < ca ? a[(((size_t)n * Ha + y / ua) * Wa + x / ua) * ca + ci]
+                                : b[(((size_t)n * H + y) * W + x) * cb + (ci - ca)];
+            dst[ci] = v;
         }
-        col[i] = v;
     }
 }
 
-// Adjoint of k_im2col: from dcol (fp32, [p][K]) accumulate the gradients of sources a and b
-// (fp32, same layouts as the forward sources). Gather form: each source element sums the col
-// entries that read it, so no atomics are needed.
+// Adjoint of k_im2col: from dcol (fp32, [p][K]) form the gradients of sources a and b (fp32,
+// same layouts as the forward sources). Gather form: each source element sums the col
+// entries that read it, so no atomics are needed. One thread per (source pixel, channel).
 __global__ void k_col2im(int B, int H, int W, const float *__restrict__ dcol, float *da, int ca,
                          int ua, float *db, int cb) {
     const int cin = ca + cb, K = 9 * cin;
     const int Ha = H / ua, Wa = W / ua;
-    const size_t na = (size_t)B * Ha * Wa * ca, nbt = (size_t)B * H * W * cb;
-    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < na + nbt;
-         i += (size_t)gridDim.x * blockDim.x) {
+    const unsigned na = (unsigned)B * Ha * Wa * ca, nbt = (unsigned)B * H * W * cb;
+    for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < na + nbt; i += gridDim.x * blockDim.x) {
         float s = 0.f;
         if (i < na) {
-            const int ci = (int)(i % ca);
-            const size_t q = i / ca;
-            const int X = (int)(q % Wa), Y = (int)((q / Wa) % Ha), n = (int)(q / ((size_t)Wa * Ha));
+            const int ci = (int)(i % (unsigned)ca);
+            const unsigned q = i / (unsigned)ca;
+            const int X = (int)(q % (unsigned)Wa), Y = (int)((q / (unsigned)Wa) % (unsigned)Ha);
+            const int n = (int)(q / (unsigned)(Wa * Ha));
             for (int sy = 0; sy < ua; ++sy)
                 for (int sx = 0; sx < ua; ++sx) {
                     const int y = Y * ua + sy, x = X * ua + sx;  // pixel of the upsampled input
@@ -176,10 +229,11 @@ __global__ void k_col2im(int B, int H, int W, const float *__restrict__ dcol, fl
                 }
             da[i] = s;
         } else {
-            const size_t j = i - na;
-            const int ci = (int)(j % cb);
-            const size_t q = j / cb;
-            const int x = (int)(q % W), y = (int)((q / W) % H), n = (int)(q / ((size_t)W * H));
+            const unsigned j = i - na;
+            const int ci = (int)(j % (unsigned)cb);
+            const unsigned q = j / (unsigned)cb;
+            const int x = (int)(q % (unsigned)W), y = (int)((q / (unsigned)W) % (unsigned)H);
+            const int n = (int)(q / (unsigned)(W * H));
             for (int tap = 0; tap < 9; ++tap) {
                 const int yo = y - (tap / 3 - 1), xo = x - (tap % 3 - 1);
                 if (yo < 0 || yo >= H || xo < 0 || xo >= W) continue;

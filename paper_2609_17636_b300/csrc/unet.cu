@@ -153,6 +153,10 @@ ivis_status check_shape(ivis_unet_s *u, int B, int H, int W) {
     if (B < 1 || B > u->max_batch) return ufail(u, IVIS_ERR_ARG, "batch outside [1, max_batch]");
     if (H < 8 || W < 8 || H % 8 || W % 8) return ufail(u, IVIS_ERR_ARG, "H and W must be multiples of 8");
     if ((size_t)H * W > (size_t)u->max_hw) return ufail(u, IVIS_ERR_ARG, "H*W above max_hw");
+    // 32-bit work-item indices of the im2col / col2im kernels: P * 9 * cin < 2^31 per layer
+    for (auto &c : u->convs)
+        if ((size_t)B * (H >> c.level) * (W >> c.level) * 9 * (c.ca + c.cb) >= (size_t)1 << 31)
+            return ufail(u, IVIS_ERR_ARG, "batch x image too large for one call");
     return IVIS_OK;
 }
 

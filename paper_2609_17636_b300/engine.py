@@ -35,7 +35,7 @@ class Plan:
     def __init__(self, n: int, nchan: int, npoint: int, nb: int, cell_rad: float,
                  precision: str = "fp32", nufft_tol: float | None = None, kernel_width: int = 0,
                  lambda_r: float = 0.0, lambda_s: float = 0.0, positivity: bool = True,
-                 stream: torch.cuda.Stream | None = None):
+                 stream: torch.cuda.Stream | None = None, serial_pairs: bool = False):
         self.L = _lib.load()
         if precision not in ("fp32", "fp64"):
             raise ValueError("precision must be 'fp32' or 'fp64'")
@@ -45,7 +45,8 @@ class Plan:
             nufft_tol = 1e-6 if precision == "fp32" else 1e-11
         self.cfg = _lib.Config(n, nchan, npoint, nb, cell_rad,
                                IVIS_FP32 if precision == "fp32" else IVIS_FP64,
-                               nufft_tol, kernel_width, lambda_r, lambda_s, int(bool(positivity)))
+                               nufft_tol, kernel_width, lambda_r, lambda_s, int(bool(positivity)),
+                               int(bool(serial_pairs)))
         self.shape = (nchan, n, n)
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         self._p = ctypes.c_void_p()

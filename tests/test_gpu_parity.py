@@ -51,6 +51,22 @@ def test_cost_and_gradient_match_oracle(mosaic, precision):
     plan.close()
 
 
+def test_serial_pairs_path_matches_oracle_and_batched_path(mosaic):
+    """The unbatched FP64 path (one pair per launch sequence) used as the solver baseline."""
+    from paper_2609_17636_b300 import plan_from_problem
+    prob, x, f, g, terms = mosaic
+    xs = torch.as_tensor(x, device="cuda")
+    ps = plan_from_problem(prob, "fp64", serial_pairs=True)
+    pb = plan_from_problem(prob, "fp64")
+    fs, gs, _ = ps.cost_grad(xs)
+    fb, gb, _ = pb.cost_grad(xs)
+    assert abs(fs - f) <= 1e-9 * abs(f) and rel_l2(gs.cpu().numpy(), g) <= 1e-9
+    assert abs(fs - fb) <= 1e-12 * abs(fb) and rel_l2(gs.cpu().numpy(), gb.cpu().numpy()) <= 1e-12
+    assert ps.launches_per_eval() > pb.launches_per_eval()
+    ps.close()
+    pb.close()
+
+
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 def test_model_visibilities_match_direct_dft(mosaic, precision):
     prob, x, *_ = mosaic

@@ -141,7 +141,7 @@ def attach_data_gpu(prob, plan_fp64_like):
         prob.sigma_sd = sig
 
 
-def build_plan(prob, precision, serial=False):
+def build_plan(prob, precision, serial=False, autotune=False):
     from paper_2609_17636_b300 import plan_from_problem
     for pair in prob.pairs:
         if pair.vis is None:
@@ -149,7 +149,7 @@ def build_plan(prob, precision, serial=False):
     if prob.lambda_s != 0.0 and getattr(prob, "tsd", None) is None:
         prob.tsd = np.zeros((prob.nchan, prob.n, prob.n), np.float32)
         prob.sigma_sd = np.ones(prob.nchan)
-    return plan_from_problem(prob, precision, serial_pairs=serial)
+    return plan_from_problem(prob, precision, serial_pairs=serial, autotune=autotune)
 
 
 # ----------------------------------------------------------------- roofline model
@@ -180,7 +180,7 @@ def run_ivis(args, rank, world):
     datagen = build_plan(prob, "fp64" if args.config in ("c1", "c2") else "fp32")
     attach_data_gpu(prob, datagen)
     datagen.close()
-    plan = build_plan(prob, args.precision)
+    plan = build_plan(prob, args.precision, autotune=True)
     plan.prepare()
     x = torch.as_tensor(prob.sky_true * 0.5, dtype=plan.dtype, device=dev)
     g = torch.empty_like(x)
@@ -273,6 +273,7 @@ def run_ivis(args, rank, world):
            "config": {"workload": WORKLOAD[args.config], "config": args.config,
                       "vis_per_step_per_gpu": vis_step, "precision": args.precision,
                       "nufft_kernel_width": plan.nufft_params()[0],
+                      "autotune": plan.tuning()["decision"],
                       "l2": "flushed before every timed step (256 MiB write)",
                       "parallelism": f"replicas x{world} (independent problems)"},
            "roofline": roofline, "clocks": clocks, "e2e": e2e,

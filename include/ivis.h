@@ -71,6 +71,9 @@ typedef struct {
     int positivity;     /* 1: bound I >= 0 in ivis_solve (Sect. 3.4)                       */
     int serial_pairs;   /* 1: process the (pointing, channel) pairs one at a time (the
                            unbatched reference path); 0: all pairs in each kernel launch     */
+    int autotune;       /* 1: ivis_prepare times candidate grid-pass chunk sizes and column-
+                           FFT widths on this plan's data and keeps the fastest (cached per
+                           shape class in the file named by IVIS_AUTOTUNE_CACHE, if set)     */
 } ivis_config;
 
 typedef struct {
@@ -166,6 +169,10 @@ ivis_status ivis_get_nufft_params(ivis_plan_t plan, int *w, double *beta, int *n
 ivis_status ivis_profile(ivis_plan_t plan, int enable);
 ivis_status ivis_stage_times(ivis_plan_t plan, const char **names, double *ms, int cap,
                              int *count);
+
+/* Tuning in use: max visibilities per grid-pass chunk, columns per CTA of the column FFT
+ * passes, and a text record of the autotuner's decision (empty when not tuned). */
+ivis_status ivis_tuning(ivis_plan_t plan, int *chunk_cap, int *fft_cols, const char **text);
 
 /* Number of kernel launches one evaluation issues (the graph's kernel nodes). */
 ivis_status ivis_launches_per_eval(ivis_plan_t plan, int *count);

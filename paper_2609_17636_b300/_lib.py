@@ -24,7 +24,7 @@ EXPORTS = ["ivis_plan", "ivis_set_pointing", "ivis_set_vis", "ivis_set_sd", "ivi
            "ivis_cost_grad", "ivis_cost_grad_async", "ivis_get_stream", "ivis_cost_grad_host", "ivis_predict", "ivis_sd_predict",
            "ivis_solve", "ivis_get_nufft_params", "ivis_profile", "ivis_stage_times",
            "ivis_launches_per_eval", "ivis_sd_predict_noalloc", "ivis_destroy", "ivis_last_error",
-           "ivis_dirty_image", "ivis_solve_target", "ivis_unet_create", "ivis_unet_num_params", "ivis_unet_set_params",
+           "ivis_dirty_image", "ivis_solve_target", "ivis_tuning", "ivis_unet_create", "ivis_unet_num_params", "ivis_unet_set_params",
            "ivis_unet_get_params", "ivis_unet_forward", "ivis_unet_backward", "ivis_unet_get_grads",
            "ivis_unet_adam_step", "ivis_unet_destroy", "ivis_unet_last_error"]
 
@@ -40,7 +40,8 @@ class Config(ctypes.Structure):
                 ("nb", ctypes.c_int), ("cell_rad", ctypes.c_double), ("precision", ctypes.c_int),
                 ("nufft_tol", ctypes.c_double), ("kernel_width", ctypes.c_int),
                 ("lambda_r", ctypes.c_double), ("lambda_s", ctypes.c_double),
-                ("positivity", ctypes.c_int), ("serial_pairs", ctypes.c_int)]
+                ("positivity", ctypes.c_int), ("serial_pairs", ctypes.c_int),
+                ("autotune", ctypes.c_int)]
 
 
 class SolveReport(ctypes.Structure):
@@ -84,6 +85,7 @@ def load(path: str = LIB_PATH):
     L.ivis_last_error.argtypes = [vp]
     L.ivis_last_error.restype = ctypes.c_char_p
     L.ivis_dirty_image.argtypes = [vp, vp, vp]
+    L.ivis_tuning.argtypes = [vp, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(ctypes.c_char_p)]
     L.ivis_solve_target.argtypes = [vp, vp, i, i, d, d, d, ctypes.POINTER(SolveReport)]
     L.ivis_unet_create.argtypes = [i, i, i, vp, ctypes.POINTER(vp)]
     L.ivis_unet_num_params.argtypes = [vp, ctypes.POINTER(i64)]

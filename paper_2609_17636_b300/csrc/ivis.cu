@@ -12,6 +12,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -56,6 +57,8 @@ struct ivis_plan_s {
     double beta = 0.0;
     int tile = 32, ntx = 0, ntiles = 0;
     int logc_cols = 0;  // log2 columns per CTA in the column FFT passes
+    int chunk_cap = 1024;  // max visibilities per grid-pass chunk
+    std::string tuned;     // autotuner decision (for reporting)
     std::vector<double> dinv_h;
     void *dinv_d = nullptr, *tw_d = nullptr, *beams_d = nullptr;
     float *kpoly_d = nullptr;  // per-tap kernel polynomials (FP32 path)
@@ -595,6 +598,116 @@ void release_prepared(ivis_plan_s *p) {
     p->prepared = false;
 }
 
+// Work list of the grid pass: per slot, per non-empty tile, runs of at most cap visibilities.
+constexpr int TUNE_CHUNKS[] = {256, 512, 1024, 2048};
+
+void build_chunks(ivis_plan_s *p, int cap, std::vector<Chunk> &chunks, std::vector<int> &first) {
+    chunks.clear();
+    first.assign(p->nslot + 1, 0);
+    for (int sl = 0; sl < p->nslot; ++sl) {
+        const PairHost &ph = p->pairs[p->slot_pair[sl]];
+        first[sl] = (int)chunks.size();
+        int acc = 0;
+        for (int t = 0; t < p->ntiles; ++t) {
+            const int cnt = ph.tile_count[t];
+            for (int b = 0; b < cnt; b += cap) chunks.push_back(Chunk{sl, t, acc + b, acc + std::min(cnt, b + cap)});
+            acc += cnt;
+        }
+    }
+    first[p->nslot] = (int)chunks.size();
+}
+
+std::string tune_key(const ivis_plan_s *p) {
+    long long m = 0;
+    for (int sl = 0; sl < p->nslot; ++sl) m += p->pairs[p->slot_pair[sl]].m;
+    int mb = 0;  // visibility-count class: power of two
+    while ((1LL << mb) < m) ++mb;
+    return "nf=" + std::to_string(p->nf) + " w=" + std::to_string(p->W) + " fp64=" + std::to_string((int)p->fp64) +
+           " nslot=" + std::to_string(p->nslot) + " m2=" + std::to_string(mb);
+}
+
+// Autotuner: picks the grid-pass chunk size and the number of columns per CTA of the column
+// FFT passes by timing candidates on this plan's data (CUDA events, after a warm-up launch).
+// Decisions are cached per shape class in the file named by IVIS_AUTOTUNE_CACHE, if set.
+template <typename T>
+ivis_status autotune(ivis_plan_s *p) {
+    const std::string key = tune_key(p);
+    const char *path = std::getenv("IVIS_AUTOTUNE_CACHE");
+    int best_cap = -1, best_logc = -1;
+    if (path) {
+        if (FILE *f = std::fopen(path, "r")) {
+            char line[512];
+            while (std::fgets(line, sizeof line, f)) {
+                std::string l(line);
+                const size_t bar = l.find('|');
+                if (bar == std::string::npos || l.substr(0, bar) != key) continue;
+                int cap = 0, lc = -1;
+                if (std::sscanf(l.c_str() + bar + 1, "%d %d", &cap, &lc) == 2) { best_cap = cap; best_logc = lc; }
+            }
+            std::fclose(f);
+        }
+    }
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    auto timed = [&](auto &&fn) -> float {
+        fn();
+        cudaEventRecord(e0, p->stream);
+        for (int r = 0; r < 3; ++r) fn();
+        cudaEventRecord(e1, p->stream);
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        return ms;
+    };
+    const bool cached = best_cap > 0 && best_logc >= 0;
+    if (!cached) {
+        // column-FFT width: the feasible values around the shared-memory default
+        const size_t csz = sizeof(typename cplx_of<T>::type);
+        const int tpl = p->nf / 16, def = p->logc_cols;
+        float bt = 1e30f;
+        for (int lc = std::max(0, def - 1); lc <= std::min(4, def + 1); ++lc) {
+            if ((size_t)fft_smem_elems(p->nf, 1 << lc) * csz > 200 * 1024 || (tpl << lc) > (p->fp64 ? 512 : 1024) ||
+                (1 << lc) > p->nf)
+                continue;
+            p->logc_cols = lc;
+            const float ms = timed([&] { launch_forward<T>(p, p->x); launch_adjoint<T>(p); });
+            if (ms < bt) { bt = ms; best_logc = lc; }
+        }
+        // grid-pass chunk size
+        std::vector<Chunk> ch;
+        std::vector<int> first;
+        float bg = 1e30f;
+        for (int cap : TUNE_CHUNKS) {
+            build_chunks(p, cap, ch, first);
+            CK(cudaMemcpy(p->chunks_d, ch.data(), ch.size() * sizeof(Chunk), cudaMemcpyHostToDevice));
+            const int n = (int)ch.size();
+            const float ms = timed([&] { launch_grid_pass<T, MODE_COSTGRAD>(p, 0, n, p->jpart, nullptr); });
+            if (ms < bg) { bg = ms; best_cap = cap; }
+        }
+        CK(cudaGetLastError());
+        if (path) {
+            if (FILE *f = std::fopen(path, "a")) {
+                std::fprintf(f, "%s|%d %d\n", key.c_str(), best_cap, best_logc);
+                std::fclose(f);
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    p->logc_cols = best_logc;
+    p->chunk_cap = best_cap;
+    std::vector<Chunk> ch;
+    build_chunks(p, p->chunk_cap, ch, p->chunk_first);
+    p->nchunk = (int)ch.size();
+    CK(cudaMemcpy(p->chunks_d, ch.data(), ch.size() * sizeof(Chunk), cudaMemcpyHostToDevice));
+    CK(cudaMemsetAsync(p->G, 0, (size_t)p->nslot * p->nf * p->nf * sizeof(typename cplx_of<T>::type), p->stream));
+    CK(cudaStreamSynchronize(p->stream));
+    p->tuned = key + " -> chunk " + std::to_string(p->chunk_cap) + ", fft columns per CTA " +
+               std::to_string(1 << p->logc_cols) + (cached ? " (cached)" : " (timed)");
+    return IVIS_OK;
+}
+
 template <typename T>
 ivis_status prepare_impl(ivis_plan_s *p) {
     typedef typename cplx_of<T>::type C;
@@ -617,8 +730,6 @@ ivis_status prepare_impl(ivis_plan_s *p) {
     std::vector<PairInfo> pinfo(p->nslot);
     std::vector<PairData<T>> pdata(p->nslot);
     std::vector<Chunk> chunks;
-    p->chunk_first.assign(p->nslot + 1, 0);
-    const int CH = 1024;
     std::vector<int> chan_start(c.nchan + 1, 0), chan_list;
     for (int sl = 0; sl < p->nslot; ++sl) {
         int pi_ = p->slot_pair[sl];
@@ -630,17 +741,16 @@ ivis_status prepare_impl(ivis_plan_s *p) {
         pdata[sl].w = (const T *)ph.w;
         pdata[sl].orig = ph.orig;
         pdata[sl].m = ph.m;
-        p->chunk_first[sl] = (int)chunks.size();
-        int acc = 0;
-        for (int t = 0; t < p->ntiles; ++t) {
-            int cnt = ph.tile_count[t];
-            for (int b = 0; b < cnt; b += CH)
-                chunks.push_back(Chunk{sl, t, acc + b, acc + std::min(cnt, b + CH)});
-            acc += cnt;
-        }
     }
-    p->chunk_first[p->nslot] = (int)chunks.size();
+    build_chunks(p, p->chunk_cap, chunks, p->chunk_first);
     p->nchunk = (int)chunks.size();
+    size_t max_chunks = 0;  // work lists of every autotuner candidate fit the device arrays
+    {
+        std::vector<Chunk> tmp;
+        std::vector<int> tf;
+        build_chunks(p, TUNE_CHUNKS[0], tmp, tf);
+        max_chunks = std::max(tmp.size(), chunks.size());
+    }
     for (int ch = 0; ch < c.nchan; ++ch) {
         chan_start[ch] = (int)chan_list.size();
         for (int sl = 0; sl < p->nslot; ++sl)
@@ -655,7 +765,8 @@ ivis_status prepare_impl(ivis_plan_s *p) {
     };
     if ((s = up((void **)&p->pinfo_d, pinfo.data(), pinfo.size() * sizeof(PairInfo)))) return s;
     if ((s = up(&p->pdata_d, pdata.data(), pdata.size() * sizeof(PairData<T>)))) return s;
-    if ((s = up((void **)&p->chunks_d, chunks.data(), chunks.size() * sizeof(Chunk)))) return s;
+    if ((s = alloc(p, (void **)&p->chunks_d, max_chunks * sizeof(Chunk)))) return s;
+    if (!chunks.empty()) CK(cudaMemcpy(p->chunks_d, chunks.data(), chunks.size() * sizeof(Chunk), cudaMemcpyHostToDevice));
     if ((s = up((void **)&p->chan_start_d, chan_start.data(), chan_start.size() * sizeof(int)))) return s;
     if ((s = up((void **)&p->chan_list_d, chan_list.data(), chan_list.size() * sizeof(int)))) return s;
     const size_t nf2 = (size_t)p->nf * p->nf;
@@ -666,7 +777,7 @@ ivis_status prepare_impl(ivis_plan_s *p) {
     if ((s = alloc(p, &p->contrib, (size_t)p->nslot * c.nb * c.nb * sizeof(T)))) return s;
     if ((s = alloc(p, &p->x, npix * sizeof(T)))) return s;
     if ((s = alloc(p, &p->g, npix * sizeof(T)))) return s;
-    if ((s = alloc(p, (void **)&p->jpart, (size_t)std::max(1, p->nchunk) * sizeof(double)))) return s;
+    if ((s = alloc(p, (void **)&p->jpart, std::max<size_t>(1, max_chunks) * sizeof(double)))) return s;
     p->nrpart = (int)((npix + 255) / 256);
     if ((s = alloc(p, (void **)&p->rpart, (size_t)p->nrpart * sizeof(double)))) return s;
     if ((s = alloc(p, (void **)&p->cost_d, 4 * sizeof(double)))) return s;
@@ -704,6 +815,7 @@ ivis_status prepare_impl(ivis_plan_s *p) {
     if (!p->kpart && (s = alloc(p, (void **)&p->kpart, sizeof(double)))) return s;
     if ((s = solver_alloc<T>(p->solver, npix))) return fail(p, s, "solver buffers: out of device memory");
     p->prepared = true;
+    if (c.autotune && p->nslot > 0 && (s = autotune<T>(p))) { p->prepared = false; return s; }
     if ((s = capture_graph(p))) { p->prepared = false; return s; }
     return IVIS_OK;
 }
@@ -1217,6 +1329,16 @@ ivis_status ivis_cost_grad_async(ivis_plan_t p, const void *sky_dev, void *grad_
     if ((s = launch_eval(p, false))) return s;
     CK(cudaMemcpyAsync(cost_dev, p->cost_d, 4 * sizeof(double), cudaMemcpyDeviceToDevice, p->stream));
     CK(cudaMemcpyAsync(grad_dev, p->g, bytes, cudaMemcpyDeviceToDevice, p->stream));
+    return IVIS_OK;
+}
+
+ivis_status ivis_tuning(ivis_plan_t p, int *chunk_cap, int *fft_cols, const char **text) {
+    if (!p) return fail(nullptr, IVIS_ERR_ARG, "null plan");
+    ivis_status s = ensure_prepared(p);
+    if (s) return s;
+    if (chunk_cap) *chunk_cap = p->chunk_cap;
+    if (fft_cols) *fft_cols = 1 << p->logc_cols;
+    if (text) *text = p->tuned.c_str();
     return IVIS_OK;
 }
 

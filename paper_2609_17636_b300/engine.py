@@ -35,7 +35,8 @@ class Plan:
     def __init__(self, n: int, nchan: int, npoint: int, nb: int, cell_rad: float,
                  precision: str = "fp32", nufft_tol: float | None = None, kernel_width: int = 0,
                  lambda_r: float = 0.0, lambda_s: float = 0.0, positivity: bool = True,
-                 stream: torch.cuda.Stream | None = None, serial_pairs: bool = False):
+                 stream: torch.cuda.Stream | None = None, serial_pairs: bool = False,
+                 autotune: bool = False):
         self.L = _lib.load()
         if precision not in ("fp32", "fp64"):
             raise ValueError("precision must be 'fp32' or 'fp64'")
@@ -46,7 +47,7 @@ class Plan:
         self.cfg = _lib.Config(n, nchan, npoint, nb, cell_rad,
                                IVIS_FP32 if precision == "fp32" else IVIS_FP64,
                                nufft_tol, kernel_width, lambda_r, lambda_s, int(bool(positivity)),
-                               int(bool(serial_pairs)))
+                               int(bool(serial_pairs)), int(bool(autotune)))
         self.shape = (nchan, n, n)
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         self._p = ctypes.c_void_p()
@@ -173,6 +174,14 @@ class Plan:
         cnt = ctypes.c_int()
         _check(self.L, self._p, self.L.ivis_stage_times(self._p, names, ms, cap, ctypes.byref(cnt)))
         return {names[i].decode(): ms[i] for i in range(min(cnt.value, cap))}
+
+    def tuning(self) -> dict:
+        cap, cols = ctypes.c_int(), ctypes.c_int()
+        txt = ctypes.c_char_p()
+        _check(self.L, self._p, self.L.ivis_tuning(self._p, ctypes.byref(cap), ctypes.byref(cols),
+                                                   ctypes.byref(txt)))
+        return {"chunk_cap": cap.value, "fft_cols": cols.value,
+                "decision": txt.value.decode() if txt.value else ""}
 
     def launches_per_eval(self) -> int:
         c = ctypes.c_int()

@@ -67,6 +67,26 @@ def test_serial_pairs_path_matches_oracle_and_batched_path(mosaic):
     pb.close()
 
 
+def test_autotuned_plan_matches_oracle_and_caches_its_choice(mosaic, tmp_path, monkeypatch):
+    from paper_2609_17636_b300 import plan_from_problem
+    prob, x, f, g, terms = mosaic
+    cache = tmp_path / "tune.txt"
+    monkeypatch.setenv("IVIS_AUTOTUNE_CACHE", str(cache))
+    xs = torch.as_tensor(x, dtype=torch.float32, device="cuda")
+    p1 = plan_from_problem(prob, "fp32", autotune=True)
+    f1, g1, _ = p1.cost_grad(xs)
+    t1 = p1.tuning()
+    assert t1["chunk_cap"] in (256, 512, 1024, 2048) and t1["fft_cols"] in (1, 2, 4, 8, 16)
+    assert "(timed)" in t1["decision"] and cache.read_text().count("|") == 1
+    assert abs(f1 - f) <= TOL["fp32"] * abs(f) and rel_l2(g1.cpu().numpy(), g) <= TOL["fp32"]
+    p2 = plan_from_problem(prob, "fp32", autotune=True)
+    p2.prepare()
+    t2 = p2.tuning()
+    assert "(cached)" in t2["decision"] and t2["chunk_cap"] == t1["chunk_cap"]
+    p1.close()
+    p2.close()
+
+
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 def test_model_visibilities_match_direct_dft(mosaic, precision):
     prob, x, *_ = mosaic

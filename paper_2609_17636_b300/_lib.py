@@ -26,7 +26,8 @@ EXPORTS = ["ivis_plan", "ivis_set_pointing", "ivis_set_vis", "ivis_set_sd", "ivi
            "ivis_launches_per_eval", "ivis_sd_predict_noalloc", "ivis_destroy", "ivis_last_error",
            "ivis_dirty_image", "ivis_solve_target", "ivis_tuning", "ivis_unet_create", "ivis_unet_num_params", "ivis_unet_set_params",
            "ivis_unet_get_params", "ivis_unet_forward", "ivis_unet_backward", "ivis_unet_get_grads",
-           "ivis_unet_adam_step", "ivis_unet_destroy", "ivis_unet_last_error"]
+           "ivis_unet_adam_step", "ivis_unet_use_tcgen05", "ivis_unet_destroy",
+           "ivis_unet_last_error"]
 
 
 class IvisError(RuntimeError):
@@ -95,6 +96,7 @@ def load(path: str = LIB_PATH):
     L.ivis_unet_backward.argtypes = [vp, vp, vp, i, i, i, dp]
     L.ivis_unet_get_grads.argtypes = [vp, vp]
     L.ivis_unet_adam_step.argtypes = [vp, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float]
+    L.ivis_unet_use_tcgen05.argtypes = [vp, i]
     L.ivis_unet_destroy.argtypes = [vp]
     L.ivis_unet_last_error.argtypes = [vp]
     L.ivis_unet_last_error.restype = ctypes.c_char_p

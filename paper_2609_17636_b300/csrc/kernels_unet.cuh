@@ -161,6 +161,154 @@ k_gemm_bf16(int M, int N, int K, int kchunk, const bf16 *__restrict__ A, const b
             }
 }
 
+// ------------------------------------------------------- tcgen05 GEMM (forward convolution)
+// C[M x N] = relu(A[M x K] B[N x K]^T + bias) in bf16, both operands K-major bf16, FP32
+// accumulation in tensor memory. One CTA of 4 warps per 128 x BN output tile: the K loop
+// stages a 128 x 64 slice of A and a BN x 64 slice of B in shared memory in the canonical
+// no-swizzle layout (8-row x 16-byte core matrices; core matrices adjacent in K are LBO bytes
+// apart, adjacent in M/N 128 bytes apart), one thread issues four tcgen05.mma (K = 16 each),
+// and tcgen05.commit signals that stage's mbarrier. Two stages: slice k + 1 is staged while
+// the tensor cores work on slice k; a stage is reused only after its barrier (bounded wait). The epilogue reads the accumulator rows with tcgen05.ld (warp w owns TMEM lanes
+// 32w..32w+31 = tile rows), adds the bias, applies the ReLU and stores bf16.
+constexpr int TC_BM = 128, TC_BK = 64;
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    // start address >> 4 (bits 0-13), leading byte offset >> 4 (16-29), stride byte offset
+    // >> 4 (32-45), descriptor version 1 (bit 46), no swizzle (bits 61-63 = 0)
+    return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+template <int BN>
+__global__ void __launch_bounds__(128)
+k_gemm_tc(int M, int N, int K, const bf16 *__restrict__ A, const bf16 *__restrict__ B,
+          bf16 *C, const float *__restrict__ bias, int relu, int *err) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    constexpr int STAGE = (TC_BM + BN) * TC_BK;  // bf16 elements per stage (A then B)
+    bf16 *stage0 = reinterpret_cast<bf16 *>(smem_raw);
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(stage0 + 2 * STAGE);  // one per stage
+    uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(mbar + 2);
+    constexpr int NCOL = BN < 32 ? 32 : BN;  // TMEM columns (power of 2)
+    constexpr uint32_t LBO_A = (TC_BM / 8) * 128, LBO_B = (BN / 8) * 128;
+    constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
+                               ((uint32_t)(TC_BM >> 4) << 24);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int m0 = blockIdx.x * TC_BM, n0 = blockIdx.y * BN;
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     :: "r"(smem_u32(tmem_holder)), "r"(NCOL));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(mbar)));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(mbar + 1)));
+        asm volatile("fence.mbarrier_init.release.cluster;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t tmem = *tmem_holder;
+    const bool vec = (K % 8) == 0;
+    const int nk = (K + TC_BK - 1) / TC_BK;
+    uint32_t phase[2] = {0u, 0u};
+    bool ok = true;
+    // bounded wait on stage s's barrier (about two seconds at most)
+    auto wait_stage = [&](int st) {
+        uint32_t done = 0;
+        const long long t_start = clock64();
+        while (!done) {
+            asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+                         "selp.u32 %0, 1, 0, p;\n}\n" : "=r"(done) : "r"(smem_u32(mbar + st)), "r"(phase[st]));
+            if (!done && clock64() - t_start > 4000000000LL) break;
+        }
+        if (!done) { ok = false; if (err) atomicExch(err, 1); }
+        phase[st] ^= 1u;
+    };
+    for (int kb = 0; kb < nk && ok; ++kb) {
+        const int st = kb & 1;
+        if (kb >= 2) wait_stage(st);  // the MMAs of slice kb - 2 used this stage
+        if (!ok) break;
+        bf16 *As = stage0 + st * STAGE, *Bs = As + TC_BM * TC_BK;
+        const int k0 = kb * TC_BK;
+        for (int v = tid; v < (TC_BM + BN) * (TC_BK / 8); v += 128) {
+            const bool isA = v < TC_BM * (TC_BK / 8);
+            const int vv = isA ? v : v - TC_BM * (TC_BK / 8);
+            const int row = vv / (TC_BK / 8), kg = vv % (TC_BK / 8);
+            const int grow = (isA ? m0 : n0) + row, gk = k0 + kg * 8;
+            const int rows = isA ? M : N;
+            const bf16 *src = isA ? A : B;
+            uint4 q = make_uint4(0u, 0u, 0u, 0u);
+            if (grow < rows) {
+                if (vec) {
+                    if (gk < K) q = *reinterpret_cast<const uint4 *>(src + (size_t)grow * K + gk);
+                } else {
+                    bf16 *e = reinterpret_cast<bf16 *>(&q);
+                    for (int t = 0; t < 8; ++t)
+                        if (gk + t < K) e[t] = src[(size_t)grow * K + gk + t];
+                }
+            }
+            const uint32_t lbo = isA ? LBO_A : LBO_B;
+            unsigned char *dst = reinterpret_cast<unsigned char *>(isA ? As : Bs) + kg * lbo +
+                                 (row >> 3) * 128 + (row & 7) * 16;
+            *reinterpret_cast<uint4 *>(dst) = q;
+        }
+        asm volatile("fence.proxy.async.shared::cta;");
+        __syncthreads();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;");
+#pragma unroll
+            for (int kk = 0; kk < TC_BK / 16; ++kk) {
+                const uint64_t ad = umma_desc(smem_u32(As) + kk * 2 * LBO_A, LBO_A, 128);
+                const uint64_t bd = umma_desc(smem_u32(Bs) + kk * 2 * LBO_B, LBO_B, 128);
+                const uint32_t acc = (kb > 0 || kk > 0) ? 1u : 0u;
+                asm volatile(
+                    "{\n.reg .pred p;\nsetp.ne.u32 p, %4, 0;\n"
+                    "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+                    :: "r"(tmem), "l"(ad), "l"(bd), "r"(IDESC), "r"(acc));
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                         :: "r"(smem_u32(mbar + st)));
+        }
+    }
+    // drain: the last one or two slices' MMAs (commits complete in issue order)
+    if (ok && nk >= 2) wait_stage(nk & 1);
+    if (ok && nk >= 1) wait_stage((nk - 1) & 1);
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    __syncthreads();
+    if (ok) {
+        const int row = m0 + warp * 32 + lane;
+        for (int c0 = 0; c0 < BN; c0 += 16) {
+            uint32_t r[16];
+            const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+            asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+                         "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
+                           "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]),
+                           "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+                         : "r"(taddr));
+            asm volatile("tcgen05.wait::ld.sync.aligned;");
+            if (row < M) {
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    const int col = n0 + c0 + j;
+                    if (col >= N) continue;
+                    float v = __uint_as_float(r[j]) + (bias ? bias[col] : 0.f);
+                    if (relu) v = fmaxf(v, 0.f);
+                    C[(size_t)row * N + col] = __float2bfloat16(v);
+                }
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(NCOL));
+}
+
 // ----------------------------------------------------------------------------- im2col
 // Input of a 3x3 'same' convolution at resolution H x W is the channel concatenation of
 // source a (ca channels, stored at H/ua x W/ua, nearest upsampling by ua in {1, 2}) and

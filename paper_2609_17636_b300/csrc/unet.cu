@@ -48,6 +48,8 @@ struct ivis_unet_s {
     double *part = nullptr, *part_h = nullptr;
     size_t col_cap = 0, dz_cap = 0;
     long long step = 0;
+    bool use_tc = true;   // forward convolutions on tcgen05 (else mma.sync)
+    int *tc_err = nullptr;
     std::string err;
 };
 
@@ -139,6 +141,28 @@ ivis_status ensure_scratch(ivis_unet_s *u, size_t col_elems, size_t dz_elems) {
     return IVIS_OK;
 }
 
+template <int BN>
+void gemm_tc_launch(cudaStream_t st, int M, int N, int K, const bf16 *A, const bf16 *B, bf16 *C,
+                    const float *bias, int relu, int *err) {
+    constexpr int NCOL = BN < 32 ? 32 : BN;
+    const size_t need = (size_t)2 * (TC_BM + BN) * TC_BK * sizeof(bf16) + 32;
+    // keep the CTAs resident on one SM within its 512 TMEM columns
+    const int allowed = 512 / NCOL;
+    const size_t smem = std::max(need, (size_t)(228 * 1024) / (allowed + 1) + 1024);
+    cudaFuncSetAttribute(k_gemm_tc<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    dim3 g((M + TC_BM - 1) / TC_BM, (N + BN - 1) / BN);
+    k_gemm_tc<BN><<<g, 128, smem, st>>>(M, N, K, A, B, C, bias, relu, err);
+}
+
+void gemm_tc(cudaStream_t st, int M, int N, int K, const bf16 *A, const bf16 *B, bf16 *C,
+             const float *bias, int relu, int *err) {
+    if (N <= 16) gemm_tc_launch<16>(st, M, N, K, A, B, C, bias, relu, err);
+    else if (N <= 32) gemm_tc_launch<32>(st, M, N, K, A, B, C, bias, relu, err);
+    else if (N <= 64) gemm_tc_launch<64>(st, M, N, K, A, B, C, bias, relu, err);
+    else if (N <= 128) gemm_tc_launch<128>(st, M, N, K, A, B, C, bias, relu, err);
+    else gemm_tc_launch<256>(st, M, N, K, A, B, C, bias, relu, err);
+}
+
 void gemm(cudaStream_t st, int ta, int tb, int epi, int M, int N, int K, const bf16 *A, const bf16 *B,
           void *Cm, const float *bias, int relu, int splitk_chunk = 0) {
     int kchunk = splitk_chunk > 0 ? splitk_chunk : K;
@@ -171,7 +195,10 @@ ivis_status forward_impl(ivis_unet_s *u, const float *in_dev, int B, int H, int 
         const int K = 9 * (s.ca + s.cb);
         k_im2col<<<nblk(P * K), 256, 0, st>>>(B, h, w, u->act[s.src_a], s.ca, s.ua,
                                                s.src_b >= 0 ? u->act[s.src_b] : nullptr, s.cb, u->col);
-        gemm(st, 0, 1, 0, (int)P, s.cout, K, u->col, u->wb + s.w_off, u->act[s.out], u->w + s.b_off, 1);
+        if (u->use_tc)
+            gemm_tc(st, (int)P, s.cout, K, u->col, u->wb + s.w_off, u->act[s.out], u->w + s.b_off, 1, u->tc_err);
+        else
+            gemm(st, 0, 1, 0, (int)P, s.cout, K, u->col, u->wb + s.w_off, u->act[s.out], u->w + s.b_off, 1);
         // pooling after the second convolution of each encoder level
         if (s.out == T_A1 || s.out == T_A3 || s.out == T_A5) {
             const int pid = s.out == T_A1 ? T_P0 : (s.out == T_A3 ? T_P1 : T_P2);
@@ -180,6 +207,12 @@ ivis_status forward_impl(ivis_unet_s *u, const float *in_dev, int B, int H, int 
     }
     k_head<<<nblk(P0), 256, 0, st>>>(P0, u->c, u->act[T_A13], u->w + u->head_w, u->w + u->head_b, u->out);
     UCK(cudaGetLastError());
+    if (u->use_tc) {
+        int herr = 0;
+        UCK(cudaMemcpyAsync(&herr, u->tc_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+        UCK(cudaStreamSynchronize(st));
+        if (herr) return ufail(u, IVIS_ERR_TIMEOUT, "tensor-core GEMM: completion wait timed out");
+    }
     return IVIS_OK;
 }
 
@@ -213,7 +246,9 @@ ivis_status ivis_unet_create(int base_channels, int max_batch, int max_hw, void 
     const size_t P0 = (size_t)max_batch * max_hw;
     ok = ok && cudaMalloc(&u->out, P0 * 4) == cudaSuccess && cudaMalloc(&u->dout, P0 * 4) == cudaSuccess &&
          cudaMalloc(&u->tgt, P0 * 4) == cudaSuccess && cudaMalloc(&u->part, 148 * 32 * sizeof(double)) == cudaSuccess &&
-         cudaMallocHost(&u->part_h, 148 * 32 * sizeof(double)) == cudaSuccess;
+         cudaMallocHost(&u->part_h, 148 * 32 * sizeof(double)) == cudaSuccess &&
+         cudaMalloc(&u->tc_err, sizeof(int)) == cudaSuccess;
+    if (ok) cudaMemset(u->tc_err, 0, sizeof(int));
     if (ok) {
         cudaMemset(u->w, 0, u->nparam * 4);
         cudaMemset(u->g, 0, u->nparam * 4);
@@ -346,13 +381,20 @@ ivis_status ivis_unet_adam_step(ivis_unet_t u, float lr, float beta1, float beta
 ivis_status ivis_unet_destroy(ivis_unet_t u) {
     if (!u) return IVIS_OK;
     if (u->stream) cudaStreamSynchronize(u->stream);
-    void *ptrs[] = {u->w, u->g, u->m, u->v, u->wb, u->col, u->dz, u->dcol, u->out, u->dout, u->tgt, u->part};
+    void *ptrs[] = {u->w, u->g, u->m, u->v, u->wb, u->col, u->dz, u->dcol, u->out, u->dout, u->tgt, u->part,
+                    u->tc_err};
     for (void *q : ptrs)
         if (q) cudaFree(q);
     for (auto q : u->act) if (q) cudaFree(q);
     for (auto q : u->dact) if (q) cudaFree(q);
     if (u->part_h) cudaFreeHost(u->part_h);
     delete u;
+    return IVIS_OK;
+}
+
+ivis_status ivis_unet_use_tcgen05(ivis_unet_t u, int enable) {
+    if (!u) return ufail(nullptr, IVIS_ERR_ARG, "null pointer");
+    u->use_tc = enable != 0;
     return IVIS_OK;
 }
 

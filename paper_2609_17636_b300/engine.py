@@ -285,6 +285,9 @@ class UNet:
                                               ctypes.byref(loss)))
         return loss.value
 
+    def use_tcgen05(self, enable: bool):
+        self._check(self.L.ivis_unet_use_tcgen05(self._p, int(bool(enable))))
+
     def adam_step(self, lr: float, beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8):
         self._check(self.L.ivis_unet_adam_step(self._p, lr, beta1, beta2, eps))
 

@@ -40,9 +40,16 @@ def test_unet_forward_and_gradient_match_oracle(c, H, W):
     inp, tgt = _batch(c, B, H, W, 4)
     net = UNet(c, max_batch=B, max_hw=H * W)
     net.set_params(p)
-    out = net.forward(torch.as_tensor(inp, device="cuda")).cpu().numpy()
+    out = net.forward(torch.as_tensor(inp, device="cuda")).cpu().numpy()  # tcgen05 path
     ref = ou.forward(p, shapes, c, inp)
     assert _rel(out, ref) <= 2e-2, _rel(out, ref)
+    net.use_tcgen05(False)
+    out_mma = net.forward(torch.as_tensor(inp, device="cuda")).cpu().numpy()
+    net.use_tcgen05(True)
+    assert _rel(out_mma, ref) <= 2e-2, _rel(out_mma, ref)
+    # same BF16 operands and FP32 accumulation on both tensor-core paths: only the summation
+    # order and the final BF16 rounding of each layer differ
+    assert _rel(out, out_mma) <= 1e-2, _rel(out, out_mma)
     loss = net.backward(torch.as_tensor(inp, device="cuda"), torch.as_tensor(tgt, device="cuda"))
     g = net.get_grads()
     lref, gref = ou.loss_and_grad(p, shapes, c, inp, tgt)

@@ -94,6 +94,14 @@ ivis_status ivis_plan(const ivis_config *cfg, void *stream, ivis_plan_t *out);
  * with A_k[q][p] at direction (l_p, m_q). Must be set before ivis_set_vis for k. */
 ivis_status ivis_set_pointing(ivis_plan_t plan, int k, int cx, int cy, const float *beam_dev);
 
+/* SIN re-projection of pointing k (Eq. 2; Sect. 3.3): grid_dev float [nb][nb][2] gives, for
+ * each window pixel (q, p), the sampling location (X, Y) in sky pixel units (X along columns,
+ * pixel centres at integers); the window becomes the bilinear interpolation of the sky there
+ * (pixels off the sky count as zero; non-finite entries give zero), and the gradient its
+ * transpose. Replaces the integer window of ivis_set_pointing for k; NULL restores it. The
+ * gradient contributions of gridded pointings are added with atomics (not bit-reproducible). */
+ivis_status ivis_set_pointing_grid(ivis_plan_t plan, int k, const float *grid_dev);
+
 /* Calibrated visibilities of pair (k, chan): m points, uvw float [m][3] in wavelengths
  * (w ignored: coplanar model of Eq. 3), vis float [m][2] (re, im), weight float [m]
  * = 1/sigma^2 from the SIGMA column (Eq. 5). m == 0 declares a pair with no data.

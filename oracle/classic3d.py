@@ -11,7 +11,7 @@ __all__ = [
     "lib", "num_threads", "window", "window_adjoint", "model_vis", "adjoint", "adjoint_pixels",
     "pair_model_vis", "data_cost_grad", "data_grad_pixels", "laplacian", "reg_cost_grad",
     "dish_kernel", "dish_conv", "fusion_cost_grad", "cost_grad", "solve_lbfgsb",
-    "LAPLACIAN_KERNEL",
+    "LAPLACIAN_KERNEL", "bilinear", "bilinear_adjoint", "pointing_window", "pointing_window_adjoint",
 ]
 
 # Eq. 7: the Laplacian kernel d of the regulariser.
@@ -78,6 +78,69 @@ def window_adjoint(win: np.ndarray, cx: int, cy: int, shape) -> np.ndarray:
     return out
 
 
+def bilinear(img: np.ndarray, grid: np.ndarray) -> np.ndarray:
+    """SIN re-projection by bilinear interpolation (Sect. 2.1, Eq. 2; Sect. 3.3): window value
+    at (q, p) = the sky interpolated at grid[q, p] = (X, Y) in sky pixel units (X along columns,
+    Y along rows), pixels off the sky counting as zero; non-finite grid entries give zero."""
+    nb = grid.shape[0]
+    out = np.zeros((nb, nb))
+    ny, nx = img.shape
+    for q in range(nb):
+        for p in range(nb):
+            X, Y = float(grid[q, p, 0]), float(grid[q, p, 1])
+            if not (np.isfinite(X) and np.isfinite(Y)):
+                continue
+            x0, y0 = int(np.floor(X)), int(np.floor(Y))
+            fx, fy = X - x0, Y - y0
+            for (dy, dx, wgt) in ((0, 0, (1 - fx) * (1 - fy)), (0, 1, fx * (1 - fy)),
+                                  (1, 0, (1 - fx) * fy), (1, 1, fx * fy)):
+                y, x = y0 + dy, x0 + dx
+                if 0 <= y < ny and 0 <= x < nx:
+                    out[q, p] += wgt * img[y, x]
+    return out
+
+
+def bilinear_adjoint(win: np.ndarray, grid: np.ndarray, shape) -> np.ndarray:
+    """Transpose of :func:`bilinear`: each window value is spread back with the same weights."""
+    out = np.zeros(shape)
+    nb = grid.shape[0]
+    for q in range(nb):
+        for p in range(nb):
+            X, Y = float(grid[q, p, 0]), float(grid[q, p, 1])
+            if not (np.isfinite(X) and np.isfinite(Y)):
+                continue
+            x0, y0 = int(np.floor(X)), int(np.floor(Y))
+            fx, fy = X - x0, Y - y0
+            for (dy, dx, wgt) in ((0, 0, (1 - fx) * (1 - fy)), (0, 1, fx * (1 - fy)),
+                                  (1, 0, (1 - fx) * fy), (1, 1, fx * fy)):
+                y, x = y0 + dy, x0 + dx
+                if 0 <= y < shape[0] and 0 <= x < shape[1]:
+                    out[y, x] += wgt * win[q, p]
+    return out
+
+
+def _grid_of(prob, k):
+    grids = getattr(prob, "grids", None)
+    return None if grids is None else grids.get(k)
+
+
+def pointing_window(prob, img2d, k):
+    """I'_k: the integer window, or the bilinear re-projection when pointing k has a grid."""
+    g = _grid_of(prob, k)
+    if g is not None:
+        return bilinear(img2d, g)
+    cx, cy = (int(t) for t in prob.centres[k])
+    return window(img2d, cx, cy, prob.nb)
+
+
+def pointing_window_adjoint(prob, win, k, shape):
+    g = _grid_of(prob, k)
+    if g is not None:
+        return bilinear_adjoint(win, g, shape)
+    cx, cy = (int(t) for t in prob.centres[k])
+    return window_adjoint(win, cx, cy, shape)
+
+
 # ------------------------------------------------------------- non-uniform DFT (Eq. 3) and adjoint
 def model_vis(f: np.ndarray, cell: float, u: np.ndarray, v: np.ndarray) -> np.ndarray:
     """Direct DFT  V~_j = sum_{q,p} f[q,p] exp(-2 pi i (u_j l_p + v_j m_q))."""
@@ -120,8 +183,7 @@ def adjoint_pixels(c, nb, cell, u, v, qs, ps) -> np.ndarray:
 # -------------------------------------------------------------------- data term (Eqs. 3-6)
 def pair_model_vis(prob, sky: np.ndarray, pair, idx=None) -> np.ndarray:
     """Model visibilities of one (pointing, channel) pair for sky cube ``sky``."""
-    cx, cy = (int(t) for t in prob.centres[pair.k])
-    f = np.asarray(prob.beams[pair.k], dtype=np.float64) * window(sky[pair.chan], cx, cy, prob.nb)
+    f = np.asarray(prob.beams[pair.k], dtype=np.float64) * pointing_window(prob, sky[pair.chan], pair.k)
     uvw = pair.uvw if idx is None else pair.uvw[idx]
     return model_vis(f, prob.cell_rad, uvw[:, 0], uvw[:, 1])
 
@@ -139,9 +201,8 @@ def data_cost_grad(prob, sky: np.ndarray, with_grad: bool = True):
         Q += 0.5 * float(np.sum(w * (r.real ** 2 + r.imag ** 2)))
         if with_grad:
             a = adjoint(w * r, prob.nb, prob.cell_rad, pair.uvw[:, 0], pair.uvw[:, 1])
-            cx, cy = (int(t) for t in prob.centres[pair.k])
             g = np.asarray(prob.beams[pair.k], dtype=np.float64) * a.real
-            grad[pair.chan] += window_adjoint(g, cx, cy, sky.shape[1:])
+            grad[pair.chan] += pointing_window_adjoint(prob, g, pair.k, sky.shape[1:])
     return Q, grad
 
 

@@ -20,7 +20,7 @@ STATUS = {0: "IVIS_OK", 1: "IVIS_ERR_ARG", 2: "IVIS_ERR_STATE", 3: "IVIS_ERR_OOM
           7: "IVIS_ERR_LINESEARCH"}
 
 # Every entry point include/ivis.h declares.
-EXPORTS = ["ivis_plan", "ivis_set_pointing", "ivis_set_vis", "ivis_set_sd", "ivis_prepare",
+EXPORTS = ["ivis_plan", "ivis_set_pointing", "ivis_set_pointing_grid", "ivis_set_vis", "ivis_set_sd", "ivis_prepare",
            "ivis_cost_grad", "ivis_cost_grad_async", "ivis_get_stream", "ivis_cost_grad_host", "ivis_predict", "ivis_sd_predict",
            "ivis_solve", "ivis_get_nufft_params", "ivis_profile", "ivis_stage_times",
            "ivis_launches_per_eval", "ivis_sd_predict_noalloc", "ivis_destroy", "ivis_last_error",
@@ -68,6 +68,7 @@ def load(path: str = LIB_PATH):
     L.ivis_plan.argtypes = [ctypes.POINTER(Config), vp, ctypes.POINTER(vp)]
     L.ivis_set_pointing.argtypes = [vp, i, i, i, vp]
     L.ivis_set_vis.argtypes = [vp, i, i, i64, vp, vp, vp]
+    L.ivis_set_pointing_grid.argtypes = [vp, i, vp]
     L.ivis_set_sd.argtypes = [vp, i, vp, d, d]
     L.ivis_prepare.argtypes = [vp]
     L.ivis_cost_grad.argtypes = [vp, vp, dp, vp, dp]

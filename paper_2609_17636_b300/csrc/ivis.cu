@@ -64,6 +64,8 @@ struct ivis_plan_s {
     float *kpoly_d = nullptr;  // per-tap kernel polynomials (FP32 path)
     std::vector<int> cx, cy;
     std::vector<char> pset;
+    std::vector<int> pgrid;       // 1: pointing k re-projects through its interpolation grid
+    void *grids_d = nullptr;      // float2 [npoint][nb][nb] sampling locations (X, Y)
     std::vector<PairHost> pairs;  // index chan * npoint + k
     // single dish
     std::vector<char> sdset;
@@ -91,6 +93,7 @@ struct ivis_plan_s {
     cudaGraphExec_t graph = nullptr;
     int launches = 0;
     bool capturing = false;
+    bool any_grid = false;  // some pair uses a re-projection grid (set at prepare)
     // solver state
     SolverBufs solver{};
     // profiling
@@ -307,7 +310,7 @@ cudaError_t launch_forward(ivis_plan_s *p, const void *sky, int slot0 = 0, int n
     cudaFuncSetAttribute(k_fwd_rows<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_row);
     k_fwd_rows<T><<<gr, 256, smem_row, p->stream>>>(
         (const T *)sky, (const T *)p->beams_d, pinfo, (const T *)p->dinv_d, rowbuf,
-        p->cfg.n, nb, p->lognf, (const C *)p->tw_d);
+        p->cfg.n, nb, p->lognf, (const C *)p->tw_d, (const float2 *)p->grids_d);
     dim3 gc(nf >> p->logc_cols, nslots);
     size_t smem_col = (size_t)fft_smem_elems(nf, 1 << p->logc_cols) * sizeof(C);
     cudaFuncSetAttribute(k_fwd_cols<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_col);
@@ -446,6 +449,12 @@ cudaError_t enqueue_eval(ivis_plan_s *p, bool capture) {
         (const T *)p->gradK, (T *)p->g, n, p->cfg.nb, nchan, (T)p->cfg.lambda_r,
         (T)p->cfg.lambda_s, use_r ? 1 : 0, use_k ? 1 : 0, p->rpart);
     launches += 1;
+    if (p->any_grid && p->nslot > 0) {
+        dim3 gs((p->cfg.nb * p->cfg.nb + 255) / 256, p->nslot);
+        k_grid_scatter<T><<<gs, 256, 0, p->stream>>>((const T *)p->contrib, p->pinfo_d,
+                                                     (const float2 *)p->grids_d, (T *)p->g, n, p->cfg.nb);
+        launches += 1;
+    }
     stage_end(p, p->stream, si);
     stage_begin(p, "finalize", p->stream, si);
     k_finalize<<<1, 1024, 0, p->stream>>>(p->jpart, p->nchunk, p->kpart, use_k ? p->nkpart : 0,
@@ -734,7 +743,7 @@ ivis_status prepare_impl(ivis_plan_s *p) {
     for (int sl = 0; sl < p->nslot; ++sl) {
         int pi_ = p->slot_pair[sl];
         int k = pi_ % c.npoint, ch = pi_ / c.npoint;
-        pinfo[sl] = PairInfo{k, ch, p->cx[k], p->cy[k]};
+        pinfo[sl] = PairInfo{k, ch, p->cx[k], p->cy[k], p->pgrid[k]};
         PairHost &ph = p->pairs[pi_];
         pdata[sl].coord = (const typename coord_of<T>::type *)ph.coord;
         pdata[sl].vis = (const C *)ph.vis;
@@ -742,6 +751,8 @@ ivis_status prepare_impl(ivis_plan_s *p) {
         pdata[sl].orig = ph.orig;
         pdata[sl].m = ph.m;
     }
+    p->any_grid = false;
+    for (int sl = 0; sl < p->nslot; ++sl) p->any_grid |= pinfo[sl].gridded != 0;
     build_chunks(p, p->chunk_cap, chunks, p->chunk_first);
     p->nchunk = (int)chunks.size();
     size_t max_chunks = 0;  // work lists of every autotuner candidate fit the device arrays
@@ -970,23 +981,31 @@ ivis_status dirty_impl(ivis_plan_s *p, void *dirty_dev, void *beamw_dev) {
     k_assemble<T><<<(unsigned)((npix + 255) / 256), 256, 0, p->stream>>>(
         (const T *)p->x, (const T *)p->contrib, p->pinfo_d, p->chan_start_d, p->chan_list_d, nullptr,
         (T *)p->g, n, p->cfg.nb, nchan, (T)0, (T)0, 0, 0, p->rpart);
+    if (p->any_grid && p->nslot > 0) {
+        dim3 gs((p->cfg.nb * p->cfg.nb + 255) / 256, p->nslot);
+        k_grid_scatter<T><<<gs, 256, 0, p->stream>>>((const T *)p->contrib, p->pinfo_d,
+                                                     (const float2 *)p->grids_d, (T *)p->g, n, p->cfg.nb);
+    }
     k_scale<T><<<(unsigned)((npix + 255) / 256), 256, 0, p->stream>>>(npix, (const T *)p->g, (T)-1, (T *)dirty_dev);
     if (beamw_dev) {
-        std::vector<int> hc(p->cx), hy(p->cy);
-        int *dc = nullptr, *dy = nullptr;
+        const int np = p->cfg.npoint;
+        std::vector<int> hv(p->cx);
+        hv.insert(hv.end(), p->cy.begin(), p->cy.end());
+        hv.insert(hv.end(), p->pgrid.begin(), p->pgrid.end());
+        int *dv = nullptr;
         ivis_status s;
-        if ((s = alloc(p, (void **)&dc, hc.size() * sizeof(int))) || (s = alloc(p, (void **)&dy, hy.size() * sizeof(int)))) {
-            void *a = dc; dfree(a);
-            return s;
-        }
-        cudaMemcpyAsync(dc, hc.data(), hc.size() * sizeof(int), cudaMemcpyHostToDevice, p->stream);
-        cudaMemcpyAsync(dy, hy.data(), hy.size() * sizeof(int), cudaMemcpyHostToDevice, p->stream);
+        if ((s = alloc(p, (void **)&dv, hv.size() * sizeof(int)))) return s;
+        cudaMemcpyAsync(dv, hv.data(), hv.size() * sizeof(int), cudaMemcpyHostToDevice, p->stream);
         k_beam_weight<T><<<(unsigned)(((size_t)n * n + 255) / 256), 256, 0, p->stream>>>(
-            (const T *)p->beams_d, dc, dy, p->cfg.npoint, n, p->cfg.nb, (T *)beamw_dev);
+            (const T *)p->beams_d, dv, dv + np, dv + 2 * np, np, n, p->cfg.nb, (T *)beamw_dev);
+        if (p->grids_d) {
+            dim3 gb((p->cfg.nb * p->cfg.nb + 255) / 256, np);
+            k_beam_weight_grid<T><<<gb, 256, 0, p->stream>>>((const T *)p->beams_d, (const float2 *)p->grids_d,
+                                                             dv + 2 * np, n, p->cfg.nb, (T *)beamw_dev);
+        }
         cudaError_t e = cudaStreamSynchronize(p->stream);
-        void *a = dc, *b = dy;
+        void *a = dv;
         dfree(a);
-        dfree(b);
         if (e != cudaSuccess) return fail(p, IVIS_ERR_CUDA, std::string("beam weight: ") + cudaGetErrorString(e));
     }
     CK(cudaGetLastError());
@@ -1088,6 +1107,7 @@ ivis_status ivis_plan(const ivis_config *cfg, void *stream, ivis_plan_t *out) {
     p->cx.assign(c.npoint, 0);
     p->cy.assign(c.npoint, 0);
     p->pset.assign(c.npoint, 0);
+    p->pgrid.assign(c.npoint, 0);
     p->pairs.resize((size_t)c.npoint * c.nchan);
     p->sdset.assign(c.nchan, 0);
     p->sig_sd.assign(c.nchan, 1.0);
@@ -1150,6 +1170,26 @@ ivis_status ivis_set_pointing(ivis_plan_t p, int k, int cx, int cy, const float 
     p->cy[k] = cy;
     p->pset[k] = 1;
     invalidate(p);
+    return IVIS_OK;
+}
+
+ivis_status ivis_set_pointing_grid(ivis_plan_t p, int k, const float *grid_dev) {
+    if (!p) return fail(nullptr, IVIS_ERR_ARG, "null plan");
+    if (k < 0 || k >= p->cfg.npoint) return fail(p, IVIS_ERR_ARG, "bad pointing index");
+    enter(p);
+    invalidate(p);
+    if (!grid_dev) {
+        p->pgrid[k] = 0;
+        return IVIS_OK;
+    }
+    const size_t per = (size_t)p->cfg.nb * p->cfg.nb * 2 * sizeof(float);
+    if (!p->grids_d) {
+        ivis_status s = alloc(p, &p->grids_d, per * p->cfg.npoint);
+        if (s) return s;
+    }
+    CK(cudaMemcpyAsync((char *)p->grids_d + per * k, grid_dev, per, cudaMemcpyDeviceToDevice, p->stream));
+    CK(cudaStreamSynchronize(p->stream));
+    p->pgrid[k] = 1;
     return IVIS_OK;
 }
 
@@ -1439,6 +1479,7 @@ ivis_status ivis_destroy(ivis_plan_t p) {
     }
     dfree(p->beams_d);
     dfree(p->tsd_d);
+    dfree(p->grids_d);
     for (auto &st : p->stages) {
         if (st.b) cudaEventDestroy(st.b);
         if (st.e) cudaEventDestroy(st.e);

@@ -41,6 +41,7 @@ k_assemble(const T *__restrict__ sky, const T *__restrict__ contrib,
         for (int t = chan_start[chan]; t < chan_start[chan + 1]; ++t) {
             const int slot = chan_list[t];
             const PairInfo pi = pinfo[slot];
+            if (pi.gridded) continue;  // added by k_grid_scatter
             const int q = y - (pi.cy - nb / 2), p = x - (pi.cx - nb / 2);
             if ((unsigned)q < (unsigned)nb && (unsigned)p < (unsigned)nb)
                 g += contrib[((size_t)slot * nb + q) * nb + p];
@@ -187,12 +188,14 @@ __global__ void k_finalize(const double *__restrict__ jpart, int nj, const doubl
 // a linear mosaic, Sect. 4.3); used as an input plane of the learned warm start.
 template <typename T>
 __global__ void k_beam_weight(const T *__restrict__ beams, const int *__restrict__ cx,
-                              const int *__restrict__ cy, int npoint, int n, int nb, T *out) {
+                              const int *__restrict__ cy, const int *__restrict__ gridded,
+                              int npoint, int n, int nb, T *out) {
     const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= (size_t)n * n) return;
     const int y = (int)(idx / n), x = (int)(idx % n);
     T s = (T)0;
     for (int k = 0; k < npoint; ++k) {
+        if (gridded[k]) continue;
         const int q = y - (cy[k] - nb / 2), p = x - (cx[k] - nb / 2);
         if ((unsigned)q < (unsigned)nb && (unsigned)p < (unsigned)nb) {
             const T a = beams[((size_t)k * nb + q) * nb + p];
@@ -200,6 +203,33 @@ __global__ void k_beam_weight(const T *__restrict__ beams, const int *__restrict
         }
     }
     out[idx] = s;
+}
+
+// Adjoint of the bilinear re-projection for gridded pointings: grad[chan] += B_k^T contrib_k.
+// One thread per window pixel of every slot (non-gridded slots return at once).
+template <typename T>
+__global__ void k_grid_scatter(const T *__restrict__ contrib, const PairInfo *__restrict__ pinfo,
+                               const float2 *__restrict__ grids, T *grad, int n, int nb) {
+    const int slot = blockIdx.y;
+    const PairInfo pi = pinfo[slot];
+    if (!pi.gridded) return;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nb * nb) return;
+    const float2 g = grids[(size_t)pi.k * nb * nb + i];
+    bilerp_adj(grad + (size_t)pi.chan * n * n, n, g.x, g.y, contrib[(size_t)slot * nb * nb + i]);
+}
+
+// Beam-weight map contribution of gridded pointings: out += B_k^T (A_k^2).
+template <typename T>
+__global__ void k_beam_weight_grid(const T *__restrict__ beams, const float2 *__restrict__ grids,
+                                   const int *__restrict__ gridded, int n, int nb, T *out) {
+    const int k = blockIdx.y;
+    if (!gridded[k]) return;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nb * nb) return;
+    const T a = beams[(size_t)k * nb * nb + i];
+    const float2 g = grids[(size_t)k * nb * nb + i];
+    bilerp_adj(out, n, g.x, g.y, a * a);
 }
 
 template <typename T>

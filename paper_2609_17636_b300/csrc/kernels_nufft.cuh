@@ -23,7 +23,45 @@ namespace ivis {
 
 struct PairInfo {
     int k, chan, cx, cy;
+    int gridded;  // 1: the window is the bilinear re-projection through the pointing's grid
 };
+
+// Bilinear interpolation of img (n x n, zero off the sky) at (X, Y) in pixel units (X along
+// columns); non-finite or far-off coordinates give zero (Eq. 2, Sect. 3.3).
+template <typename T>
+__device__ __forceinline__ T bilerp(const T *__restrict__ img, int n, float X, float Y) {
+    if (!(X > -2.0f && X < (float)n + 1.0f && Y > -2.0f && Y < (float)n + 1.0f)) return (T)0;
+    const T xf = floor((T)X), yf = floor((T)Y);
+    const int x0 = (int)xf, y0 = (int)yf;
+    const T fx = (T)X - xf, fy = (T)Y - yf;
+    T s = (T)0;
+    if (y0 >= 0 && y0 < n) {
+        if (x0 >= 0 && x0 < n) s += ((T)1 - fx) * ((T)1 - fy) * img[(size_t)y0 * n + x0];
+        if (x0 + 1 >= 0 && x0 + 1 < n) s += fx * ((T)1 - fy) * img[(size_t)y0 * n + x0 + 1];
+    }
+    if (y0 + 1 >= 0 && y0 + 1 < n) {
+        if (x0 >= 0 && x0 < n) s += ((T)1 - fx) * fy * img[(size_t)(y0 + 1) * n + x0];
+        if (x0 + 1 >= 0 && x0 + 1 < n) s += fx * fy * img[(size_t)(y0 + 1) * n + x0 + 1];
+    }
+    return s;
+}
+
+// Transpose of bilerp: out += v spread with the same four weights (atomics).
+template <typename T>
+__device__ __forceinline__ void bilerp_adj(T *out, int n, float X, float Y, T v) {
+    if (!(X > -2.0f && X < (float)n + 1.0f && Y > -2.0f && Y < (float)n + 1.0f)) return;
+    const T xf = floor((T)X), yf = floor((T)Y);
+    const int x0 = (int)xf, y0 = (int)yf;
+    const T fx = (T)X - xf, fy = (T)Y - yf;
+    if (y0 >= 0 && y0 < n) {
+        if (x0 >= 0 && x0 < n) atomicAdd(&out[(size_t)y0 * n + x0], ((T)1 - fx) * ((T)1 - fy) * v);
+        if (x0 + 1 >= 0 && x0 + 1 < n) atomicAdd(&out[(size_t)y0 * n + x0 + 1], fx * ((T)1 - fy) * v);
+    }
+    if (y0 + 1 >= 0 && y0 + 1 < n) {
+        if (x0 >= 0 && x0 < n) atomicAdd(&out[(size_t)(y0 + 1) * n + x0], ((T)1 - fx) * fy * v);
+        if (x0 + 1 >= 0 && x0 + 1 < n) atomicAdd(&out[(size_t)(y0 + 1) * n + x0 + 1], fx * fy * v);
+    }
+}
 
 struct Chunk {
     int slot;    // active pair slot
@@ -204,7 +242,7 @@ __global__ void __launch_bounds__(256)
 k_fwd_rows(const T *__restrict__ sky, const T *__restrict__ beams,
            const PairInfo *__restrict__ pinfo, const T *__restrict__ dinv,
            typename cplx_of<T>::type *rowbuf, int n, int nb, int lognf,
-           const typename cplx_of<T>::type *__restrict__ tw) {
+           const typename cplx_of<T>::type *__restrict__ tw, const float2 *__restrict__ grids) {
     typedef typename cplx_of<T>::type C;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C *s = reinterpret_cast<C *>(smem_raw);
@@ -214,19 +252,29 @@ k_fwd_rows(const T *__restrict__ sky, const T *__restrict__ beams,
     const int l = threadIdx.x / tpl, j0 = threadIdx.x - l * tpl;
     const int q = blockIdx.x * lpb + l;
     const int y = pi.cy - nb / 2 + q;
-    const bool on = q < nb && y >= 0 && y < n;
+    const bool on = q < nb && (pi.gridded || (y >= 0 && y < n));
     C *line = s;  // element e of line l at s[pidx(l * nf + e)]
     for (int e = j0; e < nf; e += tpl) line[pidx(l * nf + e)] = mk((T)0, (T)0);
     __syncthreads();
     if (on) {
-        const T *srow = sky + ((size_t)pi.chan * n + y) * n;
         const T *brow = beams + ((size_t)pi.k * nb + q) * nb;
         const T dq = dinv[q];
-        const int x0 = pi.cx - nb / 2;
-        for (int p = j0; p < nb; p += tpl) {
-            const int x = x0 + p;
-            const T val = (x >= 0 && x < n) ? srow[x] * brow[p] * dinv[p] * dq : (T)0;
-            line[pidx(l * nf + ((p - nb / 2) & (nf - 1)))] = mk(val, (T)0);
+        if (pi.gridded) {
+            const T *img = sky + (size_t)pi.chan * n * n;
+            const float2 *grow = grids + ((size_t)pi.k * nb + q) * nb;
+            for (int p = j0; p < nb; p += tpl) {
+                const float2 g = grow[p];
+                const T val = bilerp(img, n, g.x, g.y) * brow[p] * dinv[p] * dq;
+                line[pidx(l * nf + ((p - nb / 2) & (nf - 1)))] = mk(val, (T)0);
+            }
+        } else {
+            const T *srow = sky + ((size_t)pi.chan * n + y) * n;
+            const int x0 = pi.cx - nb / 2;
+            for (int p = j0; p < nb; p += tpl) {
+                const int x = x0 + p;
+                const T val = (x >= 0 && x < n) ? srow[x] * brow[p] * dinv[p] * dq : (T)0;
+                line[pidx(l * nf + ((p - nb / 2) & (nf - 1)))] = mk(val, (T)0);
+            }
         }
     }
     __syncthreads();
@@ -495,7 +543,8 @@ k_adj_rows(const typename cplx_of<T>::type *__restrict__ rowbuf,
     const int l = threadIdx.x / tpl, j0 = threadIdx.x - l * tpl;
     const int q = blockIdx.x * lpb + l;
     const int y = pi.cy - nb / 2 + q;
-    const bool on = q < nb && y >= 0 && y < n;  // rows off the sky are never gathered
+    // rows of an integer window that fall off the sky are never gathered
+    const bool on = q < nb && (pi.gridded || (y >= 0 && y < n));
     if (on) {
         const C *src = rowbuf + ((size_t)slot * nb + q) * nf;
         for (int e = j0; e < nf; e += tpl) s[pidx(l * nf + e)] = src[e];

@@ -62,6 +62,14 @@ class Plan:
         _check(self.L, self._p, self.L.ivis_set_pointing(self._p, k, int(cx), int(cy),
                                                          ctypes.c_void_p(beam.data_ptr())))
 
+    def set_pointing_grid(self, k: int, grid: torch.Tensor | None):
+        """Re-project pointing k through sampling locations grid [nb][nb][2] (X, Y)."""
+        if grid is None:
+            _check(self.L, self._p, self.L.ivis_set_pointing_grid(self._p, k, None))
+            return
+        grid = _dev_f32(grid, (self.cfg.nb, self.cfg.nb, 2))
+        _check(self.L, self._p, self.L.ivis_set_pointing_grid(self._p, k, ctypes.c_void_p(grid.data_ptr())))
+
     def set_vis(self, k: int, chan: int, uvw: torch.Tensor, vis: torch.Tensor, weight: torch.Tensor):
         m = int(uvw.shape[0])
         if m:
@@ -210,6 +218,8 @@ def plan_from_problem(prob, precision: str = "fp32", device="cuda", **kw) -> Pla
     for k in range(prob.centres.shape[0]):
         plan.set_pointing(k, int(prob.centres[k][0]), int(prob.centres[k][1]),
                           torch.as_tensor(prob.beams[k], dtype=torch.float32, device=device))
+    for k, g in (getattr(prob, "grids", None) or {}).items():
+        plan.set_pointing_grid(k, torch.as_tensor(g, dtype=torch.float32, device=device))
     seen = set()
     for pair in prob.pairs:
         uvw = torch.as_tensor(pair.uvw, dtype=torch.float32, device=device)

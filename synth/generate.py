@@ -10,7 +10,7 @@ __all__ = [
     "baseline_pairs", "uvw_tracks", "gaussian_beam", "point_source_sky",
     "lognormal_sky", "hex_footprint", "flag_keep_mask", "complex_noise",
     "gaussian_noise", "point_source_flux_law", "unet_layer_shapes", "unet_num_params",
-    "unet_init",
+    "unet_init", "projection_grid",
 ]
 
 C_LIGHT = 299_792_458.0
@@ -165,3 +165,17 @@ def unet_init(c: int = 32, seed: int = 0) -> np.ndarray:
     out.append(rng.standard_normal(c) * math.sqrt(1.0 / c))
     out.append(np.zeros(1))
     return np.concatenate(out).astype(np.float32)
+
+
+def projection_grid(nb: int, cx: float, cy: float, rot_rad: float = 0.0, scale: float = 1.0,
+                    curvature: float = 0.0) -> np.ndarray:
+    """Sampling locations (X, Y) in sky pixels for each window pixel (q, p): a rotation and a
+    scale about the pointing centre (cx, cy) (fractional allowed) plus a small quadratic term
+    standing in for the SIN projection's departure from the sky grid. float32 [nb][nb][2]."""
+    c = np.arange(nb) - nb // 2
+    P, Q = np.meshgrid(c, c)
+    cr, sr = math.cos(rot_rad), math.sin(rot_rad)
+    r2 = (P * P + Q * Q) / float(nb * nb)
+    X = cx + scale * (cr * P - sr * Q) * (1.0 + curvature * r2)
+    Y = cy + scale * (sr * P + cr * Q) * (1.0 + curvature * r2)
+    return np.stack([X, Y], axis=-1).astype(np.float32)

@@ -380,3 +380,48 @@ def test_point_source_spectrum_fixture_matches_stated_law():
     assert rows.shape == (10, 2) and meta["noise_jy"] == 0.1
     assert np.allclose(synth.point_source_flux_law(rows[:, 0]), rows[:, 1], rtol=1e-14)
     assert np.isclose(rows[:, 0].mean(), 1.0e9) and np.allclose(np.diff(rows[:, 0]), 0.1e9)
+
+
+# ------------------------------------------------------- SIN re-projection grids (Eq. 2)
+def test_bilinear_on_integer_grid_is_the_window():
+    rng = np.random.default_rng(30)
+    img = rng.standard_normal((40, 36))
+    for cx, cy in [(18, 20), (2, 35), (39, 1)]:
+        g = synth.projection_grid(16, cx, cy)
+        assert np.array_equal(oracle.bilinear(img, g), oracle.window(img, cx, cy, 16))
+
+
+def test_bilinear_reproduces_linear_functions_and_matches_scipy():
+    ny, nx = 30, 34
+    Y, X = np.mgrid[0:ny, 0:nx]
+    img = 0.5 + 0.25 * X - 0.75 * Y
+    g = synth.projection_grid(12, 16.3, 14.7, rot_rad=0.3, scale=1.1, curvature=0.05)
+    got = oracle.bilinear(img, g)
+    expect = 0.5 + 0.25 * g[..., 0].astype(np.float64) - 0.75 * g[..., 1].astype(np.float64)
+    assert np.allclose(got, expect, atol=1e-12)
+    rng = np.random.default_rng(31)
+    img = rng.standard_normal((ny, nx))
+    ref = scipy.ndimage.map_coordinates(img, [g[..., 1].astype(np.float64), g[..., 0].astype(np.float64)],
+                                        order=1, mode="constant", cval=0.0)
+    assert np.allclose(oracle.bilinear(img, g), ref, atol=1e-12)
+
+
+def test_bilinear_adjoint_identity_with_edges_and_nan():
+    rng = np.random.default_rng(32)
+    img = rng.standard_normal((20, 22))
+    g = synth.projection_grid(16, 3.4, 18.8, rot_rad=-0.5, scale=1.3)
+    g[0, 0] = np.nan
+    win = rng.standard_normal((16, 16))
+    lhs = np.sum(oracle.bilinear(img, g) * win)
+    rhs = np.sum(img * oracle.bilinear_adjoint(win, g, img.shape))
+    assert abs(lhs - rhs) < 1e-12 and oracle.bilinear(img, g)[0, 0] == 0.0
+
+
+def test_gridded_data_gradient_central_differences():
+    prob = synth.small_mosaic(33, n=40, nb=32, nchan=1, npoint=2, ndump=3, n_ant=7)
+    prob.grids = {0: synth.projection_grid(32, 20.4, 19.6, rot_rad=0.2, scale=0.9, curvature=0.03)}
+    _with_data(prob)
+    rng = np.random.default_rng(33)
+    x = prob.sky_true * rng.uniform(0.5, 1.5, prob.sky_true.shape)
+    _fd_check(lambda z: oracle.data_cost_grad(prob, z), x, rng.choice(x.size, 15, replace=False),
+              1e-4 * np.abs(x).max())

@@ -92,3 +92,44 @@ def test_fullsize_gradient_is_consistent_with_cost_along_a_direction(c2):
     ip = float(torch.sum(g * d))
     assert abs(fd - ip) <= 1e-6 * abs(ip)
     plan.close()
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_maximum_window_size_sampled_parity(precision):
+    """nb = 2048 (the largest window; 4096^2 fine grid, radix-16 FFT passes of length 4096,
+    16384 tiles per pair): two pointings of the full-footprint geometry on a 4096^2 sky at
+    5 arcsec with 630 x 400 visibilities each; sparse data and evaluation skies as above."""
+    from paper_2609_17636_b300 import plan_from_problem
+    prob = synth.config_c4(dumps=400)
+    prob.centres = prob.centres[[14, 21]]
+    prob.beams = prob.beams[:2]
+    prob.pairs = [p for p in prob.pairs if p.k in (14, 21)]
+    for i, p in enumerate(prob.pairs):
+        p.k = i
+    prob.lambda_s = 0.0
+    rng = np.random.default_rng(11)
+    truth = _sparse_sky(rng, prob.n, 30)
+    for pair in prob.pairs:
+        pair.vis = (oracle.pair_model_vis(prob, truth, pair) + pair.noise).astype(np.complex64)
+    x = _sparse_sky(rng, prob.n, 25)
+    plan = plan_from_problem(prob, precision)
+    dt = torch.float32 if precision == "fp32" else torch.float64
+    xs = torch.as_tensor(x, dtype=dt, device="cuda")
+    f, g, (Q, K, R) = plan.cost_grad(xs)
+    tol = 1e-5 if precision == "fp32" else 1e-9
+    resid = [oracle.pair_model_vis(prob, x, p) - p.vis.astype(np.complex128) for p in prob.pairs]
+    Q_ref = sum(0.5 * float(np.sum(p.weight.astype(np.float64) * np.abs(r) ** 2))
+                for p, r in zip(prob.pairs, resid))
+    R_ref, gR = oracle.reg_cost_grad(x)
+    assert abs(Q - Q_ref) <= tol * Q_ref and abs(R - R_ref) <= tol * R_ref
+    ys = rng.integers(0, prob.n, 24)
+    xs_ = rng.integers(0, prob.n, 24)
+    ys[:4], xs_[:4] = prob.centres[0][1] + np.array([0, 5, -700, 1000]), prob.centres[0][0] + np.array([0, 3, 900, -1020])
+    gq = oracle.data_grad_pixels(prob, x, 0, ys, xs_, residuals=resid)
+    g_ref = gq + prob.lambda_r * gR[0, ys, xs_]
+    assert rel_l2(g.cpu().numpy()[0, ys, xs_], g_ref) <= tol
+    for pair in prob.pairs:
+        idx = np.sort(rng.choice(pair.m, 800, replace=False))
+        got = plan.predict(xs, pair.k, pair.chan).cpu().numpy()[idx]
+        assert rel_l2(got[:, 0] + 1j * got[:, 1], oracle.pair_model_vis(prob, x, pair, idx)) <= tol
+    plan.close()

@@ -74,6 +74,19 @@ typedef struct {
     int autotune;       /* 1: ivis_prepare times candidate grid-pass chunk sizes and column-
                            FFT widths on this plan's data and keeps the fastest (cached per
                            shape class in the file named by IVIS_AUTOTUNE_CACHE, if set)     */
+    int toeplitz;       /* 1: evaluate the data term of Eq. 6 through the Toeplitz form of its
+                           normal operator (exact in exact arithmetic; the expansion of Eq. 6
+                           with Eqs. 3-5): per pair, Q = 1/2 z'Re(H)z - z'b + C with
+                           z = A .* P x, H = F^H W F, b = Re(F^H W V), C = 1/2 sum w|V|^2.
+                           H acts as a cyclic convolution of period 2 nb, so an evaluation does
+                           two pruned FFT passes per pair and no pass over the visibilities.
+                           ivis_set_vis then also computes, per pair, the real 2nb x 2nb
+                           spectrum of Re H and the window b (adjoint NUFFTs on a 2nb window;
+                           device memory 4 nb^2 + nb^2 reals per pair). Needs nb <= 1024;
+                           excludes serial_pairs. ivis_predict and ivis_dirty_image keep the
+                           NUFFT. The FP32 cost carries an absolute error of about 1e-6 C (the
+                           NUFFT path's is about 1e-6 sqrt(C Q)), so close to a fit's optimum
+                           its relative error is larger than the NUFFT path's.               */
 } ivis_config;
 
 typedef struct {
@@ -106,7 +119,8 @@ ivis_status ivis_set_pointing_grid(ivis_plan_t plan, int k, const float *grid_de
  * (w ignored: coplanar model of Eq. 3), vis float [m][2] (re, im), weight float [m]
  * = 1/sigma^2 from the SIGMA column (Eq. 5). m == 0 declares a pair with no data.
  * The data are copied, converted to oversampled-grid coordinates and sorted by grid
- * tile on the device. Errors: IVIS_ERR_NONFINITE for NaN/Inf or negative weights. */
+ * tile on the device; with toeplitz = 1 the pair's Toeplitz spectrum, b window and constant
+ * are computed here too. Errors: IVIS_ERR_NONFINITE for NaN/Inf or negative weights. */
 ivis_status ivis_set_vis(ivis_plan_t plan, int k, int chan, int64_t m, const float *uvw_dev,
                          const float *vis_dev, const float *weight_dev);
 

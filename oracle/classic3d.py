@@ -12,6 +12,7 @@ __all__ = [
     "pair_model_vis", "data_cost_grad", "data_grad_pixels", "laplacian", "reg_cost_grad",
     "dish_kernel", "dish_conv", "fusion_cost_grad", "cost_grad", "solve_lbfgsb",
     "LAPLACIAN_KERNEL", "bilinear", "bilinear_adjoint", "pointing_window", "pointing_window_adjoint",
+    "psf_kernel", "toeplitz_data_cost_grad",
 ]
 
 # Eq. 7: the Laplacian kernel d of the regulariser.
@@ -228,6 +229,45 @@ def data_grad_pixels(prob, sky, chan, ys, xs, residuals=None):
                            q[inside], p[inside])
         out[inside] += np.asarray(prob.beams[pair.k], dtype=np.float64)[q[inside], p[inside]] * a.real
     return out
+
+
+# ------------------------------------------------- Toeplitz form of the data term (Eqs. 3-6)
+def psf_kernel(pair, nb: int, cell: float) -> np.ndarray:
+    """T(d) = sum_j w_j exp(+2 pi i (u_j d_x + v_j d_y) cell) for the pixel differences
+    d in [-nb, nb)^2, as a [2nb][2nb] array indexed (d_y + nb, d_x + nb): the kernel of the
+    normal operator F^H W F of Eqs. 3-5, (F^H W F)[p, q] = T(p - q). It is the adjoint of the
+    weights on a 2nb window, whose pixel p' sits at offset p' - nb."""
+    w = pair.weight.astype(np.float64)
+    return adjoint(w, 2 * nb, cell, pair.uvw[:, 0], pair.uvw[:, 1])
+
+
+def toeplitz_data_cost_grad(prob, sky: np.ndarray):
+    """Q and dQ/dI of Eqs. 5-6 through the expansion, per pair with z = A_k * I'_k,
+        Q = 1/2 z.Re(H z) - z.b + 1/2 sum_j w_j |V_j|^2,  dQ/dz = Re(H z) - b,
+    H = F^H W F, b = Re(F^H W V). H z is the linear convolution sum_q T(p - q) z[q], taken here
+    as a cyclic convolution of period 2nb (numpy FFT) of z, zero-padded to 2nb x 2nb, with T
+    wrapped to that period; the entries at d = -nb are never reached and are left out. Equal
+    to :func:`data_cost_grad` in exact arithmetic."""
+    sky = _f64(sky)
+    nb, nf = prob.nb, 2 * prob.nb
+    Q = 0.0
+    grad = np.zeros_like(sky)
+    for pair in prob.pairs:
+        A = np.asarray(prob.beams[pair.k], dtype=np.float64)
+        z = A * pointing_window(prob, sky[pair.chan], pair.k)
+        T = psf_kernel(pair, nb, prob.cell_rad)            # offsets -nb .. nb-1
+        T[0, :] = 0.0
+        T[:, 0] = 0.0
+        Tc = np.roll(T, (-nb, -nb), axis=(0, 1))           # offset d at index d mod nf
+        zp = np.zeros((nf, nf))
+        zp[:nb, :nb] = z
+        Hz = np.fft.ifft2(np.fft.fft2(Tc) * np.fft.fft2(zp))[:nb, :nb]
+        w = pair.weight.astype(np.float64)
+        V = pair.vis.astype(np.complex128)
+        b = adjoint(w * V, nb, prob.cell_rad, pair.uvw[:, 0], pair.uvw[:, 1]).real
+        Q += 0.5 * float(np.sum(z * Hz.real)) - float(np.sum(z * b)) + 0.5 * float(np.sum(w * np.abs(V) ** 2))
+        grad[pair.chan] += pointing_window_adjoint(prob, A * (Hz.real - b), pair.k, sky.shape[1:])
+    return Q, grad
 
 
 # ------------------------------------------------------------------- regulariser (Eqs. 7-8)

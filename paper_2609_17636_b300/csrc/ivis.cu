@@ -22,6 +22,7 @@
 #include "kernels_image.cuh"
 #include "kernels_nufft.cuh"
 #include "kernels_solver.cuh"
+#include "kernels_toeplitz.cuh"
 
 using namespace ivis;
 
@@ -35,6 +36,9 @@ struct PairHost {
     void *coord = nullptr, *vis = nullptr, *w = nullptr;
     int *orig = nullptr;
     std::vector<int> tile_count;  // per tile of the fine grid
+    // Toeplitz form (toeplitz = 1): spectrum of Re H [kx][ky], window b [nb][nb], constant C
+    void *that = nullptr, *bwin = nullptr;
+    double qconst = 0.0;
 };
 
 struct Stage {
@@ -90,6 +94,12 @@ struct ivis_plan_s {
     double *cost_h = nullptr;  // pinned
     int nkpart = 0, nrpart = 0;
     void *hstage = nullptr;    // pinned staging for the host-buffer entry point
+    // Toeplitz form
+    ivis_plan_s *toep_sub = nullptr;  // 2nb-window plan that computes T and b at set_vis
+    void *ones_d = nullptr;           // nb ones (unit deapodisation for the Toeplitz passes)
+    void **that_ptr_d = nullptr, **bwin_ptr_d = nullptr;  // per slot
+    double *qconst_d = nullptr;       // per slot
+    int njpart = 0;                   // FP64 data-term partials summed by k_finalize
     cudaGraphExec_t graph = nullptr;
     int launches = 0;
     bool capturing = false;
@@ -342,6 +352,33 @@ cudaError_t launch_adjoint(ivis_plan_s *p, int slot0 = 0, int nslots = -1) {
     return cudaGetLastError();
 }
 
+// Toeplitz form of the data term for all slots: forward row DFTs of the windows (unit
+// deapodisation), column DFT x spectrum x inverse column DFT, inverse row DFTs with the
+// gradient, cost partials and the pairs' constants. Three launches.
+template <typename T>
+cudaError_t launch_toeplitz(ivis_plan_s *p) {
+    typedef typename cplx_of<T>::type C;
+    const int nb = p->cfg.nb, nf = p->nf, tpl = nf / 16, lpb = 256 / tpl;
+    C *rowbuf = (C *)p->rowbuf;
+    dim3 gr((nb + lpb - 1) / lpb, p->nslot);
+    size_t smem_row = (size_t)fft_smem_elems(nf, lpb) * sizeof(C);
+    cudaFuncSetAttribute(k_fwd_rows<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_row);
+    k_fwd_rows<T><<<gr, 256, smem_row, p->stream>>>(
+        (const T *)p->x, (const T *)p->beams_d, p->pinfo_d, (const T *)p->ones_d, rowbuf,
+        p->cfg.n, nb, p->lognf, (const C *)p->tw_d, (const float2 *)p->grids_d);
+    dim3 gc(nf >> p->logc_cols, p->nslot);
+    size_t smem_col = (size_t)fft_smem_elems(nf, 1 << p->logc_cols) * sizeof(C);
+    cudaFuncSetAttribute(k_toep_cols<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_col);
+    k_toep_cols<T><<<gc, tpl << p->logc_cols, smem_col, p->stream>>>(
+        rowbuf, (const T *const *)p->that_ptr_d, nb, p->lognf, p->logc_cols, (const C *)p->tw_d);
+    cudaFuncSetAttribute(k_toep_rows<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_row);
+    k_toep_rows<T><<<gr, 256, smem_row, p->stream>>>(
+        rowbuf, (const T *)p->x, (const T *)p->beams_d, p->pinfo_d, (const T *const *)p->bwin_ptr_d,
+        p->qconst_d, (T *)p->contrib, p->jpart, p->cfg.n, nb, p->lognf, (const C *)p->tw_d,
+        (const float2 *)p->grids_d);
+    return cudaGetLastError();
+}
+
 template <typename T>
 size_t conv_smem(int R) {
     const size_t strip = std::max((size_t)(CONV_TO + 2 * R) * 33, (size_t)(CONV_SPLIT - 1) * 8 * CONV_OPT * 32);
@@ -408,7 +445,12 @@ cudaError_t enqueue_eval(ivis_plan_s *p, bool capture) {
         stage_end(p, st, si);
         if (fork) cudaEventRecord(p->ev_join, p->side);
     }
-    if (p->nslot > 0) {
+    if (p->nslot > 0 && p->cfg.toeplitz) {
+        stage_begin(p, "toeplitz_data_term", p->stream, si);
+        if ((e = launch_toeplitz<T>(p)) != cudaSuccess) return e;
+        launches += 3;
+        stage_end(p, p->stream, si);
+    } else if (p->nslot > 0) {
         stage_begin(p, "zero_adjoint_grid", p->stream, si);
         cudaMemsetAsync(p->G, 0, (size_t)p->nslot * p->nf * p->nf * sizeof(C), p->stream);
         stage_end(p, p->stream, si);
@@ -457,7 +499,8 @@ cudaError_t enqueue_eval(ivis_plan_s *p, bool capture) {
     }
     stage_end(p, p->stream, si);
     stage_begin(p, "finalize", p->stream, si);
-    k_finalize<<<1, 1024, 0, p->stream>>>(p->jpart, p->nchunk, p->kpart, use_k ? p->nkpart : 0,
+    k_finalize<<<1, 1024, 0, p->stream>>>(p->jpart, p->cfg.toeplitz ? p->njpart : p->nchunk, p->kpart,
+                                         use_k ? p->nkpart : 0,
                                          p->rpart, use_r ? p->nrpart : 0, p->cfg.lambda_r,
                                          p->cfg.lambda_s, p->cost_d);
     launches += 1;
@@ -579,7 +622,92 @@ ivis_status set_vis_impl(ivis_plan_s *p, PairHost &ph, int m, const float *uvw, 
     return IVIS_OK;
 }
 
+// Toeplitz data of one pair (toeplitz = 1), from the caller's arrays: a plan with one
+// pointing of window 2nb and unit beam over a 2nb x 2nb sky holds the pair twice, as channel 0
+// with unit visibilities and as channel 1 with the data. Its gradient at I = 0 is
+// -Re(F^H W 1) = -Re T on the offsets d in [-nb, nb)^2 (channel 0) and -Re(F^H W V) on the
+// same window (channel 1, whose centre nb x nb is -b). The spectrum of the even cyclic
+// embedding of Re T then comes from one nf x nf DFT; C from an FP64 sum over the data.
+template <typename T>
+ivis_status toeplitz_pair(ivis_plan_s *p, PairHost &ph, int m, const float *uvw, const float *vis,
+                          const float *w) {
+    typedef typename cplx_of<T>::type C;
+    const int nb = p->cfg.nb, nf = p->nf, n2 = 2 * nb, tpl = nf / 16, lpb = 256 / tpl;
+    ivis_status s;
+    if (!p->toep_sub) {
+        ivis_config c2 = p->cfg;
+        c2.n = n2;
+        c2.nchan = 2;
+        c2.npoint = 1;
+        c2.nb = n2;
+        c2.lambda_r = c2.lambda_s = 0.0;
+        c2.positivity = 0;
+        c2.serial_pairs = 0;
+        c2.autotune = 0;
+        c2.toeplitz = 0;
+        // T and b enter the cost multiplied by the data's energy C, which near a fit's optimum
+        // exceeds Q by orders of magnitude: compute them with the widest kernel (FP64, about
+        // 1e-15) or one cell wider than the plan's (FP32, at its rounding floor)
+        c2.kernel_width = p->fp64 ? 16 : std::min(16, p->W + 1);
+        ivis_plan_t sub = nullptr;
+        if ((s = ivis_plan(&c2, p->stream, &sub))) return fail(p, s, "Toeplitz set-up plan: " + g_plan_error);
+        p->toep_sub = sub;
+        void *ones = nullptr;
+        if ((s = alloc(p, &ones, (size_t)n2 * n2 * sizeof(float)))) return s;
+        k_fill<float><<<(unsigned)(((size_t)n2 * n2 + 255) / 256), 256, 0, p->stream>>>((size_t)n2 * n2, 1.0f, (float *)ones);
+        s = ivis_set_pointing(sub, 0, nb, nb, (const float *)ones);
+        cudaStreamSynchronize(p->stream);
+        dfree(ones);
+        if (s) return fail(p, s, "Toeplitz set-up pointing: " + sub->err);
+    }
+    ivis_plan_s *sub = p->toep_sub;
+    const size_t n22 = (size_t)n2 * n2;
+    const int nblk_e = std::min(1024, (m + 255) / 256);
+    void *uvis = nullptr, *zero = nullptr, *grad = nullptr, *buf = nullptr, *part = nullptr;
+    auto cleanup = [&]() { dfree(uvis); dfree(zero); dfree(grad); dfree(buf); dfree(part); };
+    if ((s = alloc(p, &uvis, (size_t)m * sizeof(float2))) || (s = alloc(p, &zero, 2 * n22 * sizeof(T))) ||
+        (s = alloc(p, &grad, 2 * n22 * sizeof(T))) || (s = alloc(p, &buf, (size_t)nf * nf * sizeof(C))) ||
+        (s = alloc(p, &part, (size_t)nblk_e * sizeof(double))) ||
+        (s = alloc(p, &ph.that, (size_t)nf * nf * sizeof(T))) || (s = alloc(p, &ph.bwin, (size_t)nb * nb * sizeof(T)))) {
+        cleanup();
+        return s;
+    }
+    k_unit_vis<<<(m + 255) / 256, 256, 0, p->stream>>>(m, (float2 *)uvis);
+    cudaMemsetAsync(zero, 0, 2 * n22 * sizeof(T), p->stream);
+    k_vis_energy<<<nblk_e, 256, 0, p->stream>>>(m, vis, w, (double *)part);
+    double cst = 0.0;
+    if ((s = ivis_set_vis(sub, 0, 0, m, uvw, (const float *)uvis, w)) ||
+        (s = ivis_set_vis(sub, 0, 1, m, uvw, vis, w)) ||
+        (s = ivis_cost_grad(sub, zero, &cst, grad, nullptr))) {
+        std::string msg = sub->err;
+        cleanup();
+        return fail(p, s, "Toeplitz set-up: " + msg);
+    }
+    const size_t smem_row = (size_t)fft_smem_elems(nf, lpb) * sizeof(C);
+    cudaFuncSetAttribute(k_toep_embed_rows<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_row);
+    k_toep_embed_rows<T><<<(nf + lpb - 1) / lpb, 256, smem_row, p->stream>>>((const T *)grad, (T)-1, (C *)buf, p->lognf,
+                                                                 (const C *)p->tw_d);
+    const size_t smem_col = (size_t)fft_smem_elems(nf, 1 << p->logc_cols) * sizeof(C);
+    cudaFuncSetAttribute(k_toep_embed_cols<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_col);
+    k_toep_embed_cols<T><<<nf >> p->logc_cols, tpl << p->logc_cols, smem_col, p->stream>>>(
+        (const C *)buf, (T *)ph.that, p->lognf, p->logc_cols, (T)(1.0 / ((double)nf * nf)), (const C *)p->tw_d);
+    k_toep_crop<T><<<(nb * nb + 255) / 256, 256, 0, p->stream>>>((const T *)grad + n22, (T)-1, (T *)ph.bwin, nb);
+    std::vector<double> hp(nblk_e);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hp.data(), part, nblk_e * sizeof(double), cudaMemcpyDeviceToHost, p->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
+    cleanup();
+    if (e != cudaSuccess) return fail(p, IVIS_ERR_CUDA, std::string("Toeplitz set-up: ") + cudaGetErrorString(e));
+    double sum = 0.0;
+    for (double v : hp) sum += v;
+    ph.qconst = 0.5 * sum;
+    return IVIS_OK;
+}
+
 void free_pair(PairHost &ph) {
+    dfree(ph.that);
+    dfree(ph.bwin);
+    ph.qconst = 0.0;
     dfree(ph.coord);
     dfree(ph.vis);
     dfree(ph.w);
@@ -602,6 +730,10 @@ void release_prepared(ivis_plan_s *p) {
     dfree(p->x); dfree(p->g); dfree(p->tmp1); dfree(p->tmp2); dfree(p->gradK);
     void *a = p->jpart, *b = p->kpart, *c = p->rpart, *d = p->cost_d;
     dfree(a); dfree(b); dfree(c); dfree(d);
+    void *tp = p->that_ptr_d, *bp = p->bwin_ptr_d, *qc = p->qconst_d;
+    dfree(tp); dfree(bp); dfree(qc);
+    p->that_ptr_d = p->bwin_ptr_d = nullptr;
+    p->qconst_d = nullptr;
     p->jpart = p->kpart = p->rpart = p->cost_d = nullptr;
     solver_free(p->solver);
     p->prepared = false;
@@ -632,7 +764,8 @@ std::string tune_key(const ivis_plan_s *p) {
     int mb = 0;  // visibility-count class: power of two
     while ((1LL << mb) < m) ++mb;
     return "nf=" + std::to_string(p->nf) + " w=" + std::to_string(p->W) + " fp64=" + std::to_string((int)p->fp64) +
-           " nslot=" + std::to_string(p->nslot) + " m2=" + std::to_string(mb);
+           " nslot=" + std::to_string(p->nslot) + " m2=" + std::to_string(mb) +
+           (p->cfg.toeplitz ? " toeplitz" : "");
 }
 
 // Autotuner: picks the grid-pass chunk size and the number of columns per CTA of the column
@@ -680,7 +813,14 @@ ivis_status autotune(ivis_plan_s *p) {
                 (1 << lc) > p->nf)
                 continue;
             p->logc_cols = lc;
-            const float ms = timed([&] { launch_forward<T>(p, p->x); launch_adjoint<T>(p); });
+            const float ms = timed([&] {
+                if (p->cfg.toeplitz) {
+                    launch_toeplitz<T>(p);
+                } else {
+                    launch_forward<T>(p, p->x);
+                    launch_adjoint<T>(p);
+                }
+            });
             if (ms < bt) { bt = ms; best_logc = lc; }
         }
         // grid-pass chunk size
@@ -788,7 +928,30 @@ ivis_status prepare_impl(ivis_plan_s *p) {
     if ((s = alloc(p, &p->contrib, (size_t)p->nslot * c.nb * c.nb * sizeof(T)))) return s;
     if ((s = alloc(p, &p->x, npix * sizeof(T)))) return s;
     if ((s = alloc(p, &p->g, npix * sizeof(T)))) return s;
-    if ((s = alloc(p, (void **)&p->jpart, std::max<size_t>(1, max_chunks) * sizeof(double)))) return s;
+    size_t njp = std::max<size_t>(1, max_chunks);
+    if (c.toeplitz) {
+        // per-slot spectrum and b pointers, constants; one partial per row-pass CTA
+        const int lpb = 256 / (p->nf / 16);
+        p->njpart = p->nslot * ((c.nb + lpb - 1) / lpb);
+        njp = std::max<size_t>(njp, (size_t)p->njpart);
+        std::vector<void *> tp(p->nslot), bp(p->nslot);
+        std::vector<double> qc(p->nslot);
+        for (int sl = 0; sl < p->nslot; ++sl) {
+            const PairHost &ph = p->pairs[p->slot_pair[sl]];
+            if (!ph.that || !ph.bwin) return fail(p, IVIS_ERR_STATE, "Toeplitz data of a pair missing");
+            tp[sl] = ph.that;
+            bp[sl] = ph.bwin;
+            qc[sl] = ph.qconst;
+        }
+        if ((s = up((void **)&p->that_ptr_d, tp.data(), tp.size() * sizeof(void *)))) return s;
+        if ((s = up((void **)&p->bwin_ptr_d, bp.data(), bp.size() * sizeof(void *)))) return s;
+        if ((s = up((void **)&p->qconst_d, qc.data(), qc.size() * sizeof(double)))) return s;
+        if (p->toep_sub) {  // its buffers are not needed until the next ivis_set_vis
+            ivis_destroy(p->toep_sub);
+            p->toep_sub = nullptr;
+        }
+    }
+    if ((s = alloc(p, (void **)&p->jpart, njp * sizeof(double)))) return s;
     p->nrpart = (int)((npix + 255) / 256);
     if ((s = alloc(p, (void **)&p->rpart, (size_t)p->nrpart * sizeof(double)))) return s;
     if ((s = alloc(p, (void **)&p->cost_d, 4 * sizeof(double)))) return s;
@@ -1073,6 +1236,8 @@ ivis_status ivis_plan(const ivis_config *cfg, void *stream, ivis_plan_t *out) {
     if (c.kernel_width == 0 && !(c.nufft_tol > 0.0 && c.nufft_tol < 1.0)) return fail(nullptr, IVIS_ERR_ARG, "nufft_tol must be in (0, 1)");
     if (!std::isfinite(c.lambda_r) || !std::isfinite(c.lambda_s) || c.lambda_r < 0 || c.lambda_s < 0)
         return fail(nullptr, IVIS_ERR_NONFINITE, "lambda_r and lambda_s must be finite and >= 0");
+    if (c.toeplitz && c.nb > 1024) return fail(nullptr, IVIS_ERR_ARG, "toeplitz needs nb <= 1024");
+    if (c.toeplitz && c.serial_pairs) return fail(nullptr, IVIS_ERR_ARG, "toeplitz and serial_pairs are exclusive");
     ivis_plan_s *p = new (std::nothrow) ivis_plan_s();
     if (!p) return fail(nullptr, IVIS_ERR_OOM, "host allocation failed");
     p->cfg = c;
@@ -1139,6 +1304,10 @@ ivis_status ivis_plan(const ivis_config *cfg, void *stream, ivis_plan_t *out) {
         if (cudaMemset(p->beams_d, 0, (size_t)c.npoint * c.nb * c.nb * p->rsz) != cudaSuccess) s = IVIS_ERR_CUDA;
     }
     if (!s) s = alloc(p, &p->tsd_d, (size_t)c.nchan * c.n * c.n * p->rsz);
+    if (!s && c.toeplitz) {
+        s = p->fp64 ? upload_real<double>(p, &p->ones_d, std::vector<double>(c.nb, 1.0))
+                    : upload_real<float>(p, &p->ones_d, std::vector<double>(c.nb, 1.0));
+    }
     if (!s && cudaStreamCreateWithFlags(&p->side, cudaStreamNonBlocking) != cudaSuccess) s = IVIS_ERR_CUDA;
     if (!s && cudaEventCreateWithFlags(&p->ev_in, cudaEventDisableTiming) != cudaSuccess) s = IVIS_ERR_CUDA;
     for (int i = 0; i < MAX_STAGES && !s; ++i)
@@ -1207,8 +1376,13 @@ ivis_status ivis_set_vis(ivis_plan_t p, int k, int chan, int64_t m, const float 
         ph.set = true;
         return IVIS_OK;
     }
-    return p->fp64 ? set_vis_impl<double>(p, ph, (int)m, uvw_dev, vis_dev, weight_dev)
-                   : set_vis_impl<float>(p, ph, (int)m, uvw_dev, vis_dev, weight_dev);
+    ivis_status s = p->fp64 ? set_vis_impl<double>(p, ph, (int)m, uvw_dev, vis_dev, weight_dev)
+                            : set_vis_impl<float>(p, ph, (int)m, uvw_dev, vis_dev, weight_dev);
+    if (!s && p->cfg.toeplitz)
+        s = p->fp64 ? toeplitz_pair<double>(p, ph, (int)m, uvw_dev, vis_dev, weight_dev)
+                    : toeplitz_pair<float>(p, ph, (int)m, uvw_dev, vis_dev, weight_dev);
+    if (s) free_pair(ph);
+    return s;
 }
 
 ivis_status ivis_set_sd(ivis_plan_t p, int chan, const float *tsd_dev, double sigma_sd, double fwhm_pix) {
@@ -1479,6 +1653,9 @@ ivis_status ivis_destroy(ivis_plan_t p) {
     }
     dfree(p->beams_d);
     dfree(p->tsd_d);
+    dfree(p->ones_d);
+    if (p->toep_sub) ivis_destroy(p->toep_sub);
+    p->toep_sub = nullptr;
     dfree(p->grids_d);
     for (auto &st : p->stages) {
         if (st.b) cudaEventDestroy(st.b);

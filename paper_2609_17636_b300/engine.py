@@ -36,7 +36,7 @@ class Plan:
                  precision: str = "fp32", nufft_tol: float | None = None, kernel_width: int = 0,
                  lambda_r: float = 0.0, lambda_s: float = 0.0, positivity: bool = True,
                  stream: torch.cuda.Stream | None = None, serial_pairs: bool = False,
-                 autotune: bool = False):
+                 autotune: bool = False, toeplitz: bool = False):
         self.L = _lib.load()
         if precision not in ("fp32", "fp64"):
             raise ValueError("precision must be 'fp32' or 'fp64'")
@@ -47,7 +47,7 @@ class Plan:
         self.cfg = _lib.Config(n, nchan, npoint, nb, cell_rad,
                                IVIS_FP32 if precision == "fp32" else IVIS_FP64,
                                nufft_tol, kernel_width, lambda_r, lambda_s, int(bool(positivity)),
-                               int(bool(serial_pairs)), int(bool(autotune)))
+                               int(bool(serial_pairs)), int(bool(autotune)), int(bool(toeplitz)))
         self.shape = (nchan, n, n)
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         self._p = ctypes.c_void_p()

@@ -425,3 +425,61 @@ def test_gridded_data_gradient_central_differences():
     x = prob.sky_true * rng.uniform(0.5, 1.5, prob.sky_true.shape)
     _fd_check(lambda z: oracle.data_cost_grad(prob, z), x, rng.choice(x.size, 15, replace=False),
               1e-4 * np.abs(x).max())
+
+
+# ------------------------------------------------- Toeplitz form of the data term (Eqs. 3-6)
+def test_psf_kernel_centre_symmetry_and_normal_matrix():
+    """T(0) = sum w; T(-d) = conj T(d); and on a tiny window the explicit normal matrix
+    F^H W F (built column by column from the forward DFT) has entries T(p - q)."""
+    prob = _with_data(synth.small_mosaic(41, n=24, nb=8, nchan=1, npoint=1, ndump=3, n_ant=5,
+                                         lambda_r=0.0, lambda_s=0.0))
+    pair = prob.pairs[0]
+    nb = prob.nb
+    T = oracle.psf_kernel(pair, nb, prob.cell_rad)
+    w = pair.weight.astype(np.float64)
+    assert abs(T[nb, nb] - w.sum()) <= 1e-12 * w.sum()
+    for dy, dx in [(1, 2), (-3, 5), (7, -7), (0, -4)]:
+        assert abs(T[nb - dy, nb - dx] - np.conj(T[nb + dy, nb + dx])) <= 1e-9 * w.sum()
+    cols = []
+    for i in range(nb * nb):
+        e = np.zeros((nb, nb))
+        e.flat[i] = 1.0
+        cols.append(oracle.model_vis(e, prob.cell_rad, pair.uvw[:, 0], pair.uvw[:, 1]))
+    F = np.array(cols).T                                  # [m][nb*nb]
+    H = F.conj().T @ (w[:, None] * F)
+    qy, qx = np.divmod(np.arange(nb * nb), nb)
+    Tpq = T[nb + qy[:, None] - qy[None, :], nb + qx[:, None] - qx[None, :]]
+    assert np.allclose(H, Tpq, rtol=0, atol=1e-9 * w.sum())
+
+
+def test_toeplitz_data_term_equals_the_direct_one():
+    """The expansion is exact: the Toeplitz cost and gradient equal the direct ones (Eqs. 5-6)
+    to rounding, windows off the sky edge and ragged pairs included; a re-projected pointing
+    too (the operator acts on the window)."""
+    prob = _with_data(synth.small_mosaic(42, n=40, nb=16, nchan=2, npoint=3, ndump=4, n_ant=6,
+                                         lambda_r=0.0, lambda_s=0.0))
+    prob.grids = {1: synth.projection_grid(16, float(prob.centres[1][0]) + 0.3,
+                                           float(prob.centres[1][1]) - 0.6, 0.2, 1.05, 0.02)}
+    x = np.abs(np.random.default_rng(42).standard_normal(prob.sky_true.shape))
+    Q, g = oracle.data_cost_grad(prob, x)
+    Qt, gt = oracle.toeplitz_data_cost_grad(prob, x)
+    assert abs(Qt - Q) <= 1e-11 * Q
+    assert np.linalg.norm(gt - g) <= 1e-11 * np.linalg.norm(g)
+
+
+def test_toeplitz_single_zero_spacing_closed_form():
+    """One visibility at u = v = 0 (T = w everywhere): the model is the window sum, so
+    Q = w/2 |sum z - V|^2 and dQ/dz = w (sum z - Re V) on every window pixel."""
+    prob = synth.small_mosaic(43, n=16, nb=16, nchan=1, npoint=1, ndump=1, n_ant=2,
+                              lambda_r=0.0, lambda_s=0.0)
+    prob.centres[:] = [8, 8]
+    pair = prob.pairs[0]
+    pair.uvw = np.zeros((1, 3), np.float32)
+    pair.weight = np.array([2.5], np.float32)
+    pair.vis = np.array([1.5 - 0.25j], np.complex64)
+    x = np.random.default_rng(43).uniform(0, 1, (1, 16, 16))
+    A = prob.beams[0].astype(np.float64)
+    s = float(np.sum(A * x[0]))
+    Q, g = oracle.toeplitz_data_cost_grad(prob, x)
+    assert abs(Q - 0.5 * 2.5 * ((s - 1.5) ** 2 + 0.25 ** 2)) <= 1e-12 * Q
+    assert np.allclose(g[0], A * 2.5 * (s - 1.5), rtol=1e-12, atol=0)

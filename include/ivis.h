@@ -223,6 +223,23 @@ ivis_status ivis_sd_predict_noalloc(const float *sky_dev, int n, int nchan, doub
  * sum_k A_k^2 of the linear mosaic of Sect. 4.3 (real [n][n]). */
 ivis_status ivis_dirty_image(ivis_plan_t plan, void *dirty_dev, void *beamw_dev);
 
+/* Short-spacing correction by feathering (the paper's appendix; a post-processing step of the
+ * reconstructed cube): per channel, on the plan's n x n grid with no padding,
+ *     out = IDFT[ B DFT(sd_scale * sd) + (1 - B) DFT(int) ],
+ *     B(k) = exp(-2 pi^2 sigma^2 |k|^2),  sigma = theta / (2 sqrt(2 ln 2)),
+ * with k in cycles per radian (theta_rad in radians; pixels of the plan's cell_rad); the real
+ * part is returned. int_dev and out_dev: real [nchan][n][n] in the plan's precision (out must
+ * not alias int); sd_dev: float [nchan][n][n], the single-dish map regridded onto the image
+ * grid, multiplied by sd_scale (e.g. ivis_rayleigh_jeans(nu) for maps in kelvin). Needs n a
+ * power of two in [16, 4096]. Errors: IVIS_ERR_ARG. Runs on the plan's stream; returns after
+ * the result is written. */
+ivis_status ivis_feather(ivis_plan_t plan, const void *int_dev, const float *sd_dev, double theta_rad,
+                         double sd_scale, void *out_dev);
+
+/* Rayleigh-Jeans conversion of the same appendix: Jy per square arcsecond per kelvin of
+ * brightness temperature at frequency freq_hz, 2 k nu^2 / c^2 (SI constants). */
+double ivis_rayleigh_jeans(double freq_hz);
+
 /* ---- learned warm start: a 4-level U-Net [dirty image, beam-weight map] -> initial sky ----
  * No counterpart in the paper (its closest hook is the "physically motivated priors" of its
  * future prospects). Per level two 3x3 convolutions + ReLU; encoder widths c, 2c, 4c, 8c with

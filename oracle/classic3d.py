@@ -12,7 +12,7 @@ __all__ = [
     "pair_model_vis", "data_cost_grad", "data_grad_pixels", "laplacian", "reg_cost_grad",
     "dish_kernel", "dish_conv", "fusion_cost_grad", "cost_grad", "solve_lbfgsb",
     "LAPLACIAN_KERNEL", "bilinear", "bilinear_adjoint", "pointing_window", "pointing_window_adjoint",
-    "psf_kernel", "toeplitz_data_cost_grad",
+    "psf_kernel", "toeplitz_data_cost_grad", "rayleigh_jeans_factor", "feather",
 ]
 
 # Eq. 7: the Laplacian kernel d of the regulariser.
@@ -268,6 +268,38 @@ def toeplitz_data_cost_grad(prob, sky: np.ndarray):
         Q += 0.5 * float(np.sum(z * Hz.real)) - float(np.sum(z * b)) + 0.5 * float(np.sum(w * np.abs(V) ** 2))
         grad[pair.chan] += pointing_window_adjoint(prob, A * (Hz.real - b), pair.k, sky.shape[1:])
     return Q, grad
+
+
+# --------------------------------------------- short-spacing correction by feathering (appendix)
+K_BOLTZMANN = 1.380649e-23      # J / K (SI, exact)
+C_LIGHT = 299_792_458.0         # m / s (SI, exact)
+JANSKY = 1e-26                  # W m^-2 Hz^-1
+ARCSEC2_SR = (math.pi / (180.0 * 3600.0)) ** 2
+
+
+def rayleigh_jeans_factor(freq_hz: float) -> float:
+    """Jy arcsec^-2 per kelvin of brightness temperature: I = 2 k nu^2 / c^2 T_B, converted
+    from W m^-2 Hz^-1 sr^-1 to Jy per square arcsecond."""
+    return 2.0 * K_BOLTZMANN * freq_hz ** 2 / C_LIGHT ** 2 / JANSKY * ARCSEC2_SR
+
+
+def feather(i_int: np.ndarray, i_sd: np.ndarray, theta_pix: float, sd_scale: float = 1.0):
+    """Feathered image of each channel: DFT of both maps on the image grid (no padding),
+    I~_comb = B I~_SD + (1 - B) I~_int with the Gaussian transfer function
+    B(k) = exp(-2 pi^2 sigma^2 |k|^2), sigma = theta / (2 sqrt(2 ln 2)), k in cycles per pixel
+    (theta in pixels), then the inverse DFT (real part). i_sd is multiplied by sd_scale first
+    (a unit conversion such as rayleigh_jeans_factor)."""
+    i_int = _f64(i_int)
+    i_sd = _f64(i_sd) * sd_scale
+    n = i_int.shape[-1]
+    sig = theta_pix / (2.0 * math.sqrt(2.0 * math.log(2.0)))
+    k = np.fft.fftfreq(n)
+    B = np.exp(-2.0 * math.pi ** 2 * sig ** 2 * (k[:, None] ** 2 + k[None, :] ** 2))
+    out = np.empty_like(i_int)
+    for c in range(i_int.shape[0]):
+        comb = B * np.fft.fft2(i_sd[c]) + (1.0 - B) * np.fft.fft2(i_int[c])
+        out[c] = np.fft.ifft2(comb).real
+    return out
 
 
 # ------------------------------------------------------------------- regulariser (Eqs. 7-8)

@@ -27,7 +27,7 @@ EXPORTS = ["ivis_plan", "ivis_set_pointing", "ivis_set_pointing_grid", "ivis_set
            "ivis_dirty_image", "ivis_solve_target", "ivis_tuning", "ivis_unet_create", "ivis_unet_num_params", "ivis_unet_set_params",
            "ivis_unet_get_params", "ivis_unet_forward", "ivis_unet_backward", "ivis_unet_get_grads",
            "ivis_unet_adam_step", "ivis_unet_use_tcgen05", "ivis_unet_destroy",
-           "ivis_unet_last_error"]
+           "ivis_unet_last_error", "ivis_feather", "ivis_rayleigh_jeans"]
 
 
 class IvisError(RuntimeError):
@@ -101,8 +101,11 @@ def load(path: str = LIB_PATH):
     L.ivis_unet_destroy.argtypes = [vp]
     L.ivis_unet_last_error.argtypes = [vp]
     L.ivis_unet_last_error.restype = ctypes.c_char_p
+    L.ivis_feather.argtypes = [vp, vp, vp, d, d, vp]
+    L.ivis_rayleigh_jeans.argtypes = [d]
+    L.ivis_rayleigh_jeans.restype = d
     for name in EXPORTS:
-        if name not in ("ivis_last_error", "ivis_unet_last_error"):
+        if name not in ("ivis_last_error", "ivis_unet_last_error", "ivis_rayleigh_jeans"):
             getattr(L, name).restype = ctypes.c_int
     _LIB = L
     return L

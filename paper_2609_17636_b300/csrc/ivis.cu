@@ -22,6 +22,7 @@
 #include "kernels_image.cuh"
 #include "kernels_nufft.cuh"
 #include "kernels_solver.cuh"
+#include "kernels_feather.cuh"
 #include "kernels_toeplitz.cuh"
 
 using namespace ivis;
@@ -100,6 +101,8 @@ struct ivis_plan_s {
     void **that_ptr_d = nullptr, **bwin_ptr_d = nullptr;  // per slot
     double *qconst_d = nullptr;       // per slot
     int njpart = 0;                   // FP64 data-term partials summed by k_finalize
+    // feathering
+    void *feather_tw_d = nullptr, *feather_b1_d = nullptr;  // DFT twiddles and b1 of length n
     cudaGraphExec_t graph = nullptr;
     int launches = 0;
     bool capturing = false;
@@ -1178,6 +1181,59 @@ ivis_status dirty_impl(ivis_plan_s *p, void *dirty_dev, void *beamw_dev) {
 
 }  // namespace
 
+namespace {
+// Short-spacing correction by feathering (appendix): both separable passes of the Gaussian
+// transfer function on the n x n grid.
+template <typename T>
+ivis_status feather_impl(ivis_plan_s *p, const void *int_dev, const float *sd_dev, double theta_pix,
+                         double sd_scale, void *out_dev) {
+    typedef typename cplx_of<T>::type C;
+    const int n = p->cfg.n, nchan = p->cfg.nchan, logn = ilog2(n);
+    ivis_status s;
+    if (!p->feather_tw_d) {
+        std::vector<C> tw(n);
+        for (int j = 0; j < n; ++j) {
+            const double a = 2.0 * M_PI * j / n;
+            tw[j].x = (T)std::cos(a);
+            tw[j].y = (T)(-std::sin(a));
+        }
+        if ((s = alloc(p, &p->feather_tw_d, n * sizeof(C)))) return s;
+        CK(cudaMemcpy(p->feather_tw_d, tw.data(), n * sizeof(C), cudaMemcpyHostToDevice));
+        if ((s = alloc(p, &p->feather_b1_d, n * sizeof(T)))) return s;
+    }
+    // b1 at the DFT frequency of each index, k = j / n or (j - n) / n cycles per pixel
+    const double sig = theta_pix / (2.0 * std::sqrt(2.0 * std::log(2.0)));
+    std::vector<T> b1(n);
+    for (int j = 0; j < n; ++j) {
+        const double k = (j < (n + 1) / 2 ? j : j - n) / (double)n;
+        b1[j] = (T)std::exp(-2.0 * M_PI * M_PI * sig * sig * k * k);
+    }
+    CK(cudaMemcpyAsync(p->feather_b1_d, b1.data(), n * sizeof(T), cudaMemcpyHostToDevice, p->stream));
+    const int tpl = n / 16, lpb = 256 / tpl;
+    dim3 gr((n / 2 + lpb - 1) / lpb, nchan);
+    const size_t smem_row = (size_t)fft_smem_elems(n, lpb) * sizeof(C);
+    cudaFuncSetAttribute(k_feather_rows<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_row);
+    k_feather_rows<T><<<gr, 256, smem_row, p->stream>>>((const T *)int_dev, sd_dev, (T)sd_scale,
+                                                        (const T *)p->feather_b1_d, (T *)out_dev, n, logn,
+                                                        (const C *)p->feather_tw_d);
+    int logc = 0;
+    auto fits = [&](int l) {
+        return (size_t)fft_smem_elems(n, 1 << l) * sizeof(C) <= 100 * 1024 && (tpl << l) <= (p->fp64 ? 512 : 1024) &&
+               (2 << l) <= n;
+    };
+    while (logc < 4 && fits(logc + 1)) ++logc;
+    dim3 gc(n / (2 << logc), nchan);
+    const size_t smem_col = (size_t)fft_smem_elems(n, 1 << logc) * sizeof(C);
+    cudaFuncSetAttribute(k_feather_cols<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_col);
+    k_feather_cols<T><<<gc, tpl << logc, smem_col, p->stream>>>((const T *)int_dev, (const T *)p->feather_b1_d,
+                                                                (T *)out_dev, n, logn, logc,
+                                                                (const C *)p->feather_tw_d);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(p->stream));
+    return IVIS_OK;
+}
+}  // namespace
+
 // ------------------------------------------------ allocation-free single-dish prediction
 // Some callers cannot allocate device memory at the point where they need B (x) I: for
 // example code that runs while the device allocator must not be touched (inside a region
@@ -1597,6 +1653,27 @@ ivis_status ivis_dirty_image(ivis_plan_t p, void *dirty_dev, void *beamw_dev) {
     return p->fp64 ? dirty_impl<double>(p, dirty_dev, beamw_dev) : dirty_impl<float>(p, dirty_dev, beamw_dev);
 }
 
+ivis_status ivis_feather(ivis_plan_t p, const void *int_dev, const float *sd_dev, double theta_rad,
+                         double sd_scale, void *out_dev) {
+    if (!p) return fail(nullptr, IVIS_ERR_ARG, "null plan");
+    if (!int_dev || !sd_dev || !out_dev) return fail(p, IVIS_ERR_ARG, "null pointer");
+    if (out_dev == int_dev) return fail(p, IVIS_ERR_ARG, "out must not alias the interferometric map");
+    const int n = p->cfg.n;
+    if (!is_pow2(n) || n < 16 || n > 4096) return fail(p, IVIS_ERR_ARG, "feathering needs n a power of two in [16, 4096]");
+    if (!(theta_rad > 0.0) || !std::isfinite(theta_rad) || !std::isfinite(sd_scale))
+        return fail(p, IVIS_ERR_ARG, "theta must be finite and > 0, sd_scale finite");
+    enter(p);
+    const double theta_pix = theta_rad / p->cfg.cell_rad;
+    return p->fp64 ? feather_impl<double>(p, int_dev, sd_dev, theta_pix, sd_scale, out_dev)
+                   : feather_impl<float>(p, int_dev, sd_dev, theta_pix, sd_scale, out_dev);
+}
+
+double ivis_rayleigh_jeans(double freq_hz) {
+    // 2 k nu^2 / c^2 in W m^-2 Hz^-1 sr^-1 per kelvin -> Jy per square arcsecond
+    const double k_b = 1.380649e-23, c = 299792458.0, arcsec = M_PI / (180.0 * 3600.0);
+    return 2.0 * k_b * freq_hz * freq_hz / (c * c) / 1e-26 * arcsec * arcsec;
+}
+
 ivis_status ivis_sd_predict_noalloc(const float *sky_dev, int n, int nchan, double fwhm_pix,
                                     float *out_dev, void *stream) {
     if (!sky_dev || !out_dev) return noalloc_fail(IVIS_ERR_ARG, "null sky or output pointer");
@@ -1654,6 +1731,8 @@ ivis_status ivis_destroy(ivis_plan_t p) {
     dfree(p->beams_d);
     dfree(p->tsd_d);
     dfree(p->ones_d);
+    dfree(p->feather_tw_d);
+    dfree(p->feather_b1_d);
     if (p->toep_sub) ivis_destroy(p->toep_sub);
     p->toep_sub = nullptr;
     dfree(p->grids_d);

@@ -165,6 +165,17 @@ class Plan:
         return {"iterations": rep.iterations, "evaluations": rep.evaluations, "f": rep.f,
                 "pg_inf": rep.pg_inf, "seconds": rep.seconds, "status": rep.status}
 
+    def feather(self, sky: torch.Tensor, sd: torch.Tensor, theta_rad: float,
+                sd_scale: float = 1.0) -> torch.Tensor:
+        """Short-spacing correction by feathering (ivis_feather): returns a new cube."""
+        sky = self._sky(sky)
+        sd = _dev_f32(sd, self.shape)
+        out = torch.empty_like(sky)
+        _check(self.L, self._p, self.L.ivis_feather(self._p, ctypes.c_void_p(sky.data_ptr()),
+                                                    ctypes.c_void_p(sd.data_ptr()), float(theta_rad),
+                                                    float(sd_scale), ctypes.c_void_p(out.data_ptr())))
+        return out
+
     # ------------------------------------------------------------------ introspection
     def nufft_params(self):
         w, beta, nf = ctypes.c_int(), ctypes.c_double(), ctypes.c_int()
@@ -311,6 +322,11 @@ class UNet:
             self.close()
         except Exception:
             pass
+
+
+def rayleigh_jeans(freq_hz: float) -> float:
+    """Jy per square arcsecond per kelvin at freq_hz (ivis_rayleigh_jeans)."""
+    return float(_lib.load().ivis_rayleigh_jeans(float(freq_hz)))
 
 
 def dirty_image(plan: Plan):

@@ -54,3 +54,11 @@ def test_plan_rejects_bad_config_without_gpu():
     st = L.ivis_plan(ctypes.byref(cfg), None, ctypes.byref(p))
     assert st == 1 and not p.value
     assert b"power of two" in L.ivis_last_error(None)
+
+
+def test_rayleigh_jeans_entry_point_matches_the_oracle():
+    """A host-only entry point: callable without a GPU."""
+    import oracle
+    from paper_2609_17636_b300 import rayleigh_jeans
+    for f in (1.0e8, 1.4204058e9, 2.3e10):
+        assert abs(rayleigh_jeans(f) - oracle.rayleigh_jeans_factor(f)) <= 1e-14 * oracle.rayleigh_jeans_factor(f)

@@ -483,3 +483,44 @@ def test_toeplitz_single_zero_spacing_closed_form():
     Q, g = oracle.toeplitz_data_cost_grad(prob, x)
     assert abs(Q - 0.5 * 2.5 * ((s - 1.5) ** 2 + 0.25 ** 2)) <= 1e-12 * Q
     assert np.allclose(g[0], A * 2.5 * (s - 1.5), rtol=1e-12, atol=0)
+
+
+# ------------------------------------------------- feathering (short-spacing appendix)
+def test_rayleigh_jeans_factor_matches_the_radio_rule_of_thumb():
+    """T_B = 1.222e3 S / (nu^2 theta^2) (K, mJy per Gaussian beam, GHz, arcsec; the standard
+    NRAO conversion) gives S / Omega for 1 K at 1.4204 GHz with Omega = pi theta^2 / (4 ln 2)."""
+    nu_ghz, theta = 1.4204058, 7.0
+    s_mjy = nu_ghz ** 2 * theta ** 2 / 1.222e3
+    omega = math.pi * theta ** 2 / (4.0 * math.log(2.0))
+    ref = s_mjy * 1e-3 / omega
+    assert abs(oracle.rayleigh_jeans_factor(nu_ghz * 1e9) - ref) <= 1e-3 * ref
+
+
+def test_feather_limits_and_identities():
+    rng = np.random.default_rng(51)
+    a = rng.standard_normal((2, 64, 64))
+    b = rng.standard_normal((2, 64, 64))
+    # identical maps are left unchanged
+    assert np.allclose(oracle.feather(a, a, 9.0), a, atol=1e-12)
+    # theta -> 0: B = 1 everywhere, the single-dish map
+    assert np.allclose(oracle.feather(a, b, 1e-9), b, atol=1e-12)
+    # theta -> infinity: only the k = 0 term of the single-dish map survives
+    big = oracle.feather(a, b, 1e6)
+    assert np.allclose(big, a + (b - a).mean(axis=(1, 2), keepdims=True), atol=1e-10)
+    # the scale multiplies the single-dish map
+    assert np.allclose(oracle.feather(a, b, 5.0, 2.5), oracle.feather(a, 2.5 * b, 5.0), atol=1e-12)
+
+
+def test_feather_of_an_impulse_is_the_gaussian_of_the_transfer_function():
+    """Interferometric map zero, single-dish map a unit impulse: the result is the inverse
+    transform of B, a unit-area Gaussian of sigma = theta / (2 sqrt(2 ln 2)) pixels (its
+    periodic copies are negligible for sigma << n)."""
+    n, theta = 128, 12.0
+    sd = np.zeros((1, n, n))
+    sd[0, 0, 0] = 1.0
+    out = oracle.feather(np.zeros((1, n, n)), sd, theta)[0]
+    sig = theta / (2.0 * math.sqrt(2.0 * math.log(2.0)))
+    d = np.minimum(np.arange(n), n - np.arange(n))
+    g = np.exp(-(d[:, None] ** 2 + d[None, :] ** 2) / (2 * sig ** 2)) / (2 * math.pi * sig ** 2)
+    assert np.abs(out - g).max() <= 1e-12
+    assert abs(out.sum() - 1.0) <= 1e-12

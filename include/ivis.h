@@ -87,6 +87,15 @@ typedef struct {
                            NUFFT. The FP32 cost carries an absolute error of about 1e-6 C (the
                            NUFFT path's is about 1e-6 sqrt(C Q)), so close to a fit's optimum
                            its relative error is larger than the NUFFT path's.               */
+    int wterm;          /* 1: the full visibility equation (Eq. 1): the w-term
+                           exp(-2 pi i w (n - 1)) and the 1/n factor, n = sqrt(1 - l^2 - m^2),
+                           l, m the window pixel offsets times cell_rad. Computed by w-stacking:
+                           the factor is interpolated between w-planes with the ES kernel of
+                           the uv gridding (same width and accuracy); per pair the planes span
+                           its w range at a spacing 1 / (2 |x_min|), x_min = n - 1 at the
+                           window corner. Each visibility is stored W times (once per plane of
+                           its kernel support). Excludes toeplitz and serial_pairs; needs the
+                           window within l^2 + m^2 < 1/4; ivis_dirty_image is not available. */
 } ivis_config;
 
 typedef struct {

@@ -34,6 +34,10 @@ def lib():
         L.ivo_adjoint.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_int64, dp, dp, dp, dp]
         L.ivo_adjoint_pixels.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_int64, dp, dp,
                                          dp, ctypes.c_int64, ip, ip, dp]
+        L.ivo_forward_w.argtypes = [ctypes.c_int, ctypes.c_double, dp, ctypes.c_int64, dp, dp, dp, dp]
+        L.ivo_adjoint_w.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_int64, dp, dp, dp, dp, dp]
+        L.ivo_adjoint_pixels_w.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_int64, dp, dp,
+                                           dp, dp, ctypes.c_int64, ip, ip, dp]
         L.ivo_num_threads.restype = ctypes.c_int
         _LIB = L
     return _LIB
@@ -143,13 +147,18 @@ def pointing_window_adjoint(prob, win, k, shape):
 
 
 # ------------------------------------------------------------- non-uniform DFT (Eq. 3) and adjoint
-def model_vis(f: np.ndarray, cell: float, u: np.ndarray, v: np.ndarray) -> np.ndarray:
-    """Direct DFT  V~_j = sum_{q,p} f[q,p] exp(-2 pi i (u_j l_p + v_j m_q))."""
+def model_vis(f: np.ndarray, cell: float, u: np.ndarray, v: np.ndarray, w=None) -> np.ndarray:
+    """Direct DFT  V~_j = sum_{q,p} f[q,p] exp(-2 pi i (u_j l_p + v_j m_q)) (Eq. 3); with w
+    given, the full Eq. 1: f / n and the extra phase w_j (n - 1), n = sqrt(1 - l^2 - m^2)."""
     f = _f64(f)
     nb = f.shape[0]
     u, v = _f64(u), _f64(v)
     out = np.zeros(2 * u.shape[0])
-    lib().ivo_forward(nb, cell, _dp(f), u.shape[0], _dp(u), _dp(v), _dp(out))
+    if w is None:
+        lib().ivo_forward(nb, cell, _dp(f), u.shape[0], _dp(u), _dp(v), _dp(out))
+    else:
+        w = _f64(w)
+        lib().ivo_forward_w(nb, cell, _dp(f), u.shape[0], _dp(u), _dp(v), _dp(w), _dp(out))
     return out[0::2] + 1j * out[1::2]
 
 
@@ -160,25 +169,40 @@ def _cvis(c):
     return out
 
 
-def adjoint(c: np.ndarray, nb: int, cell: float, u: np.ndarray, v: np.ndarray) -> np.ndarray:
-    """a[q,p] = sum_j c_j exp(+2 pi i (u_j l_p + v_j m_q)) over the whole window."""
+def adjoint(c: np.ndarray, nb: int, cell: float, u: np.ndarray, v: np.ndarray, w=None) -> np.ndarray:
+    """a[q,p] = sum_j c_j exp(+2 pi i (u_j l_p + v_j m_q)) over the whole window; with w given,
+    the adjoint of the full Eq. 1 (extra phase +w_j (n - 1), then 1/n)."""
     u, v = _f64(u), _f64(v)
     cv = _cvis(c)
     out = np.zeros(2 * nb * nb)
-    lib().ivo_adjoint(nb, cell, u.shape[0], _dp(u), _dp(v), _dp(cv), _dp(out))
+    if w is None:
+        lib().ivo_adjoint(nb, cell, u.shape[0], _dp(u), _dp(v), _dp(cv), _dp(out))
+    else:
+        w = _f64(w)
+        lib().ivo_adjoint_w(nb, cell, u.shape[0], _dp(u), _dp(v), _dp(w), _dp(cv), _dp(out))
     return (out[0::2] + 1j * out[1::2]).reshape(nb, nb)
 
 
-def adjoint_pixels(c, nb, cell, u, v, qs, ps) -> np.ndarray:
+def adjoint_pixels(c, nb, cell, u, v, qs, ps, w=None) -> np.ndarray:
     u, v = _f64(u), _f64(v)
     cv = _cvis(c)
     qs = np.ascontiguousarray(qs, dtype=np.int32)
     ps = np.ascontiguousarray(ps, dtype=np.int32)
     out = np.zeros(2 * qs.shape[0])
     ip = ctypes.POINTER(ctypes.c_int32)
-    lib().ivo_adjoint_pixels(nb, cell, u.shape[0], _dp(u), _dp(v), _dp(cv), qs.shape[0],
-                             qs.ctypes.data_as(ip), ps.ctypes.data_as(ip), _dp(out))
+    if w is None:
+        lib().ivo_adjoint_pixels(nb, cell, u.shape[0], _dp(u), _dp(v), _dp(cv), qs.shape[0],
+                                 qs.ctypes.data_as(ip), ps.ctypes.data_as(ip), _dp(out))
+    else:
+        w = _f64(w)
+        lib().ivo_adjoint_pixels_w(nb, cell, u.shape[0], _dp(u), _dp(v), _dp(w), _dp(cv), qs.shape[0],
+                                   qs.ctypes.data_as(ip), ps.ctypes.data_as(ip), _dp(out))
     return out[0::2] + 1j * out[1::2]
+
+
+def _wcol(prob, uvw):
+    """The w column when the problem uses the full Eq. 1 (prob.wterm), else None."""
+    return uvw[:, 2] if getattr(prob, "wterm", False) else None
 
 
 # -------------------------------------------------------------------- data term (Eqs. 3-6)
@@ -186,7 +210,7 @@ def pair_model_vis(prob, sky: np.ndarray, pair, idx=None) -> np.ndarray:
     """Model visibilities of one (pointing, channel) pair for sky cube ``sky``."""
     f = np.asarray(prob.beams[pair.k], dtype=np.float64) * pointing_window(prob, sky[pair.chan], pair.k)
     uvw = pair.uvw if idx is None else pair.uvw[idx]
-    return model_vis(f, prob.cell_rad, uvw[:, 0], uvw[:, 1])
+    return model_vis(f, prob.cell_rad, uvw[:, 0], uvw[:, 1], _wcol(prob, uvw))
 
 
 def data_cost_grad(prob, sky: np.ndarray, with_grad: bool = True):
@@ -201,7 +225,7 @@ def data_cost_grad(prob, sky: np.ndarray, with_grad: bool = True):
         w = pair.weight.astype(np.float64)
         Q += 0.5 * float(np.sum(w * (r.real ** 2 + r.imag ** 2)))
         if with_grad:
-            a = adjoint(w * r, prob.nb, prob.cell_rad, pair.uvw[:, 0], pair.uvw[:, 1])
+            a = adjoint(w * r, prob.nb, prob.cell_rad, pair.uvw[:, 0], pair.uvw[:, 1], _wcol(prob, pair.uvw))
             g = np.asarray(prob.beams[pair.k], dtype=np.float64) * a.real
             grad[pair.chan] += pointing_window_adjoint(prob, g, pair.k, sky.shape[1:])
     return Q, grad
@@ -226,7 +250,7 @@ def data_grad_pixels(prob, sky, chan, ys, xs, residuals=None):
             r = pair_model_vis(prob, sky, pair) - pair.vis.astype(np.complex128)
         w = pair.weight.astype(np.float64)
         a = adjoint_pixels(w * r, prob.nb, prob.cell_rad, pair.uvw[:, 0], pair.uvw[:, 1],
-                           q[inside], p[inside])
+                           q[inside], p[inside], _wcol(prob, pair.uvw))
         out[inside] += np.asarray(prob.beams[pair.k], dtype=np.float64)[q[inside], p[inside]] * a.real
     return out
 

@@ -41,6 +41,10 @@ __device__ __forceinline__ double es_kernel(double z, double beta) {
     return a >= 0.0 ? exp(beta * (sqrt(a) - 1.0)) : 0.0;
 }
 
+// sin(pi a), cos(pi a) in the working precision.
+__device__ __forceinline__ void sincospi_t(float a, float *s, float *c) { sincospif(a, s, c); }
+__device__ __forceinline__ void sincospi_t(double a, double *s, double *c) { sincospi(a, s, c); }
+
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);

@@ -24,6 +24,7 @@
 #include "kernels_solver.cuh"
 #include "kernels_feather.cuh"
 #include "kernels_toeplitz.cuh"
+#include "kernels_wstack.cuh"
 
 using namespace ivis;
 
@@ -40,6 +41,14 @@ struct PairHost {
     // Toeplitz form (toeplitz = 1): spectrum of Re H [kx][ky], window b [nb][nb], constant C
     void *that = nullptr, *bwin = nullptr;
     double qconst = 0.0;
+    // w-stacking (wterm = 1): W entries per visibility, sorted by (plane, tile, cell)
+    int nplane = 0;
+    double w0 = 0.0;                       // plane k sits at w0 + k dw
+    std::vector<int> plane_start;          // first sorted entry of each plane (nplane + 1)
+    std::vector<int> plane_tile_count;     // [nplane][ntiles]
+    void *e_coord = nullptr, *e_val = nullptr, *e_w = nullptr;
+    int *e_orig = nullptr, *e_pos = nullptr;
+    void *v_vis = nullptr, *v_w = nullptr, *v_phase = nullptr, *v_wk = nullptr;  // caller order
 };
 
 struct Stage {
@@ -80,6 +89,8 @@ struct ivis_plan_s {
     bool prepared = false;
     int nslot = 0;
     std::vector<int> slot_pair;            // slot -> pair index
+    std::vector<const int *> slot_tc;      // slot -> per-tile visibility (entry) counts
+    std::vector<int> slot_m;               // slot -> visibilities (entries)
     std::vector<int> chunk_first;          // slot -> first chunk (size nslot + 1)
     int nchunk = 0;
     PairInfo *pinfo_d = nullptr;
@@ -101,6 +112,12 @@ struct ivis_plan_s {
     void **that_ptr_d = nullptr, **bwin_ptr_d = nullptr;  // per slot
     double *qconst_d = nullptr;       // per slot
     int njpart = 0;                   // FP64 data-term partials summed by k_finalize
+    // w-stacking
+    double w_xc = 0.0, w_dw = 0.0;         // centre of the window's n - 1 range, plane spacing
+    void *wx_d = nullptr, *wcorr_d = nullptr;  // [nb][nb] x' = n - 1 - x_c and 1/(n Phi(dw x'))
+    void *wpairs_d = nullptr, *pv_d = nullptr;
+    int wres_blocks = 0, nwpair = 0;
+    std::vector<int> pair_slot0, pair_nslot, pair_widx;  // by pair index (wterm)
     // feathering
     void *feather_tw_d = nullptr, *feather_b1_d = nullptr;  // DFT twiddles and b1 of length n
     cudaGraphExec_t graph = nullptr;
@@ -214,6 +231,45 @@ void es_deapod(int nb, int nf, int W, double beta, std::vector<double> &dinv) {
     }
 }
 
+// w-stacking geometry of a window (Eq. 1): n - 1 over the window spans [x_min, 0] (corner to
+// centre); x_c = x_min / 2, X = -x_min / 2, plane spacing dw = 1 / (4 X) (dw X <= 1/4, the
+// oversampling-2 condition of the ES kernel). Per pixel: x' = n - 1 - x_c and
+// corr = 1 / (n Phi(dw x')), Phi(xi) = int phi(t) cos(2 pi t xi) dt over t in [-W/2, W/2]
+// (Gauss-Legendre, cached by the pixel's squared radius).
+void w_tables(int nb, double cell, int W, double beta, double &xc, double &dw, std::vector<double> &wx,
+              std::vector<double> &wcorr) {
+    auto nm1 = [](double r2, double &n) { n = std::sqrt(1.0 - r2); return -r2 / (1.0 + n); };
+    double ncorner;
+    const double lc = 0.5 * nb * cell;
+    const double xmin = nm1(2.0 * lc * lc, ncorner);
+    xc = 0.5 * xmin;
+    dw = 1.0 / (4.0 * (-0.5 * xmin));
+    std::vector<double> zx, zw;
+    gauss_legendre(200, zx, zw);
+    const long long h = nb / 2;
+    std::vector<double> cache((size_t)(2 * h * h + 1), -1.0);
+    wx.resize((size_t)nb * nb);
+    wcorr.resize((size_t)nb * nb);
+    for (int q = 0; q < nb; ++q)
+        for (int p = 0; p < nb; ++p) {
+            const long long dq = q - h, dp = p - h, r2i = dq * dq + dp * dp;
+            const double r2 = (double)r2i * cell * cell;
+            double n;
+            const double xp = nm1(r2, n) - xc;
+            double &phi = cache[(size_t)r2i];
+            if (phi < 0.0) {
+                double acc = 0.0;
+                for (size_t i = 0; i < zx.size(); ++i) {
+                    const double z = zx[i];
+                    acc += zw[i] * std::exp(beta * (std::sqrt(1.0 - z * z) - 1.0)) * std::cos(M_PI * W * z * dw * xp);
+                }
+                phi = 0.5 * W * acc;
+            }
+            wx[(size_t)q * nb + p] = xp;
+            wcorr[(size_t)q * nb + p] = 1.0 / (n * phi);
+        }
+}
+
 // Per-tap polynomial of the ES kernel for the FP32 gridding kernels: for tap t and first-tap
 // fraction f in [0, 1) the kernel argument is z = (f + W/2 - 1 - t) / (W/2); the value is
 // interpolated at deg + 1 Chebyshev nodes in x = 2f - 1 and stored as monomial coefficients
@@ -323,7 +379,8 @@ cudaError_t launch_forward(ivis_plan_s *p, const void *sky, int slot0 = 0, int n
     cudaFuncSetAttribute(k_fwd_rows<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_row);
     k_fwd_rows<T><<<gr, 256, smem_row, p->stream>>>(
         (const T *)sky, (const T *)p->beams_d, pinfo, (const T *)p->dinv_d, rowbuf,
-        p->cfg.n, nb, p->lognf, (const C *)p->tw_d, (const float2 *)p->grids_d);
+        p->cfg.n, nb, p->lognf, (const C *)p->tw_d, (const float2 *)p->grids_d, (const T *)p->wx_d,
+        (const T *)p->wcorr_d);
     dim3 gc(nf >> p->logc_cols, nslots);
     size_t smem_col = (size_t)fft_smem_elems(nf, 1 << p->logc_cols) * sizeof(C);
     cudaFuncSetAttribute(k_fwd_cols<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_col);
@@ -351,7 +408,7 @@ cudaError_t launch_adjoint(ivis_plan_s *p, int slot0 = 0, int nslots = -1) {
     cudaFuncSetAttribute(k_adj_rows<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_row);
     k_adj_rows<T><<<gr, 256, smem_row, p->stream>>>(
         rowbuf, (const T *)p->beams_d, p->pinfo_d + slot0, (const T *)p->dinv_d,
-        contrib, p->cfg.n, nb, p->lognf, (const C *)p->tw_d);
+        contrib, p->cfg.n, nb, p->lognf, (const C *)p->tw_d, (const T *)p->wx_d, (const T *)p->wcorr_d);
     return cudaGetLastError();
 }
 
@@ -368,7 +425,7 @@ cudaError_t launch_toeplitz(ivis_plan_s *p) {
     cudaFuncSetAttribute(k_fwd_rows<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_row);
     k_fwd_rows<T><<<gr, 256, smem_row, p->stream>>>(
         (const T *)p->x, (const T *)p->beams_d, p->pinfo_d, (const T *)p->ones_d, rowbuf,
-        p->cfg.n, nb, p->lognf, (const C *)p->tw_d, (const float2 *)p->grids_d);
+        p->cfg.n, nb, p->lognf, (const C *)p->tw_d, (const float2 *)p->grids_d, nullptr, nullptr);
     dim3 gc(nf >> p->logc_cols, p->nslot);
     size_t smem_col = (size_t)fft_smem_elems(nf, 1 << p->logc_cols) * sizeof(C);
     cudaFuncSetAttribute(k_toep_cols<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_col);
@@ -453,6 +510,28 @@ cudaError_t enqueue_eval(ivis_plan_s *p, bool capture) {
         if ((e = launch_toeplitz<T>(p)) != cudaSuccess) return e;
         launches += 3;
         stage_end(p, p->stream, si);
+    } else if (p->nslot > 0 && p->cfg.wterm) {
+        // w-stacking: interpolation from every plane, per-visibility residuals, spreading
+        stage_begin(p, "zero_adjoint_grid", p->stream, si);
+        cudaMemsetAsync(p->G, 0, (size_t)p->nslot * p->nf * p->nf * sizeof(C), p->stream);
+        stage_end(p, p->stream, si);
+        stage_begin(p, "fwd_fft", p->stream, si);
+        if ((e = launch_forward<T>(p, p->x)) != cudaSuccess) return e;
+        stage_end(p, p->stream, si);
+        stage_begin(p, "w_interp", p->stream, si);
+        if ((e = launch_grid_pass<T, MODE_PREDICT>(p, 0, p->nchunk, nullptr, p->pv_d)) != cudaSuccess) return e;
+        stage_end(p, p->stream, si);
+        stage_begin(p, "w_residual", p->stream, si);
+        k_w_residual<T, false><<<dim3(p->wres_blocks, p->nwpair), 256, 0, p->stream>>>(
+            (const WPair<T> *)p->wpairs_d, p->W, (const C *)p->pv_d, p->jpart, nullptr);
+        stage_end(p, p->stream, si);
+        stage_begin(p, "w_spread", p->stream, si);
+        if ((e = launch_grid_pass<T, MODE_SPREAD>(p, 0, p->nchunk, nullptr, nullptr)) != cudaSuccess) return e;
+        stage_end(p, p->stream, si);
+        stage_begin(p, "adj_fft", p->stream, si);
+        if ((e = launch_adjoint<T>(p)) != cudaSuccess) return e;
+        stage_end(p, p->stream, si);
+        launches += 7;
     } else if (p->nslot > 0) {
         stage_begin(p, "zero_adjoint_grid", p->stream, si);
         cudaMemsetAsync(p->G, 0, (size_t)p->nslot * p->nf * p->nf * sizeof(C), p->stream);
@@ -502,7 +581,7 @@ cudaError_t enqueue_eval(ivis_plan_s *p, bool capture) {
     }
     stage_end(p, p->stream, si);
     stage_begin(p, "finalize", p->stream, si);
-    k_finalize<<<1, 1024, 0, p->stream>>>(p->jpart, p->cfg.toeplitz ? p->njpart : p->nchunk, p->kpart,
+    k_finalize<<<1, 1024, 0, p->stream>>>(p->jpart, (p->cfg.toeplitz || p->cfg.wterm) ? p->njpart : p->nchunk, p->kpart,
                                          use_k ? p->nkpart : 0,
                                          p->rpart, use_r ? p->nrpart : 0, p->cfg.lambda_r,
                                          p->cfg.lambda_s, p->cost_d);
@@ -625,6 +704,105 @@ ivis_status set_vis_impl(ivis_plan_s *p, PairHost &ph, int m, const float *uvw, 
     return IVIS_OK;
 }
 
+// w-stacked visibilities of one pair (wterm = 1): plane range from the pair's w extent, W
+// entries per visibility (plane k0 + t, weight phi(a - k)), sorted by (plane, tile, cell) with
+// the same counting sort as set_vis_impl; per-visibility V, w, phase and weights kept in caller
+// order for the residual kernel.
+template <typename T>
+ivis_status set_vis_w(ivis_plan_s *p, PairHost &ph, int m, const float *uvw, const float *vis,
+                      const float *w) {
+    typedef typename coord_of<T>::type CO;
+    typedef typename cplx_of<T>::type C;
+    const int W = p->W;
+    ivis_status s;
+    const int nbk = std::min(1024, (m + 255) / 256);
+    void *mmd = nullptr, *coord_tmp = nullptr, *key = nullptr, *err = nullptr, *coord_e = nullptr,
+         *key_e = nullptr, *cnt = nullptr, *cur = nullptr, *bsum = nullptr, *tst = nullptr;
+    auto cleanup = [&]() {
+        dfree(mmd); dfree(coord_tmp); dfree(key); dfree(err); dfree(coord_e); dfree(key_e);
+        dfree(cnt); dfree(cur); dfree(bsum); dfree(tst);
+    };
+    if ((s = alloc(p, &mmd, 2 * nbk * sizeof(float)))) return s;
+    k_w_minmax<<<nbk, 256, 0, p->stream>>>(m, uvw, (float *)mmd);
+    std::vector<float> hmm(2 * nbk);
+    CK(cudaMemcpyAsync(hmm.data(), mmd, 2 * nbk * sizeof(float), cudaMemcpyDeviceToHost, p->stream));
+    CK(cudaStreamSynchronize(p->stream));
+    double wmin = 1e300, wmax = -1e300;
+    for (int b = 0; b < nbk; ++b) {
+        wmin = std::min(wmin, (double)hmm[2 * b]);
+        wmax = std::max(wmax, (double)hmm[2 * b + 1]);
+    }
+    if (!std::isfinite(wmin) || !std::isfinite(wmax) || wmin > wmax) {
+        cleanup();
+        return fail(p, IVIS_ERR_NONFINITE, "set_vis: non-finite w");
+    }
+    // half a plane of margin on each side keeps every visibility's W planes in [0, nplane)
+    const double dw = p->w_dw;
+    ph.w0 = wmin - (0.5 * W - 0.5) * dw;
+    ph.nplane = (int)std::floor((wmax - wmin) / dw) + W + 1;
+    const long long nf2 = (long long)p->nf * p->nf, E = (long long)m * W;
+    if ((long long)ph.nplane * nf2 >= 0x7fffffffLL || E >= 0x7fffffffLL) {
+        cleanup();
+        return fail(p, IVIS_ERR_ARG, "set_vis: w range or visibility count too large for the w-planes");
+    }
+    const int nbins = (int)((long long)ph.nplane * nf2), nsb = (nbins + 1023) / 1024;
+    const int ntt = ph.nplane * p->ntiles;
+    if ((s = alloc(p, &coord_tmp, (size_t)m * sizeof(CO))) || (s = alloc(p, &key, (size_t)m * sizeof(int))) ||
+        (s = alloc(p, &err, sizeof(int))) || (s = alloc(p, &coord_e, (size_t)E * sizeof(CO))) ||
+        (s = alloc(p, &key_e, (size_t)E * sizeof(int))) || (s = alloc(p, &cnt, (size_t)nbins * sizeof(int))) ||
+        (s = alloc(p, &cur, (size_t)nbins * sizeof(int))) || (s = alloc(p, &bsum, (size_t)nsb * sizeof(int))) ||
+        (s = alloc(p, &tst, (size_t)(ntt + 1) * sizeof(int))) ||
+        (s = alloc(p, &ph.v_wk, (size_t)E * sizeof(T))) || (s = alloc(p, &ph.v_phase, (size_t)m * sizeof(C))) ||
+        (s = alloc(p, &ph.v_vis, (size_t)m * sizeof(C))) || (s = alloc(p, &ph.v_w, (size_t)m * sizeof(T)))) {
+        cleanup();
+        return s;
+    }
+    cudaMemsetAsync(err, 0, sizeof(int), p->stream);
+    cudaMemsetAsync(cnt, 0, (size_t)nbins * sizeof(int), p->stream);
+    const int nblk = (m + 255) / 256;
+    const unsigned eblk = (unsigned)((E + 255) / 256);
+    k_vis_prepare<T><<<nblk, 256, 0, p->stream>>>(m, uvw, vis, w, p->cfg.cell_rad * p->nf, p->lognf, W, p->tile,
+                                                   p->ntx, (CO *)coord_tmp, (int *)key, (int *)err);
+    k_w_entries<T><<<nblk, 256, 0, p->stream>>>(m, W, ph.nplane, uvw, vis, w, ph.w0, dw, p->w_xc, p->beta, nf2,
+                                                 (const CO *)coord_tmp, (const int *)key, (CO *)coord_e,
+                                                 (int *)key_e, (T *)ph.v_wk, (C *)ph.v_phase, (C *)ph.v_vis,
+                                                 (T *)ph.v_w, (int *)err);
+    k_hist<<<eblk, 256, 0, p->stream>>>((int)E, (const int *)key_e, (int *)cnt);
+    k_scan_block<<<nsb, 256, 0, p->stream>>>(nbins, (const int *)cnt, (int *)cur, (int *)bsum);
+    k_scan_top<<<1, 1024, 0, p->stream>>>(nsb, (int *)bsum);
+    k_scan_add<<<nsb, 256, 0, p->stream>>>(nbins, (int *)cur, (const int *)bsum);
+    k_tile_starts<<<(ntt + 256) / 256, 256, 0, p->stream>>>(ntt, p->tile * p->tile, (int)E, (const int *)cur,
+                                                           (int *)tst);
+    int herr = 0;
+    std::vector<int> starts(ntt + 1, 0);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, p->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(starts.data(), tst, (size_t)(ntt + 1) * sizeof(int), cudaMemcpyDeviceToHost, p->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
+    if (e != cudaSuccess) { cleanup(); return fail(p, IVIS_ERR_CUDA, std::string("set_vis: ") + cudaGetErrorString(e)); }
+    if (herr) { cleanup(); return fail(p, IVIS_ERR_NONFINITE, "set_vis: non-finite uvw/vis/weight or negative weight"); }
+    ph.plane_tile_count.assign(ntt, 0);
+    for (int t = 0; t < ntt; ++t) ph.plane_tile_count[t] = starts[t + 1] - starts[t];
+    ph.plane_start.assign(ph.nplane + 1, 0);
+    for (int k = 0; k <= ph.nplane; ++k) ph.plane_start[k] = starts[(size_t)k * p->ntiles];
+    if ((s = alloc(p, &ph.e_coord, (size_t)E * sizeof(CO))) || (s = alloc(p, &ph.e_val, (size_t)E * sizeof(C))) ||
+        (s = alloc(p, &ph.e_w, (size_t)E * sizeof(T))) || (s = alloc(p, (void **)&ph.e_orig, (size_t)E * sizeof(int))) ||
+        (s = alloc(p, (void **)&ph.e_pos, (size_t)E * sizeof(int)))) {
+        cleanup();
+        return s;
+    }
+    cudaMemsetAsync(ph.e_val, 0, (size_t)E * sizeof(C), p->stream);
+    k_w_scatter<T><<<eblk, 256, 0, p->stream>>>(E, (const int *)key_e, (const CO *)coord_e, (const T *)ph.v_wk,
+                                                 (int *)cur, (CO *)ph.e_coord, (T *)ph.e_w, ph.e_orig, ph.e_pos);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
+    cleanup();
+    if (e != cudaSuccess) return fail(p, IVIS_ERR_CUDA, std::string("set_vis scatter: ") + cudaGetErrorString(e));
+    ph.m = m;
+    ph.set = true;
+    return IVIS_OK;
+}
+
 // Toeplitz data of one pair (toeplitz = 1), from the caller's arrays: a plan with one
 // pointing of window 2nb and unit beam over a 2nb x 2nb sky holds the pair twice, as channel 0
 // with unit visibilities and as channel 1 with the data. Its gradient at I = 0 is
@@ -708,6 +886,22 @@ ivis_status toeplitz_pair(ivis_plan_s *p, PairHost &ph, int m, const float *uvw,
 }
 
 void free_pair(PairHost &ph) {
+    dfree(ph.e_coord);
+    dfree(ph.e_val);
+    dfree(ph.e_w);
+    {
+        void *a = ph.e_orig, *b = ph.e_pos;
+        dfree(a);
+        dfree(b);
+        ph.e_orig = ph.e_pos = nullptr;
+    }
+    dfree(ph.v_vis);
+    dfree(ph.v_w);
+    dfree(ph.v_phase);
+    dfree(ph.v_wk);
+    ph.nplane = 0;
+    ph.plane_start.clear();
+    ph.plane_tile_count.clear();
     dfree(ph.that);
     dfree(ph.bwin);
     ph.qconst = 0.0;
@@ -735,6 +929,8 @@ void release_prepared(ivis_plan_s *p) {
     dfree(a); dfree(b); dfree(c); dfree(d);
     void *tp = p->that_ptr_d, *bp = p->bwin_ptr_d, *qc = p->qconst_d;
     dfree(tp); dfree(bp); dfree(qc);
+    dfree(p->wpairs_d);
+    dfree(p->pv_d);
     p->that_ptr_d = p->bwin_ptr_d = nullptr;
     p->qconst_d = nullptr;
     p->jpart = p->kpart = p->rpart = p->cost_d = nullptr;
@@ -749,11 +945,11 @@ void build_chunks(ivis_plan_s *p, int cap, std::vector<Chunk> &chunks, std::vect
     chunks.clear();
     first.assign(p->nslot + 1, 0);
     for (int sl = 0; sl < p->nslot; ++sl) {
-        const PairHost &ph = p->pairs[p->slot_pair[sl]];
+        const int *tc = p->slot_tc[sl];
         first[sl] = (int)chunks.size();
         int acc = 0;
         for (int t = 0; t < p->ntiles; ++t) {
-            const int cnt = ph.tile_count[t];
+            const int cnt = tc[t];
             for (int b = 0; b < cnt; b += cap) chunks.push_back(Chunk{sl, t, acc + b, acc + std::min(cnt, b + cap)});
             acc += cnt;
         }
@@ -763,12 +959,12 @@ void build_chunks(ivis_plan_s *p, int cap, std::vector<Chunk> &chunks, std::vect
 
 std::string tune_key(const ivis_plan_s *p) {
     long long m = 0;
-    for (int sl = 0; sl < p->nslot; ++sl) m += p->pairs[p->slot_pair[sl]].m;
+    for (int sl = 0; sl < p->nslot; ++sl) m += p->slot_m[sl];
     int mb = 0;  // visibility-count class: power of two
     while ((1LL << mb) < m) ++mb;
     return "nf=" + std::to_string(p->nf) + " w=" + std::to_string(p->W) + " fp64=" + std::to_string((int)p->fp64) +
            " nslot=" + std::to_string(p->nslot) + " m2=" + std::to_string(mb) +
-           (p->cfg.toeplitz ? " toeplitz" : "");
+           (p->cfg.toeplitz ? " toeplitz" : "") + (p->cfg.wterm ? " wterm" : "");
 }
 
 // Autotuner: picks the grid-pass chunk size and the number of columns per CTA of the column
@@ -834,7 +1030,14 @@ ivis_status autotune(ivis_plan_s *p) {
             build_chunks(p, cap, ch, first);
             CK(cudaMemcpy(p->chunks_d, ch.data(), ch.size() * sizeof(Chunk), cudaMemcpyHostToDevice));
             const int n = (int)ch.size();
-            const float ms = timed([&] { launch_grid_pass<T, MODE_COSTGRAD>(p, 0, n, p->jpart, nullptr); });
+            const float ms = timed([&] {
+                if (p->cfg.wterm) {
+                    launch_grid_pass<T, MODE_PREDICT>(p, 0, n, nullptr, p->pv_d);
+                    launch_grid_pass<T, MODE_SPREAD>(p, 0, n, nullptr, nullptr);
+                } else {
+                    launch_grid_pass<T, MODE_COSTGRAD>(p, 0, n, p->jpart, nullptr);
+                }
+            });
             if (ms < bg) { bg = ms; best_cap = cap; }
         }
         CK(cudaGetLastError());
@@ -874,26 +1077,74 @@ ivis_status prepare_impl(ivis_plan_s *p) {
     if (c.lambda_s != 0.0)
         for (int ch = 0; ch < c.nchan; ++ch)
             if (!p->sdset[ch]) return fail(p, IVIS_ERR_STATE, "single-dish map of channel " + std::to_string(ch) + " not set");
-    // slots: pairs with data, in (chan, k) order
+    // slots: pairs with data, in (chan, k) order; with the w-term, one slot per non-empty
+    // w-plane of each such pair
     p->slot_pair.clear();
-    for (size_t i = 0; i < p->pairs.size(); ++i)
-        if (p->pairs[i].m > 0) p->slot_pair.push_back((int)i);
-    p->nslot = (int)p->slot_pair.size();
-    std::vector<PairInfo> pinfo(p->nslot);
-    std::vector<PairData<T>> pdata(p->nslot);
+    p->slot_tc.clear();
+    p->slot_m.clear();
+    std::vector<PairInfo> pinfo;
+    std::vector<PairData<T>> pdata;
+    std::vector<WPair<T>> wpairs;
+    long long pv_total = 0;
+    int max_m = 0;
+    p->pair_slot0.assign(p->pairs.size(), 0);
+    p->pair_nslot.assign(p->pairs.size(), 0);
+    p->pair_widx.assign(p->pairs.size(), -1);
+    typedef typename coord_of<T>::type CO;
+    for (size_t i = 0; i < p->pairs.size(); ++i) {
+        PairHost &ph = p->pairs[i];
+        if (ph.m <= 0) continue;
+        const int k = (int)(i % c.npoint), ch = (int)(i / c.npoint);
+        p->pair_slot0[i] = (int)pinfo.size();
+        if (!c.wterm) {
+            pinfo.push_back(PairInfo{k, ch, p->cx[k], p->cy[k], p->pgrid[k], 0, 0.0});
+            PairData<T> pd{};
+            pd.coord = (const CO *)ph.coord;
+            pd.vis = (const C *)ph.vis;
+            pd.w = (const T *)ph.w;
+            pd.orig = ph.orig;
+            pd.m = ph.m;
+            pd.pred_off = 0;
+            pdata.push_back(pd);
+            p->slot_pair.push_back((int)i);
+            p->slot_tc.push_back(ph.tile_count.data());
+            p->slot_m.push_back(ph.m);
+        } else {
+            for (int pl = 0; pl < ph.nplane; ++pl) {
+                const int b = ph.plane_start[pl], e = ph.plane_start[pl + 1];
+                if (e <= b) continue;
+                pinfo.push_back(PairInfo{k, ch, p->cx[k], p->cy[k], p->pgrid[k], 1, ph.w0 + pl * p->w_dw});
+                PairData<T> pd{};
+                pd.coord = (const CO *)ph.e_coord + b;
+                pd.vis = (const C *)ph.e_val + b;
+                pd.w = (const T *)ph.e_w + b;
+                pd.orig = ph.e_orig + b;
+                pd.m = e - b;
+                pd.pred_off = pv_total;
+                pdata.push_back(pd);
+                p->slot_pair.push_back((int)i);
+                p->slot_tc.push_back(ph.plane_tile_count.data() + (size_t)pl * p->ntiles);
+                p->slot_m.push_back(e - b);
+            }
+            WPair<T> wp{};
+            wp.V = (const C *)ph.v_vis;
+            wp.w = (const T *)ph.v_w;
+            wp.phase = (const C *)ph.v_phase;
+            wp.wk = (const T *)ph.v_wk;
+            wp.epos = ph.e_pos;
+            wp.ent_val = (C *)ph.e_val;
+            wp.pv_off = pv_total;
+            wp.m = ph.m;
+            p->pair_widx[i] = (int)wpairs.size();
+            wpairs.push_back(wp);
+            pv_total += (long long)ph.m * p->W;
+            max_m = std::max(max_m, ph.m);
+        }
+        p->pair_nslot[i] = (int)pinfo.size() - p->pair_slot0[i];
+    }
+    p->nslot = (int)pinfo.size();
     std::vector<Chunk> chunks;
     std::vector<int> chan_start(c.nchan + 1, 0), chan_list;
-    for (int sl = 0; sl < p->nslot; ++sl) {
-        int pi_ = p->slot_pair[sl];
-        int k = pi_ % c.npoint, ch = pi_ / c.npoint;
-        pinfo[sl] = PairInfo{k, ch, p->cx[k], p->cy[k], p->pgrid[k]};
-        PairHost &ph = p->pairs[pi_];
-        pdata[sl].coord = (const typename coord_of<T>::type *)ph.coord;
-        pdata[sl].vis = (const C *)ph.vis;
-        pdata[sl].w = (const T *)ph.w;
-        pdata[sl].orig = ph.orig;
-        pdata[sl].m = ph.m;
-    }
     p->any_grid = false;
     for (int sl = 0; sl < p->nslot; ++sl) p->any_grid |= pinfo[sl].gridded != 0;
     build_chunks(p, p->chunk_cap, chunks, p->chunk_first);
@@ -932,6 +1183,14 @@ ivis_status prepare_impl(ivis_plan_s *p) {
     if ((s = alloc(p, &p->x, npix * sizeof(T)))) return s;
     if ((s = alloc(p, &p->g, npix * sizeof(T)))) return s;
     size_t njp = std::max<size_t>(1, max_chunks);
+    if (c.wterm && !wpairs.empty()) {
+        p->wres_blocks = (max_m + 255) / 256;
+        p->nwpair = (int)wpairs.size();
+        p->njpart = p->nwpair * p->wres_blocks;
+        njp = std::max<size_t>(njp, (size_t)p->njpart);
+        if ((s = up(&p->wpairs_d, wpairs.data(), wpairs.size() * sizeof(WPair<T>)))) return s;
+        if ((s = alloc(p, &p->pv_d, (size_t)pv_total * sizeof(C)))) return s;
+    }
     if (c.toeplitz) {
         // per-slot spectrum and b pointers, constants; one partial per row-pass CTA
         const int lpb = 256 / (p->nf / 16);
@@ -1129,11 +1388,31 @@ ivis_status solve_impl(ivis_plan_s *p, void *sky_dev, int maxiter, int m_hist, d
 }  // namespace
 
 namespace {
+// Model visibilities of one pair at p->x into out (caller order).
+template <typename T>
+cudaError_t predict_impl(ivis_plan_s *p, int pair, void *out) {
+    typedef typename cplx_of<T>::type C;
+    const int s0 = p->pair_slot0[pair], ns = p->pair_nslot[pair];
+    cudaError_t e = launch_forward<T>(p, p->x, s0, ns);
+    const int c0 = p->chunk_first[s0], nc = p->chunk_first[s0 + ns] - c0;
+    if (!p->cfg.wterm) {
+        if (e == cudaSuccess) e = launch_grid_pass<T, MODE_PREDICT>(p, c0, nc, nullptr, out);
+        return e;
+    }
+    if (e == cudaSuccess) e = launch_grid_pass<T, MODE_PREDICT>(p, c0, nc, nullptr, p->pv_d);
+    if (e != cudaSuccess) return e;
+    const int wi = p->pair_widx[pair], m = p->pairs[pair].m;
+    k_w_residual<T, true><<<(m + 255) / 256, 256, 0, p->stream>>>((const WPair<T> *)p->wpairs_d + wi, p->W,
+                                                                  (const C *)p->pv_d, nullptr, (C *)out);
+    return cudaGetLastError();
+}
+
 template <typename T>
 ivis_status dirty_impl(ivis_plan_s *p, void *dirty_dev, void *beamw_dev) {
     typedef typename cplx_of<T>::type C;
     const int n = p->cfg.n, nchan = p->cfg.nchan;
     const size_t npix = (size_t)nchan * n * n;
+    if (p->cfg.wterm) return fail(p, IVIS_ERR_STATE, "the dirty image is not available on a wterm plan");
     CK(cudaMemsetAsync(p->x, 0, npix * sizeof(T), p->stream));
     if (p->nslot > 0) {
         // at I = 0 the model visibilities vanish: the residual is -V and the data-term
@@ -1294,6 +1573,10 @@ ivis_status ivis_plan(const ivis_config *cfg, void *stream, ivis_plan_t *out) {
         return fail(nullptr, IVIS_ERR_NONFINITE, "lambda_r and lambda_s must be finite and >= 0");
     if (c.toeplitz && c.nb > 1024) return fail(nullptr, IVIS_ERR_ARG, "toeplitz needs nb <= 1024");
     if (c.toeplitz && c.serial_pairs) return fail(nullptr, IVIS_ERR_ARG, "toeplitz and serial_pairs are exclusive");
+    if (c.wterm && (c.toeplitz || c.serial_pairs))
+        return fail(nullptr, IVIS_ERR_ARG, "wterm excludes toeplitz and serial_pairs");
+    if (c.wterm && 2.0 * (0.5 * c.nb * c.cell_rad) * (0.5 * c.nb * c.cell_rad) >= 0.25)
+        return fail(nullptr, IVIS_ERR_ARG, "wterm: the window reaches too far from its centre (l^2 + m^2 >= 1/4)");
     ivis_plan_s *p = new (std::nothrow) ivis_plan_s();
     if (!p) return fail(nullptr, IVIS_ERR_OOM, "host allocation failed");
     p->cfg = c;
@@ -1364,6 +1647,12 @@ ivis_status ivis_plan(const ivis_config *cfg, void *stream, ivis_plan_t *out) {
         s = p->fp64 ? upload_real<double>(p, &p->ones_d, std::vector<double>(c.nb, 1.0))
                     : upload_real<float>(p, &p->ones_d, std::vector<double>(c.nb, 1.0));
     }
+    if (!s && c.wterm) {
+        std::vector<double> wx, wcorr;
+        w_tables(c.nb, c.cell_rad, p->W, p->beta, p->w_xc, p->w_dw, wx, wcorr);
+        s = p->fp64 ? upload_real<double>(p, &p->wx_d, wx) : upload_real<float>(p, &p->wx_d, wx);
+        if (!s) s = p->fp64 ? upload_real<double>(p, &p->wcorr_d, wcorr) : upload_real<float>(p, &p->wcorr_d, wcorr);
+    }
     if (!s && cudaStreamCreateWithFlags(&p->side, cudaStreamNonBlocking) != cudaSuccess) s = IVIS_ERR_CUDA;
     if (!s && cudaEventCreateWithFlags(&p->ev_in, cudaEventDisableTiming) != cudaSuccess) s = IVIS_ERR_CUDA;
     for (int i = 0; i < MAX_STAGES && !s; ++i)
@@ -1432,8 +1721,13 @@ ivis_status ivis_set_vis(ivis_plan_t p, int k, int chan, int64_t m, const float 
         ph.set = true;
         return IVIS_OK;
     }
-    ivis_status s = p->fp64 ? set_vis_impl<double>(p, ph, (int)m, uvw_dev, vis_dev, weight_dev)
-                            : set_vis_impl<float>(p, ph, (int)m, uvw_dev, vis_dev, weight_dev);
+    ivis_status s;
+    if (p->cfg.wterm)
+        s = p->fp64 ? set_vis_w<double>(p, ph, (int)m, uvw_dev, vis_dev, weight_dev)
+                    : set_vis_w<float>(p, ph, (int)m, uvw_dev, vis_dev, weight_dev);
+    else
+        s = p->fp64 ? set_vis_impl<double>(p, ph, (int)m, uvw_dev, vis_dev, weight_dev)
+                    : set_vis_impl<float>(p, ph, (int)m, uvw_dev, vis_dev, weight_dev);
     if (!s && p->cfg.toeplitz)
         s = p->fp64 ? toeplitz_pair<double>(p, ph, (int)m, uvw_dev, vis_dev, weight_dev)
                     : toeplitz_pair<float>(p, ph, (int)m, uvw_dev, vis_dev, weight_dev);
@@ -1515,23 +1809,11 @@ ivis_status ivis_predict(ivis_plan_t p, const void *sky_dev, int k, int chan, vo
     enter(p);
     ivis_status s = ensure_prepared(p);
     if (s) return s;
-    int pair = chan * p->cfg.npoint + k;
-    int slot = -1;
-    for (int i = 0; i < p->nslot; ++i)
-        if (p->slot_pair[i] == pair) slot = i;
-    if (slot < 0) return IVIS_OK;  // no visibilities
+    const int pair = chan * p->cfg.npoint + k;
+    if (p->pairs[pair].m <= 0) return IVIS_OK;  // no visibilities
     size_t bytes = (size_t)p->cfg.nchan * p->cfg.n * p->cfg.n * p->rsz;
     CK(cudaMemcpyAsync(p->x, sky_dev, bytes, cudaMemcpyDeviceToDevice, p->stream));
-    cudaError_t e;
-    if (p->fp64) {
-        e = launch_forward<double>(p, p->x, slot, 1);
-        if (e == cudaSuccess)
-            e = launch_grid_pass<double, MODE_PREDICT>(p, p->chunk_first[slot], p->chunk_first[slot + 1] - p->chunk_first[slot], nullptr, vis_out_dev);
-    } else {
-        e = launch_forward<float>(p, p->x, slot, 1);
-        if (e == cudaSuccess)
-            e = launch_grid_pass<float, MODE_PREDICT>(p, p->chunk_first[slot], p->chunk_first[slot + 1] - p->chunk_first[slot], nullptr, vis_out_dev);
-    }
+    cudaError_t e = p->fp64 ? predict_impl<double>(p, pair, vis_out_dev) : predict_impl<float>(p, pair, vis_out_dev);
     if (e != cudaSuccess) return fail(p, IVIS_ERR_CUDA, std::string("predict: ") + cudaGetErrorString(e));
     CK(cudaStreamSynchronize(p->stream));
     return IVIS_OK;
@@ -1731,6 +2013,8 @@ ivis_status ivis_destroy(ivis_plan_t p) {
     dfree(p->beams_d);
     dfree(p->tsd_d);
     dfree(p->ones_d);
+    dfree(p->wx_d);
+    dfree(p->wcorr_d);
     dfree(p->feather_tw_d);
     dfree(p->feather_b1_d);
     if (p->toep_sub) ivis_destroy(p->toep_sub);

@@ -24,6 +24,8 @@ namespace ivis {
 struct PairInfo {
     int k, chan, cx, cy;
     int gridded;  // 1: the window is the bilinear re-projection through the pointing's grid
+    int wplane;   // 1: a w-plane slot of the full Eq. 1 (modulation by exp(-2 pi i wk x'))
+    double wk;    // the plane's w (wavelengths)
 };
 
 // Bilinear interpolation of img (n x n, zero off the sky) at (X, Y) in pixel units (X along
@@ -80,6 +82,7 @@ template <typename T> struct PairData {
     const T *w;
     const int *orig;
     int m;
+    long long pred_off;  // MODE_PREDICT writes pred[pred_off + orig[v]]
 };
 
 constexpr int FRAC_BITS = 20;
@@ -242,7 +245,8 @@ __global__ void __launch_bounds__(256)
 k_fwd_rows(const T *__restrict__ sky, const T *__restrict__ beams,
            const PairInfo *__restrict__ pinfo, const T *__restrict__ dinv,
            typename cplx_of<T>::type *rowbuf, int n, int nb, int lognf,
-           const typename cplx_of<T>::type *__restrict__ tw, const float2 *__restrict__ grids) {
+           const typename cplx_of<T>::type *__restrict__ tw, const float2 *__restrict__ grids,
+           const T *__restrict__ wx, const T *__restrict__ wcorr) {
     typedef typename cplx_of<T>::type C;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C *s = reinterpret_cast<C *>(smem_raw);
@@ -253,6 +257,18 @@ k_fwd_rows(const T *__restrict__ sky, const T *__restrict__ beams,
     const int q = blockIdx.x * lpb + l;
     const int y = pi.cy - nb / 2 + q;
     const bool on = q < nb && (pi.gridded || (y >= 0 && y < n));
+    // w-plane slot: window value times corr exp(-2 pi i wk x') (complex)
+    auto put = [&](int p, T val) {
+        C v = mk(val, (T)0);
+        if (pi.wplane) {
+            const size_t t = (size_t)q * nb + p;
+            T sn, cs;
+            sincospi_t((T)(-2.0 * pi.wk) * wx[t], &sn, &cs);
+            const T a = val * wcorr[t];
+            v = mk(a * cs, a * sn);
+        }
+        s[pidx(l * nf + ((p - nb / 2) & (nf - 1)))] = v;
+    };
     C *line = s;  // element e of line l at s[pidx(l * nf + e)]
     for (int e = j0; e < nf; e += tpl) line[pidx(l * nf + e)] = mk((T)0, (T)0);
     __syncthreads();
@@ -264,16 +280,14 @@ k_fwd_rows(const T *__restrict__ sky, const T *__restrict__ beams,
             const float2 *grow = grids + ((size_t)pi.k * nb + q) * nb;
             for (int p = j0; p < nb; p += tpl) {
                 const float2 g = grow[p];
-                const T val = bilerp(img, n, g.x, g.y) * brow[p] * dinv[p] * dq;
-                line[pidx(l * nf + ((p - nb / 2) & (nf - 1)))] = mk(val, (T)0);
+                put(p, bilerp(img, n, g.x, g.y) * brow[p] * dinv[p] * dq);
             }
         } else {
             const T *srow = sky + ((size_t)pi.chan * n + y) * n;
             const int x0 = pi.cx - nb / 2;
             for (int p = j0; p < nb; p += tpl) {
                 const int x = x0 + p;
-                const T val = (x >= 0 && x < n) ? srow[x] * brow[p] * dinv[p] * dq : (T)0;
-                line[pidx(l * nf + ((p - nb / 2) & (nf - 1)))] = mk(val, (T)0);
+                put(p, (x >= 0 && x < n) ? srow[x] * brow[p] * dinv[p] * dq : (T)0);
             }
         }
     }
@@ -336,7 +350,7 @@ __device__ __forceinline__ void decode(double2 c, int nf, int &gx, int &gy, doub
     gy = gy < 0 ? gy + nf : gy;
 }
 
-enum { MODE_COSTGRAD = 0, MODE_PREDICT = 1 };
+enum { MODE_COSTGRAD = 0, MODE_PREDICT = 1, MODE_SPREAD = 2 };
 
 // Vector reduction into global memory for one complex cell (sm_90+ has 2-wide float adds).
 __device__ __forceinline__ void red_add_c(float2 *p, float2 v) { atomicAdd(p, v); }
@@ -353,7 +367,8 @@ __device__ __forceinline__ void red_add_c(double2 *p, double2 v) {
 // kernel values serve the spreading. Each group walks a contiguous run of the chunk, whose
 // visibilities are sorted by first-tap cell: while the cell repeats, a lane keeps its row of
 // the spread in registers and only adds it to the shared sub-grid (atomics) when the cell
-// changes. MODE_PREDICT writes V~ to pred[orig] instead of spreading.
+// changes. MODE_PREDICT writes V~ to pred[pred_off + orig] instead of spreading; MODE_SPREAD
+// skips the interpolation and spreads w times the record's value (the w-stacked entries).
 template <typename T, int W, int MODE>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 5 : 2)
 k_grid_pass(const Chunk *__restrict__ chunks, const PairData<T> *__restrict__ pdata,
@@ -370,17 +385,18 @@ k_grid_pass(const Chunk *__restrict__ chunks, const PairData<T> *__restrict__ pd
     __shared__ double red[32];
     const int nf = 1 << lognf;
     C *Fs = reinterpret_cast<C *>(smem_raw);
-    C *Gs = Fs + PW * PW;
+    C *Gs = MODE == MODE_SPREAD ? Fs : Fs + PW * PW;  // MODE_SPREAD stages no F tile
     const Chunk ch = chunks[blockIdx.x];
     const PairData<T> pd = pdata[ch.slot];
     const int ty = ch.tile / ntx, tx = ch.tile - ty * ntx;
     const int x0 = tx * tile, y0 = ty * tile;
     const C *Fp = F + (size_t)ch.slot * nf * nf;
+    constexpr bool SPREAD = MODE != MODE_PREDICT;
     for (int i = threadIdx.x; i < PW * PW; i += blockDim.x) {
         const int ly = i / PW, lx = i - ly * PW;
         const int gy = (y0 + ly) & (nf - 1), gx = (x0 + lx) & (nf - 1);
-        Fs[i] = Fp[(size_t)gy * nf + gx];
-        if (MODE == MODE_COSTGRAD) Gs[i] = mk((T)0, (T)0);
+        if (MODE != MODE_SPREAD) Fs[i] = Fp[(size_t)gy * nf + gx];
+        if (SPREAD) Gs[i] = mk((T)0, (T)0);
     }
     __syncthreads();
     const T zs = (T)2 / (T)W;
@@ -406,7 +422,7 @@ k_grid_pass(const Chunk *__restrict__ chunks, const PairData<T> *__restrict__ pd
     T wnext = (T)0;
     if (vbeg < vend) {
         cnext = pd.coord[vbeg];
-        if (MODE == MODE_COSTGRAD) { vnext = pd.vis[vbeg]; wnext = pd.w[vbeg]; }
+        if (SPREAD) { vnext = pd.vis[vbeg]; wnext = pd.w[vbeg]; }
     }
     for (int i = 0; i < len; ++i) {
         const int v = vbeg + i;
@@ -416,13 +432,13 @@ k_grid_pass(const Chunk *__restrict__ chunks, const PairData<T> *__restrict__ pd
         const T w = wnext;
         if (v + 1 < vend) {
             cnext = pd.coord[v + 1];
-            if (MODE == MODE_COSTGRAD) { vnext = pd.vis[v + 1]; wnext = pd.w[v + 1]; }
+            if (SPREAD) { vnext = pd.vis[v + 1]; wnext = pd.w[v + 1]; }
         }
         int gx = x0, gy = y0;
         T dx = (T)(0.5 * W), dy = (T)(0.5 * W);
         if (valid) decode<W>(ccur, nf, gx, gy, dx, dy);
         const int lx = gx - x0, ly = gy - y0;
-        if (MODE == MODE_COSTGRAD && valid && (lx != clx || ly != cly)) {
+        if (SPREAD && valid && (lx != clx || ly != cly)) {
             if (clx >= 0 && active_row) {
                 C *gr = Gs + (cly + r) * PW + clx;
 #pragma unroll
@@ -447,31 +463,34 @@ k_grid_pass(const Chunk *__restrict__ chunks, const PairData<T> *__restrict__ pd
         T kx[W];
 #pragma unroll
         for (int a = 0; a < W; ++a) kx[a] = __shfl_sync(0xffffffffu, kxr, a, GS);
-        C row = mk((T)0, (T)0);
-        if (row_on) {
-            const C *fr = Fs + (ly + r) * PW + lx;
+        C acc = mk((T)0, (T)0);
+        if constexpr (MODE != MODE_SPREAD) {
+            C row = mk((T)0, (T)0);
+            if (row_on) {
+                const C *fr = Fs + (ly + r) * PW + lx;
 #pragma unroll
-            for (int a = 0; a < W; ++a) {
-                const C f = fr[a];
-                row.x += kx[a] * f.x;
-                row.y += kx[a] * f.y;
+                for (int a = 0; a < W; ++a) {
+                    const C f = fr[a];
+                    row.x += kx[a] * f.x;
+                    row.y += kx[a] * f.y;
+                }
             }
-        }
-        C acc = mk(kyr * row.x, kyr * row.y);
+            acc = mk(kyr * row.x, kyr * row.y);
 #pragma unroll
-        for (int o = GS / 2; o > 0; o >>= 1) {
-            acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o, GS);
-            acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o, GS);
+            for (int o = GS / 2; o > 0; o >>= 1) {
+                acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o, GS);
+                acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o, GS);
+            }
         }
         if (!valid) continue;
         if (MODE == MODE_PREDICT) {
-            if (r == 0) pred[pd.orig[v]] = acc;
+            if (r == 0) pred[pd.pred_off + pd.orig[v]] = acc;
             continue;
         }
-        const C res = mk(acc.x - vv.x, acc.y - vv.y);
+        const C res = MODE == MODE_SPREAD ? vv : mk(acc.x - vv.x, acc.y - vv.y);
         // per-visibility term in the working precision; a lane sums at most len (<= 32) terms
         // before the FP64 block and global reductions (FP64 issue is scarce on this part)
-        if (r == 0) jacc += (T)0.5 * w * (res.x * res.x + res.y * res.y);
+        if (MODE == MODE_COSTGRAD && r == 0) jacc += (T)0.5 * w * (res.x * res.x + res.y * res.y);
         if (active_row) {
             const T cyx = kyr * w * res.x, cyy = kyr * w * res.y;
 #pragma unroll
@@ -490,8 +509,10 @@ k_grid_pass(const Chunk *__restrict__ chunks, const PairData<T> *__restrict__ pd
             atomicAdd(&gr[a].y, racc[a].y);
         }
     }
-    const double js = block_sum((double)jacc, red);
-    if (threadIdx.x == 0) jpart[blockIdx.x] = js;
+    if (MODE == MODE_COSTGRAD) {
+        const double js = block_sum((double)jacc, red);
+        if (threadIdx.x == 0) jpart[blockIdx.x] = js;
+    }
     __syncthreads();
     C *Gp = G + (size_t)ch.slot * nf * nf;
     for (int i = threadIdx.x; i < PW * PW; i += blockDim.x) {
@@ -533,7 +554,8 @@ __global__ void __launch_bounds__(256)
 k_adj_rows(const typename cplx_of<T>::type *__restrict__ rowbuf,
            const T *__restrict__ beams, const PairInfo *__restrict__ pinfo,
            const T *__restrict__ dinv, T *contrib, int n, int nb, int lognf,
-           const typename cplx_of<T>::type *__restrict__ tw) {
+           const typename cplx_of<T>::type *__restrict__ tw, const T *__restrict__ wx,
+           const T *__restrict__ wcorr) {
     typedef typename cplx_of<T>::type C;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C *s = reinterpret_cast<C *>(smem_raw);
@@ -557,7 +579,15 @@ k_adj_rows(const typename cplx_of<T>::type *__restrict__ rowbuf,
     T *out = contrib + ((size_t)slot * nb + q) * nb;
     for (int p = j0; p < nb; p += tpl) {
         const int idx = (p - nb / 2) & (nf - 1);
-        out[p] = s[pidx(l * nf + idx)].x * dinv[p] * dq * brow[p];
+        const C v = s[pidx(l * nf + idx)];
+        T re = v.x;
+        if (pi.wplane) {  // Re(corr exp(+2 pi i wk x') v)
+            const size_t t = (size_t)q * nb + p;
+            T sn, cs;
+            sincospi_t((T)(2.0 * pi.wk) * wx[t], &sn, &cs);
+            re = (v.x * cs - v.y * sn) * wcorr[t];
+        }
+        out[p] = re * dinv[p] * dq * brow[p];
     }
 }
 

@@ -36,7 +36,7 @@ class Plan:
                  precision: str = "fp32", nufft_tol: float | None = None, kernel_width: int = 0,
                  lambda_r: float = 0.0, lambda_s: float = 0.0, positivity: bool = True,
                  stream: torch.cuda.Stream | None = None, serial_pairs: bool = False,
-                 autotune: bool = False, toeplitz: bool = False):
+                 autotune: bool = False, toeplitz: bool = False, wterm: bool = False):
         self.L = _lib.load()
         if precision not in ("fp32", "fp64"):
             raise ValueError("precision must be 'fp32' or 'fp64'")
@@ -47,7 +47,8 @@ class Plan:
         self.cfg = _lib.Config(n, nchan, npoint, nb, cell_rad,
                                IVIS_FP32 if precision == "fp32" else IVIS_FP64,
                                nufft_tol, kernel_width, lambda_r, lambda_s, int(bool(positivity)),
-                               int(bool(serial_pairs)), int(bool(autotune)), int(bool(toeplitz)))
+                               int(bool(serial_pairs)), int(bool(autotune)), int(bool(toeplitz)),
+                               int(bool(wterm)))
         self.shape = (nchan, n, n)
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         self._p = ctypes.c_void_p()
@@ -225,7 +226,7 @@ def plan_from_problem(prob, precision: str = "fp32", device="cuda", **kw) -> Pla
     for lambda_s != 0, tsd / sigma_sd / sd_fwhm_pix). Host arrays are copied to the device."""
     plan = Plan(prob.n, prob.nchan, prob.centres.shape[0], prob.nb, prob.cell_rad, precision,
                 lambda_r=kw.pop("lambda_r", prob.lambda_r), lambda_s=kw.pop("lambda_s", prob.lambda_s),
-                positivity=prob.positivity, **kw)
+                positivity=prob.positivity, wterm=kw.pop("wterm", getattr(prob, "wterm", False)), **kw)
     for k in range(prob.centres.shape[0]):
         plan.set_pointing(k, int(prob.centres[k][0]), int(prob.centres[k][1]),
                           torch.as_tensor(prob.beams[k], dtype=torch.float32, device=device))

@@ -62,6 +62,7 @@ class Problem:
     sd_noise_unit: np.ndarray | None = None   # float64 [nchan, n, n], unit normal draw
     sigma_vis: float = 1e-3
     freqs_hz: np.ndarray = field(default_factory=lambda: np.array([HI_FREQ_HZ]))
+    wterm: bool = False          # model the full Eq. 1 (w-term and 1/n) instead of Eq. 3
 
     @property
     def npoint(self) -> int:

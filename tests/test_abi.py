@@ -49,7 +49,7 @@ def test_plan_rejects_bad_config_without_gpu():
     """Argument validation happens on the host before any device call."""
     from paper_2609_17636_b300 import _lib
     L = _lib.load()
-    cfg = _lib.Config(64, 1, 1, 48, 1e-5, 0, 1e-9, 0, 0.0, 0.0, 1, 0, 0, 0)  # nb not a power of two
+    cfg = _lib.Config(64, 1, 1, 48, 1e-5, 0, 1e-9, 0, 0.0, 0.0, 1, 0, 0, 0, 0)  # nb not a power of two
     p = ctypes.c_void_p()
     st = L.ivis_plan(ctypes.byref(cfg), None, ctypes.byref(p))
     assert st == 1 and not p.value

@@ -524,3 +524,61 @@ def test_feather_of_an_impulse_is_the_gaussian_of_the_transfer_function():
     g = np.exp(-(d[:, None] ** 2 + d[None, :] ** 2) / (2 * sig ** 2)) / (2 * math.pi * sig ** 2)
     assert np.abs(out - g).max() <= 1e-12
     assert abs(out.sum() - 1.0) <= 1e-12
+
+
+# ------------------------------------------------- full visibility equation (Eq. 1, w-term)
+def test_wterm_phase_is_the_geometric_delay():
+    """Eq. 1's phase u l + v m + w (n - 1) is the geometric delay difference b.(s - s0)/lambda
+    between a source direction s and the phase centre s0, with b and s taken in the equatorial
+    frame of the hour angle (independent of the (u, v, w) decomposition); the coplanar Eq. 3
+    misses w (n - 1). Amplitude f / n."""
+    lat, dec0, ha = synth.LAT_ASKAP_RAD, synth.DEC_LMC_RAD, 1.3
+    enu = np.array([[0.0, 0.0, 0.0], [4200.0, -2500.0, 30.0]])
+    uvw = synth.uvw_tracks(enu, np.array([ha]), dec0, lat, synth.HI_FREQ_HZ)
+    lam = synth.C_LIGHT / synth.HI_FREQ_HZ
+    b = enu[1] - enu[0]
+    bxyz = np.array([-math.sin(lat) * b[1] + math.cos(lat) * b[2], b[0],
+                     math.cos(lat) * b[1] + math.sin(lat) * b[2]]) / lam
+    # phase centre and a source 25 and 19 pixels off it (1 arcmin cells), as unit vectors
+    nb, cell = 64, 60.0 * synth.ARCSEC
+    p, q = nb // 2 + 25, nb // 2 - 19
+    l, m = (p - nb // 2) * cell, (q - nb // 2) * cell
+    n = math.sqrt(1.0 - l * l - m * m)
+    ch, sh, cd, sd = math.cos(ha), math.sin(ha), math.cos(dec0), math.sin(dec0)
+    s0 = np.array([cd * ch, -cd * sh, sd])
+    # tangent-plane axes at s0: east (increasing right ascension) and north
+    e_l = np.array([sh, ch, 0.0])
+    e_m = np.cross(s0, e_l)
+    s = l * e_l + m * e_m + n * s0
+    delay = float(bxyz @ (s - s0))
+    f = np.zeros((nb, nb))
+    f[q, p] = 2.0
+    V = oracle.model_vis(f, cell, uvw[:, 0], uvw[:, 1], uvw[:, 2])[0]
+    assert abs(abs(V) - 2.0 / n) <= 1e-12
+    ph = -2.0 * math.pi * delay
+    assert abs(V - 2.0 / n * complex(math.cos(ph), math.sin(ph))) <= 1e-9
+    Vc = oracle.model_vis(f, cell, uvw[:, 0], uvw[:, 1])[0]
+    assert abs(np.angle(V / Vc) - np.angle(np.exp(-2j * math.pi * uvw[0, 2] * (n - 1.0)))) <= 1e-9
+    assert abs(uvw[0, 2] * (n - 1.0)) > 0.05  # the test geometry makes the w-term visible
+
+
+def test_wterm_adjoint_identity_and_gradient():
+    rng = np.random.default_rng(61)
+    nb, cell, m = 24, 90.0 * synth.ARCSEC, 40
+    uvw = rng.standard_normal((m, 3)) * np.array([3000.0, 3000.0, 8000.0])
+    f = rng.standard_normal((nb, nb))
+    c = rng.standard_normal(m) + 1j * rng.standard_normal(m)
+    Ff = oracle.model_vis(f, cell, uvw[:, 0], uvw[:, 1], uvw[:, 2])
+    a = oracle.adjoint(c, nb, cell, uvw[:, 0], uvw[:, 1], uvw[:, 2])
+    lhs = np.vdot(c, Ff)
+    rhs = np.vdot(a, f.astype(complex))
+    assert abs(lhs - rhs) <= 1e-11 * abs(lhs)
+    qs, ps = rng.integers(0, nb, 9), rng.integers(0, nb, 9)
+    ap = oracle.adjoint_pixels(c, nb, cell, uvw[:, 0], uvw[:, 1], qs, ps, uvw[:, 2])
+    assert np.allclose(ap, a[qs, ps], rtol=0, atol=1e-11 * np.abs(a).max())
+    prob = synth.small_mosaic(62, n=40, nb=32, nchan=1, npoint=2, ndump=3, n_ant=7,
+                              cell_arcsec=120.0, lambda_r=0.0, lambda_s=0.0)
+    prob.wterm = True
+    _with_data(prob)
+    x = prob.sky_true * rng.uniform(0.5, 1.5, prob.sky_true.shape)
+    _fd_check(lambda z: oracle.data_cost_grad(prob, z), x, rng.choice(x.size, 10, replace=False), 1e-4)

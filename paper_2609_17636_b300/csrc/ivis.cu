@@ -23,6 +23,7 @@
 #include "kernels_nufft.cuh"
 #include "kernels_solver.cuh"
 #include "kernels_feather.cuh"
+#include "kernels_sdconv.cuh"
 #include "kernels_toeplitz.cuh"
 #include "kernels_wstack.cuh"
 
@@ -99,6 +100,9 @@ struct ivis_plan_s {
     int *chan_start_d = nullptr, *chan_list_d = nullptr;
     int Rsd = 0;
     void *taps_d = nullptr;
+    // dish-beam convolution by line DFTs of period sd_N >= n + R (0: direct taps)
+    int sd_N = 0, sd_logN = 0, sd_logc = 0;
+    void *sd_spec_d = nullptr, *sd_tw_d = nullptr;
     double *inv_sig2_d = nullptr;
     void *rowbuf = nullptr, *F = nullptr, *G = nullptr, *contrib = nullptr;
     void *x = nullptr, *g = nullptr, *tmp1 = nullptr, *tmp2 = nullptr, *gradK = nullptr;
@@ -395,7 +399,7 @@ cudaError_t launch_adjoint(ivis_plan_s *p, int slot0 = 0, int nslots = -1) {
     typedef typename cplx_of<T>::type C;
     const int nb = p->cfg.nb, nf = p->nf, tpl = nf / 16, lpb = 256 / tpl;
     if (nslots < 0) nslots = p->nslot;
-    const C *G = (const C *)p->G + (size_t)slot0 * nf * nf;
+    C *G = (C *)p->G + (size_t)slot0 * nf * nf;
     C *rowbuf = (C *)p->rowbuf + (size_t)slot0 * nb * nf;
     T *contrib = (T *)p->contrib + (size_t)slot0 * nb * nb;
     dim3 gc(nf >> p->logc_cols, nslots);
@@ -441,7 +445,7 @@ cudaError_t launch_toeplitz(ivis_plan_s *p) {
 
 template <typename T>
 size_t conv_smem(int R) {
-    const size_t strip = std::max((size_t)(CONV_TO + 2 * R) * 33, (size_t)(CONV_SPLIT - 1) * 8 * CONV_OPT * 32);
+    const size_t strip = std::max((size_t)(CONV_TO + 2 * R) * 33, (size_t)(CONV_SPLIT - 1) * CONV_NWO * CONV_OPT * 32);
     return (strip + 2 * R + 1) * sizeof(T);
 }
 
@@ -449,22 +453,47 @@ template <typename T>
 cudaError_t launch_fusion(ivis_plan_s *p, cudaStream_t st, const void *sky, void *tsd_out_e,
                           void *gradK_out, bool fused) {
     const int n = p->cfg.n, nchan = p->cfg.nchan, R = p->Rsd;
+    if (p->sd_N) {
+        // rows then columns, each a line DFT x taps' spectrum x inverse DFT
+        typedef typename cplx_of<T>::type C;
+        const int N = p->sd_N, tpl = N / 16, lpb = std::max(1, 256 / tpl), logc = p->sd_logc;
+        const dim3 gr(((n + 1) / 2 + lpb - 1) / lpb, nchan), gc((n + (2 << logc) - 1) / (2 << logc), nchan);
+        const size_t smr = (size_t)fft_smem_elems(N, lpb) * sizeof(C), smc = (size_t)fft_smem_elems(N, 1 << logc) * sizeof(C);
+        cudaFuncSetAttribute(k_sdconv_rows<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smr);
+        cudaFuncSetAttribute(k_sdconv_cols<T, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smc);
+        cudaFuncSetAttribute(k_sdconv_cols<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smc);
+        const T *sp = (const T *)p->sd_spec_d;
+        const C *tw = (const C *)p->sd_tw_d;
+        const int nt = lpb * tpl, ntc = tpl << logc;
+        k_sdconv_rows<T><<<gr, nt, smr, st>>>((const T *)sky, (T *)p->tmp1, sp, n, p->sd_logN, tw);
+        if (!fused) {
+            k_sdconv_cols<T, 0><<<gc, ntc, smc, st>>>((const T *)p->tmp1, (T *)tsd_out_e, sp, n, p->sd_logN, logc, tw,
+                                                      nullptr, nullptr, nullptr);
+            return cudaGetLastError();
+        }
+        k_sdconv_cols<T, 1><<<gc, ntc, smc, st>>>((const T *)p->tmp1, (T *)p->tmp2, sp, n, p->sd_logN, logc, tw,
+                                                  (const T *)p->tsd_d, p->inv_sig2_d, p->kpart);
+        k_sdconv_rows<T><<<gr, nt, smr, st>>>((const T *)p->tmp2, (T *)p->tmp1, sp, n, p->sd_logN, tw);
+        k_sdconv_cols<T, 0><<<gc, ntc, smc, st>>>((const T *)p->tmp1, (T *)gradK_out, sp, n, p->sd_logN, logc, tw,
+                                                  nullptr, nullptr, nullptr);
+        return cudaGetLastError();
+    }
     const size_t sm = conv_smem<T>(R);
     cudaFuncSetAttribute(k_conv_axis<T, 0, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     cudaFuncSetAttribute(k_conv_axis<T, 1, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     cudaFuncSetAttribute(k_conv_axis<T, 1, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     dim3 gr((n + 31) / 32, (n + CONV_TO - 1) / CONV_TO, nchan);
     const T *taps = (const T *)p->taps_d;
-    k_conv_axis<T, 0, 0><<<gr, 256 * CONV_SPLIT, sm, st>>>((const T *)sky, (T *)p->tmp1, taps, R, n, nullptr, nullptr, nullptr);
+    k_conv_axis<T, 0, 0><<<gr, CONV_THREADS, sm, st>>>((const T *)sky, (T *)p->tmp1, taps, R, n, nullptr, nullptr, nullptr);
     if (!fused) {  // plain B (x) I into tsd_out_e
-        k_conv_axis<T, 1, 0><<<gr, 256 * CONV_SPLIT, sm, st>>>((const T *)p->tmp1, (T *)tsd_out_e, taps, R, n, nullptr,
+        k_conv_axis<T, 1, 0><<<gr, CONV_THREADS, sm, st>>>((const T *)p->tmp1, (T *)tsd_out_e, taps, R, n, nullptr,
                                                   nullptr, nullptr);
         return cudaGetLastError();
     }
-    k_conv_axis<T, 1, 1><<<gr, 256 * CONV_SPLIT, sm, st>>>((const T *)p->tmp1, (T *)p->tmp2, taps, R, n,
+    k_conv_axis<T, 1, 1><<<gr, CONV_THREADS, sm, st>>>((const T *)p->tmp1, (T *)p->tmp2, taps, R, n,
                                               (const T *)p->tsd_d, p->inv_sig2_d, p->kpart);
-    k_conv_axis<T, 0, 0><<<gr, 256 * CONV_SPLIT, sm, st>>>((const T *)p->tmp2, (T *)p->tmp1, taps, R, n, nullptr, nullptr, nullptr);
-    k_conv_axis<T, 1, 0><<<gr, 256 * CONV_SPLIT, sm, st>>>((const T *)p->tmp1, (T *)gradK_out, taps, R, n, nullptr,
+    k_conv_axis<T, 0, 0><<<gr, CONV_THREADS, sm, st>>>((const T *)p->tmp2, (T *)p->tmp1, taps, R, n, nullptr, nullptr, nullptr);
+    k_conv_axis<T, 1, 0><<<gr, CONV_THREADS, sm, st>>>((const T *)p->tmp1, (T *)gradK_out, taps, R, n, nullptr,
                                               nullptr, nullptr);
     return cudaGetLastError();
 }
@@ -512,9 +541,6 @@ cudaError_t enqueue_eval(ivis_plan_s *p, bool capture) {
         stage_end(p, p->stream, si);
     } else if (p->nslot > 0 && p->cfg.wterm) {
         // w-stacking: interpolation from every plane, per-visibility residuals, spreading
-        stage_begin(p, "zero_adjoint_grid", p->stream, si);
-        cudaMemsetAsync(p->G, 0, (size_t)p->nslot * p->nf * p->nf * sizeof(C), p->stream);
-        stage_end(p, p->stream, si);
         stage_begin(p, "fwd_fft", p->stream, si);
         if ((e = launch_forward<T>(p, p->x)) != cudaSuccess) return e;
         stage_end(p, p->stream, si);
@@ -533,9 +559,7 @@ cudaError_t enqueue_eval(ivis_plan_s *p, bool capture) {
         stage_end(p, p->stream, si);
         launches += 7;
     } else if (p->nslot > 0) {
-        stage_begin(p, "zero_adjoint_grid", p->stream, si);
-        cudaMemsetAsync(p->G, 0, (size_t)p->nslot * p->nf * p->nf * sizeof(C), p->stream);
-        stage_end(p, p->stream, si);
+        // the adjoint grid is zero here: zeroed at prepare and by every adjoint column pass
         if (p->cfg.serial_pairs) {
             // one (pointing, channel) pair at a time: the unbatched reference path
             stage_begin(p, "serial_pairs", p->stream, si);
@@ -922,6 +946,9 @@ void release_prepared(ivis_plan_s *p) {
     dfree(pi); dfree(p->pdata_d); dfree(ck); dfree(cs); dfree(cl);
     p->pinfo_d = nullptr; p->chunks_d = nullptr; p->chan_start_d = nullptr; p->chan_list_d = nullptr;
     dfree(p->taps_d);
+    dfree(p->sd_spec_d);
+    dfree(p->sd_tw_d);
+    p->sd_N = 0;
     void *is = p->inv_sig2_d; dfree(is); p->inv_sig2_d = nullptr;
     dfree(p->rowbuf); dfree(p->F); dfree(p->G); dfree(p->contrib);
     dfree(p->x); dfree(p->g); dfree(p->tmp1); dfree(p->tmp2); dfree(p->gradK);
@@ -1179,6 +1206,7 @@ ivis_status prepare_impl(ivis_plan_s *p) {
     if ((s = alloc(p, &p->rowbuf, (size_t)p->nslot * c.nb * p->nf * sizeof(C)))) return s;
     if ((s = alloc(p, &p->F, (size_t)p->nslot * nf2 * sizeof(C)))) return s;
     if ((s = alloc(p, &p->G, (size_t)p->nslot * nf2 * sizeof(C)))) return s;
+    CK(cudaMemset(p->G, 0, (size_t)p->nslot * nf2 * sizeof(C)));
     if ((s = alloc(p, &p->contrib, (size_t)p->nslot * c.nb * c.nb * sizeof(T)))) return s;
     if ((s = alloc(p, &p->x, npix * sizeof(T)))) return s;
     if ((s = alloc(p, &p->g, npix * sizeof(T)))) return s;
@@ -1240,12 +1268,50 @@ ivis_status prepare_impl(ivis_plan_s *p) {
         }
         if ((s = upload_real<T>(p, &p->taps_d, taps))) return s;
         if ((s = up((void **)&p->inv_sig2_d, is2.data(), is2.size() * sizeof(double)))) return s;
-        if (conv_smem<T>(R) > 220 * 1024)
-            return fail(p, IVIS_ERR_ARG, "single-dish beam too wide for the convolution strip");
         if ((s = alloc(p, &p->tmp1, npix * sizeof(T)))) return s;
         if ((s = alloc(p, &p->tmp2, npix * sizeof(T)))) return s;
         if ((s = alloc(p, &p->gradK, npix * sizeof(T)))) return s;
         p->nkpart = ((c.n + 31) / 32) * ((c.n + CONV_TO - 1) / CONV_TO) * c.nchan;
+        // line-DFT convolution when the padded period fits one CTA's line (N <= 8192)
+        p->sd_N = 0;
+        int N = 16;
+        while (N < c.n + R) N *= 2;
+        if (N <= 8192) {
+            typedef typename cplx_of<T>::type C;
+            const int tpl = N / 16;
+            int logc = 0;
+            auto fits = [&](int l) {
+                return (size_t)fft_smem_elems(N, 1 << l) * sizeof(C) <= 100 * 1024 &&
+                       (tpl << l) <= (p->fp64 ? 512 : 1024) && (2 << l) <= std::max(2, c.n);
+            };
+            while (logc < 4 && fits(logc + 1)) ++logc;
+            if ((size_t)fft_smem_elems(N, 1 << logc) * sizeof(C) <= 200 * 1024 &&
+                (size_t)fft_smem_elems(N, std::max(1, 256 / tpl)) * sizeof(C) <= 200 * 1024) {
+                std::vector<double> spec((size_t)c.nchan * N, 0.0), twd(2 * (size_t)N);
+                for (int ch = 0; ch < c.nchan; ++ch) {
+                    const double *b = taps.data() + (size_t)ch * (2 * R + 1) + R;  // b[0] at offset R
+                    for (int k = 0; k < N; ++k) {
+                        double acc = b[0];
+                        for (int t = 1; t <= R; ++t) acc += 2.0 * b[t] * std::cos(2.0 * M_PI * (double)((long long)k * t % N) / N);
+                        spec[(size_t)ch * N + k] = acc / N;
+                    }
+                }
+                std::vector<C> tw(N);
+                for (int j = 0; j < N; ++j) {
+                    tw[j].x = (T)std::cos(2.0 * M_PI * j / N);
+                    tw[j].y = (T)(-std::sin(2.0 * M_PI * j / N));
+                }
+                if ((s = upload_real<T>(p, &p->sd_spec_d, spec))) return s;
+                if ((s = alloc(p, &p->sd_tw_d, N * sizeof(C)))) return s;
+                CK(cudaMemcpy(p->sd_tw_d, tw.data(), N * sizeof(C), cudaMemcpyHostToDevice));
+                p->sd_N = N;
+                p->sd_logN = ilog2(N);
+                p->sd_logc = logc;
+                p->nkpart = (c.n + (2 << logc) - 1) / (2 << logc) * c.nchan;
+            }
+        }
+        if (!p->sd_N && conv_smem<T>(R) > 220 * 1024)
+            return fail(p, IVIS_ERR_ARG, "single-dish beam too wide for the convolution strip");
         if ((s = alloc(p, (void **)&p->kpart, (size_t)p->nkpart * sizeof(double)))) return s;
     }
     if (!p->kpart && (s = alloc(p, (void **)&p->kpart, sizeof(double)))) return s;
@@ -1989,8 +2055,8 @@ ivis_status ivis_sd_predict_noalloc(const float *sky_dev, int n, int nchan, doub
     for (int c = 0; c < nchan && e == cudaSuccess; ++c) {
         const float *in = sky_dev + (size_t)c * n * n;
         float *out = out_dev + (size_t)c * n * n;
-        k_conv_axis<float, 0, 0><<<gr, 256 * CONV_SPLIT, sm, cs>>>(in, mid_d, taps_d, R, n, nullptr, nullptr, nullptr);
-        k_conv_axis<float, 1, 0><<<gr, 256 * CONV_SPLIT, sm, cs>>>(mid_d, out, taps_d, R, n, nullptr, nullptr, nullptr);
+        k_conv_axis<float, 0, 0><<<gr, CONV_THREADS, sm, cs>>>(in, mid_d, taps_d, R, n, nullptr, nullptr, nullptr);
+        k_conv_axis<float, 1, 0><<<gr, CONV_THREADS, sm, cs>>>(mid_d, out, taps_d, R, n, nullptr, nullptr, nullptr);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(cs);

@@ -66,31 +66,35 @@ k_assemble(const T *__restrict__ sky, const T *__restrict__ contrib,
 
 // Separable dish-beam convolution, one axis per launch: out = sum_{t=-R..R} b_c[t] in(. - t),
 // zero outside the image. A CTA covers 32 lines (one per lane) x CONV_TO outputs along the
-// convolution axis. Warp w produces CONV_OPT consecutive outputs (w % 8) over one of
-// CONV_SPLIT segments of the taps (w / 8) from a sliding window of registers, so each
-// shared-memory load feeds CONV_OPT FMAs; the segments are summed through shared memory in a
-// fixed order. The staged strip is laid out [position][line] with a 33-word pitch (rows
-// pass: lines are image rows and the transpose would otherwise serialise on one bank).
+// convolution axis. Warp w produces CONV_OPT consecutive outputs (w % CONV_NWO) over one of
+// CONV_SPLIT segments of the taps (w / CONV_NWO) from a sliding window of registers, so each
+// shared-memory load feeds CONV_OPT FMAs; the window is a ring indexed by the tap step modulo
+// CONV_OPT (taps unrolled by CONV_OPT, no register moves); the segments are summed through
+// shared memory in a fixed order. The staged strip is laid out [position][line] with a
+// 33-word pitch (rows pass: lines are image rows and the transpose would otherwise serialise
+// on one bank). 32-output strips keep the grid at >= 2 CTAs per SM on a 512^2 image.
 constexpr int CONV_OPT = 8;
-constexpr int CONV_TO = 8 * CONV_OPT;  // outputs per CTA along the axis
-constexpr int CONV_SPLIT = 4;          // tap segments (CTA = 256 * CONV_SPLIT threads)
+constexpr int CONV_NWO = 4;                            // output warps per tap segment
+constexpr int CONV_TO = CONV_NWO * CONV_OPT;           // outputs per CTA along the axis
+constexpr int CONV_SPLIT = 4;                          // tap segments
+constexpr int CONV_THREADS = 32 * CONV_NWO * CONV_SPLIT;
 
 // AXIS 0: along x (lines = rows); AXIS 1: along y (lines = columns).
 // FUSED (AXIS 1 only): out = e = (t - T)/sigma^2 and the CTA's share of K goes to kpart.
 template <typename T, int AXIS, int FUSED>
-__global__ void __launch_bounds__(256 * CONV_SPLIT)
+__global__ void __launch_bounds__(CONV_THREADS)
 k_conv_axis(const T *__restrict__ in, T *out, const T *__restrict__ taps, int R, int n,
             const T *__restrict__ tsd, const double *__restrict__ inv_sig2, double *kpart) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double red[32];
     const int P = 33;
     const int L = CONV_TO + 2 * R;  // staged positions
-    constexpr int NPART = (CONV_SPLIT - 1) * 8 * CONV_OPT * 32;
+    constexpr int NPART = (CONV_SPLIT - 1) * CONV_NWO * CONV_OPT * 32;
     T *sh = reinterpret_cast<T *>(smem_raw);
     T *tp = sh + max(L * P, NPART);
-    T *part = sh;  // [CONV_SPLIT - 1][8 warps][CONV_OPT][32], reuses the strip after the taps loop
+    T *part = sh;  // [CONV_SPLIT - 1][CONV_NWO][CONV_OPT][32], reuses the strip after the taps loop
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int wo = wid & 7, seg = wid >> 3;
+    const int wo = wid % CONV_NWO, seg = wid / CONV_NWO;
     const int line0 = blockIdx.x * 32, pos0 = blockIdx.y * CONV_TO, c = blockIdx.z;
     const T *img = in + (size_t)c * n * n;
     const T *b = taps + (size_t)c * (2 * R + 1);
@@ -120,8 +124,19 @@ k_conv_axis(const T *__restrict__ in, T *out, const T *__restrict__ taps, int R,
         acc[j] = (T)0;
         win[j] = sh[(o0 + j + 2 * R - tb) * P + lane];
     }
-#pragma unroll 4
-    for (int t = tb; t < te; ++t) {
+    // at step u of a block of CONV_OPT taps, logical window entry j is win[(j - u) mod OPT];
+    // the entry dropped after step u takes the next staged value
+    int t = tb;
+    for (; t + CONV_OPT <= te; t += CONV_OPT) {
+#pragma unroll
+        for (int u = 0; u < CONV_OPT; ++u) {
+            const T bt = tp[t + u];
+#pragma unroll
+            for (int j = 0; j < CONV_OPT; ++j) acc[j] += bt * win[(j - u + CONV_OPT) % CONV_OPT];
+            win[(CONV_OPT - 1 - u) % CONV_OPT] = sh[max(o0 + 2 * R - (t + u) - 1, 0) * P + lane];
+        }
+    }
+    for (; t < te; ++t) {
         const T bt = tp[t];
 #pragma unroll
         for (int j = 0; j < CONV_OPT; ++j) acc[j] += bt * win[j];
@@ -132,7 +147,7 @@ k_conv_axis(const T *__restrict__ in, T *out, const T *__restrict__ taps, int R,
     __syncthreads();  // every warp is done reading the strip
     if (seg > 0) {
 #pragma unroll
-        for (int j = 0; j < CONV_OPT; ++j) part[(((seg - 1) * 8 + wo) * CONV_OPT + j) * 32 + lane] = acc[j];
+        for (int j = 0; j < CONV_OPT; ++j) part[(((seg - 1) * CONV_NWO + wo) * CONV_OPT + j) * 32 + lane] = acc[j];
     }
     __syncthreads();
     T kloc = (T)0;  // <= CONV_OPT terms per thread in the working precision, then FP64
@@ -140,7 +155,7 @@ k_conv_axis(const T *__restrict__ in, T *out, const T *__restrict__ taps, int R,
 #pragma unroll
         for (int q = 1; q < CONV_SPLIT; ++q)
 #pragma unroll
-            for (int j = 0; j < CONV_OPT; ++j) acc[j] += part[(((q - 1) * 8 + wo) * CONV_OPT + j) * 32 + lane];
+            for (int j = 0; j < CONV_OPT; ++j) acc[j] += part[(((q - 1) * CONV_NWO + wo) * CONV_OPT + j) * 32 + lane];
         const T is2 = FUSED ? (T)inv_sig2[c] : (T)0;
         const int line = line0 + lane;
 #pragma unroll
@@ -164,15 +179,27 @@ k_conv_axis(const T *__restrict__ in, T *out, const T *__restrict__ taps, int R,
     }
 }
 
+// This thread's share of sum(v[0..n)): elements threadIdx.x + i * blockDim.x, eight
+// independent loads in flight per step, combined in a fixed order.
+__device__ __forceinline__ double strided_sum(const double *__restrict__ v, int n) {
+    double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    const int B = blockDim.x;
+    for (int i0 = threadIdx.x; i0 < n; i0 += 8 * B) {
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int i = i0 + u * B;
+            acc[u] += i < n ? __ldcg(v + i) : 0.0;
+        }
+    }
+    return ((acc[0] + acc[1]) + (acc[2] + acc[3])) + ((acc[4] + acc[5]) + (acc[6] + acc[7]));
+}
+
 // out = {Q_tot, Q, K, R}; fixed summation order (deterministic for a fixed launch shape).
 __global__ void k_finalize(const double *__restrict__ jpart, int nj, const double *__restrict__ kpart,
                            int nk, const double *__restrict__ rpart, int nr, double lr, double ls,
                            double *out) {
     __shared__ double red[32];
-    double a = 0.0, b = 0.0, c = 0.0;
-    for (int i = threadIdx.x; i < nj; i += blockDim.x) a += jpart[i];
-    for (int i = threadIdx.x; i < nk; i += blockDim.x) b += kpart[i];
-    for (int i = threadIdx.x; i < nr; i += blockDim.x) c += rpart[i];
+    const double a = strided_sum(jpart, nj), b = strided_sum(kpart, nk), c = strided_sum(rpart, nr);
     const double Q = block_sum(a, red);
     const double K = block_sum(b, red);
     const double R = block_sum(c, red);

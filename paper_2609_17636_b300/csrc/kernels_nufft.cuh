@@ -365,10 +365,12 @@ __device__ __forceinline__ void red_add_c(double2 *p, double2 v) {
 // row r. Each lane evaluates one x and one y kernel value, the x values are exchanged by
 // shuffles, the row sums of the interpolation are reduced across the group, and the same 2W
 // kernel values serve the spreading. Each group walks a contiguous run of the chunk, whose
-// visibilities are sorted by first-tap cell: while the cell repeats, a lane keeps its row of
-// the spread in registers and only adds it to the shared sub-grid (atomics) when the cell
-// changes. MODE_PREDICT writes V~ to pred[pred_off + orig] instead of spreading; MODE_SPREAD
-// skips the interpolation and spreads w times the record's value (the w-stacked entries).
+// visibilities are sorted by first-tap cell (row-major within the tile): a lane keeps its row
+// of the spread in registers; while the cell repeats nothing is written, and when the next
+// first tap lies d < W cells further right on the same row only the d cells that leave the
+// window are added to the shared sub-grid (atomics) before the window slides. MODE_PREDICT
+// writes V~ to pred[pred_off + orig] instead of spreading; MODE_SPREAD skips the
+// interpolation and spreads w times the record's value (the w-stacked entries).
 template <typename T, int W, int MODE>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 5 : 2)
 k_grid_pass(const Chunk *__restrict__ chunks, const PairData<T> *__restrict__ pdata,
@@ -441,11 +443,27 @@ k_grid_pass(const Chunk *__restrict__ chunks, const PairData<T> *__restrict__ pd
         if (SPREAD && valid && (lx != clx || ly != cly)) {
             if (clx >= 0 && active_row) {
                 C *gr = Gs + (cly + r) * PW + clx;
+                // same kernel-row band, first tap d cells further right (the sort makes d >= 0):
+                // only the d leftmost cells of the held row are final; the rest slide along
+                const int d = (ly == cly && lx >= clx) ? lx - clx : W;
+                if (d >= W) {
 #pragma unroll
-                for (int a = 0; a < W; ++a) {
-                    atomicAdd(&gr[a].x, racc[a].x);
-                    atomicAdd(&gr[a].y, racc[a].y);
-                    racc[a] = mk((T)0, (T)0);
+                    for (int a = 0; a < W; ++a) {
+                        atomicAdd(&gr[a].x, racc[a].x);
+                        atomicAdd(&gr[a].y, racc[a].y);
+                        racc[a] = mk((T)0, (T)0);
+                    }
+                } else {
+#pragma unroll
+                    for (int sft = 0; sft < W - 1; ++sft) {
+                        if (sft < d) {
+                            atomicAdd(&gr[sft].x, racc[0].x);
+                            atomicAdd(&gr[sft].y, racc[0].y);
+#pragma unroll
+                            for (int a = 0; a < W - 1; ++a) racc[a] = racc[a + 1];
+                            racc[W - 1] = mk((T)0, (T)0);
+                        }
+                    }
                 }
             }
             clx = lx;
@@ -527,7 +545,7 @@ k_grid_pass(const Chunk *__restrict__ chunks, const PairData<T> *__restrict__ pd
 // ---------------------------------------------------------------- adjoint column pass (a5)
 template <typename T>
 __global__ void __launch_bounds__(sizeof(T) == 8 ? 512 : 1024)
-k_adj_cols(const typename cplx_of<T>::type *__restrict__ G,
+k_adj_cols(typename cplx_of<T>::type *__restrict__ G,
            typename cplx_of<T>::type *rowbuf, int nb, int lognf, int logc,
            const typename cplx_of<T>::type *__restrict__ tw) {
     typedef typename cplx_of<T>::type C;
@@ -537,9 +555,11 @@ k_adj_cols(const typename cplx_of<T>::type *__restrict__ G,
     const int c0 = blockIdx.x << logc, slot = blockIdx.y;
     const int c = threadIdx.x & (ncol - 1), j0 = threadIdx.x >> logc;
     const int tpl = nf >> 4;
-    const C *src = G + (size_t)slot * nf * nf;
+    // the adjoint grid is consumed here and left zeroed for the next spreading pass
+    C *src = G + (size_t)slot * nf * nf;
     for (int e = j0; e < nf; e += tpl) s[pidx((e << logc) + c)] = src[(size_t)e * nf + c0 + c];
     __syncthreads();
+    for (int e = j0; e < nf; e += tpl) src[(size_t)e * nf + c0 + c] = mk((T)0, (T)0);
     line_fft<C, +1>(s, ncol, c, lognf, j0, tw);
     C *dst = rowbuf + (size_t)slot * nb * nf;
     for (int q = j0; q < nb; q += tpl) {

@@ -21,6 +21,7 @@
 #include "../../include/ivis.h"
 #include "kernels_image.cuh"
 #include "kernels_nufft.cuh"
+#include "kernels_packed.cuh"
 #include "kernels_solver.cuh"
 #include "kernels_feather.cuh"
 #include "kernels_sdconv.cuh"
@@ -370,11 +371,31 @@ cudaError_t launch_grid_pass(ivis_plan_s *p, int first_chunk, int nchunk, double
 
 // Row passes: 256 threads = lpb lines of nf/16 threads. Column passes: ncol x nf/16 threads.
 // Forward passes for slots [slot0, slot0 + nslots) (all slots by default).
+// Whole-plan passes over real windows (no w-planes) carry two slots per transform.
+bool packed_pass(const ivis_plan_s *p, int slot0, int nslots) {
+    return slot0 == 0 && nslots == p->nslot && !p->cfg.wterm && !p->cfg.serial_pairs;
+}
+
 template <typename T>
 cudaError_t launch_forward(ivis_plan_s *p, const void *sky, int slot0 = 0, int nslots = -1) {
     typedef typename cplx_of<T>::type C;
     const int nb = p->cfg.nb, nf = p->nf, tpl = nf / 16, lpb = 256 / tpl;
     if (nslots < 0) nslots = p->nslot;
+    if (packed_pass(p, slot0, nslots)) {
+        const int npk = (nslots + 1) / 2, lc = std::max(0, p->logc_cols - 1);
+        dim3 gr((nb + lpb - 1) / lpb, npk);
+        size_t smem_row = (size_t)fft_smem_elems(nf, lpb) * sizeof(C);
+        cudaFuncSetAttribute(k_fwd_rows_pk<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_row);
+        k_fwd_rows_pk<T><<<gr, 256, smem_row, p->stream>>>(
+            (const T *)sky, (const T *)p->beams_d, p->pinfo_d, nslots, (const T *)p->dinv_d, (C *)p->rowbuf,
+            p->cfg.n, nb, p->lognf, (const C *)p->tw_d, (const float2 *)p->grids_d);
+        dim3 gc(nf / (2 << lc), npk);
+        size_t smem_col = (size_t)fft_smem_elems(nf, 2 << lc) * sizeof(C);
+        cudaFuncSetAttribute(k_fwd_cols_pk<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_col);
+        k_fwd_cols_pk<T><<<gc, tpl << (lc + 1), smem_col, p->stream>>>(
+            (const C *)p->rowbuf, (C *)p->F, nslots, nb, p->lognf, lc, (const C *)p->tw_d);
+        return cudaGetLastError();
+    }
     const PairInfo *pinfo = p->pinfo_d + slot0;
     C *rowbuf = (C *)p->rowbuf + (size_t)slot0 * nb * nf;
     C *F = (C *)p->F + (size_t)slot0 * nf * nf;
@@ -399,6 +420,21 @@ cudaError_t launch_adjoint(ivis_plan_s *p, int slot0 = 0, int nslots = -1) {
     typedef typename cplx_of<T>::type C;
     const int nb = p->cfg.nb, nf = p->nf, tpl = nf / 16, lpb = 256 / tpl;
     if (nslots < 0) nslots = p->nslot;
+    if (packed_pass(p, slot0, nslots)) {
+        const int npk = (nslots + 1) / 2, lc = std::max(0, p->logc_cols - 1);
+        dim3 gc(nf / (2 << lc), npk);
+        size_t smem_col = (size_t)fft_smem_elems(nf, 2 << lc) * sizeof(C);
+        cudaFuncSetAttribute(k_adj_cols_pk<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_col);
+        k_adj_cols_pk<T><<<gc, tpl << (lc + 1), smem_col, p->stream>>>((C *)p->G, (C *)p->rowbuf, nslots, nb,
+                                                                       p->lognf, lc, (const C *)p->tw_d);
+        dim3 gr((nb + lpb - 1) / lpb, npk);
+        size_t smem_row = (size_t)fft_smem_elems(nf, lpb) * sizeof(C);
+        cudaFuncSetAttribute(k_adj_rows_pk<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_row);
+        k_adj_rows_pk<T><<<gr, 256, smem_row, p->stream>>>((const C *)p->rowbuf, (const T *)p->beams_d, p->pinfo_d,
+                                                           nslots, (const T *)p->dinv_d, (T *)p->contrib, p->cfg.n,
+                                                           nb, p->lognf, (const C *)p->tw_d);
+        return cudaGetLastError();
+    }
     C *G = (C *)p->G + (size_t)slot0 * nf * nf;
     C *rowbuf = (C *)p->rowbuf + (size_t)slot0 * nb * nf;
     T *contrib = (T *)p->contrib + (size_t)slot0 * nb * nb;
@@ -423,23 +459,24 @@ template <typename T>
 cudaError_t launch_toeplitz(ivis_plan_s *p) {
     typedef typename cplx_of<T>::type C;
     const int nb = p->cfg.nb, nf = p->nf, tpl = nf / 16, lpb = 256 / tpl;
+    const int npk = (p->nslot + 1) / 2, lc = std::max(0, p->logc_cols - 1);
     C *rowbuf = (C *)p->rowbuf;
-    dim3 gr((nb + lpb - 1) / lpb, p->nslot);
+    dim3 gr((nb + lpb - 1) / lpb, npk);
     size_t smem_row = (size_t)fft_smem_elems(nf, lpb) * sizeof(C);
-    cudaFuncSetAttribute(k_fwd_rows<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_row);
-    k_fwd_rows<T><<<gr, 256, smem_row, p->stream>>>(
-        (const T *)p->x, (const T *)p->beams_d, p->pinfo_d, (const T *)p->ones_d, rowbuf,
-        p->cfg.n, nb, p->lognf, (const C *)p->tw_d, (const float2 *)p->grids_d, nullptr, nullptr);
-    dim3 gc(nf >> p->logc_cols, p->nslot);
-    size_t smem_col = (size_t)fft_smem_elems(nf, 1 << p->logc_cols) * sizeof(C);
-    cudaFuncSetAttribute(k_toep_cols<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_col);
-    k_toep_cols<T><<<gc, tpl << p->logc_cols, smem_col, p->stream>>>(
-        rowbuf, (const T *const *)p->that_ptr_d, nb, p->lognf, p->logc_cols, (const C *)p->tw_d);
-    cudaFuncSetAttribute(k_toep_rows<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_row);
-    k_toep_rows<T><<<gr, 256, smem_row, p->stream>>>(
-        rowbuf, (const T *)p->x, (const T *)p->beams_d, p->pinfo_d, (const T *const *)p->bwin_ptr_d,
+    cudaFuncSetAttribute(k_fwd_rows_pk<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_row);
+    k_fwd_rows_pk<T><<<gr, 256, smem_row, p->stream>>>(
+        (const T *)p->x, (const T *)p->beams_d, p->pinfo_d, p->nslot, (const T *)p->ones_d, rowbuf,
+        p->cfg.n, nb, p->lognf, (const C *)p->tw_d, (const float2 *)p->grids_d);
+    dim3 gc(nf / (2 << lc), npk);
+    size_t smem_col = (size_t)fft_smem_elems(nf, 2 << lc) * sizeof(C);
+    cudaFuncSetAttribute(k_toep_cols_pk<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_col);
+    k_toep_cols_pk<T><<<gc, tpl << (lc + 1), smem_col, p->stream>>>(
+        rowbuf, (const T *const *)p->that_ptr_d, p->nslot, nb, p->lognf, lc, (const C *)p->tw_d);
+    cudaFuncSetAttribute(k_toep_rows_pk<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_row);
+    k_toep_rows_pk<T><<<gr, 256, smem_row, p->stream>>>(
+        rowbuf, (const T *)p->x, (const T *)p->beams_d, p->pinfo_d, p->nslot, (const T *const *)p->bwin_ptr_d,
         p->qconst_d, (T *)p->contrib, p->jpart, p->cfg.n, nb, p->lognf, (const C *)p->tw_d,
-        (const float2 *)p->grids_d);
+        (const float2 *)p->grids_d, (const T *)p->ones_d);
     return cudaGetLastError();
 }
 

@@ -194,20 +194,35 @@ __device__ __forceinline__ double strided_sum(const double *__restrict__ v, int 
     return ((acc[0] + acc[1]) + (acc[2] + acc[3])) + ((acc[4] + acc[5]) + (acc[6] + acc[7]));
 }
 
-// out = {Q_tot, Q, K, R}; fixed summation order (deterministic for a fixed launch shape).
+// out = {Q_tot, Q, K, R}; fixed summation order (deterministic for a fixed launch shape). The
+// three sums run interleaved (FP64 latency is long on this part: independent chains overlap).
 __global__ void k_finalize(const double *__restrict__ jpart, int nj, const double *__restrict__ kpart,
                            int nk, const double *__restrict__ rpart, int nr, double lr, double ls,
                            double *out) {
-    __shared__ double red[32];
-    const double a = strided_sum(jpart, nj), b = strided_sum(kpart, nk), c = strided_sum(rpart, nr);
-    const double Q = block_sum(a, red);
-    const double K = block_sum(b, red);
-    const double R = block_sum(c, red);
-    if (threadIdx.x == 0) {
-        out[1] = Q;
-        out[2] = K;
-        out[3] = R;
-        out[0] = Q + ls * K + lr * R;
+    __shared__ double red[3][32];
+    double v[3] = {strided_sum(jpart, nj), strided_sum(kpart, nk), strided_sum(rpart, nr)};
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) v[a] += __shfl_xor_sync(0xffffffffu, v[a], o);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    if (lane == 0)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) red[a][wid] = v[a];
+    __syncthreads();
+    if (wid == 0) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) v[a] = lane < nw ? red[a][lane] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+            for (int a = 0; a < 3; ++a) v[a] += __shfl_xor_sync(0xffffffffu, v[a], o);
+        if (lane == 0) {
+            out[1] = v[0];
+            out[2] = v[1];
+            out[3] = v[2];
+            out[0] = v[0] + ls * v[1] + lr * v[2];
+        }
     }
 }
 

@@ -1,0 +1,288 @@
+// kernels_packed.cuh -- two pointing windows per 2D FFT.
+//
+// The windows A I' of two slots a and b are real, so one complex transform carries both:
+// Z = DFT2(z_a + i z_b), and with M(k) = conj(Z(-k)) the two spectra separate as
+//     DFT2(z_a) = (Z + M) / 2,      DFT2(z_b) = (Z - M) / (2 i).
+// Backwards, only Re IDFT2(G) is needed on each window, and Re IDFT2(G) = IDFT2(H) with the
+// Hermitian part H(k) = (G(k) + conj G(-k)) / 2, whose inverse is real; so
+//     IDFT2(H_a + i H_b) = Re IDFT2(G_a) + i Re IDFT2(G_b).
+// Both identities pair the column kx with its mirror -kx: a column CTA holds the columns
+// c0 .. c0 + ncol - 1 of [0, nf/2) and their mirrors (nf - c) mod nf, with column 0 (its own
+// mirror) replaced by column nf/2 (also its own mirror) in the mirror half. The row passes
+// carry slot a in the real and slot b in the imaginary part. An odd last slot runs with an
+// empty partner (zero input, nothing written).
+#pragma once
+#include "common.cuh"
+#include "fft.cuh"
+#include "kernels_nufft.cuh"
+
+namespace ivis {
+
+// A[q][p] I'[q][p] dinv[p] dinv[q] of one slot (bilinear through the pointing's grid if it
+// has one), zero off the sky.
+template <typename T>
+__device__ __forceinline__ T window_value(const PairInfo &pi, int q, int p, const T *__restrict__ sky,
+                                          const T *__restrict__ beams, const T *__restrict__ dinv,
+                                          const float2 *__restrict__ grids, int n, int nb) {
+    const T a = beams[((size_t)pi.k * nb + q) * nb + p] * dinv[p] * dinv[q];
+    const T *img = sky + (size_t)pi.chan * n * n;
+    if (pi.gridded) {
+        const float2 g = grids[((size_t)pi.k * nb + q) * nb + p];
+        return a * bilerp(img, n, g.x, g.y);
+    }
+    const int y = pi.cy - nb / 2 + q, x = pi.cx - nb / 2 + p;
+    return (y >= 0 && y < n && x >= 0 && x < n) ? a * img[(size_t)y * n + x] : (T)0;
+}
+
+// Column held by line L of a packed column CTA (2 ncol lines), and the line holding its mirror.
+__device__ __forceinline__ int pk_col(int L, int c0, int ncol, int nf) {
+    if (L < ncol) return c0 + L;
+    const int c = c0 + L - ncol;
+    return c == 0 ? nf / 2 : nf - c;
+}
+__device__ __forceinline__ int pk_mirror_line(int L, int c0, int ncol) {
+    if (L < ncol) return (c0 + L == 0) ? 0 : L + ncol;
+    return (c0 + L - ncol == 0) ? L : L - ncol;
+}
+
+// ------------------------------------------------------------------------- forward rows
+// Line l: window row q of the slot pair (2 blockIdx.y, 2 blockIdx.y + 1) -> DFT along x.
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_fwd_rows_pk(const T *__restrict__ sky, const T *__restrict__ beams, const PairInfo *__restrict__ pinfo,
+              int nslot, const T *__restrict__ dinv, typename cplx_of<T>::type *rowbuf, int n, int nb,
+              int lognf, const typename cplx_of<T>::type *__restrict__ tw, const float2 *__restrict__ grids) {
+    typedef typename cplx_of<T>::type C;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C *s = reinterpret_cast<C *>(smem_raw);
+    const int nf = 1 << lognf, tpl = nf >> 4, lpb = blockDim.x / tpl;
+    const int sa = 2 * blockIdx.y, sb = sa + 1;
+    const PairInfo pa = pinfo[sa];
+    const bool hasb = sb < nslot;
+    const PairInfo pb = hasb ? pinfo[sb] : pa;
+    const int l = threadIdx.x / tpl, j0 = threadIdx.x - l * tpl;
+    const int q = blockIdx.x * lpb + l;
+    for (int e = j0; e < nf; e += tpl) s[pidx(l * nf + e)] = mk((T)0, (T)0);
+    __syncthreads();
+    if (q < nb) {
+        for (int p = j0; p < nb; p += tpl) {
+            const T va = window_value(pa, q, p, sky, beams, dinv, grids, n, nb);
+            const T vb = hasb ? window_value(pb, q, p, sky, beams, dinv, grids, n, nb) : (T)0;
+            s[pidx(l * nf + ((p - nb / 2) & (nf - 1)))] = mk(va, vb);
+        }
+    }
+    __syncthreads();
+    line_fft<C, -1>(s, 1, l * nf, lognf, j0, tw);
+    if (q < nb) {
+        C *out = rowbuf + ((size_t)blockIdx.y * nb + q) * nf;
+        for (int e = j0; e < nf; e += tpl) out[e] = s[pidx(l * nf + e)];
+    }
+}
+
+// ---------------------------------------------------------------------- forward columns
+// DFT along y of the packed rows, then the two spectra to F[slot a] and F[slot b].
+template <typename T>
+__global__ void __launch_bounds__(sizeof(T) == 8 ? 512 : 1024)
+k_fwd_cols_pk(const typename cplx_of<T>::type *__restrict__ rowbuf, typename cplx_of<T>::type *F,
+              int nslot, int nb, int lognf, int logc, const typename cplx_of<T>::type *__restrict__ tw) {
+    typedef typename cplx_of<T>::type C;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C *s = reinterpret_cast<C *>(smem_raw);
+    const int nf = 1 << lognf, ncol = 1 << logc, nl = 2 * ncol, lgl = logc + 1, tpl = nf >> 4;
+    const int c0 = blockIdx.x * ncol, pk = blockIdx.y;
+    const int L = threadIdx.x & (nl - 1), j0 = threadIdx.x >> lgl;
+    const int col = pk_col(L, c0, ncol, nf);
+    for (int e = j0; e < nf; e += tpl) s[pidx((e << lgl) + L)] = mk((T)0, (T)0);
+    __syncthreads();
+    const C *src = rowbuf + (size_t)pk * nb * nf;
+    for (int q = j0; q < nb; q += tpl)
+        s[pidx((((q - nb / 2) & (nf - 1)) << lgl) + L)] = src[(size_t)q * nf + col];
+    __syncthreads();
+    line_fft<C, -1>(s, nl, L, lognf, j0, tw);
+    const int Lm = pk_mirror_line(L, c0, ncol);
+    const int sa = 2 * pk, sb = sa + 1;
+    C *Fa = F + (size_t)sa * nf * nf, *Fb = F + (size_t)sb * nf * nf;
+    const bool hasb = sb < nslot;
+    for (int e = j0; e < nf; e += tpl) {
+        const C z = s[pidx((e << lgl) + L)];
+        const C zm = s[pidx((((nf - e) & (nf - 1)) << lgl) + Lm)];  // Z(-ky, -kx)
+        Fa[(size_t)e * nf + col] = mk((T)0.5 * (z.x + zm.x), (T)0.5 * (z.y - zm.y));
+        if (hasb) Fb[(size_t)e * nf + col] = mk((T)0.5 * (z.y + zm.y), (T)0.5 * (zm.x - z.x));
+    }
+}
+
+// ---------------------------------------------------------------------- adjoint columns
+// Z = H_a + i H_b from the two adjoint grids (which are consumed and zeroed), inverse DFT along
+// y, the nb window rows to the packed row buffer.
+template <typename T>
+__global__ void __launch_bounds__(sizeof(T) == 8 ? 512 : 1024)
+k_adj_cols_pk(typename cplx_of<T>::type *G, typename cplx_of<T>::type *rowbuf, int nslot, int nb,
+              int lognf, int logc, const typename cplx_of<T>::type *__restrict__ tw) {
+    typedef typename cplx_of<T>::type C;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C *s = reinterpret_cast<C *>(smem_raw);
+    const int nf = 1 << lognf, ncol = 1 << logc, nl = 2 * ncol, lgl = logc + 1, tpl = nf >> 4;
+    const int c0 = blockIdx.x * ncol, pk = blockIdx.y;
+    const int L = threadIdx.x & (nl - 1), j0 = threadIdx.x >> lgl;
+    const int col = pk_col(L, c0, ncol, nf), colm = pk_col(pk_mirror_line(L, c0, ncol), c0, ncol, nf);
+    const int sa = 2 * pk, sb = sa + 1;
+    const bool hasb = sb < nslot;
+    C *Ga = G + (size_t)sa * nf * nf, *Gb = G + (size_t)sb * nf * nf;
+    for (int e = j0; e < nf; e += tpl) {
+        const size_t i0 = (size_t)e * nf + col, i1 = (size_t)((nf - e) & (nf - 1)) * nf + colm;
+        const C a = Ga[i0], am = Ga[i1];
+        C b = mk((T)0, (T)0), bm = b;
+        if (hasb) {
+            b = Gb[i0];
+            bm = Gb[i1];
+        }
+        // H_a = (a + conj am)/2, H_b = (b + conj bm)/2, Z = H_a + i H_b
+        const C ha = mk((T)0.5 * (a.x + am.x), (T)0.5 * (a.y - am.y));
+        const C hb = mk((T)0.5 * (b.x + bm.x), (T)0.5 * (b.y - bm.y));
+        s[pidx((e << lgl) + L)] = mk(ha.x - hb.y, ha.y + hb.x);
+    }
+    __syncthreads();
+    for (int e = j0; e < nf; e += tpl) {  // every column of both grids is read by exactly one CTA
+        Ga[(size_t)e * nf + col] = mk((T)0, (T)0);
+        if (hasb) Gb[(size_t)e * nf + col] = mk((T)0, (T)0);
+    }
+    line_fft<C, +1>(s, nl, L, lognf, j0, tw);
+    C *dst = rowbuf + (size_t)pk * nb * nf;
+    for (int q = j0; q < nb; q += tpl) dst[(size_t)q * nf + col] = s[pidx((((q - nb / 2) & (nf - 1)) << lgl) + L)];
+}
+
+// ------------------------------------------------------------------------- adjoint rows
+// Inverse DFT along x; the real part is slot a's window gradient, the imaginary part slot b's.
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_adj_rows_pk(const typename cplx_of<T>::type *__restrict__ rowbuf, const T *__restrict__ beams,
+              const PairInfo *__restrict__ pinfo, int nslot, const T *__restrict__ dinv, T *contrib, int n,
+              int nb, int lognf, const typename cplx_of<T>::type *__restrict__ tw) {
+    typedef typename cplx_of<T>::type C;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C *s = reinterpret_cast<C *>(smem_raw);
+    const int nf = 1 << lognf, tpl = nf >> 4, lpb = blockDim.x / tpl;
+    const int sa = 2 * blockIdx.y, sb = sa + 1;
+    const bool hasb = sb < nslot;
+    const PairInfo pa = pinfo[sa];
+    const PairInfo pb = hasb ? pinfo[sb] : pa;
+    const int l = threadIdx.x / tpl, j0 = threadIdx.x - l * tpl;
+    const int q = blockIdx.x * lpb + l;
+    if (q < nb) {
+        const C *src = rowbuf + ((size_t)blockIdx.y * nb + q) * nf;
+        for (int e = j0; e < nf; e += tpl) s[pidx(l * nf + e)] = src[e];
+    }
+    __syncthreads();
+    line_fft<C, +1>(s, 1, l * nf, lognf, j0, tw);
+    if (q >= nb) return;
+    const T dq = dinv[q];
+    const int ya = pa.cy - nb / 2 + q, yb = pb.cy - nb / 2 + q;
+    const bool ona = pa.gridded || (ya >= 0 && ya < n), onb = hasb && (pb.gridded || (yb >= 0 && yb < n));
+    T *oa = contrib + ((size_t)sa * nb + q) * nb, *ob = contrib + ((size_t)sb * nb + q) * nb;
+    const T *ba = beams + ((size_t)pa.k * nb + q) * nb, *bb = beams + ((size_t)pb.k * nb + q) * nb;
+    for (int p = j0; p < nb; p += tpl) {
+        const C v = s[pidx(l * nf + ((p - nb / 2) & (nf - 1)))];
+        const T d = dinv[p] * dq;
+        if (ona) oa[p] = v.x * d * ba[p];
+        if (onb) ob[p] = v.y * d * bb[p];
+    }
+}
+
+// ---------------------------------------------------------------- Toeplitz, packed pairs
+// Column DFT of the packed rows, separation, products with the two spectra recombined as
+// W = That_a Z_a + i That_b Z_b, inverse column DFT, the nb window rows back (in place).
+template <typename T>
+__global__ void __launch_bounds__(sizeof(T) == 8 ? 512 : 1024)
+k_toep_cols_pk(typename cplx_of<T>::type *rowbuf, const T *const *__restrict__ that_ptr, int nslot, int nb,
+               int lognf, int logc, const typename cplx_of<T>::type *__restrict__ tw) {
+    typedef typename cplx_of<T>::type C;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C *s = reinterpret_cast<C *>(smem_raw);
+    const int nf = 1 << lognf, ncol = 1 << logc, nl = 2 * ncol, lgl = logc + 1, tpl = nf >> 4;
+    const int c0 = blockIdx.x * ncol, pk = blockIdx.y;
+    const int L = threadIdx.x & (nl - 1), j0 = threadIdx.x >> lgl;
+    const int col = pk_col(L, c0, ncol, nf), Lm = pk_mirror_line(L, c0, ncol);
+    const int sa = 2 * pk, sb = sa + 1;
+    const bool hasb = sb < nslot;
+    for (int e = j0; e < nf; e += tpl) s[pidx((e << lgl) + L)] = mk((T)0, (T)0);
+    __syncthreads();
+    C *buf = rowbuf + (size_t)pk * nb * nf;
+    for (int q = j0; q < nb; q += tpl) s[pidx((((q - nb / 2) & (nf - 1)) << lgl) + L)] = buf[(size_t)q * nf + col];
+    __syncthreads();
+    line_fft<C, -1>(s, nl, L, lognf, j0, tw);
+    const T *tha = that_ptr[sa] + (size_t)col * nf;
+    const T *thb = hasb ? that_ptr[sb] + (size_t)col * nf : tha;
+    C w[16];  // nf / tpl = 16 elements per thread
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+        const int e = j0 + i * tpl;
+        const C z = s[pidx((e << lgl) + L)];
+        const C zm = s[pidx((((nf - e) & (nf - 1)) << lgl) + Lm)];
+        const C za = mk((T)0.5 * (z.x + zm.x), (T)0.5 * (z.y - zm.y));
+        const C zb = mk((T)0.5 * (z.y + zm.y), (T)0.5 * (zm.x - z.x));
+        const T ta = tha[e], tb = hasb ? thb[e] : (T)0;
+        w[i] = mk(ta * za.x - tb * zb.y, ta * za.y + tb * zb.x);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < 16; ++i) s[pidx(((j0 + i * tpl) << lgl) + L)] = w[i];
+    __syncthreads();
+    line_fft<C, +1>(s, nl, L, lognf, j0, tw);
+    for (int q = j0; q < nb; q += tpl) buf[(size_t)q * nf + col] = s[pidx((((q - nb / 2) & (nf - 1)) << lgl) + L)];
+}
+
+// Row pass of the packed Toeplitz form: y_a = Re, y_b = Im of the inverse row DFT; per slot
+// the gradient times the beam and the cost partial z (y/2 - b) (+ C in the first CTA).
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_toep_rows_pk(const typename cplx_of<T>::type *__restrict__ rowbuf, const T *__restrict__ sky,
+               const T *__restrict__ beams, const PairInfo *__restrict__ pinfo, int nslot,
+               const T *const *__restrict__ bwin_ptr, const double *__restrict__ qconst, T *contrib,
+               double *jpart, int n, int nb, int lognf, const typename cplx_of<T>::type *__restrict__ tw,
+               const float2 *__restrict__ grids, const T *__restrict__ ones) {
+    typedef typename cplx_of<T>::type C;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C *s = reinterpret_cast<C *>(smem_raw);
+    __shared__ double red[32];
+    const int nf = 1 << lognf, tpl = nf >> 4, lpb = blockDim.x / tpl;
+    const int sa = 2 * blockIdx.y, sb = sa + 1;
+    const bool hasb = sb < nslot;
+    const PairInfo pa = pinfo[sa];
+    const PairInfo pb = hasb ? pinfo[sb] : pa;
+    const int l = threadIdx.x / tpl, j0 = threadIdx.x - l * tpl;
+    const int q = blockIdx.x * lpb + l;
+    if (q < nb) {
+        const C *src = rowbuf + ((size_t)blockIdx.y * nb + q) * nf;
+        for (int e = j0; e < nf; e += tpl) s[pidx(l * nf + e)] = src[e];
+    }
+    __syncthreads();
+    line_fft<C, +1>(s, 1, l * nf, lognf, j0, tw);
+    double acc_a = 0.0, acc_b = 0.0;
+    if (q < nb) {
+        const int ya = pa.cy - nb / 2 + q, yb = pb.cy - nb / 2 + q;
+        const bool ona = pa.gridded || (ya >= 0 && ya < n), onb = hasb && (pb.gridded || (yb >= 0 && yb < n));
+        T *oa = contrib + ((size_t)sa * nb + q) * nb, *ob = contrib + ((size_t)sb * nb + q) * nb;
+        const T *ba = beams + ((size_t)pa.k * nb + q) * nb, *bb = beams + ((size_t)pb.k * nb + q) * nb;
+        const T *wa = bwin_ptr[sa] + (size_t)q * nb, *wb = hasb ? bwin_ptr[sb] + (size_t)q * nb : wa;
+        for (int p = j0; p < nb; p += tpl) {
+            const C v = s[pidx(l * nf + ((p - nb / 2) & (nf - 1)))];
+            if (ona) {
+                const T z = window_value(pa, q, p, sky, beams, ones, grids, n, nb);
+                oa[p] = ba[p] * (v.x - wa[p]);
+                acc_a += (double)z * ((double)v.x * 0.5 - (double)wa[p]);
+            }
+            if (onb) {
+                const T z = window_value(pb, q, p, sky, beams, ones, grids, n, nb);
+                ob[p] = bb[p] * (v.y - wb[p]);
+                acc_b += (double)z * ((double)v.y * 0.5 - (double)wb[p]);
+            }
+        }
+    }
+    acc_a = block_sum(acc_a, red);
+    if (threadIdx.x == 0) jpart[(size_t)sa * gridDim.x + blockIdx.x] = acc_a + (blockIdx.x == 0 ? qconst[sa] : 0.0);
+    __syncthreads();
+    acc_b = block_sum(acc_b, red);
+    if (hasb && threadIdx.x == 0) jpart[(size_t)sb * gridDim.x + blockIdx.x] = acc_b + (blockIdx.x == 0 ? qconst[sb] : 0.0);
+}
+
+}  // namespace ivis

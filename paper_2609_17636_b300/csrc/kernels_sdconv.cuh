@@ -84,7 +84,7 @@ k_sdconv_cols(const T *__restrict__ in, T *out, const T *__restrict__ spec, int 
     }
     __syncthreads();
     line_fft<C, +1>(s, ncol, q, logN, j0, tw);
-    double kloc = 0.0;
+    T kloc = (T)0;  // at most 2 n / tpl terms per thread in the working precision, then FP64
     const T is2 = FUSED ? (T)inv_sig2[c] : (T)0;
     for (int e = j0; e < n; e += tpl) {
         const C v = s[pidx((e << logc) + q)];
@@ -92,12 +92,12 @@ k_sdconv_cols(const T *__restrict__ in, T *out, const T *__restrict__ spec, int 
         if (FUSED) {
             if (xa < n) {
                 const T d = v.x - tsd[ia];
-                kloc += 0.5 * (double)(d * d * is2);
+                kloc += (T)0.5 * d * d * is2;
                 out[ia] = d * is2;
             }
             if (xb < n) {
                 const T d = v.y - tsd[ib];
-                kloc += 0.5 * (double)(d * d * is2);
+                kloc += (T)0.5 * d * d * is2;
                 out[ib] = d * is2;
             }
         } else {
@@ -106,8 +106,8 @@ k_sdconv_cols(const T *__restrict__ in, T *out, const T *__restrict__ spec, int 
         }
     }
     if (FUSED) {
-        kloc = block_sum(kloc, red);
-        if (threadIdx.x == 0) kpart[(size_t)c * gridDim.x + blockIdx.x] = kloc;
+        const double ks = block_sum((double)kloc, red);
+        if (threadIdx.x == 0) kpart[(size_t)c * gridDim.x + blockIdx.x] = ks;
     }
 }
 

@@ -163,14 +163,18 @@ k_gemm_bf16(int M, int N, int K, int kchunk, const bf16 *__restrict__ A, const b
 
 // ------------------------------------------------------- tcgen05 GEMM (forward convolution)
 // C[M x N] = relu(A[M x K] B[N x K]^T + bias) in bf16, both operands K-major bf16, FP32
-// accumulation in tensor memory. One CTA of 4 warps per 128 x BN output tile: the K loop
-// stages a 128 x 64 slice of A and a BN x 64 slice of B in shared memory in the canonical
-// no-swizzle layout (8-row x 16-byte core matrices; core matrices adjacent in K are LBO bytes
-// apart, adjacent in M/N 128 bytes apart), one thread issues four tcgen05.mma (K = 16 each),
-// and tcgen05.commit signals that stage's mbarrier. Two stages: slice k + 1 is staged while
-// the tensor cores work on slice k; a stage is reused only after its barrier (bounded wait). The epilogue reads the accumulator rows with tcgen05.ld (warp w owns TMEM lanes
+// accumulation in tensor memory. One CTA of 4 warps per 128 x BN output tile. The K loop moves
+// 128 x 64 slices of A and BN x 64 slices of B into shared memory with 16-byte cp.async copies
+// (zero-filled past the edges) in the canonical no-swizzle layout (8-row x 16-byte core
+// matrices; core matrices adjacent in K are LBO bytes apart, adjacent in M/N 128 bytes apart),
+// TC_STAGES(BN) slices in flight: while the tensor cores work on slice k, the copies of the
+// next slices are outstanding. One thread issues four tcgen05.mma (K = 16 each) per slice and
+// tcgen05.commit signals that stage's mbarrier; a stage is refilled only after its barrier
+// (bounded wait). Operands whose K is not a multiple of 8 (the first layer) are staged through
+// registers. The epilogue reads the accumulator rows with tcgen05.ld (warp w owns TMEM lanes
 // 32w..32w+31 = tile rows), adds the bias, applies the ReLU and stores bf16.
 constexpr int TC_BM = 128, TC_BK = 64;
+template <int BN> struct tc_stages { static constexpr int value = BN <= 64 ? 4 : 3; };
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
     return (uint32_t)__cvta_generic_to_shared(p);
@@ -183,15 +187,26 @@ __device__ __forceinline__ uint64_t umma_desc(uint32_t saddr, uint32_t lbo, uint
            ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
 }
 
-template <int BN>
+// Geometry of an implicit-GEMM 3x3 'same' convolution (the A operand gathered on the fly in
+// the im2col order of k_im2col, nothing materialised): output H x W per image, sources a
+// (ca channels at H/ua x W/ua, nearest upsampling) and b (cb channels at H x W), NHWC bf16,
+// channel counts multiples of 8.
+struct ConvGeom {
+    const bf16 *a;
+    const bf16 *b;
+    int ca, ua, cb, H, W;
+};
+
+template <int BN, bool IMPLICIT>
 __global__ void __launch_bounds__(128)
 k_gemm_tc(int M, int N, int K, const bf16 *__restrict__ A, const bf16 *__restrict__ B,
-          bf16 *C, const float *__restrict__ bias, int relu, int *err) {
+          bf16 *C, const float *__restrict__ bias, int relu, int *err, ConvGeom cg) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
+    constexpr int S = tc_stages<BN>::value;
     constexpr int STAGE = (TC_BM + BN) * TC_BK;  // bf16 elements per stage (A then B)
     bf16 *stage0 = reinterpret_cast<bf16 *>(smem_raw);
-    uint64_t *mbar = reinterpret_cast<uint64_t *>(stage0 + 2 * STAGE);  // one per stage
-    uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(mbar + 2);
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(stage0 + S * STAGE);  // one per stage
+    uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(mbar + S);
     constexpr int NCOL = BN < 32 ? 32 : BN;  // TMEM columns (power of 2)
     constexpr uint32_t LBO_A = (TC_BM / 8) * 128, LBO_B = (BN / 8) * 128;
     constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
@@ -204,8 +219,7 @@ k_gemm_tc(int M, int N, int K, const bf16 *__restrict__ A, const bf16 *__restric
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(mbar)));
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(mbar + 1)));
+        for (int st = 0; st < S; ++st) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(mbar + st)));
         asm volatile("fence.mbarrier_init.release.cluster;");
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
@@ -214,9 +228,15 @@ k_gemm_tc(int M, int N, int K, const bf16 *__restrict__ A, const bf16 *__restric
     const uint32_t tmem = *tmem_holder;
     const bool vec = (K % 8) == 0;
     const int nk = (K + TC_BK - 1) / TC_BK;
-    uint32_t phase[2] = {0u, 0u};
+    uint32_t phase[S];
+    bool pending[S];
+#pragma unroll
+    for (int st = 0; st < S; ++st) {
+        phase[st] = 0u;
+        pending[st] = false;
+    }
     bool ok = true;
-    // bounded wait on stage s's barrier (about two seconds at most)
+    // bounded wait on stage st's barrier (about two seconds at most)
     auto wait_stage = [&](int st) {
         uint32_t done = 0;
         const long long t_start = clock64();
@@ -227,38 +247,87 @@ k_gemm_tc(int M, int N, int K, const bf16 *__restrict__ A, const bf16 *__restric
         }
         if (!done) { ok = false; if (err) atomicExch(err, 1); }
         phase[st] ^= 1u;
+        pending[st] = false;
     };
-    for (int kb = 0; kb < nk && ok; ++kb) {
-        const int st = kb & 1;
-        if (kb >= 2) wait_stage(st);  // the MMAs of slice kb - 2 used this stage
-        if (!ok) break;
+    // implicit GEMM: this thread always copies chunk kg = tid % 8 of the tile rows
+    // tid / 8 + 16 i; their pixel coordinates are fixed for the whole K loop
+    int pn[8], pyx[8];
+    if constexpr (IMPLICIT) {
+        const int HW = cg.H * cg.W;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int pidx_ = m0 + (tid >> 3) + 16 * i;
+            const int nimg = pidx_ / HW, rem = pidx_ - nimg * HW, yy = rem / cg.W;
+            pn[i] = pidx_ < M ? nimg : -1;
+            pyx[i] = (yy << 16) | (rem - yy * cg.W);
+        }
+    }
+    // copies of slice kb into stage st (asynchronous when K is a multiple of 8)
+    auto load_slice = [&](int kb, int st) {
         bf16 *As = stage0 + st * STAGE, *Bs = As + TC_BM * TC_BK;
         const int k0 = kb * TC_BK;
-        for (int v = tid; v < (TC_BM + BN) * (TC_BK / 8); v += 128) {
+        if constexpr (IMPLICIT) {
+            const int kg = tid & 7, kglob = k0 + kg * 8, cin = cg.ca + cg.cb;
+            const bool kin = kglob < K;
+            const int tap = kin ? kglob / cin : 0, ci = kglob - tap * cin;
+            const int dy = tap / 3 - 1, dx = tap - (tap / 3) * 3 - 1;
+            const int Ha = cg.H / cg.ua, Wa = cg.W / cg.ua;
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const int row = (tid >> 3) + 16 * i;
+                const int yy = (pyx[i] >> 16) + dy, xx = (pyx[i] & 0xFFFF) + dx;
+                const bool in = kin && pn[i] >= 0 && yy >= 0 && yy < cg.H && xx >= 0 && xx < cg.W;
+                const bf16 *g = cg.b ? cg.b : cg.a;
+                if (in) {
+                    g = ci < cg.ca
+                            ? cg.a + (((size_t)pn[i] * Ha + yy / cg.ua) * Wa + xx / cg.ua) * cg.ca + ci
+                            : cg.b + (((size_t)pn[i] * cg.H + yy) * cg.W + xx) * cg.cb + (ci - cg.ca);
+                }
+                unsigned char *dst = reinterpret_cast<unsigned char *>(As) + kg * LBO_A + (row >> 3) * 128 +
+                                     (row & 7) * 16;
+                asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;"
+                             :: "r"(smem_u32(dst)), "l"(g), "r"(in ? 16 : 0));
+            }
+        }
+        for (int v = (IMPLICIT ? TC_BM * (TC_BK / 8) : 0) + tid; v < (TC_BM + BN) * (TC_BK / 8); v += 128) {
             const bool isA = v < TC_BM * (TC_BK / 8);
             const int vv = isA ? v : v - TC_BM * (TC_BK / 8);
             const int row = vv / (TC_BK / 8), kg = vv % (TC_BK / 8);
             const int grow = (isA ? m0 : n0) + row, gk = k0 + kg * 8;
             const int rows = isA ? M : N;
             const bf16 *src = isA ? A : B;
-            uint4 q = make_uint4(0u, 0u, 0u, 0u);
-            if (grow < rows) {
-                if (vec) {
-                    if (gk < K) q = *reinterpret_cast<const uint4 *>(src + (size_t)grow * K + gk);
-                } else {
+            const uint32_t lbo = isA ? LBO_A : LBO_B;
+            unsigned char *dst = reinterpret_cast<unsigned char *>(isA ? As : Bs) + kg * lbo +
+                                 (row >> 3) * 128 + (row & 7) * 16;
+            if (vec) {
+                const bool in = grow < rows && gk < K;
+                const bf16 *g = in ? src + (size_t)grow * K + gk : src;
+                asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;"
+                             :: "r"(smem_u32(dst)), "l"(g), "r"(in ? 16 : 0));
+            } else {
+                uint4 q = make_uint4(0u, 0u, 0u, 0u);
+                if (grow < rows) {
                     bf16 *e = reinterpret_cast<bf16 *>(&q);
                     for (int t = 0; t < 8; ++t)
                         if (gk + t < K) e[t] = src[(size_t)grow * K + gk + t];
                 }
+                *reinterpret_cast<uint4 *>(dst) = q;
             }
-            const uint32_t lbo = isA ? LBO_A : LBO_B;
-            unsigned char *dst = reinterpret_cast<unsigned char *>(isA ? As : Bs) + kg * lbo +
-                                 (row >> 3) * 128 + (row & 7) * 16;
-            *reinterpret_cast<uint4 *>(dst) = q;
         }
+    };
+    // prologue: slices 0 .. S - 2 in flight (one commit group per slice, empty ones included)
+#pragma unroll
+    for (int s0 = 0; s0 < S - 1; ++s0) {
+        if (s0 < nk) load_slice(s0, s0);
+        asm volatile("cp.async.commit_group;");
+    }
+    for (int kb = 0; kb < nk && ok; ++kb) {
+        const int st = kb % S;
+        asm volatile("cp.async.wait_group %0;" :: "n"(S - 2));  // slice kb has landed
         asm volatile("fence.proxy.async.shared::cta;");
         __syncthreads();
         if (tid == 0) {
+            bf16 *As = stage0 + st * STAGE, *Bs = As + TC_BM * TC_BK;
             asm volatile("tcgen05.fence::after_thread_sync;");
 #pragma unroll
             for (int kk = 0; kk < TC_BK / 16; ++kk) {
@@ -273,10 +342,24 @@ k_gemm_tc(int M, int N, int K, const bf16 *__restrict__ A, const bf16 *__restric
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
                          :: "r"(smem_u32(mbar + st)));
         }
+        pending[st] = true;
+        // refill the stage of slice kb - 1 with slice kb + S - 1 once its MMAs are done
+        const int nxt = kb + S - 1;
+        if (nxt < nk) {
+            const int sn = nxt % S;
+            if (pending[sn]) wait_stage(sn);
+            if (!ok) break;
+            load_slice(nxt, sn);
+        }
+        asm volatile("cp.async.commit_group;");
     }
-    // drain: the last one or two slices' MMAs (commits complete in issue order)
-    if (ok && nk >= 2) wait_stage(nk & 1);
-    if (ok && nk >= 1) wait_stage((nk - 1) & 1);
+    asm volatile("cp.async.wait_group 0;");
+    // drain: the commits still unwaited complete in issue order; wait for all of them
+    for (int i = 0; i < nk && ok; ++i) {
+        const int st = (nk - 1 - i) % S;
+        if (i >= S) break;
+        if (pending[st]) wait_stage(st);
+    }
     asm volatile("tcgen05.fence::after_thread_sync;");
     __syncthreads();
     if (ok) {

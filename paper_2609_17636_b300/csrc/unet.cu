@@ -141,26 +141,34 @@ ivis_status ensure_scratch(ivis_unet_s *u, size_t col_elems, size_t dz_elems) {
     return IVIS_OK;
 }
 
-template <int BN>
+template <int BN, bool IMPLICIT>
 void gemm_tc_launch(cudaStream_t st, int M, int N, int K, const bf16 *A, const bf16 *B, bf16 *C,
-                    const float *bias, int relu, int *err) {
+                    const float *bias, int relu, int *err, ConvGeom cg) {
     constexpr int NCOL = BN < 32 ? 32 : BN;
-    const size_t need = (size_t)2 * (TC_BM + BN) * TC_BK * sizeof(bf16) + 32;
+    const size_t need = (size_t)tc_stages<BN>::value * (TC_BM + BN) * TC_BK * sizeof(bf16) + 64;
     // keep the CTAs resident on one SM within its 512 TMEM columns
     const int allowed = 512 / NCOL;
     const size_t smem = std::max(need, (size_t)(228 * 1024) / (allowed + 1) + 1024);
-    cudaFuncSetAttribute(k_gemm_tc<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(k_gemm_tc<BN, IMPLICIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     dim3 g((M + TC_BM - 1) / TC_BM, (N + BN - 1) / BN);
-    k_gemm_tc<BN><<<g, 128, smem, st>>>(M, N, K, A, B, C, bias, relu, err);
+    k_gemm_tc<BN, IMPLICIT><<<g, 128, smem, st>>>(M, N, K, A, B, C, bias, relu, err, cg);
+}
+
+// cg.a == nullptr: explicit A (an im2col matrix); otherwise A is gathered from cg.
+template <bool IMPLICIT>
+void gemm_tc_n(cudaStream_t st, int M, int N, int K, const bf16 *A, const bf16 *B, bf16 *C,
+               const float *bias, int relu, int *err, ConvGeom cg) {
+    if (N <= 16) gemm_tc_launch<16, IMPLICIT>(st, M, N, K, A, B, C, bias, relu, err, cg);
+    else if (N <= 32) gemm_tc_launch<32, IMPLICIT>(st, M, N, K, A, B, C, bias, relu, err, cg);
+    else if (N <= 64) gemm_tc_launch<64, IMPLICIT>(st, M, N, K, A, B, C, bias, relu, err, cg);
+    else if (N <= 128) gemm_tc_launch<128, IMPLICIT>(st, M, N, K, A, B, C, bias, relu, err, cg);
+    else gemm_tc_launch<256, IMPLICIT>(st, M, N, K, A, B, C, bias, relu, err, cg);
 }
 
 void gemm_tc(cudaStream_t st, int M, int N, int K, const bf16 *A, const bf16 *B, bf16 *C,
-             const float *bias, int relu, int *err) {
-    if (N <= 16) gemm_tc_launch<16>(st, M, N, K, A, B, C, bias, relu, err);
-    else if (N <= 32) gemm_tc_launch<32>(st, M, N, K, A, B, C, bias, relu, err);
-    else if (N <= 64) gemm_tc_launch<64>(st, M, N, K, A, B, C, bias, relu, err);
-    else if (N <= 128) gemm_tc_launch<128>(st, M, N, K, A, B, C, bias, relu, err);
-    else gemm_tc_launch<256>(st, M, N, K, A, B, C, bias, relu, err);
+             const float *bias, int relu, int *err, ConvGeom cg = ConvGeom{}) {
+    if (cg.a) gemm_tc_n<true>(st, M, N, K, A, B, C, bias, relu, err, cg);
+    else gemm_tc_n<false>(st, M, N, K, A, B, C, bias, relu, err, cg);
 }
 
 void gemm(cudaStream_t st, int ta, int tb, int epi, int M, int N, int K, const bf16 *A, const bf16 *B,
@@ -193,12 +201,18 @@ ivis_status forward_impl(ivis_unet_s *u, const float *in_dev, int B, int H, int 
         const int h = H >> s.level, w = W >> s.level;
         const size_t P = (size_t)B * h * w;
         const int K = 9 * (s.ca + s.cb);
-        k_im2col<<<nblk(P * K), 256, 0, st>>>(B, h, w, u->act[s.src_a], s.ca, s.ua,
-                                               s.src_b >= 0 ? u->act[s.src_b] : nullptr, s.cb, u->col);
-        if (u->use_tc)
-            gemm_tc(st, (int)P, s.cout, K, u->col, u->wb + s.w_off, u->act[s.out], u->w + s.b_off, 1, u->tc_err);
-        else
-            gemm(st, 0, 1, 0, (int)P, s.cout, K, u->col, u->wb + s.w_off, u->act[s.out], u->w + s.b_off, 1);
+        const bf16 *srcb = s.src_b >= 0 ? u->act[s.src_b] : nullptr;
+        if (u->use_tc && s.ca % 8 == 0 && s.cb % 8 == 0 && h < 32768 && w < 32768) {
+            // implicit GEMM: the 3x3 gather happens in the operand copies
+            gemm_tc(st, (int)P, s.cout, K, nullptr, u->wb + s.w_off, u->act[s.out], u->w + s.b_off, 1, u->tc_err,
+                    ConvGeom{u->act[s.src_a], srcb, s.ca, s.ua, s.cb, h, w});
+        } else {
+            k_im2col<<<nblk(P * K), 256, 0, st>>>(B, h, w, u->act[s.src_a], s.ca, s.ua, srcb, s.cb, u->col);
+            if (u->use_tc)
+                gemm_tc(st, (int)P, s.cout, K, u->col, u->wb + s.w_off, u->act[s.out], u->w + s.b_off, 1, u->tc_err);
+            else
+                gemm(st, 0, 1, 0, (int)P, s.cout, K, u->col, u->wb + s.w_off, u->act[s.out], u->w + s.b_off, 1);
+        }
         // pooling after the second convolution of each encoder level
         if (s.out == T_A1 || s.out == T_A3 || s.out == T_A5) {
             const int pid = s.out == T_A1 ? T_P0 : (s.out == T_A3 ? T_P1 : T_P2);

@@ -42,9 +42,11 @@ def c2():
 
 
 def test_fullsize_cost_terms_gradient_samples_and_visibilities(c2):
+    """In the bench's launch configuration: FP32 plan with the autotuner's chunk size and
+    column width, evaluation through the captured graph."""
     from paper_2609_17636_b300 import plan_from_problem
     prob, x = c2
-    plan = plan_from_problem(prob, "fp32")
+    plan = plan_from_problem(prob, "fp32", autotune=True)
     xs = torch.as_tensor(x, dtype=torch.float32, device="cuda")
     f, g, (Q, K, R) = plan.cost_grad(xs)
     g = g.cpu().numpy()

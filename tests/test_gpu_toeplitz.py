@@ -158,7 +158,7 @@ def test_toeplitz_fullsize_sampled_parity():
     prob.sigma_sd = np.array([0.05 * np.sqrt(np.mean(t ** 2))])
     prob.tsd = (t + prob.sd_noise_unit * prob.sigma_sd[0]).astype(np.float32)
     x = sparse(40)
-    plan = plan_from_problem(prob, "fp32", toeplitz=True)
+    plan = plan_from_problem(prob, "fp32", toeplitz=True, autotune=True)
     xs = torch.as_tensor(x, dtype=torch.float32, device="cuda")
     f, g, (Q, K, R) = plan.cost_grad(xs)
     g = g.cpu().numpy()

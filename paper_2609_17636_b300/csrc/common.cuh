@@ -67,6 +67,21 @@ __device__ __forceinline__ double block_sum(double v, double *scratch) {
     return s;  // valid in thread 0
 }
 
+// Block sum of per-thread float terms: FP32 within each warp (5 pairwise levels), FP64 across
+// the warps by one thread (FP64 issue is scarce on this part). Fixed order; valid in thread 0.
+__device__ __forceinline__ double block_sum_warpf(float v, double *scratch) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    __syncthreads();
+    if (lane == 0) scratch[wid] = (double)v;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < nw; ++w) s += scratch[w];
+    return s;
+}
+
 __device__ __forceinline__ void atomic_add_c(float2 *p, float2 v) {
     atomicAdd(&p->x, v.x);
     atomicAdd(&p->y, v.y);

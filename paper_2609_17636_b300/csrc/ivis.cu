@@ -642,7 +642,7 @@ cudaError_t enqueue_eval(ivis_plan_s *p, bool capture) {
     }
     stage_end(p, p->stream, si);
     stage_begin(p, "finalize", p->stream, si);
-    k_finalize<<<1, 1024, 0, p->stream>>>(p->jpart, (p->cfg.toeplitz || p->cfg.wterm) ? p->njpart : p->nchunk, p->kpart,
+    k_finalize<<<FIN_BLOCKS, 256, 0, p->stream>>>(p->jpart, (p->cfg.toeplitz || p->cfg.wterm) ? p->njpart : p->nchunk, p->kpart,
                                          use_k ? p->nkpart : 0,
                                          p->rpart, use_r ? p->nrpart : 0, p->cfg.lambda_r,
                                          p->cfg.lambda_s, p->cost_d);
@@ -1281,7 +1281,8 @@ ivis_status prepare_impl(ivis_plan_s *p) {
     if ((s = alloc(p, (void **)&p->jpart, njp * sizeof(double)))) return s;
     p->nrpart = (int)((npix + 255) / 256);
     if ((s = alloc(p, (void **)&p->rpart, (size_t)p->nrpart * sizeof(double)))) return s;
-    if ((s = alloc(p, (void **)&p->cost_d, 4 * sizeof(double)))) return s;
+    if ((s = alloc(p, (void **)&p->cost_d, FIN_WORDS * sizeof(double)))) return s;
+    CK(cudaMemset(p->cost_d, 0, FIN_WORDS * sizeof(double)));  // the reduction's ticket starts at 0
     // single dish: taps with a common half-width, per-channel 1/sigma^2
     bool need_sd = false;
     for (int ch = 0; ch < c.nchan; ++ch) need_sd |= (bool)p->sdset[ch];

@@ -179,28 +179,26 @@ k_conv_axis(const T *__restrict__ in, T *out, const T *__restrict__ taps, int R,
     }
 }
 
-// This thread's share of sum(v[0..n)): elements threadIdx.x + i * blockDim.x, eight
-// independent loads in flight per step, combined in a fixed order.
-__device__ __forceinline__ double strided_sum(const double *__restrict__ v, int n) {
-    double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    const int B = blockDim.x;
-    for (int i0 = threadIdx.x; i0 < n; i0 += 8 * B) {
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            const int i = i0 + u * B;
-            acc[u] += i < n ? __ldcg(v + i) : 0.0;
-        }
-    }
-    return ((acc[0] + acc[1]) + (acc[2] + acc[3])) + ((acc[4] + acc[5]) + (acc[6] + acc[7]));
-}
+// out[0..3] = {Q_tot, Q, K, R} from the FP64 partials. FP64 issue is scarce on this part (a
+// few lanes per clock per SM), so the sums are spread over FIN_BLOCKS CTAs: each CTA adds its
+// grid-strided share of the three partial arrays and writes three block sums to out[4..];
+// the last CTA to finish (atomic ticket in the word after them, reset for the next call)
+// adds the block sums in index order. Fixed summation order for a fixed launch shape.
+constexpr int FIN_BLOCKS = 32;
+constexpr int FIN_WORDS = 4 + 3 * FIN_BLOCKS + 1;  // doubles of the cost record incl. scratch
 
-// out = {Q_tot, Q, K, R}; fixed summation order (deterministic for a fixed launch shape). The
-// three sums run interleaved (FP64 latency is long on this part: independent chains overlap).
-__global__ void k_finalize(const double *__restrict__ jpart, int nj, const double *__restrict__ kpart,
-                           int nk, const double *__restrict__ rpart, int nr, double lr, double ls,
-                           double *out) {
+__global__ void __launch_bounds__(256)
+k_finalize(const double *__restrict__ jpart, int nj, const double *__restrict__ kpart, int nk,
+           const double *__restrict__ rpart, int nr, double lr, double ls, double *out) {
     __shared__ double red[3][32];
-    double v[3] = {strided_sum(jpart, nj), strided_sum(kpart, nk), strided_sum(rpart, nr)};
+    __shared__ int last;
+    double *bp = out + 4;
+    unsigned *ticket = reinterpret_cast<unsigned *>(out + 4 + 3 * FIN_BLOCKS);
+    const int G = gridDim.x * blockDim.x, gt = blockIdx.x * blockDim.x + threadIdx.x;
+    double v[3] = {0.0, 0.0, 0.0};
+    for (int i = gt; i < nj; i += G) v[0] += __ldcg(jpart + i);
+    for (int i = gt; i < nk; i += G) v[1] += __ldcg(kpart + i);
+    for (int i = gt; i < nr; i += G) v[2] += __ldcg(rpart + i);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1)
 #pragma unroll
@@ -218,11 +216,27 @@ __global__ void k_finalize(const double *__restrict__ jpart, int nj, const doubl
 #pragma unroll
             for (int a = 0; a < 3; ++a) v[a] += __shfl_xor_sync(0xffffffffu, v[a], o);
         if (lane == 0) {
-            out[1] = v[0];
-            out[2] = v[1];
-            out[3] = v[2];
-            out[0] = v[0] + ls * v[1] + lr * v[2];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) bp[3 * blockIdx.x + a] = v[a];
+            __threadfence();
+            last = atomicAdd(ticket, 1u) == gridDim.x - 1;
         }
+    }
+    __syncthreads();
+    if (!last || wid != 0) return;
+    __threadfence();
+#pragma unroll
+    for (int a = 0; a < 3; ++a) v[a] = lane < (int)gridDim.x ? __ldcg(bp + 3 * lane + a) : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) v[a] += __shfl_xor_sync(0xffffffffu, v[a], o);
+    if (lane == 0) {
+        out[1] = v[0];
+        out[2] = v[1];
+        out[3] = v[2];
+        out[0] = v[0] + ls * v[1] + lr * v[2];
+        *ticket = 0u;
     }
 }
 

@@ -528,7 +528,9 @@ k_grid_pass(const Chunk *__restrict__ chunks, const PairData<T> *__restrict__ pd
         }
     }
     if (MODE == MODE_COSTGRAD) {
-        const double js = block_sum((double)jacc, red);
+        double js;
+        if constexpr (sizeof(T) == 4) js = block_sum_warpf(jacc, red);  // <= 4 lanes per warp carry terms
+        else js = block_sum((double)jacc, red);
         if (threadIdx.x == 0) jpart[blockIdx.x] = js;
     }
     __syncthreads();

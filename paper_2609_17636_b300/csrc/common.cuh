@@ -82,6 +82,11 @@ __device__ __forceinline__ double block_sum_warpf(float v, double *scratch) {
     return s;
 }
 
+// Block sum in the working precision's scheme: FP32 terms summed per warp in FP32 then in
+// FP64 across warps; FP64 terms in FP64 throughout.
+__device__ __forceinline__ double block_sum_t(float v, double *scratch) { return block_sum_warpf(v, scratch); }
+__device__ __forceinline__ double block_sum_t(double v, double *scratch) { return block_sum(v, scratch); }
+
 __device__ __forceinline__ void atomic_add_c(float2 *p, float2 v) {
     atomicAdd(&p->x, v.x);
     atomicAdd(&p->y, v.y);

@@ -32,7 +32,7 @@ k_assemble(const T *__restrict__ sky, const T *__restrict__ contrib,
     __shared__ double red[32];
     const size_t npix = (size_t)n * n;
     const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    double rloc = 0.0;
+    T rloc = (T)0;
     if (idx < npix * nchan) {
         const int chan = (int)(idx / npix);
         const int rem = (int)(idx - (size_t)chan * npix);
@@ -55,12 +55,12 @@ k_assemble(const T *__restrict__ sky, const T *__restrict__ contrib,
             if (x > 0) gr -= lap(I, n, y, x - 1);
             if (x < n - 1) gr -= lap(I, n, y, x + 1);
             g += lr * gr;
-            rloc = (double)((T)0.5 * d0 * d0);
+            rloc = (T)0.5 * d0 * d0;
         }
         if (use_k) g += ls * gradK[idx];
         grad[idx] = g;
     }
-    const double s = block_sum(rloc, red);
+    const double s = block_sum_t(rloc, red);
     if (threadIdx.x == 0) rpart[blockIdx.x] = s;
 }
 

@@ -257,7 +257,7 @@ k_toep_rows_pk(const typename cplx_of<T>::type *__restrict__ rowbuf, const T *__
     }
     __syncthreads();
     line_fft<C, +1>(s, 1, l * nf, lognf, j0, tw);
-    double acc_a = 0.0, acc_b = 0.0;
+    T acc_a = (T)0, acc_b = (T)0;  // nb / tpl terms per thread in the working precision
     if (q < nb) {
         const int ya = pa.cy - nb / 2 + q, yb = pb.cy - nb / 2 + q;
         const bool ona = pa.gridded || (ya >= 0 && ya < n), onb = hasb && (pb.gridded || (yb >= 0 && yb < n));
@@ -269,20 +269,20 @@ k_toep_rows_pk(const typename cplx_of<T>::type *__restrict__ rowbuf, const T *__
             if (ona) {
                 const T z = window_value(pa, q, p, sky, beams, ones, grids, n, nb);
                 oa[p] = ba[p] * (v.x - wa[p]);
-                acc_a += (double)z * ((double)v.x * 0.5 - (double)wa[p]);
+                acc_a += z * (v.x * (T)0.5 - wa[p]);
             }
             if (onb) {
                 const T z = window_value(pb, q, p, sky, beams, ones, grids, n, nb);
                 ob[p] = bb[p] * (v.y - wb[p]);
-                acc_b += (double)z * ((double)v.y * 0.5 - (double)wb[p]);
+                acc_b += z * (v.y * (T)0.5 - wb[p]);
             }
         }
     }
-    acc_a = block_sum(acc_a, red);
-    if (threadIdx.x == 0) jpart[(size_t)sa * gridDim.x + blockIdx.x] = acc_a + (blockIdx.x == 0 ? qconst[sa] : 0.0);
+    const double sa_ = block_sum_t(acc_a, red);
+    if (threadIdx.x == 0) jpart[(size_t)sa * gridDim.x + blockIdx.x] = sa_ + (blockIdx.x == 0 ? qconst[sa] : 0.0);
     __syncthreads();
-    acc_b = block_sum(acc_b, red);
-    if (hasb && threadIdx.x == 0) jpart[(size_t)sb * gridDim.x + blockIdx.x] = acc_b + (blockIdx.x == 0 ? qconst[sb] : 0.0);
+    const double sb_ = block_sum_t(acc_b, red);
+    if (hasb && threadIdx.x == 0) jpart[(size_t)sb * gridDim.x + blockIdx.x] = sb_ + (blockIdx.x == 0 ? qconst[sb] : 0.0);
 }
 
 }  // namespace ivis

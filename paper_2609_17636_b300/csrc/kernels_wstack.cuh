@@ -119,7 +119,7 @@ k_w_residual(const WPair<T> *__restrict__ wpairs, int W, const typename cplx_of<
     __shared__ double red[32];
     const WPair<T> wp = wpairs[blockIdx.y];
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    double jacc = 0.0;
+    T jacc = (T)0;
     if (j < wp.m) {
         const C *pj = pv + wp.pv_off + (size_t)j * W;
         const T *kj = wp.wk + (size_t)j * W;
@@ -137,15 +137,15 @@ k_w_residual(const WPair<T> *__restrict__ wpairs, int W, const typename cplx_of<
             const C V = wp.V[j];
             const T w = wp.w[j];
             const C r = mk(vt.x - V.x, vt.y - V.y);
-            jacc = 0.5 * (double)w * ((double)r.x * r.x + (double)r.y * r.y);
+            jacc = (T)0.5 * w * (r.x * r.x + r.y * r.y);
             const C c = cmulc(mk(w * r.x, w * r.y), wp.phase[j]);
             const int *ej = wp.epos + (size_t)j * W;
             for (int t = 0; t < W; ++t) wp.ent_val[ej[t]] = c;
         }
     }
     if (PREDICT) return;
-    jacc = block_sum(jacc, red);
-    if (threadIdx.x == 0) jpart[(size_t)blockIdx.y * gridDim.x + blockIdx.x] = jacc;
+    const double js = block_sum_t(jacc, red);
+    if (threadIdx.x == 0) jpart[(size_t)blockIdx.y * gridDim.x + blockIdx.x] = js;
 }
 
 }  // namespace ivis

@@ -1403,7 +1403,7 @@ ivis_status solve_impl(ivis_plan_s *p, void *sky_dev, int maxiter, int m_hist, d
         ord.m = (int)order.size();
         for (int t = 0; t < ord.m; ++t) ord.slot[t] = order[t];
         k_sol_dots<T><<<nb, 256, 0, p->stream>>>(n, xk, gk, pos, S, Y, ord, stride, B.part);
-        k_sol_small<<<1, 128, 0, p->stream>>>(B.nblk, stride, B.part, ord, B.SY, B.YY, B.mcap, B.coef, B.scal);
+        k_sol_small<<<1, 1024, 0, p->stream>>>(B.nblk, stride, B.part, ord, B.SY, B.YY, B.mcap, B.coef, B.scal);
         k_sol_dir<T><<<nb, 256, 0, p->stream>>>(n, xk, gk, pos, S, Y, ord, B.coef, B.scal, d, stride, B.part);
         k_sol_sum<<<1, 256, 0, p->stream>>>(B.nblk, stride, B.part, B.scal, 1);
         CK(cudaGetLastError());
@@ -1465,7 +1465,7 @@ ivis_status solve_impl(ivis_plan_s *p, void *sky_dev, int maxiter, int m_hist, d
         for (size_t t = 0; t < order.size(); ++t) ou.slot[t] = order[t];
         ou.slot[ou.m - 1] = slot;
         k_sol_update<T><<<nb, 256, 0, p->stream>>>(n, x, g, xk, gk, S, Y, slot, ou, stride, B.part);
-        k_sol_update_small<<<1, 128, 0, p->stream>>>(B.nblk, stride, B.part, slot, ou, B.SY, B.YY,
+        k_sol_update_small<<<1, 1024, 0, p->stream>>>(B.nblk, stride, B.part, slot, ou, B.SY, B.YY,
                                                      B.mcap, 2.2e-16, B.scal);
         CK(cudaGetLastError());
         CK(cudaMemcpyAsync(B.scal_h + 5, B.scal + 5, sizeof(double), cudaMemcpyDeviceToHost, p->stream));

@@ -118,16 +118,18 @@ k_sol_dots(size_t n, const T *__restrict__ x, const T *__restrict__ g, int pos,
     __shared__ T gf[SOL_CHUNK];
     __shared__ double red[32];
     const size_t base = (size_t)blockIdx.x * SOL_CHUNK;
-    double gg = 0.0, pg = 0.0;
+    // per-thread terms (SOL_CHUNK / blockDim of them) in the working precision; FP64 from the
+    // warp partials on (block_sum_t)
+    T gg = (T)0, pg = (T)0;
     for (int i = threadIdx.x; i < SOL_CHUNK; i += blockDim.x) {
         const size_t idx = base + i;
         T v = (T)0;
         if (idx < n) {
             const T xi = x[idx], gi = g[idx];
             v = is_free(xi, gi, pos) ? gi : (T)0;
-            const double pgi = pos ? fabs(fmax((double)xi - (double)gi, 0.0) - (double)xi) : fabs((double)gi);
+            const T pgi = pos ? fabs(fmax(xi - gi, (T)0) - xi) : fabs(gi);
             pg = fmax(pg, pgi);
-            gg += (double)v * (double)v;
+            gg += v * v;
         }
         gf[i] = v;
     }
@@ -135,18 +137,18 @@ k_sol_dots(size_t n, const T *__restrict__ x, const T *__restrict__ g, int pos,
     double *out = part + (size_t)blockIdx.x * stride;
     for (int t = 0; t < 2 * ord.m; ++t) {
         const T *vec = (t < ord.m ? S : Y) + (size_t)ord.slot[t < ord.m ? t : t - ord.m] * n;
-        double acc = 0.0;
+        T acc = (T)0;
         for (int i = threadIdx.x; i < SOL_CHUNK; i += blockDim.x) {
             const size_t idx = base + i;
-            if (idx < n) acc += (double)vec[idx] * (double)gf[i];
+            if (idx < n) acc += vec[idx] * gf[i];
         }
-        acc = block_sum(acc, red);
-        if (threadIdx.x == 0) out[t] = acc;
+        const double sum = block_sum_t(acc, red);
+        if (threadIdx.x == 0) out[t] = sum;
     }
-    gg = block_sum(gg, red);
-    if (threadIdx.x == 0) out[2 * ord.m] = gg;
-    pg = block_max(pg, red);
-    if (threadIdx.x == 0) out[2 * ord.m + 1] = pg;
+    const double ggs = block_sum_t(gg, red);
+    if (threadIdx.x == 0) out[2 * ord.m] = ggs;
+    const double pgm = block_max((double)pg, red);
+    if (threadIdx.x == 0) out[2 * ord.m + 1] = pgm;
 }
 
 // Sum the per-CTA partials (fixed order) and form the compact-representation coefficients.
@@ -156,14 +158,21 @@ __global__ void k_sol_small(int nblk, int stride, const double *__restrict__ par
                             double *coef, double *scal) {
     __shared__ double sums[2 * SOL_MAXM + 2];
     const int nd = 2 * ord.m + 2;
-    for (int t = threadIdx.x; t < nd; t += blockDim.x) {
+    // one warp per sum: lanes stride over the CTA partials, then a fixed shuffle tree
+    const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int t = threadIdx.x >> 5; t < nd; t += nw) {
+        const bool mx = t == 2 * ord.m + 1;
         double acc = 0.0;
-        if (t == 2 * ord.m + 1) {
-            for (int b = 0; b < nblk; ++b) acc = fmax(acc, part[(size_t)b * stride + t]);
-        } else {
-            for (int b = 0; b < nblk; ++b) acc += part[(size_t)b * stride + t];
+        for (int b = lane; b < nblk; b += 32) {
+            const double v = part[(size_t)b * stride + t];
+            acc = mx ? fmax(acc, v) : acc + v;
         }
-        sums[t] = acc;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const double u = __shfl_xor_sync(0xffffffffu, acc, o);
+            acc = mx ? fmax(acc, u) : acc + u;
+        }
+        if (lane == 0) sums[t] = acc;
     }
     __syncthreads();
     if (threadIdx.x != 0) return;
@@ -206,27 +215,30 @@ k_sol_dir(size_t n, const T *__restrict__ x, const T *__restrict__ g, int pos,
           const double *__restrict__ coef, const double *__restrict__ scal, T *d, int stride,
           double *part) {
     __shared__ double red[32];
+    __shared__ T cf[2 * SOL_MAXM];
     const size_t base = (size_t)blockIdx.x * SOL_CHUNK;
-    const double gamma = ord.m ? scal[0] : 1.0;
-    double gd = 0.0;
+    const T gamma = ord.m ? (T)scal[0] : (T)1;
+    for (int t = threadIdx.x; t < 2 * ord.m; t += blockDim.x) cf[t] = (T)coef[t];
+    __syncthreads();
+    T gd = (T)0;  // d is stored in the working precision; so is its per-pixel arithmetic
     for (int i = threadIdx.x; i < SOL_CHUNK; i += blockDim.x) {
         const size_t idx = base + i;
         if (idx >= n) continue;
         const T xi = x[idx], gi = g[idx];
-        double dv = 0.0;
+        T dv = (T)0;
         if (is_free(xi, gi, pos)) {
-            double acc = gamma * (double)gi;
+            T acc = gamma * gi;
             for (int t = 0; t < ord.m; ++t) {
-                acc += coef[t] * (double)S[(size_t)ord.slot[t] * n + idx];
-                acc += coef[ord.m + t] * (double)Y[(size_t)ord.slot[t] * n + idx];
+                acc += cf[t] * S[(size_t)ord.slot[t] * n + idx];
+                acc += cf[ord.m + t] * Y[(size_t)ord.slot[t] * n + idx];
             }
             dv = -acc;
         }
-        d[idx] = (T)dv;
-        gd += (double)gi * dv;
+        d[idx] = dv;
+        gd += gi * dv;
     }
-    gd = block_sum(gd, red);
-    if (threadIdx.x == 0) part[(size_t)blockIdx.x * stride] = gd;
+    const double gds = block_sum_t(gd, red);
+    if (threadIdx.x == 0) part[(size_t)blockIdx.x * stride] = gds;
 }
 
 // scal[slot_out] = sum of part[b * stride] over CTAs (fixed order).
@@ -246,18 +258,19 @@ k_sol_trial(size_t n, const T *__restrict__ xk, const T *__restrict__ gk, const 
             double alpha, int pos, T *x, int stride, double *part) {
     __shared__ double red[32];
     const size_t base = (size_t)blockIdx.x * SOL_CHUNK;
-    double acc = 0.0;
+    const T al = (T)alpha;
+    T acc = (T)0;
     for (int i = threadIdx.x; i < SOL_CHUNK; i += blockDim.x) {
         const size_t idx = base + i;
         if (idx >= n) continue;
-        double v = (double)xk[idx] + alpha * (double)d[idx];
-        if (pos && v < 0.0) v = 0.0;
-        const T vt = (T)v;
-        x[idx] = vt;
-        acc += (double)gk[idx] * ((double)vt - (double)xk[idx]);
+        const T xo = xk[idx];
+        T v = xo + al * d[idx];
+        if (pos && v < (T)0) v = (T)0;
+        x[idx] = v;
+        acc += gk[idx] * (v - xo);
     }
-    acc = block_sum(acc, red);
-    if (threadIdx.x == 0) part[(size_t)blockIdx.x * stride] = acc;
+    const double sum = block_sum_t(acc, red);
+    if (threadIdx.x == 0) part[(size_t)blockIdx.x * stride] = sum;
 }
 
 // New correction pair into slot `slot`: s = x - xk, y = g - gk; xk <- x, gk <- g. Per CTA
@@ -288,23 +301,23 @@ k_sol_update(size_t n, const T *__restrict__ x, const T *__restrict__ g, T *xk, 
     double *out = part + (size_t)blockIdx.x * stride;
     for (int t = 0; t < ord.m; ++t) {
         const int st = ord.slot[t];
-        double a = 0.0, b = 0.0, c = 0.0;
+        T a = (T)0, b = (T)0, c = (T)0;
         for (int i = threadIdx.x; i < SOL_CHUNK; i += blockDim.x) {
             const size_t idx = base + i;
             if (idx >= n) continue;
-            const double ys = st == slot ? (double)yv[i] : (double)Y[(size_t)st * n + idx];
-            const double ss = st == slot ? (double)sv[i] : (double)S[(size_t)st * n + idx];
-            a += (double)sv[i] * ys;
-            b += ss * (double)yv[i];
-            c += (double)yv[i] * ys;
+            const T ys = st == slot ? yv[i] : Y[(size_t)st * n + idx];
+            const T ss = st == slot ? sv[i] : S[(size_t)st * n + idx];
+            a += sv[i] * ys;
+            b += ss * yv[i];
+            c += yv[i] * ys;
         }
-        a = block_sum(a, red);
-        b = block_sum(b, red);
-        c = block_sum(c, red);
+        const double as = block_sum_t(a, red);
+        const double bs = block_sum_t(b, red);
+        const double cs = block_sum_t(c, red);
         if (threadIdx.x == 0) {
-            out[3 * t] = a;
-            out[3 * t + 1] = b;
-            out[3 * t + 2] = c;
+            out[3 * t] = as;
+            out[3 * t + 1] = bs;
+            out[3 * t + 2] = cs;
         }
     }
 }
@@ -316,10 +329,13 @@ __global__ void k_sol_update_small(int nblk, int stride, const double *__restric
                                    double eps, double *scal) {
     __shared__ double sums[3 * SOL_MAXM];
     const int nd = 3 * ord.m;
-    for (int t = threadIdx.x; t < nd; t += blockDim.x) {
+    const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int t = threadIdx.x >> 5; t < nd; t += nw) {  // one warp per sum, fixed order
         double acc = 0.0;
-        for (int b = 0; b < nblk; ++b) acc += part[(size_t)b * stride + t];
-        sums[t] = acc;
+        for (int b = lane; b < nblk; b += 32) acc += part[(size_t)b * stride + t];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) sums[t] = acc;
     }
     __syncthreads();
     if (threadIdx.x != 0) return;

@@ -1426,11 +1426,13 @@ ivis_status solve_impl(ivis_plan_s *p, void *sky_dev, int maxiter, int m_hist, d
             k_sol_trial<T><<<nb, 256, 0, p->stream>>>(n, xk, gk, d, alpha, pos, x, stride, B.part);
             k_sol_sum<<<1, 256, 0, p->stream>>>(B.nblk, stride, B.part, B.scal, 4);
             CK(cudaGetLastError());
-            ivis_status es = run_eval(p);
+            // one host wait per trial: the evaluation and the trial's g.(x - xk) together
+            ivis_status es = launch_eval(p, false);
             ++evals;
-            if (es && es != IVIS_ERR_NONFINITE) return es;
+            if (es) return es;
             CK(cudaMemcpyAsync(B.scal_h + 4, B.scal + 4, sizeof(double), cudaMemcpyDeviceToHost, p->stream));
             CK(cudaStreamSynchronize(p->stream));
+            if (!std::isfinite(p->cost_h[0])) es = IVIS_ERR_NONFINITE;
             fnew = p->cost_h[0];
             const double dd = B.scal_h[4];
             if (es == IVIS_OK && fnew <= f + c1 * dd && dd <= 0.0) { accepted = true; break; }

@@ -104,96 +104,7 @@ __global__ void k_unit_vis(int m, float2 *v) {
     if (j < m) v[j] = make_float2(1.0f, 0.0f);
 }
 
-// ----------------------------------------------------------------------- per evaluation
-// Column pass: DFT along y of the row-transformed window, multiply by That, inverse DFT along
-// y, keep the nb window rows (in place in rowbuf).
-template <typename T>
-__global__ void __launch_bounds__(sizeof(T) == 8 ? 512 : 1024)
-k_toep_cols(typename cplx_of<T>::type *rowbuf, const T *const *__restrict__ that_ptr, int nb,
-            int lognf, int logc, const typename cplx_of<T>::type *__restrict__ tw) {
-    typedef typename cplx_of<T>::type C;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    C *s = reinterpret_cast<C *>(smem_raw);
-    const int nf = 1 << lognf, ncol = 1 << logc, tpl = nf >> 4;
-    const int c0 = blockIdx.x << logc, slot = blockIdx.y;
-    const int c = threadIdx.x & (ncol - 1), j0 = threadIdx.x >> logc;
-    for (int e = j0; e < nf; e += tpl) s[pidx((e << logc) + c)] = mk((T)0, (T)0);
-    __syncthreads();
-    C *buf = rowbuf + (size_t)slot * nb * nf;
-    for (int q = j0; q < nb; q += tpl) {
-        const int idx = (q - nb / 2) & (nf - 1);
-        s[pidx((idx << logc) + c)] = buf[(size_t)q * nf + c0 + c];
-    }
-    __syncthreads();
-    line_fft<C, -1>(s, ncol, c, lognf, j0, tw);
-    const T *th = that_ptr[slot] + (size_t)c0 * nf;
-    for (int idx = threadIdx.x; idx < (nf << logc); idx += blockDim.x) {
-        const int cc = idx >> lognf, e = idx & (nf - 1);
-        const T t = th[idx];
-        C &v = s[pidx((e << logc) + cc)];
-        v = mk(v.x * t, v.y * t);
-    }
-    __syncthreads();
-    line_fft<C, +1>(s, ncol, c, lognf, j0, tw);
-    for (int q = j0; q < nb; q += tpl) {
-        const int idx = (q - nb / 2) & (nf - 1);
-        buf[(size_t)q * nf + c0 + c] = s[pidx((idx << logc) + c)];
-    }
-}
-
-// Row pass: inverse DFT along x, then per window pixel y = (Re H z)(p):
-//   contrib = A (y - b)                       (window gradient times the beam)
-//   partial += z (y/2 - b),  z = A * (P x)    (the pair's data term minus its constant C)
-// jpart gets one FP64 partial per CTA: index slot * gridDim.x + blockIdx.x; the first CTA of
-// a slot adds the pair's constant C.
-template <typename T>
-__global__ void __launch_bounds__(256)
-k_toep_rows(const typename cplx_of<T>::type *__restrict__ rowbuf, const T *__restrict__ sky,
-            const T *__restrict__ beams, const PairInfo *__restrict__ pinfo,
-            const T *const *__restrict__ bwin_ptr, const double *__restrict__ qconst, T *contrib,
-            double *jpart, int n, int nb, int lognf,
-            const typename cplx_of<T>::type *__restrict__ tw, const float2 *__restrict__ grids) {
-    typedef typename cplx_of<T>::type C;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    C *s = reinterpret_cast<C *>(smem_raw);
-    __shared__ double red[32];
-    const int nf = 1 << lognf, tpl = nf >> 4, lpb = blockDim.x / tpl;
-    const int slot = blockIdx.y;
-    const PairInfo pi = pinfo[slot];
-    const int l = threadIdx.x / tpl, j0 = threadIdx.x - l * tpl;
-    const int q = blockIdx.x * lpb + l;
-    const int y = pi.cy - nb / 2 + q;
-    const bool on = q < nb && (pi.gridded || (y >= 0 && y < n));
-    if (on) {
-        const C *src = rowbuf + ((size_t)slot * nb + q) * nf;
-        for (int e = j0; e < nf; e += tpl) s[pidx(l * nf + e)] = src[e];
-    }
-    __syncthreads();
-    line_fft<C, +1>(s, 1, l * nf, lognf, j0, tw);
-    double acc = 0.0;
-    if (on) {
-        const T *brow = beams + ((size_t)pi.k * nb + q) * nb;
-        const T *bw = bwin_ptr[slot] + (size_t)q * nb;
-        const T *img = sky + (size_t)pi.chan * n * n;
-        T *out = contrib + ((size_t)slot * nb + q) * nb;
-        const int x0 = pi.cx - nb / 2;
-        for (int p = j0; p < nb; p += tpl) {
-            const T yv = s[pidx(l * nf + ((p - nb / 2) & (nf - 1)))].x;
-            const T a = brow[p], bv = bw[p];
-            T xv;
-            if (pi.gridded) {
-                const float2 g = grids[((size_t)pi.k * nb + q) * nb + p];
-                xv = bilerp(img, n, g.x, g.y);
-            } else {
-                const int x = x0 + p;
-                xv = (x >= 0 && x < n) ? img[(size_t)y * n + x] : (T)0;
-            }
-            out[p] = a * (yv - bv);
-            acc += (double)(a * xv) * ((double)yv * 0.5 - (double)bv);
-        }
-    }
-    acc = block_sum(acc, red);
-    if (threadIdx.x == 0) jpart[(size_t)slot * gridDim.x + blockIdx.x] = acc + (blockIdx.x == 0 ? qconst[slot] : 0.0);
-}
+// The per-evaluation passes (two slots per transform) are k_fwd_rows_pk, k_toep_cols_pk and
+// k_toep_rows_pk in kernels_packed.cuh.
 
 }  // namespace ivis

@@ -444,25 +444,27 @@ k_grid_pass(const Chunk *__restrict__ chunks, const PairData<T> *__restrict__ pd
             if (clx >= 0 && active_row) {
                 C *gr = Gs + (cly + r) * PW + clx;
                 // same kernel-row band, first tap d cells further right (the sort makes d >= 0):
-                // only the d leftmost cells of the held row are final; the rest slide along
+                // only the d leftmost cells of the held row are final. For the common steps of
+                // one or two cells those are added and the rest slides along; otherwise the
+                // whole row is added (adding early is always correct: the sub-grid sums parts)
                 const int d = (ly == cly && lx >= clx) ? lx - clx : W;
-                if (d >= W) {
+                if (d == 1 || d == 2) {
+                    atomicAdd(&gr[0].x, racc[0].x);
+                    atomicAdd(&gr[0].y, racc[0].y);
+                    if (d == 2) {
+                        atomicAdd(&gr[1].x, racc[1].x);
+                        atomicAdd(&gr[1].y, racc[1].y);
+                    }
+#pragma unroll
+                    for (int a = 0; a < W - 2; ++a) racc[a] = d == 1 ? racc[a + 1] : racc[a + 2];
+                    racc[W - 2] = d == 1 ? racc[W - 1] : mk((T)0, (T)0);
+                    racc[W - 1] = mk((T)0, (T)0);
+                } else {
 #pragma unroll
                     for (int a = 0; a < W; ++a) {
                         atomicAdd(&gr[a].x, racc[a].x);
                         atomicAdd(&gr[a].y, racc[a].y);
                         racc[a] = mk((T)0, (T)0);
-                    }
-                } else {
-#pragma unroll
-                    for (int sft = 0; sft < W - 1; ++sft) {
-                        if (sft < d) {
-                            atomicAdd(&gr[sft].x, racc[0].x);
-                            atomicAdd(&gr[sft].y, racc[0].y);
-#pragma unroll
-                            for (int a = 0; a < W - 1; ++a) racc[a] = racc[a + 1];
-                            racc[W - 1] = mk((T)0, (T)0);
-                        }
                     }
                 }
             }

@@ -113,7 +113,7 @@ struct ivis_plan_s {
     void *hstage = nullptr;    // pinned staging for the host-buffer entry point
     // Toeplitz form
     ivis_plan_s *toep_sub = nullptr;  // 2nb-window plan that computes T and b at set_vis
-    void *ones_d = nullptr;           // nb ones (unit deapodisation for the Toeplitz passes)
+    void *wbeam_d = nullptr;          // [npoint][nb][nb] beam x dinv[p] dinv[q] (packed passes)
     void **that_ptr_d = nullptr, **bwin_ptr_d = nullptr;  // per slot
     double *qconst_d = nullptr;       // per slot
     int njpart = 0;                   // FP64 data-term partials summed by k_finalize
@@ -387,7 +387,7 @@ cudaError_t launch_forward(ivis_plan_s *p, const void *sky, int slot0 = 0, int n
         size_t smem_row = (size_t)fft_smem_elems(nf, lpb) * sizeof(C);
         cudaFuncSetAttribute(k_fwd_rows_pk<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_row);
         k_fwd_rows_pk<T><<<gr, 256, smem_row, p->stream>>>(
-            (const T *)sky, (const T *)p->beams_d, p->pinfo_d, nslots, (const T *)p->dinv_d, (C *)p->rowbuf,
+            (const T *)sky, (const T *)p->wbeam_d, p->pinfo_d, nslots, (C *)p->rowbuf,
             p->cfg.n, nb, p->lognf, (const C *)p->tw_d, (const float2 *)p->grids_d);
         dim3 gc(nf / (2 << lc), npk);
         size_t smem_col = (size_t)fft_smem_elems(nf, 2 << lc) * sizeof(C);
@@ -430,8 +430,8 @@ cudaError_t launch_adjoint(ivis_plan_s *p, int slot0 = 0, int nslots = -1) {
         dim3 gr((nb + lpb - 1) / lpb, npk);
         size_t smem_row = (size_t)fft_smem_elems(nf, lpb) * sizeof(C);
         cudaFuncSetAttribute(k_adj_rows_pk<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_row);
-        k_adj_rows_pk<T><<<gr, 256, smem_row, p->stream>>>((const C *)p->rowbuf, (const T *)p->beams_d, p->pinfo_d,
-                                                           nslots, (const T *)p->dinv_d, (T *)p->contrib, p->cfg.n,
+        k_adj_rows_pk<T><<<gr, 256, smem_row, p->stream>>>((const C *)p->rowbuf, (const T *)p->wbeam_d, p->pinfo_d,
+                                                           nslots, (T *)p->contrib, p->cfg.n,
                                                            nb, p->lognf, (const C *)p->tw_d);
         return cudaGetLastError();
     }
@@ -465,7 +465,7 @@ cudaError_t launch_toeplitz(ivis_plan_s *p) {
     size_t smem_row = (size_t)fft_smem_elems(nf, lpb) * sizeof(C);
     cudaFuncSetAttribute(k_fwd_rows_pk<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_row);
     k_fwd_rows_pk<T><<<gr, 256, smem_row, p->stream>>>(
-        (const T *)p->x, (const T *)p->beams_d, p->pinfo_d, p->nslot, (const T *)p->ones_d, rowbuf,
+        (const T *)p->x, (const T *)p->beams_d, p->pinfo_d, p->nslot, rowbuf,
         p->cfg.n, nb, p->lognf, (const C *)p->tw_d, (const float2 *)p->grids_d);
     dim3 gc(nf / (2 << lc), npk);
     size_t smem_col = (size_t)fft_smem_elems(nf, 2 << lc) * sizeof(C);
@@ -476,7 +476,7 @@ cudaError_t launch_toeplitz(ivis_plan_s *p) {
     k_toep_rows_pk<T><<<gr, 256, smem_row, p->stream>>>(
         rowbuf, (const T *)p->x, (const T *)p->beams_d, p->pinfo_d, p->nslot, (const T *const *)p->bwin_ptr_d,
         p->qconst_d, (T *)p->contrib, p->jpart, p->cfg.n, nb, p->lognf, (const C *)p->tw_d,
-        (const float2 *)p->grids_d, (const T *)p->ones_d);
+        (const float2 *)p->grids_d);
     return cudaGetLastError();
 }
 
@@ -987,7 +987,7 @@ void release_prepared(ivis_plan_s *p) {
     dfree(p->sd_tw_d);
     p->sd_N = 0;
     void *is = p->inv_sig2_d; dfree(is); p->inv_sig2_d = nullptr;
-    dfree(p->rowbuf); dfree(p->F); dfree(p->G); dfree(p->contrib);
+    dfree(p->rowbuf); dfree(p->F); dfree(p->G); dfree(p->contrib); dfree(p->wbeam_d);
     dfree(p->x); dfree(p->g); dfree(p->tmp1); dfree(p->tmp2); dfree(p->gradK);
     void *a = p->jpart, *b = p->kpart, *c = p->rpart, *d = p->cost_d;
     dfree(a); dfree(b); dfree(c); dfree(d);
@@ -1245,6 +1245,13 @@ ivis_status prepare_impl(ivis_plan_s *p) {
     if ((s = alloc(p, &p->G, (size_t)p->nslot * nf2 * sizeof(C)))) return s;
     CK(cudaMemset(p->G, 0, (size_t)p->nslot * nf2 * sizeof(C)));
     if ((s = alloc(p, &p->contrib, (size_t)p->nslot * c.nb * c.nb * sizeof(T)))) return s;
+    {   // beam x deapodisation per pointing, read by the packed row passes
+        const size_t nw = (size_t)c.npoint * c.nb * c.nb;
+        if ((s = alloc(p, &p->wbeam_d, nw * sizeof(T)))) return s;
+        k_beam_deapod<T><<<(unsigned)((nw + 255) / 256), 256, 0, p->stream>>>(
+            (const T *)p->beams_d, (const T *)p->dinv_d, c.nb, nw, (T *)p->wbeam_d);
+        CK(cudaGetLastError());
+    }
     if ((s = alloc(p, &p->x, npix * sizeof(T)))) return s;
     if ((s = alloc(p, &p->g, npix * sizeof(T)))) return s;
     size_t njp = std::max<size_t>(1, max_chunks);
@@ -1749,10 +1756,6 @@ ivis_status ivis_plan(const ivis_config *cfg, void *stream, ivis_plan_t *out) {
         if (cudaMemset(p->beams_d, 0, (size_t)c.npoint * c.nb * c.nb * p->rsz) != cudaSuccess) s = IVIS_ERR_CUDA;
     }
     if (!s) s = alloc(p, &p->tsd_d, (size_t)c.nchan * c.n * c.n * p->rsz);
-    if (!s && c.toeplitz) {
-        s = p->fp64 ? upload_real<double>(p, &p->ones_d, std::vector<double>(c.nb, 1.0))
-                    : upload_real<float>(p, &p->ones_d, std::vector<double>(c.nb, 1.0));
-    }
     if (!s && c.wterm) {
         std::vector<double> wx, wcorr;
         w_tables(c.nb, c.cell_rad, p->W, p->beta, p->w_xc, p->w_dw, wx, wcorr);
@@ -2118,7 +2121,6 @@ ivis_status ivis_destroy(ivis_plan_t p) {
     }
     dfree(p->beams_d);
     dfree(p->tsd_d);
-    dfree(p->ones_d);
     dfree(p->wx_d);
     dfree(p->wcorr_d);
     dfree(p->feather_tw_d);

@@ -288,6 +288,16 @@ __global__ void k_beam_weight_grid(const T *__restrict__ beams, const float2 *__
     bilerp_adj(out, n, g.x, g.y, a * a);
 }
 
+// out[k][q][p] = beams[k][q][p] dinv[p] dinv[q] for every pointing (n = npoint nb^2).
+template <typename T>
+__global__ void k_beam_deapod(const T *__restrict__ beams, const T *__restrict__ dinv, int nb, size_t n,
+                              T *out) {
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int p = (int)(i % nb), q = (int)((i / nb) % nb);
+    out[i] = beams[i] * dinv[p] * dinv[q];
+}
+
 template <typename T>
 __global__ void k_scale(size_t n, const T *__restrict__ in, T a, T *out) {
     size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;

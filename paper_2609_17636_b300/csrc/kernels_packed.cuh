@@ -18,13 +18,14 @@
 
 namespace ivis {
 
-// A[q][p] I'[q][p] dinv[p] dinv[q] of one slot (bilinear through the pointing's grid if it
-// has one), zero off the sky.
+// wts[k][q][p] I'[q][p] of one slot (bilinear through the pointing's grid if it has one),
+// zero off the sky; wts is the beam, or the beam times the deapodisation dinv[p] dinv[q]
+// (precomputed per pointing at prepare).
 template <typename T>
 __device__ __forceinline__ T window_value(const PairInfo &pi, int q, int p, const T *__restrict__ sky,
-                                          const T *__restrict__ beams, const T *__restrict__ dinv,
-                                          const float2 *__restrict__ grids, int n, int nb) {
-    const T a = beams[((size_t)pi.k * nb + q) * nb + p] * dinv[p] * dinv[q];
+                                          const T *__restrict__ wts, const float2 *__restrict__ grids,
+                                          int n, int nb) {
+    const T a = wts[((size_t)pi.k * nb + q) * nb + p];
     const T *img = sky + (size_t)pi.chan * n * n;
     if (pi.gridded) {
         const float2 g = grids[((size_t)pi.k * nb + q) * nb + p];
@@ -49,8 +50,8 @@ __device__ __forceinline__ int pk_mirror_line(int L, int c0, int ncol) {
 // Line l: window row q of the slot pair (2 blockIdx.y, 2 blockIdx.y + 1) -> DFT along x.
 template <typename T>
 __global__ void __launch_bounds__(256)
-k_fwd_rows_pk(const T *__restrict__ sky, const T *__restrict__ beams, const PairInfo *__restrict__ pinfo,
-              int nslot, const T *__restrict__ dinv, typename cplx_of<T>::type *rowbuf, int n, int nb,
+k_fwd_rows_pk(const T *__restrict__ sky, const T *__restrict__ wts, const PairInfo *__restrict__ pinfo,
+              int nslot, typename cplx_of<T>::type *rowbuf, int n, int nb,
               int lognf, const typename cplx_of<T>::type *__restrict__ tw, const float2 *__restrict__ grids) {
     typedef typename cplx_of<T>::type C;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -66,8 +67,8 @@ k_fwd_rows_pk(const T *__restrict__ sky, const T *__restrict__ beams, const Pair
     __syncthreads();
     if (q < nb) {
         for (int p = j0; p < nb; p += tpl) {
-            const T va = window_value(pa, q, p, sky, beams, dinv, grids, n, nb);
-            const T vb = hasb ? window_value(pb, q, p, sky, beams, dinv, grids, n, nb) : (T)0;
+            const T va = window_value(pa, q, p, sky, wts, grids, n, nb);
+            const T vb = hasb ? window_value(pb, q, p, sky, wts, grids, n, nb) : (T)0;
             s[pidx(l * nf + ((p - nb / 2) & (nf - 1)))] = mk(va, vb);
         }
     }
@@ -155,8 +156,8 @@ k_adj_cols_pk(typename cplx_of<T>::type *G, typename cplx_of<T>::type *rowbuf, i
 // Inverse DFT along x; the real part is slot a's window gradient, the imaginary part slot b's.
 template <typename T>
 __global__ void __launch_bounds__(256)
-k_adj_rows_pk(const typename cplx_of<T>::type *__restrict__ rowbuf, const T *__restrict__ beams,
-              const PairInfo *__restrict__ pinfo, int nslot, const T *__restrict__ dinv, T *contrib, int n,
+k_adj_rows_pk(const typename cplx_of<T>::type *__restrict__ rowbuf, const T *__restrict__ wts,
+              const PairInfo *__restrict__ pinfo, int nslot, T *contrib, int n,
               int nb, int lognf, const typename cplx_of<T>::type *__restrict__ tw) {
     typedef typename cplx_of<T>::type C;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -175,16 +176,14 @@ k_adj_rows_pk(const typename cplx_of<T>::type *__restrict__ rowbuf, const T *__r
     __syncthreads();
     line_fft<C, +1>(s, 1, l * nf, lognf, j0, tw);
     if (q >= nb) return;
-    const T dq = dinv[q];
     const int ya = pa.cy - nb / 2 + q, yb = pb.cy - nb / 2 + q;
     const bool ona = pa.gridded || (ya >= 0 && ya < n), onb = hasb && (pb.gridded || (yb >= 0 && yb < n));
     T *oa = contrib + ((size_t)sa * nb + q) * nb, *ob = contrib + ((size_t)sb * nb + q) * nb;
-    const T *ba = beams + ((size_t)pa.k * nb + q) * nb, *bb = beams + ((size_t)pb.k * nb + q) * nb;
+    const T *ba = wts + ((size_t)pa.k * nb + q) * nb, *bb = wts + ((size_t)pb.k * nb + q) * nb;
     for (int p = j0; p < nb; p += tpl) {
         const C v = s[pidx(l * nf + ((p - nb / 2) & (nf - 1)))];
-        const T d = dinv[p] * dq;
-        if (ona) oa[p] = v.x * d * ba[p];
-        if (onb) ob[p] = v.y * d * bb[p];
+        if (ona) oa[p] = v.x * ba[p];
+        if (onb) ob[p] = v.y * bb[p];
     }
 }
 
@@ -239,7 +238,7 @@ k_toep_rows_pk(const typename cplx_of<T>::type *__restrict__ rowbuf, const T *__
                const T *__restrict__ beams, const PairInfo *__restrict__ pinfo, int nslot,
                const T *const *__restrict__ bwin_ptr, const double *__restrict__ qconst, T *contrib,
                double *jpart, int n, int nb, int lognf, const typename cplx_of<T>::type *__restrict__ tw,
-               const float2 *__restrict__ grids, const T *__restrict__ ones) {
+               const float2 *__restrict__ grids) {
     typedef typename cplx_of<T>::type C;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C *s = reinterpret_cast<C *>(smem_raw);
@@ -267,12 +266,12 @@ k_toep_rows_pk(const typename cplx_of<T>::type *__restrict__ rowbuf, const T *__
         for (int p = j0; p < nb; p += tpl) {
             const C v = s[pidx(l * nf + ((p - nb / 2) & (nf - 1)))];
             if (ona) {
-                const T z = window_value(pa, q, p, sky, beams, ones, grids, n, nb);
+                const T z = window_value(pa, q, p, sky, beams, grids, n, nb);
                 oa[p] = ba[p] * (v.x - wa[p]);
                 acc_a += z * (v.x * (T)0.5 - wa[p]);
             }
             if (onb) {
-                const T z = window_value(pb, q, p, sky, beams, ones, grids, n, nb);
+                const T z = window_value(pb, q, p, sky, beams, grids, n, nb);
                 ob[p] = bb[p] * (v.y - wb[p]);
                 acc_b += z * (v.y * (T)0.5 - wb[p]);
             }

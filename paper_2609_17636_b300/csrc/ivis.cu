@@ -1745,7 +1745,7 @@ ivis_status ivis_plan(const ivis_config *cfg, void *stream, ivis_plan_t *out) {
     }
     if (!s) {
         std::vector<double> kp;
-        es_fit(p->W, p->beta, std::min(p->W + 2, ES_MAXDEG), kp);
+        es_fit(p->W, p->beta, std::min(p->W + 1, ES_MAXDEG), kp);  // the degree of es_deg<W>
         std::vector<float> kpf(kp.begin(), kp.end());
         s = alloc(p, (void **)&p->kpoly_d, kpf.size() * sizeof(float));
         if (!s && cudaMemcpy(p->kpoly_d, kpf.data(), kpf.size() * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess)

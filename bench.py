@@ -2,7 +2,7 @@
 
 One step = one evaluation of Q_tot and its gradient over the whole workload (all pointings
 and channels: window/beam/deapodisation + row/column FFTs, fused degrid/residual/spread,
-adjoint FFTs, joint sum, Laplacian, single-dish fusion, FP64 reductions), with the sky,
+adjoint FFTs, joint sum, Laplacian, single-dish fusion, cost reductions), with the sky,
 visibilities and maps resident in HBM. The metric is visibilities per second per
 cost+gradient evaluation. L2 is flushed (a 256 MiB write) before every timed step.
 
@@ -409,7 +409,8 @@ def solve_compare(prob, args):
                                                   if bt["reached_fp64_cost"] else None)
     pt.close()
     res["note"] = ("baseline: all-FP64 path, one (pointing, channel) pair per launch sequence; "
-                   "compared: FP32 grids / FP64 reductions, all pairs batched per launch (and the "
+                   "compared: FP32 grids and per-pixel solver passes (FP64 across warps and CTAs), all "
+                   "pairs batched per launch (and the "
                    "same through the Toeplitz form of the data term); "
                    "equal cost = FP64 final cost x (1 + 1e-6), judged by the FP64 cost function")
     p64.close()

@@ -63,7 +63,8 @@ typedef struct {
     int nb;             /* pointing window nb x nb, power of two, 16 <= nb <= 2048         */
     double cell_rad;    /* pixel size (radians); the same grid for sky and windows         */
     int precision;      /* IVIS_FP64: all arithmetic double. IVIS_FP32: gridding, FFTs and
-                           residuals in float; cost, gradient and solver reductions in double */
+                           residuals in float; cost and solver sums: terms in float within a
+                           thread and a warp, combined in double across warps and CTAs      */
     double nufft_tol;   /* target relative accuracy of the NUFFT when kernel_width == 0    */
     int kernel_width;   /* ES kernel width w in grid cells (2..16); 0 = chosen from tol     */
     double lambda_r;    /* weight of R (Eq. 14)                                            */

@@ -8,7 +8,7 @@
 // spectrum spec[k] = (b[0] + 2 sum_{t>=1} b[t] cos(2 pi k t / N)) / N (real and even), inverse
 // DFT, crop. Two real lines share one complex line (the real-even filter keeps the real and
 // imaginary parts apart). The column pass can fuse the single-dish residual
-// e = (t - T) / sigma^2 and the FP64 partials of K = 1/2 sum (t - T)^2 / sigma^2.
+// e = (t - T) / sigma^2 and the per-CTA partials of K = 1/2 sum (t - T)^2 / sigma^2.
 #pragma once
 #include "common.cuh"
 #include "fft.cuh"

@@ -109,7 +109,7 @@ __global__ void k_w_scatter(long long E, const int *__restrict__ key_e,
 }
 
 // Per visibility: V~ = phase sum_t phi_t pv[t]. PREDICT: V~ to out (caller order). Otherwise
-// r = V~ - V, FP64 partial of 1/2 w |r|^2 per CTA (jpart[pair * gridDim.x + blockIdx.x]) and
+// r = V~ - V, the CTA's partial of 1/2 w |r|^2 (FP64 across warps) to jpart[pair * gridDim.x + blockIdx.x], and
 // the spread value w r conj(phase) to the visibility's W entries.
 template <typename T, bool PREDICT>
 __global__ void __launch_bounds__(256)

@@ -8,14 +8,16 @@
  * with the joint data term Q = sum_k J_k over every (pointing k, channel) pair
  * (Eqs. 5-6), J_k = 1/2 sum_j w_j |V~_j - V_j|^2, the model visibilities
  * V~ of the primary-beam-weighted window I'_k (Eqs. 2-3, w-term and n-term
- * neglected as the paper does), the Laplacian regulariser R (Eqs. 7-8) and
+ * neglected as the paper does by default; the full Eq. 1 with wterm = 1 in
+ * ivis_config), the Laplacian regulariser R (Eqs. 7-8) and
  * the single-dish fusion term K (Eqs. 11-13); and its analytic gradient.
  * The bounded quasi-Newton solve of Eq. 10 (I >= 0 when positivity is on) runs
  * on the device.
  *
  * Conventions used by every call:
  *  - Window of pointing k: I'_k[q][p] = I[cy - nb/2 + q][cx - nb/2 + p] (zero off
- *    the sky); direction cosines l_p = (p - nb/2) cell, m_q = (q - nb/2) cell;
+ *    the sky), or its bilinear re-projection (ivis_set_pointing_grid); direction
+ *    cosines l_p = (p - nb/2) cell, m_q = (q - nb/2) cell;
  *    V~_j = sum_{q,p} A_k[q][p] I'_k[q][p] exp(-2 pi i (u_j l_p + v_j m_q)).
  *  - Real arrays whose type follows the plan's precision ("real" below) are
  *    double for IVIS_FP64 and float for IVIS_FP32. Costs are always double.

@@ -440,12 +440,14 @@ def run_c5(args):
     hist = warmstart.train(net, ts, epochs=args.c5_epochs, batch=8, lr=1e-3, rng=rng,
                            log=lambda ep, l: log(f"c5: epoch {ep} loss {l:.4g}"))
     t_train = time.perf_counter() - t0
+    for _ in range(3):  # untimed warm-up of the inference path (first-use module loading)
+        warmstart.predict_x0(net, prob)
     res = [warmstart.compare_solves(net, prob, synth.lognormal_sky(synth.make_rng(900_000 + i), desc.n)[None],
                                     rng, maxiter=500) for i in range(args.c5_eval)]
     cold_s = float(np.mean([r["cold_seconds"] for r in res]))
     warm_s = float(np.mean([r["warm_seconds"] for r in res]))
     out = {"metric": "solve time to the cold start's final cost (1e-4 rel.), learned warm start",
-           "value": round(warm_s, 5), "unit": "s", "n_gpus": 1, "steps": args.c5_eval, "warmup": 0,
+           "value": round(warm_s, 5), "unit": "s", "n_gpus": 1, "steps": args.c5_eval, "warmup": 3,
            "higher_is_better": False, "vs_baseline": None, "dtype": "f32 solve / bf16 network",
            "data": "synthetic lognormal k^-3 skies, seeded", "config": {"workload": WORKLOAD["c5"]},
            "cold": {"seconds": round(cold_s, 5),

@@ -277,6 +277,21 @@ ivis_status ivis_unet_get_params(ivis_unet_t net, float *host_params);
  * float [B][H][W]; H and W multiples of 8. */
 ivis_status ivis_unet_forward(ivis_unet_t net, const float *in_dev, float *out_dev, int B, int H,
                               int W);
+/* The warm start of one channel, straight from the solver's planes: dirty_dev and beamw_dev
+ * (the planes ivis_dirty_image writes; [H][W], double if fp64 else float) become the network
+ * input (s0 dirty, s1 beam weight) and x0_dev ([H][W], same type) receives
+ * max(s_out * U-Net(input), 0), the initial sky for ivis_solve. One image (B = 1), H and W
+ * as for ivis_unet_forward. Runs on the network's stream and returns after it; inputs must be
+ * complete on that stream. Scales must be finite. */
+ivis_status ivis_unet_warm_start(ivis_unet_t net, const void *dirty_dev, const void *beamw_dev,
+                                 int fp64, int H, int W, double s0, double s1, double s_out,
+                                 void *x0_dev);
+/* Training tensors from the solver's planes: out_dev (float) gets sa * a in its first npix
+ * entries and, when b_dev is not NULL, sb * b in the next npix (a network input [2][H][W]);
+ * a and b are double if fp64 else float; products are taken in that type. Queued on stream
+ * (cudaStream_t; NULL = legacy default); does not wait. Errors: ivis_unet_last_error(NULL). */
+ivis_status ivis_unet_planes(const void *a_dev, const void *b_dev, int fp64, int64_t npix,
+                             double sa, double sb, float *out_dev, void *stream);
 /* Forward + backward of the MSE loss against tgt_dev (float [B][H][W]); the parameter
  * gradient (zeroed first) stays on the device; loss_out (host, may be NULL) gets the loss. */
 ivis_status ivis_unet_backward(ivis_unet_t net, const float *in_dev, const float *tgt_dev, int B,

@@ -27,7 +27,8 @@ EXPORTS = ["ivis_plan", "ivis_set_pointing", "ivis_set_pointing_grid", "ivis_set
            "ivis_dirty_image", "ivis_solve_target", "ivis_tuning", "ivis_unet_create", "ivis_unet_num_params", "ivis_unet_set_params",
            "ivis_unet_get_params", "ivis_unet_forward", "ivis_unet_backward", "ivis_unet_get_grads",
            "ivis_unet_adam_step", "ivis_unet_use_tcgen05", "ivis_unet_destroy",
-           "ivis_unet_last_error", "ivis_feather", "ivis_rayleigh_jeans"]
+           "ivis_unet_last_error", "ivis_feather", "ivis_rayleigh_jeans", "ivis_unet_warm_start",
+           "ivis_unet_planes"]
 
 
 class IvisError(RuntimeError):
@@ -94,6 +95,8 @@ def load(path: str = LIB_PATH):
     L.ivis_unet_set_params.argtypes = [vp, vp]
     L.ivis_unet_get_params.argtypes = [vp, vp]
     L.ivis_unet_forward.argtypes = [vp, vp, vp, i, i, i]
+    L.ivis_unet_warm_start.argtypes = [vp, vp, vp, i, i, i, d, d, d, vp]
+    L.ivis_unet_planes.argtypes = [vp, vp, i, i64, d, d, vp, vp]
     L.ivis_unet_backward.argtypes = [vp, vp, vp, i, i, i, dp]
     L.ivis_unet_get_grads.argtypes = [vp, vp]
     L.ivis_unet_adam_step.argtypes = [vp, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float]

@@ -587,6 +587,35 @@ __global__ void k_pack_input(int B, int H, int W, const float *__restrict__ in, 
     }
 }
 
+// The warm start's network input, one image straight from the solver's planes (float or
+// double [H][W]): NHWC bf16 [H][W][2] = (s0 a, s1 b), the products taken in T.
+template <typename T>
+__global__ void k_pack_planes(size_t P, const T *__restrict__ a, const T *__restrict__ b, T s0, T s1, bf16 *out) {
+    for (size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x; p < P; p += (size_t)gridDim.x * blockDim.x) {
+        out[2 * p] = __float2bfloat16((float)(s0 * a[p]));
+        out[2 * p + 1] = __float2bfloat16((float)(s1 * b[p]));
+    }
+}
+
+// Scaled float planes from the solver's planes: out[0] = s0 a, out[1] = s1 b (b may be null:
+// one plane), products in T, each plane [P].
+template <typename T>
+__global__ void k_scale_planes(size_t P, const T *__restrict__ a, const T *__restrict__ b, T s0, T s1, float *out) {
+    for (size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x; p < P; p += (size_t)gridDim.x * blockDim.x) {
+        out[p] = (float)(s0 * a[p]);
+        if (b) out[P + p] = (float)(s1 * b[p]);
+    }
+}
+
+// The warm start itself: x0 = max(s out, 0) in the solver's type.
+template <typename T>
+__global__ void k_x0_from_output(size_t P, const float *__restrict__ out, T s, T *x0) {
+    for (size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x; p < P; p += (size_t)gridDim.x * blockDim.x) {
+        const T v = s * (T)out[p];
+        x0[p] = v > (T)0 ? v : (T)0;
+    }
+}
+
 // Adam on fp32 masters; refresh the bf16 copies. step >= 1.
 __global__ void k_adam(size_t n, float *w, const float *__restrict__ g, float *m, float *v, bf16 *wb,
                        float lr, float b1, float b2, float eps, float c1, float c2) {

@@ -192,10 +192,11 @@ ivis_status check_shape(ivis_unet_s *u, int B, int H, int W) {
     return IVIS_OK;
 }
 
+// in_dev == nullptr: the caller has packed the input tensor already.
 ivis_status forward_impl(ivis_unet_s *u, const float *in_dev, int B, int H, int W) {
     cudaStream_t st = u->stream;
     const size_t P0 = (size_t)B * H * W;
-    k_pack_input<<<nblk(P0), 256, 0, st>>>(B, H, W, in_dev, u->act[T_IN]);
+    if (in_dev) k_pack_input<<<nblk(P0), 256, 0, st>>>(B, H, W, in_dev, u->act[T_IN]);
     for (size_t li = 0; li < u->convs.size(); ++li) {
         const ConvSpec &s = u->convs[li];
         const int h = H >> s.level, w = W >> s.level;
@@ -320,6 +321,50 @@ ivis_status ivis_unet_forward(ivis_unet_t u, const float *in_dev, float *out_dev
     if ((s = forward_impl(u, in_dev, B, H, W))) return s;
     UCK(cudaMemcpyAsync(out_dev, u->out, (size_t)B * H * W * 4, cudaMemcpyDeviceToDevice, u->stream));
     UCK(cudaStreamSynchronize(u->stream));
+    return IVIS_OK;
+}
+
+ivis_status ivis_unet_warm_start(ivis_unet_t u, const void *dirty_dev, const void *beamw_dev, int fp64, int H,
+                                 int W, double s0, double s1, double s_out, void *x0_dev) {
+    if (!u || !dirty_dev || !beamw_dev || !x0_dev) return ufail(u, IVIS_ERR_ARG, "null pointer");
+    if (!std::isfinite(s0) || !std::isfinite(s1) || !std::isfinite(s_out))
+        return ufail(u, IVIS_ERR_ARG, "scales must be finite");
+    ivis_status s = check_shape(u, 1, H, W);
+    if (s) return s;
+    size_t colmax = 0;
+    for (auto &c : u->convs) colmax = std::max(colmax, (size_t)(H >> c.level) * (W >> c.level) * 9 * (c.ca + c.cb));
+    if ((s = ensure_scratch(u, colmax, 1))) return s;
+    cudaStream_t st = u->stream;
+    const size_t P = (size_t)H * W;
+    if (fp64)
+        k_pack_planes<double><<<nblk(P), 256, 0, st>>>(P, (const double *)dirty_dev, (const double *)beamw_dev, s0,
+                                                       s1, u->act[T_IN]);
+    else
+        k_pack_planes<float><<<nblk(P), 256, 0, st>>>(P, (const float *)dirty_dev, (const float *)beamw_dev,
+                                                      (float)s0, (float)s1, u->act[T_IN]);
+    if ((s = forward_impl(u, nullptr, 1, H, W))) return s;
+    if (fp64) k_x0_from_output<double><<<nblk(P), 256, 0, st>>>(P, u->out, s_out, (double *)x0_dev);
+    else k_x0_from_output<float><<<nblk(P), 256, 0, st>>>(P, u->out, (float)s_out, (float *)x0_dev);
+    UCK(cudaGetLastError());
+    UCK(cudaStreamSynchronize(st));
+    return IVIS_OK;
+}
+
+ivis_status ivis_unet_planes(const void *a_dev, const void *b_dev, int fp64, int64_t npix, double sa, double sb,
+                             float *out_dev, void *stream) {
+    if (!a_dev || !out_dev) return ufail(nullptr, IVIS_ERR_ARG, "null pointer");
+    if (npix < 0) return ufail(nullptr, IVIS_ERR_ARG, "negative pixel count");
+    if (!std::isfinite(sa) || !std::isfinite(sb)) return ufail(nullptr, IVIS_ERR_ARG, "scales must be finite");
+    if (npix == 0) return IVIS_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t P = (size_t)npix;
+    if (fp64)
+        k_scale_planes<double><<<nblk(P), 256, 0, st>>>(P, (const double *)a_dev, (const double *)b_dev, sa, sb, out_dev);
+    else
+        k_scale_planes<float><<<nblk(P), 256, 0, st>>>(P, (const float *)a_dev, (const float *)b_dev, (float)sa,
+                                                       (float)sb, out_dev);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return ufail(nullptr, IVIS_ERR_CUDA, std::string("unet planes: ") + cudaGetErrorString(e));
     return IVIS_OK;
 }
 

@@ -307,6 +307,25 @@ class UNet:
                                               ctypes.byref(loss)))
         return loss.value
 
+    def warm_start(self, dirty: torch.Tensor, beamw: torch.Tensor, s0: float, s1: float,
+                   s_out: float) -> torch.Tensor:
+        """max(s_out * U-Net([s0 dirty, s1 beamw]), 0) for one channel's [H][W] planes, in their
+        dtype (ivis_unet_warm_start)."""
+        if dirty.dtype != beamw.dtype or dirty.dtype not in (torch.float32, torch.float64):
+            raise ValueError("dirty and beam-weight planes must share float32 or float64")
+        if dirty.dim() != 2 or beamw.shape != dirty.shape:
+            raise ValueError("dirty and beam-weight planes must be [H][W] of one shape")
+        if not (dirty.is_cuda and beamw.is_cuda and dirty.is_contiguous() and beamw.is_contiguous()):
+            raise ValueError("planes must be contiguous CUDA tensors")
+        H, W = dirty.shape
+        x0 = torch.empty_like(dirty)
+        fp64 = int(dirty.dtype == torch.float64)
+        self._check(self.L.ivis_unet_warm_start(self._p, ctypes.c_void_p(dirty.data_ptr()),
+                                                ctypes.c_void_p(beamw.data_ptr()), fp64, H, W,
+                                                float(s0), float(s1), float(s_out),
+                                                ctypes.c_void_p(x0.data_ptr())))
+        return x0
+
     def use_tcgen05(self, enable: bool):
         self._check(self.L.ivis_unet_use_tcgen05(self._p, int(bool(enable))))
 
@@ -323,6 +342,26 @@ class UNet:
             self.close()
         except Exception:
             pass
+
+
+def unet_planes(a: torch.Tensor, b: torch.Tensor | None, sa: float, sb: float = 1.0) -> torch.Tensor:
+    """float32 [2][...] = (sa a, sb b), or [...] = sa a without b (ivis_unet_planes): network
+    inputs and targets from the solver's planes."""
+    if a.dtype not in (torch.float32, torch.float64) or not (a.is_cuda and a.is_contiguous()):
+        raise ValueError("a must be a contiguous float32/float64 CUDA tensor")
+    if b is not None and (b.dtype != a.dtype or b.shape != a.shape or not (b.is_cuda and b.is_contiguous())):
+        raise ValueError("b must match a in dtype and shape and be contiguous on the device")
+    L = _lib.load()
+    out = torch.empty(((2,) if b is not None else ()) + tuple(a.shape), dtype=torch.float32, device=a.device)
+    st = torch.cuda.current_stream(a.device).cuda_stream
+    status = L.ivis_unet_planes(ctypes.c_void_p(a.data_ptr()),
+                                ctypes.c_void_p(b.data_ptr() if b is not None else None),
+                                int(a.dtype == torch.float64), a.numel(), float(sa), float(sb),
+                                ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(st))
+    if status != 0:
+        msg = L.ivis_unet_last_error(None)
+        raise IvisError(status, msg.decode() if msg else "")
+    return out
 
 
 def rayleigh_jeans(freq_hz: float) -> float:

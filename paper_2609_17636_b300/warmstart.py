@@ -5,8 +5,9 @@ channel's sky; the solver then starts from max(network output, 0) instead of a n
 The plain cold-start solve stays the reference: a warm start is judged by the iterations and
 wall time it needs to reach the cold start's final cost.
 
-Every step runs in libivis.so (dirty image, solver, U-Net forward/backward/Adam); this module
-orchestrates and only moves crops between tensors.
+Every step runs in libivis.so (dirty image, input and target scaling, solver, U-Net
+forward/backward/Adam, the clamped warm start); this module orchestrates and only moves crops
+between tensors.
 """
 from __future__ import annotations
 
@@ -16,7 +17,7 @@ from dataclasses import dataclass, field
 import numpy as np
 import torch
 
-from .engine import Plan, UNet, dirty_image
+from .engine import Plan, UNet, dirty_image, unet_planes
 
 __all__ = ["SkyProblem", "sky_problem", "TrainingSet", "observe", "make_pairs", "train", "predict_x0",
            "compare_solves"]
@@ -75,9 +76,9 @@ def observe(prob: SkyProblem, sky: np.ndarray, rng):
 
 
 def network_input(prob: SkyProblem):
+    """float32 [2][n][n]: dirty image / (sum of weights x I_SCALE), beam-weight map."""
     d, b = dirty_image(prob.plan)
-    d = d.float() / prob.sum_w / I_SCALE
-    return torch.stack([d[0], b.float()])  # [2][n][n]
+    return unet_planes(d[0], b, 1.0 / (prob.sum_w * I_SCALE), 1.0)
 
 
 def make_pairs(prob: SkyProblem, skies, crop: int, crops_per_sky: int, maxiter: int, rng,
@@ -95,7 +96,7 @@ def make_pairs(prob: SkyProblem, skies, crop: int, crops_per_sky: int, maxiter: 
         rep = p.solve(x, maxiter=maxiter, pgtol=0.0, ftol=ftol)
         ts.solve_seconds += time.perf_counter() - t0
         ts.solve_iters.append(rep["iterations"])
-        tgt = x[0].float() / I_SCALE
+        tgt = unet_planes(x[0], None, 1.0 / I_SCALE)
         for _ in range(crops_per_sky):
             y0 = int(rng.integers(0, n - crop + 1))
             x0 = int(rng.integers(0, n - crop + 1))
@@ -125,10 +126,10 @@ def train(net: UNet, ts: TrainingSet, epochs: int, batch: int, lr: float, rng, l
 
 
 def predict_x0(net: UNet, prob: SkyProblem) -> torch.Tensor:
-    """Initial sky max(U-Net(dirty, beam weight), 0) in the plan's dtype and shape."""
-    inp = network_input(prob)[None].contiguous()
-    out = net.forward(inp)[0] * I_SCALE
-    return torch.clamp(out, min=0.0).to(prob.plan.dtype).reshape(prob.plan.shape).contiguous()
+    """Initial sky max(I_SCALE U-Net(dirty, beam weight), 0) in the plan's dtype and shape."""
+    d, b = dirty_image(prob.plan)
+    x0 = net.warm_start(d[0], b, 1.0 / (prob.sum_w * I_SCALE), 1.0, I_SCALE)
+    return x0.reshape(prob.plan.shape)
 
 
 def compare_solves(net: UNet, prob: SkyProblem, sky, rng, maxiter: int, rel_tol: float = 1e-4,

@@ -81,3 +81,49 @@ def test_unet_adam_training_reduces_loss_on_a_fixed_batch():
     last = net.backward(x, t)
     assert last < 0.3 * first, (first, last)
     net.close()
+
+
+@pytest.mark.parametrize("dtype", [torch.float32, torch.float64])
+def test_warm_start_from_solver_planes(dtype):
+    """ivis_unet_warm_start: the network input (s0 dirty, s1 beam weight) is built from the
+    solver's planes and the output max(s_out U-Net, 0) is written in their dtype. Against the
+    oracle network at the forward test's tolerance, and against ivis_unet_forward on the planes
+    ivis_unet_planes scales (the same kernels then: equal to float rounding). The scaling itself
+    is one IEEE product per value in the planes' type, so it is compared bit for bit."""
+    from paper_2609_17636_b300 import IvisError, UNet, unet_planes
+    c, H, W = 8, 32, 40
+    shapes = synth.unet_layer_shapes(c)
+    p = synth.unet_init(c, 5)
+    rng = np.random.default_rng(6)
+    npdt = np.float32 if dtype == torch.float32 else np.float64
+    dirty = (rng.standard_normal((H, W)) * 3e-4).astype(npdt)
+    beam = rng.uniform(0.0, 1.0, (H, W)).astype(npdt)
+    s0, s1, s_out = 1.0 / 3e-4, 0.5, 1e-3
+    net = UNet(c, max_batch=1, max_hw=H * W)
+    net.set_params(p)
+    d_t = torch.as_tensor(dirty, device="cuda")
+    b_t = torch.as_tensor(beam, device="cuda")
+    x0 = net.warm_start(d_t, b_t, s0, s1, s_out)
+    assert x0.dtype == dtype and tuple(x0.shape) == (H, W)
+    x0 = x0.cpu().numpy()
+    planes = unet_planes(d_t, b_t, s0, s1).cpu().numpy()
+    want = np.stack([(npdt(s0) * dirty).astype(np.float32), (npdt(s1) * beam).astype(np.float32)])
+    assert np.array_equal(planes, want)
+    tgt = unet_planes(b_t, None, s1).cpu().numpy()
+    assert tgt.shape == (H, W) and np.array_equal(tgt, want[1])
+    r = s_out * ou.forward(p, shapes, c, want[None].astype(np.float64))[0]
+    assert x0.min() >= 0.0
+    # the clamp is 1-Lipschitz, so the forward test's bound carries over unchanged:
+    # ||x0 - max(r, 0)|| <= ||s_out out - r|| <= 2e-2 ||r||. (Most outputs of this untrained
+    # network are negative: the clamped vector keeps a third of ||r||, so a bound relative to it
+    # would be three times tighter than the forward's.)
+    err = float(np.linalg.norm(x0 - np.maximum(r, 0.0)))
+    assert err <= 2e-2 * np.linalg.norm(r), err / np.linalg.norm(r)
+    out = net.forward(torch.as_tensor(want[None], device="cuda")).cpu().numpy()[0]
+    via_forward = np.maximum(npdt(s_out) * out.astype(npdt), 0.0)
+    assert _rel(x0, via_forward) <= 1e-6, _rel(x0, via_forward)
+    with pytest.raises(IvisError):  # W not a multiple of 8
+        net.warm_start(d_t[:, :36].contiguous(), b_t[:, :36].contiguous(), s0, s1, s_out)
+    with pytest.raises(ValueError):
+        net.warm_start(d_t, b_t.float() if dtype == torch.float64 else b_t.double(), s0, s1, s_out)
+    net.close()

@@ -19,13 +19,17 @@ import numpy as np
 
 from .generate import (ARCSEC, DEG, HI_FREQ_HZ, antenna_layout, complex_noise,
                        flag_keep_mask, gaussian_beam, hex_footprint, lognormal_sky,
-                       make_rng, point_source_sky, uvw_tracks)
+                       make_rng, point_source_flux_law, point_source_sky, uvw_tracks)
 
 __all__ = ["VisSet", "Problem", "config_c1", "config_c2", "config_c3", "config_c4",
-           "small_mosaic", "LAT_ASKAP_RAD", "DEC_LMC_RAD"]
+           "small_mosaic", "point_source_spectrum", "LAT_ASKAP_RAD", "DEC_LMC_RAD",
+           "SPECTRUM_FREQS_HZ"]
 
 LAT_ASKAP_RAD = -26.7 * DEG
 DEC_LMC_RAD = -69.0 * DEG
+# channel centres of the multi-frequency point-source observation (Sect. 4.1): one window
+# centred at 1.0 GHz, 1.0 GHz wide, ten equal channels
+SPECTRUM_FREQS_HZ = 0.55e9 + 0.1e9 * np.arange(10)
 
 
 @dataclass
@@ -102,6 +106,31 @@ def config_c1(seed: int = 1001) -> Problem:
     return Problem("c1_single_pointing", n, cell, 1, nb, np.array([[n // 2, n // 2]]),
                    beam, pairs, sky, lambda_r=0.0, lambda_s=0.0, positivity=True,
                    sigma_vis=1e-3)
+
+
+def point_source_spectrum(seed: int = 1010, n: int = 16, cell_arcsec: float = 120.0,
+                          sigma: float = 0.1) -> Problem:
+    """Stand-in for the multi-frequency point-source observation of Sect. 4.1: one pointing,
+    27 antennas in a 1 km disk (a compact, VLA-D-sized array), +-5 h around transit in 2000 s
+    integrations (18 dumps) at declination +40.7 deg from latitude +34.1 deg, ten channels
+    (SPECTRUM_FREQS_HZ), a point source at the phase centre with S = 5 Jy (nu / 1.5 GHz)^-1,
+    Gaussian noise sigma per real and imaginary component, natural weights, a 45' Gaussian
+    beam, no regularisation, positivity. The pixel (2' by default) is coarser than the
+    synthesised beam at every channel, so the source is unresolved in the pixel basis."""
+    rng = make_rng(seed)
+    cell = cell_arcsec * ARCSEC
+    enu = antenna_layout(rng, 27, 1000.0)
+    ha = (np.arange(18) + 0.5 - 9.0) * (2000.0 / 86400.0) * (2.0 * math.pi)
+    dec, lat = 40.73 * DEG, 34.08 * DEG
+    flux = point_source_flux_law(SPECTRUM_FREQS_HZ)
+    sky = np.zeros((SPECTRUM_FREQS_HZ.size, n, n))
+    sky[:, n // 2, n // 2] = flux
+    pairs = [_vis_set(rng, 0, c, uvw_tracks(enu, ha, dec, lat, f), sigma)
+             for c, f in enumerate(SPECTRUM_FREQS_HZ)]
+    beam = gaussian_beam(n, 45.0 * 60.0 * ARCSEC / cell).astype(np.float32)[None]
+    return Problem("point_source_spectrum", n, cell, SPECTRUM_FREQS_HZ.size, n,
+                   np.array([[n // 2, n // 2]]), beam, pairs, sky, lambda_r=0.0, lambda_s=0.0,
+                   positivity=True, sigma_vis=sigma, freqs_hz=SPECTRUM_FREQS_HZ.copy())
 
 
 def config_c2(seed: int = 1002, lambda_r: float = 1e-2, dumps: int = 360) -> Problem:

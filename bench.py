@@ -486,6 +486,19 @@ def oracle_rate(prob, seconds_target=15.0, nvis=None, seed=0):
     return len(idx) / dt, len(idx), dt
 
 
+def oracle_solve(prob, maxiter=30):
+    """The oracle's scipy L-BFGS-B solve (FP64, direct DFT, host cores) from a null image with
+    the GPU solve's stopping rule (a fixed iteration count): its time and final cost."""
+    import oracle
+    tsd = getattr(prob, "tsd", None) if prob.lambda_s > 0 else None
+    sig = getattr(prob, "sigma_sd", None) if prob.lambda_s > 0 else None
+    t0 = time.perf_counter()
+    _, f, nit, nfev = oracle.solve_lbfgsb(prob, maxiter=maxiter, tsd=tsd, sigma_sd=sig,
+                                          pgtol=0.0, factr=0.0)
+    return {"seconds": round(time.perf_counter() - t0, 3), "iterations": nit, "evaluations": nfev,
+            "f": f, "cores": oracle.num_threads(), "kind": "oracle", "cpu": cpu_model()}
+
+
 def cpu_model():
     try:
         for line in open("/proc/cpuinfo"):
@@ -581,6 +594,13 @@ def main():
                                    "sample": f"{nv} sampled visibilities of the largest pair: direct-DFT "
                                              f"forward over the {prob.nb}^2 window + adjoint at every "
                                              f"window pixel ({dt:.1f} s)"}
+            if args.config == "c1" and "solve" in out:
+                # the oracle's own solve beside the GPU solves (30 iterations at C1: seconds)
+                osv = oracle_solve(prob, maxiter=30)
+                out["solve"]["oracle_scipy_lbfgsb"] = osv
+                g32 = out["solve"].get("fp32", {})
+                if g32.get("seconds"):
+                    out["solve"]["speedup_fp32_vs_oracle"] = round(osv["seconds"] / g32["seconds"], 1)
         print(json.dumps(out), flush=True)
     if world > 1:
         import torch.distributed as dist

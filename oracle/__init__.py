@@ -23,7 +23,54 @@ What it computes (Sect. 2 of the paper, the simplified coplanar forward model):
 * solver (Eq. 10): scipy's L-BFGS-B, the optimiser the paper calls, with
   bounds ``I >= 0`` when positivity is on and a null initial image.
 
-Every function that has a pin says which test pins it; there is no unpinned
-function.
+Beyond the simplified model:
+
+* the general SIN re-projection (Eq. 2) by bilinear interpolation on a
+  per-pointing grid of sampling locations, and its adjoint;
+* the full visibility equation (Eq. 1): the w-term phase and the 1/n factor
+  (``*_w`` functions of ``ivis_oracle.c``, selected by ``prob.wterm``);
+* the Toeplitz restatement of the data term (the exact expansion of Eq. 6):
+  ``psf_kernel`` and ``toeplitz_data_cost_grad``;
+* the appendix's short-spacing feathering and Rayleigh-Jeans factor;
+* the learned warm start's network (``oracle/unet.py``; not in the paper).
+
+Pins (``tests/test_oracle_pins.py`` unless named), each against something
+other than the oracle itself -- a numpy FFT, scipy, a closed form, brute
+force or the paper's printed numbers:
+
+* ``window``, ``window_adjoint``: transpose identity; the bilinear form on an
+  integer grid equals the window.
+* ``bilinear``, ``bilinear_adjoint``, ``pointing_window*``: scipy
+  ``map_coordinates``, exact linear fields, adjoint identity with off-sky and
+  non-finite grid entries, central differences of the data gradient.
+* ``model_vis``: a numpy FFT on grid-aligned uv, flat phase-centre source,
+  phase direction of a one-pixel offset, Hermitian symmetry and 1/cell
+  periodicity, linearity; with w: the geometric delay computed in the
+  equatorial frame.
+* ``adjoint``, ``adjoint_pixels``: adjoint identity to 1e-13, ``nb^2 ifft2``
+  on grid points, pixel subsets equal the full window; with w: adjoint
+  identity and central differences.
+* ``pair_model_vis``, ``data_cost_grad``, ``data_grad_pixels``: zero cost at
+  the noiseless truth, the weighted half square for one visibility, central
+  differences, pixel subsets equal the full gradient.
+* ``psf_kernel``, ``toeplitz_data_cost_grad``: the explicit normal matrix
+  built column by column, equality with the direct data term, the closed form
+  of a single zero-spacing visibility.
+* ``laplacian``, ``reg_cost_grad``: the paper's kernel (golden file), scipy's
+  zero-boundary convolution, the impulse response and hand-derived
+  biharmonic stencil (golden file), central differences.
+* ``dish_kernel``, ``dish_conv``, ``fusion_cost_grad``: half maximum and
+  truncation, scipy ``convolve2d``, flux preservation, zero at a consistent
+  map, central differences.
+* ``cost_grad``: the weighted sum of the three terms.
+* ``solve_lbfgsb``: scipy NNLS on a tiny well-conditioned problem, the
+  point-source flux of Sect. 4.1 (one channel, and ten channels against the
+  noise-propagated error).
+* ``feather``, ``rayleigh_jeans_factor``: limits and identities of the
+  transfer function, an impulse gives the Gaussian, the radio rule of thumb.
+* ``unet`` (``tests/test_oracle_unet.py``): parameter count, layers equal
+  scipy zero-padded cross-correlation, flat layout, central differences.
+
+There is no unpinned function.
 """
 from .classic3d import *  # noqa: F401,F403

@@ -28,8 +28,12 @@ def _worker(rank, world, port, q):
     assert (r, w) == (rank, world)
     bench.barrier(w)
     t = bench.allreduce_max(1.0 + rank, w)  # each rank's step time; the job's time is the max
-    seeds = bench.make_problem.__code__.co_varnames  # the problem factory takes a rank offset
-    q.put((rank, t, "seed_offset" in seeds))
+    # weak scaling: every rank builds its own independent problem of the same size
+    prob = bench.make_problem("c1", seed_offset=rank)
+    fp = float(sum(abs(p.uvw.astype("float64")).sum() for p in prob.pairs))
+    # the reference arm runs on rank 0 alone; the other ranks return without work
+    ref = bench.run_reference(None, rank, w) if rank != 0 else None
+    q.put((rank, t, prob.total_vis, fp, ref))
     import torch.distributed as dist
     dist.destroy_process_group()
 
@@ -44,6 +48,8 @@ def test_two_gloo_ranks_barrier_and_max_time():
     for p in procs:
         p.join(120)
         assert p.exitcode == 0
-    out = sorted(q.get(timeout=10) for _ in range(2))
+    out = sorted((q.get(timeout=10) for _ in range(2)), key=lambda o: o[0])
     assert [o[1] for o in out] == [2.0, 2.0]
-    assert all(o[2] for o in out)
+    assert out[0][2] == out[1][2] == 8190       # same units per rank
+    assert out[0][3] != out[1][3]               # but different (independently seeded) problems
+    assert out[1][4] is None

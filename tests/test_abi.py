@@ -62,3 +62,86 @@ def test_rayleigh_jeans_entry_point_matches_the_oracle():
     from paper_2609_17636_b300 import rayleigh_jeans
     for f in (1.0e8, 1.4204058e9, 2.3e10):
         assert abs(rayleigh_jeans(f) - oracle.rayleigh_jeans_factor(f)) <= 1e-14 * oracle.rayleigh_jeans_factor(f)
+
+
+GOOD = dict(n=64, nchan=1, npoint=1, nb=32, cell_rad=1e-5, precision=1, nufft_tol=1e-6,
+            kernel_width=0, lambda_r=0.0, lambda_s=0.0, positivity=1, serial_pairs=0, autotune=0,
+            toeplitz=0, wterm=0)
+
+# (overrides of a valid configuration, expected status, fragment of the error message)
+BAD = [
+    ({"n": 0}, 1, b">= 1"),
+    ({"npoint": 0}, 1, b">= 1"),
+    ({"nb": 8}, 1, b"power of two"),
+    ({"nb": 4096}, 1, b"power of two"),
+    ({"cell_rad": 0.0}, 1, b"cell_rad"),
+    ({"cell_rad": float("inf")}, 1, b"cell_rad"),
+    ({"precision": 7}, 1, b"precision"),
+    ({"kernel_width": 1}, 1, b"kernel_width"),
+    ({"kernel_width": 17}, 1, b"kernel_width"),
+    ({"nufft_tol": 1.5}, 1, b"nufft_tol"),
+    ({"lambda_r": -1.0}, 6, b"lambda"),
+    ({"lambda_s": float("nan")}, 6, b"lambda"),
+    ({"toeplitz": 1, "nb": 2048}, 1, b"toeplitz"),
+    ({"toeplitz": 1, "serial_pairs": 1}, 1, b"exclusive"),
+    ({"wterm": 1, "toeplitz": 1}, 1, b"wterm"),
+    ({"wterm": 1, "nb": 2048, "cell_rad": 1e-3}, 1, b"too far"),
+]
+
+
+@pytest.mark.parametrize("over,status,msg", BAD)
+def test_plan_configuration_checks_run_on_the_host(over, status, msg):
+    """Every configuration check of ivis_plan (include/ivis.h, ivis_config) happens before any
+    device call: a bad field returns its status, no plan, and a message naming the field."""
+    from paper_2609_17636_b300 import _lib
+    L = _lib.load()
+    cfg = _lib.Config(**{**GOOD, **over})
+    p = ctypes.c_void_p()
+    assert L.ivis_plan(ctypes.byref(cfg), None, ctypes.byref(p)) == status
+    assert not p.value
+    assert msg in L.ivis_last_error(None)
+
+
+def test_entry_points_reject_null_handles_without_a_device_call():
+    """A null plan or network handle is an argument error, never a crash; destroying NULL is a
+    no-op."""
+    from paper_2609_17636_b300 import _lib
+    L = _lib.load()
+    N = None
+    calls = {
+        "ivis_set_pointing": (N, 0, 0, 0, N), "ivis_set_pointing_grid": (N, 0, N),
+        "ivis_set_vis": (N, 0, 0, 0, N, N, N), "ivis_set_sd": (N, 0, N, 1.0, 1.0),
+        "ivis_prepare": (N,), "ivis_cost_grad": (N, N, N, N, N), "ivis_cost_grad_host": (N, N, N, N, N),
+        "ivis_cost_grad_async": (N, N, N, N), "ivis_predict": (N, N, 0, 0, N), "ivis_sd_predict": (N, N, N),
+        "ivis_solve": (N, N, 1, 10, 0.0, 0.0, N), "ivis_solve_target": (N, N, 1, 10, 0.0, 0.0, 0.0, N),
+        "ivis_dirty_image": (N, N, N), "ivis_feather": (N, N, N, 1.0, 1.0, N),
+        "ivis_get_nufft_params": (N, N, N, N), "ivis_profile": (N, 0),
+        "ivis_stage_times": (N, N, N, 0, N), "ivis_tuning": (N, N, N, N),
+        "ivis_launches_per_eval": (N, N), "ivis_get_stream": (N, N),
+    }
+    for name, args in calls.items():
+        assert getattr(L, name)(*args) == 1, name
+        assert L.ivis_last_error(None), name
+    assert L.ivis_destroy(N) == 0
+    unet_calls = {
+        "ivis_unet_num_params": (N, N), "ivis_unet_set_params": (N, N), "ivis_unet_get_params": (N, N),
+        "ivis_unet_get_grads": (N, N), "ivis_unet_forward": (N, N, N, 1, 8, 8),
+        "ivis_unet_backward": (N, N, N, 1, 8, 8, N), "ivis_unet_adam_step": (N, 1e-3, 0.9, 0.999, 1e-8),
+        "ivis_unet_use_tcgen05": (N, 1), "ivis_unet_warm_start": (N, N, N, 0, 8, 8, 1.0, 1.0, 1.0, N),
+        "ivis_unet_planes": (N, N, 0, 64, 1.0, 1.0, N, N),
+    }
+    for name, args in unet_calls.items():
+        assert getattr(L, name)(*args) == 1, name
+    assert b"null" in L.ivis_unet_last_error(None)
+    assert L.ivis_unet_destroy(N) == 0
+
+
+def test_network_and_allocation_free_entry_checks_run_on_the_host():
+    from paper_2609_17636_b300 import _lib
+    L = _lib.load()
+    u = ctypes.c_void_p()
+    assert L.ivis_unet_create(12, 1, 64, None, ctypes.byref(u)) == 1 and not u.value
+    assert b"multiple of 8" in L.ivis_unet_last_error(None)
+    assert L.ivis_unet_create(8, 0, 64, None, ctypes.byref(u)) == 1 and not u.value
+    assert L.ivis_sd_predict_noalloc(None, 16, 1, 3.0, None, None) == 1
+    assert b"null" in L.ivis_last_error(None)

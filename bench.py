@@ -157,7 +157,13 @@ def build_plan(prob, precision, serial=False, autotune=False, toeplitz=False, wt
 
 # ----------------------------------------------------------------- roofline model
 def stage_bytes(prob, plan):
-    """Algorithmic bytes per launch of each stage (measurement section)."""
+    """Algorithmic bytes per launch of each stage: what the step must move at least once.
+      degrid_spread      per visibility its record (coordinates, V, weight: 20 B in FP32,
+                         40 B in FP64) + per pair the fine grid read (F) and written (G)
+      fwd_fft / adj_fft  per pair the window (nb^2 reals), the nb x nf row-pass buffer written
+                         and read, and the nf^2 grid
+      zero_adjoint_grid  per pair the nf^2 grid
+      assemble_R         sky and gradient images + per pair the nb^2 window contribution"""
     w, beta, nf = plan.nufft_params()
     cs = 8 if plan.precision == "fp32" else 16      # complex sample
     rs = cs // 2                                     # real sample

@@ -229,7 +229,7 @@ ivis_status ivis_launches_per_eval(ivis_plan_t plan, int *count);
 ivis_status ivis_sd_predict_noalloc(const float *sky_dev, int n, int nchan, double fwhm_pix,
                                     float *out_dev, void *stream);
 
-/* Inputs of the learned warm start (not in the paper; spec extension): the dirty
+/* Inputs of the learned warm start (an extension; not in the paper): the dirty
  * image -grad Q(0) of each channel (the adjoint of the weighted data, Eqs. 5-6 at I = 0;
  * real [nchan][n][n] on the device) and, if beamw_dev is not NULL, the beam-weight map
  * sum_k A_k^2 of the linear mosaic of Sect. 4.3 (real [n][n]). */

@@ -43,11 +43,13 @@ force or the paper's printed numbers:
 * ``bilinear``, ``bilinear_adjoint``, ``pointing_window*``: scipy
   ``map_coordinates``, exact linear fields, adjoint identity with off-sky and
   non-finite grid entries, central differences of the data gradient.
-* ``model_vis``: a numpy FFT on grid-aligned uv, flat phase-centre source,
+* ``model_vis``: pure-Python brute force at off-grid uv (nb = 8), a numpy FFT
+  on grid-aligned uv, flat phase-centre source,
   phase direction of a one-pixel offset, Hermitian symmetry and 1/cell
   periodicity, linearity; with w: the geometric delay computed in the
   equatorial frame.
-* ``adjoint``, ``adjoint_pixels``: adjoint identity to 1e-13, ``nb^2 ifft2``
+* ``adjoint``, ``adjoint_pixels``: pure-Python brute force, adjoint identity to
+  1e-13, ``nb^2 ifft2``
   on grid points, pixel subsets equal the full window; with w: adjoint
   identity and central differences.
 * ``pair_model_vis``, ``data_cost_grad``, ``data_grad_pixels``: zero cost at

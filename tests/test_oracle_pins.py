@@ -97,6 +97,35 @@ def test_forward_linear_and_sparse_skip_consistent():
     assert np.allclose(lhs, rhs, atol=1e-11)
 
 
+def test_forward_and_adjoint_brute_force_off_grid():
+    """Eq. 3 and its adjoint written out term by term in pure Python (cmath, one loop per
+    index), independent of the C library and of numpy's vectorisation, at arbitrary off-grid
+    uv on a tiny window (nb = 8, 50 visibilities, odd and even offsets from the origin)."""
+    import cmath
+    rng = np.random.default_rng(12)
+    nb, cell, m = 8, 7e-5, 50
+    f = rng.standard_normal((nb, nb))
+    u, v = rng.uniform(-9e3, 9e3, m), rng.uniform(-9e3, 9e3, m)
+    c = rng.standard_normal(m) + 1j * rng.standard_normal(m)
+    fwd = []
+    for j in range(m):
+        acc = 0j
+        for q in range(nb):
+            for p in range(nb):
+                l, mm = (p - nb // 2) * cell, (q - nb // 2) * cell
+                acc += f[q, p] * cmath.exp(-2j * cmath.pi * (u[j] * l + v[j] * mm))
+        fwd.append(acc)
+    adj = np.zeros((nb, nb), complex)
+    for q in range(nb):
+        for p in range(nb):
+            l, mm = (p - nb // 2) * cell, (q - nb // 2) * cell
+            adj[q, p] = sum(c[j] * cmath.exp(2j * cmath.pi * (u[j] * l + v[j] * mm)) for j in range(m))
+    got_f = oracle.model_vis(f, cell, u, v)
+    got_a = oracle.adjoint(c, nb, cell, u, v)
+    assert np.max(np.abs(got_f - np.array(fwd))) <= 1e-12 * np.max(np.abs(fwd))
+    assert np.max(np.abs(got_a - adj)) <= 1e-12 * np.max(np.abs(adj))
+
+
 # ------------------------------------------------------------------------------ adjoint
 def test_adjoint_identity():
     rng = np.random.default_rng(5)

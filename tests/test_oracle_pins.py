@@ -511,6 +511,56 @@ def test_fusion_restores_the_large_scales_the_interferometer_misses():
     assert err[1.0][0] < 0.1 * err[0.0][0], err
 
 
+def test_joint_deconvolution_recovers_more_large_scale_structure_than_linear_mosaicking():
+    """Sect. 4.3: jointly deconvolving all pointings of a mosaic recovers the large scales
+    better than mosaicking independently deconvolved pointings. Seven pointings (hexagonal,
+    pitch 12 px, Gaussian beams of 12 px FWHM on 32 px windows) over a 48^2 lognormal sky,
+    no baseline below 3 cycles per window, positivity, no regularisation, 60 iterations each.
+    Linear mosaic (our reading; the paper prints no weights): sum_k A_k^2 x_k / sum_k A_k^2,
+    x_k the pointing's own solve. Inside the effective-beam mask (sum_k A_k^2 >= 0.2 of its
+    peak, as in the paper's figure) the k < 4 part of the joint image is closer to the truth
+    by more than a factor two."""
+    n, nb = 48, 32
+    cell = 20.0 * synth.ARCSEC
+    rng = synth.make_rng(1040)
+    enu = synth.antenna_layout(rng, 24, 1000.0)
+    ha = (np.arange(12) + 0.5 - 6) * (3000.0 / 86400.0) * 2 * np.pi
+    uvw = synth.uvw_tracks(enu, ha, synth.DEC_LMC_RAD, synth.LAT_ASKAP_RAD, synth.HI_FREQ_HZ)
+    k_uv = np.hypot(uvw[:, 0], uvw[:, 1]) * nb * cell
+    assert k_uv.max() < nb / 2
+    uvw = uvw[k_uv >= 3.0].astype(np.float32)
+    centres = np.array([[12, 24], [24, 24], [36, 24], [18, 14], [30, 14], [18, 34], [30, 34]])
+    sky = synth.lognormal_sky(rng, n)[None]
+    beam = synth.gaussian_beam(nb, 12.0).astype(np.float32)
+    beams = np.stack([beam] * len(centres))
+    m, sig = uvw.shape[0], 1e-3
+    pairs = [synth.VisSet(k, 0, uvw, np.full(m, 1 / sig ** 2, np.float32), synth.complex_noise(rng, m, sig))
+             for k in range(len(centres))]
+    prob = synth.Problem("mosaic", n, cell, 1, nb, centres, beams, pairs, sky, positivity=True)
+    attach_data(prob)
+    x_joint, *_ = oracle.solve_lbfgsb(prob, maxiter=60)
+    num, den = np.zeros((n, n)), np.zeros((n, n))
+    for k, pair in enumerate(pairs):
+        one = synth.Problem("pointing", n, cell, 1, nb, centres[k:k + 1], beams[k:k + 1],
+                            [synth.VisSet(0, 0, pair.uvw, pair.weight, pair.noise, pair.vis)], sky,
+                            positivity=True)
+        xk, *_ = oracle.solve_lbfgsb(one, maxiter=60)
+        a2 = oracle.window_adjoint(beam.astype(np.float64) ** 2, int(centres[k][0]), int(centres[k][1]), (n, n))
+        num += a2 * xk[0]
+        den += a2
+    x_lin = num / np.maximum(den, 1e-30)
+    mask = den >= 0.2 * den.max()
+    kk = np.hypot(np.fft.fftfreq(n)[:, None], np.fft.fftfreq(n)[None, :]) * n
+
+    def low_k_error(img):
+        F = np.fft.fft2((img - sky[0]) * mask)
+        F0 = np.fft.fft2(sky[0] * mask)
+        return np.linalg.norm(F[kk < 4]) / np.linalg.norm(F0[kk < 4])
+
+    e_joint, e_lin = low_k_error(x_joint[0]), low_k_error(x_lin)
+    assert e_joint < 0.5 * e_lin, (e_joint, e_lin)
+
+
 # ------------------------------------------------------- SIN re-projection grids (Eq. 2)
 def test_bilinear_on_integer_grid_is_the_window():
     rng = np.random.default_rng(30)

@@ -129,7 +129,8 @@ ivis_status ivis_set_pointing_grid(ivis_plan_t plan, int k, const float *grid_de
 
 /* Calibrated visibilities of pair (k, chan): m points, uvw float [m][3] in wavelengths
  * (w ignored: coplanar model of Eq. 3), vis float [m][2] (re, im), weight float [m]
- * = 1/sigma^2 from the SIGMA column (Eq. 5). m == 0 declares a pair with no data.
+ * = 1/sigma^2 from the SIGMA column (Eq. 5). m == 0 declares a pair with no data;
+ * 0 <= m <= 2^31 - 1025 (IVIS_ERR_ARG beyond).
  * The data are copied, converted to oversampled-grid coordinates and sorted by grid
  * tile on the device; with toeplitz = 1 the pair's Toeplitz spectrum, b window and constant
  * are computed here too. Errors: IVIS_ERR_NONFINITE for NaN/Inf or negative weights. */

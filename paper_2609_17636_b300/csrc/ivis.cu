@@ -1819,7 +1819,8 @@ ivis_status ivis_set_pointing_grid(ivis_plan_t p, int k, const float *grid_dev) 
 ivis_status ivis_set_vis(ivis_plan_t p, int k, int chan, int64_t m, const float *uvw_dev,
                          const float *vis_dev, const float *weight_dev) {
     if (!p) return fail(nullptr, IVIS_ERR_ARG, "null plan");
-    if (k < 0 || k >= p->cfg.npoint || chan < 0 || chan >= p->cfg.nchan || m < 0 || m > (int64_t)0x7fffffff)
+    // m + 1023 must stay within int (block counts of the per-visibility kernels)
+    if (k < 0 || k >= p->cfg.npoint || chan < 0 || chan >= p->cfg.nchan || m < 0 || m > (int64_t)0x7fffffff - 1024)
         return fail(p, IVIS_ERR_ARG, "bad pair index or visibility count");
     if (m > 0 && (!uvw_dev || !vis_dev || !weight_dev)) return fail(p, IVIS_ERR_ARG, "null visibility pointer");
     enter(p);

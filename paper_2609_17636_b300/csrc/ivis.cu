@@ -110,7 +110,6 @@ struct ivis_plan_s {
     double *jpart = nullptr, *kpart = nullptr, *rpart = nullptr, *cost_d = nullptr;
     double *cost_h = nullptr;  // pinned
     int nkpart = 0, nrpart = 0;
-    void *hstage = nullptr;    // pinned staging for the host-buffer entry point
     // Toeplitz form
     ivis_plan_s *toep_sub = nullptr;  // 2nb-window plan that computes T and b at set_vis
     void *wbeam_d = nullptr;          // [npoint][nb][nb] beam x dinv[p] dinv[q] (packed passes)
@@ -786,8 +785,16 @@ ivis_status set_vis_w(ivis_plan_s *p, PairHost &ph, int m, const float *uvw, con
     if ((s = alloc(p, &mmd, 2 * nbk * sizeof(float)))) return s;
     k_w_minmax<<<nbk, 256, 0, p->stream>>>(m, uvw, (float *)mmd);
     std::vector<float> hmm(2 * nbk);
-    CK(cudaMemcpyAsync(hmm.data(), mmd, 2 * nbk * sizeof(float), cudaMemcpyDeviceToHost, p->stream));
-    CK(cudaStreamSynchronize(p->stream));
+    {
+        cudaError_t e0 = cudaGetLastError();
+        if (e0 == cudaSuccess)
+            e0 = cudaMemcpyAsync(hmm.data(), mmd, 2 * nbk * sizeof(float), cudaMemcpyDeviceToHost, p->stream);
+        if (e0 == cudaSuccess) e0 = cudaStreamSynchronize(p->stream);
+        if (e0 != cudaSuccess) {
+            cleanup();
+            return fail(p, IVIS_ERR_CUDA, std::string("set_vis w range: ") + cudaGetErrorString(e0));
+        }
+    }
     double wmin = 1e300, wmax = -1e300;
     for (int b = 0; b < nbk; ++b) {
         wmin = std::min(wmin, (double)hmm[2 * b]);
@@ -1590,8 +1597,11 @@ ivis_status feather_impl(ivis_plan_s *p, const void *int_dev, const float *sd_de
             tw[j].y = (T)(-std::sin(a));
         }
         if ((s = alloc(p, &p->feather_tw_d, n * sizeof(C)))) return s;
-        CK(cudaMemcpy(p->feather_tw_d, tw.data(), n * sizeof(C), cudaMemcpyHostToDevice));
-        if ((s = alloc(p, &p->feather_b1_d, n * sizeof(T)))) return s;
+        const cudaError_t e0 = cudaMemcpy(p->feather_tw_d, tw.data(), n * sizeof(C), cudaMemcpyHostToDevice);
+        if (e0 != cudaSuccess || (s = alloc(p, &p->feather_b1_d, n * sizeof(T)))) {
+            dfree(p->feather_tw_d);  // set up both tables again on the next call
+            return e0 != cudaSuccess ? fail(p, IVIS_ERR_CUDA, std::string("feather twiddles: ") + cudaGetErrorString(e0)) : s;
+        }
     }
     // b1 at the DFT frequency of each index, k = j / n or (j - n) / n cycles per pixel
     const double sig = theta_pix / (2.0 * std::sqrt(2.0 * std::log(2.0)));

@@ -1059,6 +1059,18 @@ ivis_status autotune(ivis_plan_s *p) {
             std::fclose(f);
         }
     }
+    // column-FFT widths the kernels can run: shared memory, threads per CTA, columns per grid
+    const size_t csz = sizeof(typename cplx_of<T>::type);
+    const int tpl = p->nf / 16;
+    auto feasible_logc = [&](int lc) {
+        return lc >= 0 && lc <= 4 && (size_t)fft_smem_elems(p->nf, 1 << lc) * csz <= 200 * 1024 &&
+               (tpl << lc) <= (p->fp64 ? 512 : 1024) && (1 << lc) <= p->nf;
+    };
+    // a cached decision is used only if it is one the tuner itself could have made (the chunk
+    // buffers are sized for the smallest candidate chunk)
+    if (best_cap > 0 && (std::find(std::begin(TUNE_CHUNKS), std::end(TUNE_CHUNKS), best_cap) == std::end(TUNE_CHUNKS) ||
+                         !feasible_logc(best_logc)))
+        best_cap = best_logc = -1;
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
@@ -1075,13 +1087,10 @@ ivis_status autotune(ivis_plan_s *p) {
     const bool cached = best_cap > 0 && best_logc >= 0;
     if (!cached) {
         // column-FFT width: the feasible values around the shared-memory default
-        const size_t csz = sizeof(typename cplx_of<T>::type);
-        const int tpl = p->nf / 16, def = p->logc_cols;
+        const int def = p->logc_cols;
         float bt = 1e30f;
         for (int lc = std::max(0, def - 1); lc <= std::min(4, def + 1); ++lc) {
-            if ((size_t)fft_smem_elems(p->nf, 1 << lc) * csz > 200 * 1024 || (tpl << lc) > (p->fp64 ? 512 : 1024) ||
-                (1 << lc) > p->nf)
-                continue;
+            if (!feasible_logc(lc)) continue;
             p->logc_cols = lc;
             const float ms = timed([&] {
                 if (p->cfg.toeplitz) {

@@ -145,3 +145,37 @@ def test_network_and_allocation_free_entry_checks_run_on_the_host():
     assert L.ivis_unet_create(8, 0, 64, None, ctypes.byref(u)) == 1 and not u.value
     assert L.ivis_sd_predict_noalloc(None, 16, 1, 3.0, None, None) == 1
     assert b"null" in L.ivis_last_error(None)
+
+
+def test_header_is_plain_c_and_the_library_links_from_c(tmp_path):
+    """include/ivis.h compiles as strict C99 (no C++ or torch types cross the boundary) and a C
+    program links libivis.so and calls host-only entry points."""
+    import shutil
+    import subprocess
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    from paper_2609_17636_b300 import build
+    lib = build.build()
+    src = tmp_path / "use.c"
+    src.write_text(r'''
+#include <stdio.h>
+#include "ivis.h"
+int main(void) {
+    ivis_config cfg = {0};
+    ivis_plan_t plan = 0;
+    cfg.n = 64; cfg.nchan = 1; cfg.npoint = 1; cfg.nb = 48; cfg.cell_rad = 1e-5;
+    cfg.precision = IVIS_FP32; cfg.nufft_tol = 1e-6;
+    ivis_status s = ivis_plan(&cfg, 0, &plan);
+    printf("%d %d %.6e\n", (int)s, plan == 0, ivis_rayleigh_jeans(1.4204058e9));
+    return ivis_destroy(plan);
+}
+''')
+    exe = tmp_path / "use"
+    libdir = os.path.dirname(lib)
+    subprocess.run([gcc, "-std=c99", "-pedantic", "-Wall", "-Wextra", "-Werror", "-I", os.path.join(ROOT, "include"),
+                    str(src), "-L", libdir, "-livis", f"-Wl,-rpath,{libdir}", "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()
+    assert out[0] == "1" and out[1] == "1"  # nb = 48 is not a power of two: IVIS_ERR_ARG, no plan
+    import oracle
+    assert abs(float(out[2]) - oracle.rayleigh_jeans_factor(1.4204058e9)) <= 1e-6 * float(out[2])

@@ -127,6 +127,20 @@ ivis_status ivis_set_pointing(ivis_plan_t plan, int k, int cx, int cy, const flo
  * gradient contributions of gridded pointings are added with atomics (not bit-reproducible). */
 ivis_status ivis_set_pointing_grid(ivis_plan_t plan, int k, const float *grid_dev);
 
+/* Host-side pre-computation of such a grid for the common case of Eq. 2 where the sky image is
+ * itself a SIN (orthographic) projection: window pixel (q, p) of pointing k has direction
+ * cosines l = (p - nb/2) cell_rad, m = (q - nb/2) cell_rad about the pointing centre
+ * (ra_k, dec_k); the same direction, projected about the sky image's reference direction
+ * (ra0, dec0), lands at X = crpix_x + l' / cell_rad, Y = crpix_y + m' / cell_rad (the same pixel
+ * size; x grows with right ascension, y with declination, in both frames; angles in radians).
+ * grid_host: float [nb][nb][2] (X, Y), written on the host (no device call); a direction on the
+ * far side of the sky image's tangent point gets NaN (read as zero by the gather). With
+ * (ra_k, dec_k) = (ra0, dec0) and integer crpix the grid is the integer window of
+ * ivis_set_pointing centred at (crpix_x, crpix_y). Errors: IVIS_ERR_ARG for nb < 1, cell_rad
+ * not finite and > 0, non-finite angles or a null grid. */
+ivis_status ivis_sin_grid(int nb, double cell_rad, double ra_k, double dec_k, double ra0, double dec0,
+                          double crpix_x, double crpix_y, float *grid_host);
+
 /* Calibrated visibilities of pair (k, chan): m points, uvw float [m][3] in wavelengths
  * (w ignored: coplanar model of Eq. 3), vis float [m][2] (re, im), weight float [m]
  * = 1/sigma^2 from the SIGMA column (Eq. 5). m == 0 declares a pair with no data;

@@ -14,6 +14,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <limits>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -2077,6 +2078,44 @@ ivis_status ivis_feather(ivis_plan_t p, const void *int_dev, const float *sd_dev
     const double theta_pix = theta_rad / p->cfg.cell_rad;
     return p->fp64 ? feather_impl<double>(p, int_dev, sd_dev, theta_pix, sd_scale, out_dev)
                    : feather_impl<float>(p, int_dev, sd_dev, theta_pix, sd_scale, out_dev);
+}
+
+ivis_status ivis_sin_grid(int nb, double cell_rad, double ra_k, double dec_k, double ra0, double dec0,
+                          double crpix_x, double crpix_y, float *grid_host) {
+    if (!grid_host) return fail(nullptr, IVIS_ERR_ARG, "null grid pointer");
+    if (nb < 1 || !(cell_rad > 0.0) || !std::isfinite(cell_rad)) return fail(nullptr, IVIS_ERR_ARG, "nb >= 1 and cell_rad > 0 required");
+    for (double a : {ra_k, dec_k, ra0, dec0, crpix_x, crpix_y})
+        if (!std::isfinite(a)) return fail(nullptr, IVIS_ERR_ARG, "non-finite angle or reference pixel");
+    // orthonormal frames (east, north, centre) at a direction, in equatorial coordinates
+    auto frame = [](double ra, double dec, double e[3], double nn[3], double c[3]) {
+        const double sa = std::sin(ra), ca = std::cos(ra), sd = std::sin(dec), cd = std::cos(dec);
+        e[0] = -sa; e[1] = ca; e[2] = 0.0;
+        nn[0] = -sd * ca; nn[1] = -sd * sa; nn[2] = cd;
+        c[0] = cd * ca; c[1] = cd * sa; c[2] = sd;
+    };
+    double ek[3], nk[3], ck[3], e0[3], n0[3], c0[3];
+    frame(ra_k, dec_k, ek, nk, ck);
+    frame(ra0, dec0, e0, n0, c0);
+    // the rotation from pointing-frame to sky-frame direction cosines
+    double R[3][3];
+    const double *src[3] = {ek, nk, ck}, *dst[3] = {e0, n0, c0};
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) R[i][j] = dst[i][0] * src[j][0] + dst[i][1] * src[j][1] + dst[i][2] * src[j][2];
+    const float qnan = std::numeric_limits<float>::quiet_NaN();
+    for (int q = 0; q < nb; ++q)
+        for (int p = 0; p < nb; ++p) {
+            const double l = (p - nb / 2) * cell_rad, m = (q - nb / 2) * cell_rad, r2 = l * l + m * m;
+            float *g = grid_host + ((size_t)q * nb + p) * 2;
+            if (r2 >= 1.0) { g[0] = g[1] = qnan; continue; }
+            const double n = std::sqrt(1.0 - r2);
+            const double l1 = R[0][0] * l + R[0][1] * m + R[0][2] * n;
+            const double m1 = R[1][0] * l + R[1][1] * m + R[1][2] * n;
+            const double n1 = R[2][0] * l + R[2][1] * m + R[2][2] * n;
+            if (n1 <= 0.0) { g[0] = g[1] = qnan; continue; }
+            g[0] = (float)(crpix_x + l1 / cell_rad);
+            g[1] = (float)(crpix_y + m1 / cell_rad);
+        }
+    return IVIS_OK;
 }
 
 double ivis_rayleigh_jeans(double freq_hz) {

@@ -364,6 +364,22 @@ def unet_planes(a: torch.Tensor, b: torch.Tensor | None, sa: float, sb: float = 
     return out
 
 
+def sin_grid(nb: int, cell_rad: float, ra_k: float, dec_k: float, ra0: float, dec0: float,
+             crpix_x: float, crpix_y: float):
+    """Re-projection grid float32 [nb][nb][2] (X, Y) of a pointing centred at (ra_k, dec_k) into
+    a SIN sky image with reference direction (ra0, dec0) at pixel (crpix_x, crpix_y), angles in
+    radians (ivis_sin_grid, computed on the host). Pass it to Plan.set_pointing_grid."""
+    import numpy as np
+    L = _lib.load()
+    out = np.empty((nb, nb, 2), np.float32)
+    status = L.ivis_sin_grid(int(nb), float(cell_rad), float(ra_k), float(dec_k), float(ra0), float(dec0),
+                             float(crpix_x), float(crpix_y), ctypes.c_void_p(out.ctypes.data))
+    if status != 0:
+        msg = L.ivis_last_error(None)
+        raise IvisError(status, msg.decode() if msg else "")
+    return out
+
+
 def rayleigh_jeans(freq_hz: float) -> float:
     """Jy per square arcsecond per kelvin at freq_hz (ivis_rayleigh_jeans)."""
     return float(_lib.load().ivis_rayleigh_jeans(float(freq_hz)))

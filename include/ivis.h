@@ -127,19 +127,28 @@ ivis_status ivis_set_pointing(ivis_plan_t plan, int k, int cx, int cy, const flo
  * gradient contributions of gridded pointings are added with atomics (not bit-reproducible). */
 ivis_status ivis_set_pointing_grid(ivis_plan_t plan, int k, const float *grid_dev);
 
-/* Host-side pre-computation of such a grid for the common case of Eq. 2 where the sky image is
- * itself a SIN (orthographic) projection: window pixel (q, p) of pointing k has direction
- * cosines l = (p - nb/2) cell_rad, m = (q - nb/2) cell_rad about the pointing centre
- * (ra_k, dec_k); the same direction, projected about the sky image's reference direction
- * (ra0, dec0), lands at X = crpix_x + l' / cell_rad, Y = crpix_y + m' / cell_rad (the same pixel
- * size; x grows with right ascension, y with declination, in both frames; angles in radians).
- * grid_host: float [nb][nb][2] (X, Y), written on the host (no device call); a direction on the
- * far side of the sky image's tangent point gets NaN (read as zero by the gather). With
- * (ra_k, dec_k) = (ra0, dec0) and integer crpix the grid is the integer window of
- * ivis_set_pointing centred at (crpix_x, crpix_y). Errors: IVIS_ERR_ARG for nb < 1, cell_rad
- * not finite and > 0, non-finite angles or a null grid. */
-ivis_status ivis_sin_grid(int nb, double cell_rad, double ra_k, double dec_k, double ra0, double dec0,
-                          double crpix_x, double crpix_y, float *grid_host);
+/* Host-side pre-computation of such a grid (Eq. 2; the paper's pre-processing step): window
+ * pixel (q, p) of pointing k has direction cosines l = (p - nb/2) cell_rad,
+ * m = (q - nb/2) cell_rad in the SIN (orthographic) frame about the pointing centre
+ * (ra_k, dec_k); the same direction is projected about the sky image's reference direction
+ * (ra0, dec0) with the sky image's zenithal projection sky_proj:
+ *     IVIS_PROJ_SIN  (x, y) = (l', m')                         (orthographic)
+ *     IVIS_PROJ_TAN  (x, y) = (l', m') / n'                    (gnomonic)
+ *     IVIS_PROJ_ARC  (x, y) = (l', m') theta / sin(theta)       (zenithal equidistant,
+ *                                                                theta = acos n')
+ * where (l', m', n') are its direction cosines about (ra0, dec0), and lands at
+ * X = crpix_x + x / cell_rad, Y = crpix_y + y / cell_rad (the same pixel size; x grows with
+ * right ascension, y with declination, in both frames; angles in radians). grid_host: float
+ * [nb][nb][2] (X, Y), written on the host (no device call). Directions the projection cannot
+ * show (behind the tangent point for SIN and TAN, the antipode for ARC) get NaN, which the
+ * gather reads as zero. With (ra_k, dec_k) = (ra0, dec0), SIN and integer crpix the grid is the
+ * integer window of ivis_set_pointing centred at (crpix_x, crpix_y). Errors: IVIS_ERR_ARG for
+ * nb < 1, cell_rad not finite and > 0, non-finite angles, an unknown projection or a null
+ * grid. */
+enum { IVIS_PROJ_SIN = 0, IVIS_PROJ_TAN = 1, IVIS_PROJ_ARC = 2 };
+ivis_status ivis_reproject_grid(int nb, double cell_rad, double ra_k, double dec_k, double ra0,
+                                double dec0, double crpix_x, double crpix_y, int sky_proj,
+                                float *grid_host);
 
 /* Calibrated visibilities of pair (k, chan): m points, uvw float [m][3] in wavelengths
  * (w ignored: coplanar model of Eq. 3), vis float [m][2] (re, im), weight float [m]

@@ -14,6 +14,7 @@ LIB_PATH = os.path.join(HERE, "libivis.so")
 
 IVIS_FP64 = 0
 IVIS_FP32 = 1
+IVIS_PROJ = {"SIN": 0, "TAN": 1, "ARC": 2}
 
 STATUS = {0: "IVIS_OK", 1: "IVIS_ERR_ARG", 2: "IVIS_ERR_STATE", 3: "IVIS_ERR_OOM",
           4: "IVIS_ERR_CUDA", 5: "IVIS_ERR_TIMEOUT", 6: "IVIS_ERR_NONFINITE",
@@ -28,7 +29,7 @@ EXPORTS = ["ivis_plan", "ivis_set_pointing", "ivis_set_pointing_grid", "ivis_set
            "ivis_unet_get_params", "ivis_unet_forward", "ivis_unet_backward", "ivis_unet_get_grads",
            "ivis_unet_adam_step", "ivis_unet_use_tcgen05", "ivis_unet_destroy",
            "ivis_unet_last_error", "ivis_feather", "ivis_rayleigh_jeans", "ivis_unet_warm_start",
-           "ivis_unet_planes", "ivis_sin_grid"]
+           "ivis_unet_planes", "ivis_reproject_grid"]
 
 
 class IvisError(RuntimeError):
@@ -106,7 +107,7 @@ def load(path: str = LIB_PATH):
     L.ivis_unet_last_error.restype = ctypes.c_char_p
     L.ivis_feather.argtypes = [vp, vp, vp, d, d, vp]
     L.ivis_rayleigh_jeans.argtypes = [d]
-    L.ivis_sin_grid.argtypes = [i, d, d, d, d, d, d, d, vp]
+    L.ivis_reproject_grid.argtypes = [i, d, d, d, d, d, d, d, i, vp]
     L.ivis_rayleigh_jeans.restype = d
     for name in EXPORTS:
         if name not in ("ivis_last_error", "ivis_unet_last_error", "ivis_rayleigh_jeans"):

@@ -2080,9 +2080,11 @@ ivis_status ivis_feather(ivis_plan_t p, const void *int_dev, const float *sd_dev
                    : feather_impl<float>(p, int_dev, sd_dev, theta_pix, sd_scale, out_dev);
 }
 
-ivis_status ivis_sin_grid(int nb, double cell_rad, double ra_k, double dec_k, double ra0, double dec0,
-                          double crpix_x, double crpix_y, float *grid_host) {
+ivis_status ivis_reproject_grid(int nb, double cell_rad, double ra_k, double dec_k, double ra0, double dec0,
+                                double crpix_x, double crpix_y, int sky_proj, float *grid_host) {
     if (!grid_host) return fail(nullptr, IVIS_ERR_ARG, "null grid pointer");
+    if (sky_proj != IVIS_PROJ_SIN && sky_proj != IVIS_PROJ_TAN && sky_proj != IVIS_PROJ_ARC)
+        return fail(nullptr, IVIS_ERR_ARG, "unknown sky projection");
     if (nb < 1 || !(cell_rad > 0.0) || !std::isfinite(cell_rad)) return fail(nullptr, IVIS_ERR_ARG, "nb >= 1 and cell_rad > 0 required");
     for (double a : {ra_k, dec_k, ra0, dec0, crpix_x, crpix_y})
         if (!std::isfinite(a)) return fail(nullptr, IVIS_ERR_ARG, "non-finite angle or reference pixel");
@@ -2111,9 +2113,17 @@ ivis_status ivis_sin_grid(int nb, double cell_rad, double ra_k, double dec_k, do
             const double l1 = R[0][0] * l + R[0][1] * m + R[0][2] * n;
             const double m1 = R[1][0] * l + R[1][1] * m + R[1][2] * n;
             const double n1 = R[2][0] * l + R[2][1] * m + R[2][2] * n;
-            if (n1 <= 0.0) { g[0] = g[1] = qnan; continue; }
-            g[0] = (float)(crpix_x + l1 / cell_rad);
-            g[1] = (float)(crpix_y + m1 / cell_rad);
+            double f = 1.0;  // (x, y) = f (l', m')
+            if (sky_proj == IVIS_PROJ_ARC) {
+                const double st = std::sqrt(l1 * l1 + m1 * m1);  // sin(theta)
+                if (n1 <= -1.0 + 1e-12) { g[0] = g[1] = qnan; continue; }
+                f = st > 1e-12 ? std::atan2(st, n1) / st : 1.0;
+            } else {
+                if (n1 <= 0.0) { g[0] = g[1] = qnan; continue; }
+                if (sky_proj == IVIS_PROJ_TAN) f = 1.0 / n1;
+            }
+            g[0] = (float)(crpix_x + f * l1 / cell_rad);
+            g[1] = (float)(crpix_y + f * m1 / cell_rad);
         }
     return IVIS_OK;
 }

@@ -364,16 +364,20 @@ def unet_planes(a: torch.Tensor, b: torch.Tensor | None, sa: float, sb: float = 
     return out
 
 
-def sin_grid(nb: int, cell_rad: float, ra_k: float, dec_k: float, ra0: float, dec0: float,
-             crpix_x: float, crpix_y: float):
-    """Re-projection grid float32 [nb][nb][2] (X, Y) of a pointing centred at (ra_k, dec_k) into
-    a SIN sky image with reference direction (ra0, dec0) at pixel (crpix_x, crpix_y), angles in
-    radians (ivis_sin_grid, computed on the host). Pass it to Plan.set_pointing_grid."""
+def reproject_grid(nb: int, cell_rad: float, ra_k: float, dec_k: float, ra0: float, dec0: float,
+                   crpix_x: float, crpix_y: float, sky_proj: str = "SIN"):
+    """Re-projection grid float32 [nb][nb][2] (X, Y) of a pointing centred at (ra_k, dec_k)
+    (its window a SIN frame) into a sky image of zenithal projection sky_proj ("SIN", "TAN" or
+    "ARC") with reference direction (ra0, dec0) at pixel (crpix_x, crpix_y), angles in radians
+    (ivis_reproject_grid, computed on the host). Pass it to Plan.set_pointing_grid."""
     import numpy as np
+    if sky_proj not in _lib.IVIS_PROJ:
+        raise ValueError("sky_proj must be one of " + ", ".join(_lib.IVIS_PROJ))
     L = _lib.load()
     out = np.empty((nb, nb, 2), np.float32)
-    status = L.ivis_sin_grid(int(nb), float(cell_rad), float(ra_k), float(dec_k), float(ra0), float(dec0),
-                             float(crpix_x), float(crpix_y), ctypes.c_void_p(out.ctypes.data))
+    status = L.ivis_reproject_grid(int(nb), float(cell_rad), float(ra_k), float(dec_k), float(ra0),
+                                   float(dec0), float(crpix_x), float(crpix_y), _lib.IVIS_PROJ[sky_proj],
+                                   ctypes.c_void_p(out.ctypes.data))
     if status != 0:
         msg = L.ivis_last_error(None)
         raise IvisError(status, msg.decode() if msg else "")

@@ -49,7 +49,7 @@ def loss_and_grad(params, shapes, c, inp, tgt):
     out = _net(layers, hw, hb, torch.as_tensor(np.asarray(inp, dtype=np.float64)))
     loss = torch.mean((out - torch.as_tensor(np.asarray(tgt, dtype=np.float64))) ** 2)
     loss.backward()
-    return float(loss), p.grad.numpy().copy()
+    return float(loss.detach()), p.grad.numpy().copy()
 
 
 def _unpack_t(p, shapes, c):

@@ -45,7 +45,7 @@ def forward(params, shapes, c, inp):
 def loss_and_grad(params, shapes, c, inp, tgt):
     """Mean squared error against tgt [B][H][W] and its gradient w.r.t. the flat parameters."""
     p = torch.as_tensor(np.asarray(params, dtype=np.float64)).clone().requires_grad_(True)
-    layers, hw, hb = unpack(p, shapes, c) if False else _unpack_t(p, shapes, c)
+    layers, hw, hb = _unpack_t(p, shapes, c)
     out = _net(layers, hw, hb, torch.as_tensor(np.asarray(inp, dtype=np.float64)))
     loss = torch.mean((out - torch.as_tensor(np.asarray(tgt, dtype=np.float64))) ** 2)
     loss.backward()

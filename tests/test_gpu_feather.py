@@ -1,6 +1,5 @@
 """Feathering (the paper's short-spacing appendix) through ivis_feather against the oracle's
 numpy restatement, relative L2 1e-9 (FP64) and 1e-5 (FP32)."""
-import math
 
 import numpy as np
 import pytest

@@ -6,7 +6,6 @@ for the maximum of their step times. Those two collectives are what this test ex
 import os
 import socket
 
-import pytest
 import torch.multiprocessing as mp
 
 

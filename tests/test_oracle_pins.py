@@ -8,7 +8,6 @@ import math
 import os
 
 import numpy as np
-import pytest
 import scipy.ndimage
 import scipy.optimize
 import scipy.signal

@@ -1,0 +1,90 @@
+"""The pins catch plausible mistakes: each case plants one mistake in the oracle (on the CPU,
+by replacing one oracle function for the duration of the test) and checks that the pins aimed
+at it fail. A pin that still passed with the mistake in place would not be pinning anything.
+Every planted mistake changes what the method computes (conjugating the adjoint's output, for
+instance, does not: only its real part enters the gradient; using the forward's exponent sign
+in the adjoint does)."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import test_oracle_pins as pins
+
+
+def _conj_forward(orig):
+    return lambda f, cell, u, v, w=None: np.conj(orig(f, cell, u, v, w))
+
+
+def _swap_uv(orig):
+    return lambda f, cell, u, v, w=None: orig(f, cell, v, u, w)
+
+
+def _origin_off_by_one(orig):
+    return lambda f, cell, u, v, w=None: orig(np.roll(np.asarray(f, dtype=np.float64), 1, axis=1), cell, u, v, w)
+
+
+def _adjoint_forward_sign(orig):
+    # sum_j c_j exp(-2 pi i (u l + v m)): the forward's sign in the adjoint
+    return lambda c, nb, cell, u, v, w=None: np.conj(orig(np.conj(np.asarray(c)), nb, cell, u, v, w))
+
+
+def _no_half_in_j(orig):
+    def f(prob, sky, with_grad=True):
+        Q, g = orig(prob, sky, with_grad)
+        return 2.0 * Q, g
+    return f
+
+
+def _fwhm_as_sigma(orig):
+    return lambda fwhm: orig(fwhm * 2.0 * math.sqrt(2.0 * math.log(2.0)))
+
+
+def _fusion_grad_without_inverse_variance(orig):
+    def f(x, tsd, sigma_sd, fwhm):
+        K, g = orig(x, tsd, sigma_sd, fwhm)
+        return K, g * np.asarray(sigma_sd, dtype=np.float64)[:, None, None] ** 2
+    return f
+
+
+def _laplacian_centre_five(orig):
+    return lambda img: orig(img) + np.asarray(img, dtype=np.float64)
+
+
+def _window_transposed(orig):
+    return lambda img, cx, cy, nb: orig(img, cx, cy, nb).T
+
+
+MUTANTS = [
+    ("sign of the forward exponent", "model_vis", _conj_forward,
+     [pins.test_forward_offset_source_phase_direction, pins.test_forward_on_grid_points_equals_fft2]),
+    ("u and v exchanged (l, m transposed)", "model_vis", _swap_uv,
+     [pins.test_forward_offset_source_phase_direction, pins.test_forward_and_adjoint_brute_force_off_grid]),
+    ("pixel origin off by one", "model_vis", _origin_off_by_one,
+     [pins.test_forward_phase_centre_source_is_flat, pins.test_forward_and_adjoint_brute_force_off_grid]),
+    ("adjoint with the forward's exponent sign", "adjoint", _adjoint_forward_sign,
+     [pins.test_adjoint_identity, pins.test_adjoint_on_grid_points_equals_ifft2]),
+    ("the 1/2 of J dropped", "data_cost_grad", _no_half_in_j, [pins.test_data_cost_is_weighted_half_square]),
+    ("dish FWHM used as sigma", "dish_kernel", _fwhm_as_sigma, [pins.test_dish_kernel_half_maximum_and_truncation]),
+    ("fusion gradient without 1/sigma_sd^2", "fusion_cost_grad", _fusion_grad_without_inverse_variance,
+     [pins.test_fusion_zero_at_consistent_map_and_gradient]),
+    ("Laplacian centre weight 5", "laplacian", _laplacian_centre_five, [pins.test_regulariser_impulse_and_constant]),
+    ("window transposed", "window", _window_transposed, [pins.test_bilinear_on_integer_grid_is_the_window]),
+]
+
+
+@pytest.mark.parametrize("what,name,mutate,targets", MUTANTS, ids=[m[0] for m in MUTANTS])
+def test_pins_fail_on_a_planted_mistake(monkeypatch, what, name, mutate, targets):
+    bad = mutate(getattr(oracle.classic3d, name))
+    monkeypatch.setattr(oracle.classic3d, name, bad)
+    monkeypatch.setattr(oracle, name, bad)
+    for pin in targets:
+        with pytest.raises(AssertionError):
+            pin()
+
+
+def test_the_same_pins_pass_on_the_oracle_as_it_is():
+    for _, _, _, targets in MUTANTS:
+        for pin in targets:
+            pin()

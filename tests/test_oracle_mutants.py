@@ -56,6 +56,28 @@ def _window_transposed(orig):
     return lambda img, cx, cy, nb: orig(img, cx, cy, nb).T
 
 
+def _bilinear_xy_exchanged(orig):
+    return lambda img, grid: orig(img, np.ascontiguousarray(np.asarray(grid)[..., ::-1]))
+
+
+def _w_sign(orig):
+    return lambda f, cell, u, v, w=None: orig(f, cell, u, v, None if w is None else -np.asarray(w, dtype=np.float64))
+
+
+def _psf_conjugated(orig):
+    return lambda pair, nb, cell: np.conj(orig(pair, nb, cell))
+
+
+def _feather_weights_exchanged(orig):
+    # B applied to the interferometric map and 1 - B to the single-dish one
+    return lambda i_int, i_sd, theta_pix, sd_scale=1.0: orig(np.asarray(i_sd) * sd_scale, np.asarray(i_int) / sd_scale,
+                                                            theta_pix, sd_scale)
+
+
+def _rj_twice(orig):
+    return lambda freq_hz: 2.0 * orig(freq_hz)
+
+
 MUTANTS = [
     ("sign of the forward exponent", "model_vis", _conj_forward,
      [pins.test_forward_offset_source_phase_direction, pins.test_forward_on_grid_points_equals_fft2]),
@@ -71,6 +93,13 @@ MUTANTS = [
      [pins.test_fusion_zero_at_consistent_map_and_gradient]),
     ("Laplacian centre weight 5", "laplacian", _laplacian_centre_five, [pins.test_regulariser_impulse_and_constant]),
     ("window transposed", "window", _window_transposed, [pins.test_bilinear_on_integer_grid_is_the_window]),
+    ("re-projection grid's X and Y exchanged", "bilinear", _bilinear_xy_exchanged,
+     [pins.test_bilinear_reproduces_linear_functions_and_matches_scipy]),
+    ("sign of the w-term", "model_vis", _w_sign, [pins.test_wterm_phase_is_the_geometric_delay]),
+    ("Toeplitz kernel conjugated", "psf_kernel", _psf_conjugated, [pins.test_psf_kernel_centre_symmetry_and_normal_matrix]),
+    ("feathering weights exchanged", "feather", _feather_weights_exchanged, [pins.test_feather_limits_and_identities]),
+    ("Rayleigh-Jeans factor doubled", "rayleigh_jeans_factor", _rj_twice,
+     [pins.test_rayleigh_jeans_factor_matches_the_radio_rule_of_thumb]),
 ]
 
 

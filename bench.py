@@ -160,9 +160,9 @@ def stage_bytes(prob, plan):
     """Algorithmic bytes per launch of each stage: what the step must move at least once.
       degrid_spread      per visibility its record (coordinates, V, weight: 20 B in FP32,
                          40 B in FP64) + per pair the fine grid read (F) and written (G)
-      fwd_fft / adj_fft  per pair the window (nb^2 reals), the nb x nf row-pass buffer written
-                         and read, and the nf^2 grid
-      zero_adjoint_grid  per pair the nf^2 grid
+      fwd_fft / adj_fft  per pair the window in (or out) and its beam (nb^2 reals each), the
+                         row-pass buffer written and read (two windows share one complex
+                         nb x nf buffer: c nb nf / 2 each way per pair) and the nf^2 grid
       assemble_R         sky and gradient images + per pair the nb^2 window contribution"""
     w, beta, nf = plan.nufft_params()
     cs = 8 if plan.precision == "fp32" else 16      # complex sample
@@ -172,11 +172,11 @@ def stage_bytes(prob, plan):
     nb = prob.nb
     M = prob.total_vis
     npix = prob.nchan * prob.n * prob.n
+    fft = npair * (2 * rs * nb * nb + cs * nb * nf + cs * nf * nf)
     return {
         "degrid_spread": vis_b * M + 2 * cs * nf * nf * npair,
-        "fwd_fft": npair * (2 * rs * nb * nb + 2 * cs * nb * nf + cs * nf * nf),
-        "adj_fft": npair * (cs * nf * nf + 2 * cs * nb * nf + 2 * rs * nb * nb),
-        "zero_adjoint_grid": cs * nf * nf * npair,
+        "fwd_fft": fft,
+        "adj_fft": fft,
         "assemble_R": npix * rs * 2 + npair * nb * nb * rs,
     }
 

@@ -1,0 +1,43 @@
+"""The benchmark's algorithmic-byte accounting (the numerators of its roofline fractions) on the
+CPU: the formulas of the per-stage minimal traffic, and the C2 figures they give."""
+import os
+import sys
+
+sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+
+import bench  # noqa: E402
+import synth  # noqa: E402
+
+
+class _Plan:
+    def __init__(self, precision, nf):
+        self.precision, self.nf = precision, nf
+
+    def nufft_params(self):
+        return (7, 16.1, self.nf)
+
+
+def test_grid_pass_bytes_are_the_visibility_stream_plus_one_grid_read_and_write():
+    prob = synth.config_c2()
+    M, npair, nf = prob.total_vis, 7, 1024
+    sb = bench.stage_bytes(prob, _Plan("fp32", nf))
+    assert M == 1_363_257
+    assert sb["degrid_spread"] == 20 * M + 2 * 8 * nf * nf * npair == 144_705_652
+    sb64 = bench.stage_bytes(prob, _Plan("fp64", nf))
+    assert sb64["degrid_spread"] == 40 * M + 2 * 16 * nf * nf * npair
+
+
+def test_fft_bytes_count_the_packed_passes_once():
+    prob = synth.config_c2()
+    nb, nf = 512, 1024
+    sb = bench.stage_bytes(prob, _Plan("fp32", nf))
+    per_pair = 2 * 4 * nb * nb + 8 * nb * nf + 8 * nf * nf  # window + beam, half a row buffer each way, grid
+    assert sb["fwd_fft"] == sb["adj_fft"] == 7 * per_pair
+    assert sb["assemble_R"] == 2 * 4 * 512 * 512 + 7 * 4 * nb * nb
+
+
+def test_pairs_without_data_move_nothing():
+    prob = synth.small_mosaic(3, n=48, nb=32, nchan=1, npoint=3, ndump=2, n_ant=5)
+    prob.pairs[1].uvw = prob.pairs[1].uvw[:0]
+    sb = bench.stage_bytes(prob, _Plan("fp32", 64))
+    assert sb["fwd_fft"] == 2 * (2 * 4 * 32 * 32 + 8 * 32 * 64 + 8 * 64 * 64)

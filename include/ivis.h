@@ -110,8 +110,10 @@ typedef struct {
     int status;         /* 0 converged (pgtol/ftol), 1 maxiter reached, 2 line search stop */
 } ivis_solve_report;
 
-/* Create a plan. stream: a cudaStream_t (NULL = the legacy default stream).
- * Errors: IVIS_ERR_ARG for sizes out of range, IVIS_ERR_OOM, IVIS_ERR_CUDA. */
+/* Create a plan. stream: a cudaStream_t (NULL = the legacy default stream). Every field of
+ * cfg is checked on the host before any device call. Errors: IVIS_ERR_ARG for sizes, widths,
+ * tolerances or option combinations out of range; IVIS_ERR_NONFINITE for a negative or
+ * non-finite lambda_r / lambda_s; IVIS_ERR_OOM; IVIS_ERR_CUDA (e.g. no device). */
 ivis_status ivis_plan(const ivis_config *cfg, void *stream, ivis_plan_t *out);
 
 /* Pointing k (0 <= k < npoint): window centre at sky pixel (cx, cy) (any integers; the

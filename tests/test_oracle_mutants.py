@@ -113,6 +113,26 @@ def test_pins_fail_on_a_planted_mistake(monkeypatch, what, name, mutate, targets
             pin()
 
 
+def test_unet_tap_order_mistake_is_caught(monkeypatch):
+    """The network oracle reading the flat vector with dy and dx exchanged."""
+    import test_oracle_unet as upins
+    from oracle import unet as ou
+
+    def swapped(p, shapes, c):
+        out, off = [], 0
+        for (ca, _, cb, co, _) in shapes:
+            cin = ca + cb
+            w = p[off:off + co * 9 * cin].reshape(co, 3, 3, cin).permute(0, 3, 2, 1)
+            off += co * 9 * cin
+            out.append((w, p[off:off + co]))
+            off += co
+        return out, p[off:off + c], p[off + c:off + c + 1]
+
+    monkeypatch.setattr(ou, "_unpack_t", swapped)
+    with pytest.raises(AssertionError):
+        upins.test_flat_layout_tap_order()
+
+
 def test_the_same_pins_pass_on_the_oracle_as_it_is():
     for _, _, _, targets in MUTANTS:
         for pin in targets:

@@ -133,6 +133,30 @@ def test_unet_tap_order_mistake_is_caught(monkeypatch):
         upins.test_flat_layout_tap_order()
 
 
+def test_unet_concatenation_order_mistake_is_caught(monkeypatch):
+    """The network oracle concatenating the skip tensor before the upsampled one."""
+    import test_oracle_unet as upins
+    import torch
+    import torch.nn.functional as F
+    from oracle import unet as ou
+
+    def net_swapped(layers, hw, hb, x):
+        conv = lambda t, wb: torch.relu(F.conv2d(t, wb[0], wb[1], padding=1))
+        up = lambda t: F.interpolate(t, scale_factor=2, mode="nearest")
+        a0 = conv(x, layers[0]); a1 = conv(a0, layers[1])
+        a2 = conv(F.max_pool2d(a1, 2), layers[2]); a3 = conv(a2, layers[3])
+        a4 = conv(F.max_pool2d(a3, 2), layers[4]); a5 = conv(a4, layers[5])
+        a6 = conv(F.max_pool2d(a5, 2), layers[6]); a7 = conv(a6, layers[7])
+        a8 = conv(torch.cat([a5, up(a7)], 1), layers[8]); a9 = conv(a8, layers[9])
+        a10 = conv(torch.cat([a3, up(a9)], 1), layers[10]); a11 = conv(a10, layers[11])
+        a12 = conv(torch.cat([a1, up(a11)], 1), layers[12]); a13 = conv(a12, layers[13])
+        return torch.einsum("bchw,c->bhw", a13, hw) + hb
+
+    monkeypatch.setattr(ou, "_net", net_swapped)
+    with pytest.raises(AssertionError):
+        upins.test_decoder_concatenation_order_by_hand()
+
+
 def test_the_same_pins_pass_on_the_oracle_as_it_is():
     for _, _, _, targets in MUTANTS:
         for pin in targets:

@@ -57,3 +57,33 @@ def test_gradient_central_differences_tiny_net():
         lm, _ = ou.loss_and_grad(p - e, shapes, c, inp, tgt)
         fd = (lp - lm) / (2 * h)
         assert abs(fd - g[i]) <= 1e-6 * max(1.0, abs(g).max()) + 1e-4 * abs(g[i]), (i, fd, g[i])
+
+
+def _offsets(shapes):
+    """(weight offset, bias offset) of each 3x3 layer in the flat vector, and the head's."""
+    offs, off = [], 0
+    for (ca, _, cb, co, _) in shapes:
+        offs.append((off, off + co * 9 * (ca + cb)))
+        off += co * 9 * (ca + cb) + co
+    return offs, off
+
+
+def test_decoder_concatenation_order_by_hand():
+    """Decoder 'a' layers read the upsampled deeper tensor's channels first, then the skip
+    channels. Hand-built weights: every layer outputs the constant relu(bias) = its index + 1,
+    except that from decoder layer L on channel 0 is passed through the centre tap alone. The
+    output is then the deeper tensor's constant (L) -- the skip tensor's would differ."""
+    c = 8
+    shapes = synth.unet_layer_shapes(c)
+    offs, head = _offsets(shapes)
+    for L in (8, 10, 12):
+        p = np.zeros(synth.unet_num_params(c))
+        for i, (ca, _, cb, co, _) in enumerate(shapes):
+            w_off, b_off = offs[i]
+            if i < L:
+                p[b_off:b_off + co] = i + 1
+            else:  # W[co=0][tap=4 (dy=1, dx=1)][ci=0] = 1, zero bias
+                p[w_off + 0 * 9 * (ca + cb) + 4 * (ca + cb) + 0] = 1.0
+        p[head] = 1.0  # head weight of channel 0; head bias 0
+        out = ou.forward(p, shapes, c, np.zeros((1, 2, 16, 16)))
+        assert np.all(out == float(L)), (L, np.unique(out))

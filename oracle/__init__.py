@@ -76,7 +76,8 @@ force or the paper's printed numbers:
 * ``feather``, ``rayleigh_jeans_factor``: limits and identities of the
   transfer function, an impulse gives the Gaussian, the radio rule of thumb.
 * ``unet`` (``tests/test_oracle_unet.py``): parameter count, layers equal
-  scipy zero-padded cross-correlation, flat layout, central differences.
+  scipy zero-padded cross-correlation, flat layout, central differences, and a
+  hand-built network whose output reveals the decoder's concatenation order.
 
 There is no unpinned function.
 """

@@ -77,7 +77,8 @@ force or the paper's printed numbers:
   transfer function, an impulse gives the Gaussian, the radio rule of thumb.
 * ``unet`` (``tests/test_oracle_unet.py``): parameter count, layers equal
   scipy zero-padded cross-correlation, flat layout, central differences, and a
-  hand-built network whose output reveals the decoder's concatenation order.
+  hand-built networks whose outputs reveal the decoder's concatenation order,
+  max pooling and nearest upsampling.
 
 There is no unpinned function.
 """

@@ -133,28 +133,51 @@ def test_unet_tap_order_mistake_is_caught(monkeypatch):
         upins.test_flat_layout_tap_order()
 
 
-def test_unet_concatenation_order_mistake_is_caught(monkeypatch):
-    """The network oracle concatenating the skip tensor before the upsampled one."""
-    import test_oracle_unet as upins
+def _net_variant(swap_concat=False, avg_pool=False, bilinear_up=False):
     import torch
     import torch.nn.functional as F
-    from oracle import unet as ou
 
-    def net_swapped(layers, hw, hb, x):
+    def net(layers, hw, hb, x):
         conv = lambda t, wb: torch.relu(F.conv2d(t, wb[0], wb[1], padding=1))
-        up = lambda t: F.interpolate(t, scale_factor=2, mode="nearest")
+        if bilinear_up:
+            up = lambda t: F.interpolate(t, scale_factor=2, mode="bilinear", align_corners=False)
+        else:
+            up = lambda t: F.interpolate(t, scale_factor=2, mode="nearest")
+        pool = (lambda t: F.avg_pool2d(t, 2)) if avg_pool else (lambda t: F.max_pool2d(t, 2))
+        cat = (lambda deep, skip: torch.cat([skip, deep], 1)) if swap_concat else (lambda deep, skip: torch.cat([deep, skip], 1))
         a0 = conv(x, layers[0]); a1 = conv(a0, layers[1])
-        a2 = conv(F.max_pool2d(a1, 2), layers[2]); a3 = conv(a2, layers[3])
-        a4 = conv(F.max_pool2d(a3, 2), layers[4]); a5 = conv(a4, layers[5])
-        a6 = conv(F.max_pool2d(a5, 2), layers[6]); a7 = conv(a6, layers[7])
-        a8 = conv(torch.cat([a5, up(a7)], 1), layers[8]); a9 = conv(a8, layers[9])
-        a10 = conv(torch.cat([a3, up(a9)], 1), layers[10]); a11 = conv(a10, layers[11])
-        a12 = conv(torch.cat([a1, up(a11)], 1), layers[12]); a13 = conv(a12, layers[13])
+        a2 = conv(pool(a1), layers[2]); a3 = conv(a2, layers[3])
+        a4 = conv(pool(a3), layers[4]); a5 = conv(a4, layers[5])
+        a6 = conv(pool(a5), layers[6]); a7 = conv(a6, layers[7])
+        a8 = conv(cat(up(a7), a5), layers[8]); a9 = conv(a8, layers[9])
+        a10 = conv(cat(up(a9), a3), layers[10]); a11 = conv(a10, layers[11])
+        a12 = conv(cat(up(a11), a1), layers[12]); a13 = conv(a12, layers[13])
         return torch.einsum("bchw,c->bhw", a13, hw) + hb
+    return net
 
-    monkeypatch.setattr(ou, "_net", net_swapped)
+
+NET_MUTANTS = [
+    ("skip tensor concatenated first", dict(swap_concat=True), "test_decoder_concatenation_order_by_hand"),
+    ("average pooling", dict(avg_pool=True), "test_pooling_is_max_and_upsampling_is_nearest_by_hand"),
+    ("bilinear upsampling", dict(bilinear_up=True), "test_pooling_is_max_and_upsampling_is_nearest_by_hand"),
+]
+
+
+@pytest.mark.parametrize("what,kw,pin", NET_MUTANTS, ids=[m[0] for m in NET_MUTANTS])
+def test_unet_structure_mistakes_are_caught(monkeypatch, what, kw, pin):
+    import test_oracle_unet as upins
+    from oracle import unet as ou
+    monkeypatch.setattr(ou, "_net", _net_variant(**kw))
     with pytest.raises(AssertionError):
-        upins.test_decoder_concatenation_order_by_hand()
+        getattr(upins, pin)()
+
+
+def test_the_unmutated_network_variant_passes_its_pins(monkeypatch):
+    import test_oracle_unet as upins
+    from oracle import unet as ou
+    monkeypatch.setattr(ou, "_net", _net_variant())
+    upins.test_decoder_concatenation_order_by_hand()
+    upins.test_pooling_is_max_and_upsampling_is_nearest_by_hand()
 
 
 def test_the_same_pins_pass_on_the_oracle_as_it_is():

@@ -87,3 +87,24 @@ def test_decoder_concatenation_order_by_hand():
         p[head] = 1.0  # head weight of channel 0; head bias 0
         out = ou.forward(p, shapes, c, np.zeros((1, 2, 16, 16)))
         assert np.all(out == float(L)), (L, np.unique(out))
+
+
+def test_pooling_is_max_and_upsampling_is_nearest_by_hand():
+    """Hand-built weights that pass input plane 0 through channel 0 of every layer (centre tap
+    1, zero bias) make the network the composition of its resampling steps: three 2x2 max
+    poolings down and three nearest 2x upsamplings back, i.e. the maximum of each 8x8 block
+    repeated over the block (the input is non-negative, so the ReLUs pass it unchanged)."""
+    c = 8
+    shapes = synth.unet_layer_shapes(c)
+    offs, head = _offsets(shapes)
+    p = np.zeros(synth.unet_num_params(c))
+    for i, (ca, _, cb, co, _) in enumerate(shapes):
+        p[offs[i][0] + 4 * (ca + cb)] = 1.0  # W[0][tap 4][ci 0]
+    p[head] = 1.0
+    rng = np.random.default_rng(5)
+    inp = np.zeros((1, 2, 16, 24))
+    inp[0, 0] = rng.uniform(0.0, 1.0, (16, 24))
+    inp[0, 1] = rng.standard_normal((16, 24))  # plane 1 is not routed anywhere
+    out = ou.forward(p, shapes, c, inp)[0]
+    block = inp[0, 0].reshape(2, 8, 3, 8).max(axis=(1, 3))
+    assert np.array_equal(out, np.kron(block, np.ones((8, 8))))

@@ -180,6 +180,24 @@ def test_the_unmutated_network_variant_passes_its_pins(monkeypatch):
     upins.test_pooling_is_max_and_upsampling_is_nearest_by_hand()
 
 
+def test_solver_without_the_bound_is_caught(monkeypatch):
+    """The oracle's L-BFGS-B run without the I >= 0 bound of Eq. 10."""
+    orig = oracle.classic3d.solve_lbfgsb
+
+    def unbounded(prob, maxiter, *a, **kw):
+        saved = prob.positivity
+        prob.positivity = False
+        try:
+            return orig(prob, maxiter, *a, **kw)
+        finally:
+            prob.positivity = saved
+
+    monkeypatch.setattr(oracle.classic3d, "solve_lbfgsb", unbounded)
+    monkeypatch.setattr(oracle, "solve_lbfgsb", unbounded)
+    with pytest.raises(AssertionError):
+        pins.test_solver_reaches_nnls_solution_of_tiny_problem()
+
+
 def test_the_same_pins_pass_on_the_oracle_as_it_is():
     for _, _, _, targets in MUTANTS:
         for pin in targets:

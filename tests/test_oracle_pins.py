@@ -355,6 +355,7 @@ def test_solver_reaches_nnls_solution_of_tiny_problem():
                               lambda_r=0.0, lambda_s=0.0, sky_kind="points")
     prob.centres[:] = [4, 4]
     prob.sky_true = np.abs(np.random.default_rng(21).standard_normal((1, 8, 8)))
+    prob.sky_true[0, :2] = 0.0  # part of the answer sits on the bound of Eq. 10
     _with_data(prob)
     pair = prob.pairs[0]
     cols = []
@@ -372,6 +373,7 @@ def test_solver_reaches_nnls_solution_of_tiny_problem():
     assert f <= f_ref * (1 + 1e-6) + 1e-12
     assert np.linalg.cond(M) < 1e4
     assert np.allclose(x.ravel(), x_ref, atol=1e-3 * x_ref.max())
+    assert np.count_nonzero(x_ref == 0.0) >= 4  # the bound is active: the pin tests it
 
 
 def test_solver_point_source_flux_recovery():

@@ -78,6 +78,26 @@ def _rj_twice(orig):
     return lambda freq_hz: 2.0 * orig(freq_hz)
 
 
+def _laplacian_periodic(orig):
+    def f(img):
+        img = np.asarray(img, dtype=np.float64)
+        return (4 * img - np.roll(img, 1, 0) - np.roll(img, -1, 0) - np.roll(img, 1, 1) - np.roll(img, -1, 1))
+    return f
+
+
+def _data_gradient_without_beam(orig):
+    def f(prob, sky, with_grad=True):
+        saved = prob.beams
+        Q, _ = orig(prob, sky, with_grad=False)
+        prob.beams = np.ones_like(saved)
+        try:
+            _, g = orig(prob, sky, with_grad)
+        finally:
+            prob.beams = saved
+        return Q, g
+    return f
+
+
 MUTANTS = [
     ("sign of the forward exponent", "model_vis", _conj_forward,
      [pins.test_forward_offset_source_phase_direction, pins.test_forward_on_grid_points_equals_fft2]),
@@ -98,6 +118,10 @@ MUTANTS = [
     ("sign of the w-term", "model_vis", _w_sign, [pins.test_wterm_phase_is_the_geometric_delay]),
     ("Toeplitz kernel conjugated", "psf_kernel", _psf_conjugated, [pins.test_psf_kernel_centre_symmetry_and_normal_matrix]),
     ("feathering weights exchanged", "feather", _feather_weights_exchanged, [pins.test_feather_limits_and_identities]),
+    ("Laplacian with a periodic boundary", "laplacian", _laplacian_periodic,
+     [pins.test_laplacian_matches_scipy_with_zero_boundary]),
+    ("data gradient without the primary beam", "data_cost_grad", _data_gradient_without_beam,
+     [pins.test_data_gradient_central_differences]),
     ("Rayleigh-Jeans factor doubled", "rayleigh_jeans_factor", _rj_twice,
      [pins.test_rayleigh_jeans_factor_matches_the_radio_rule_of_thumb]),
 ]

@@ -41,3 +41,27 @@ def test_pairs_without_data_move_nothing():
     prob.pairs[1].uvw = prob.pairs[1].uvw[:0]
     sb = bench.stage_bytes(prob, _Plan("fp32", 64))
     assert sb["fwd_fft"] == 2 * (2 * 4 * 32 * 32 + 8 * 32 * 64 + 8 * 64 * 64)
+
+
+def test_clock_record_takes_the_median_inside_the_timed_region_and_the_active_reasons():
+    """The clocks object of the bench line: median SM clock of the samples taken inside the
+    timed region, the maximum clock, and every throttle reason seen active there."""
+    class _Proc:
+        def terminate(self):
+            pass
+
+        def wait(self, timeout=None):
+            return 0
+
+    cs = bench.ClockSampler(0)
+    cs.proc = _Proc()
+    row = lambda sm, hw, pc: [str(sm), "2032", "900.0", "0x0", hw, "Not Active", "Not Active", pc]
+    cs.rows = [(0.5, row(900, "Not Active", "Not Active")),      # before the timed region
+               (1.1, row(1900, "Not Active", "Not Active")),
+               (1.2, row(1950, "Not Active", "Active")),
+               (1.3, row(2000, "Not Active", "Not Active")),
+               (5.0, row(700, "Active", "Not Active"))]          # after it
+    cs.t_begin, cs.t_end = 1.0, 1.4
+    rec = cs.stop()
+    assert rec["sm_mhz"] == 1950.0 and rec["sm_max_mhz"] == 2032.0
+    assert rec["reasons"] == ["sw_power_cap"] and rec["samples_in_timed_region"] == 3

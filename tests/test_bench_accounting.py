@@ -65,3 +65,22 @@ def test_clock_record_takes_the_median_inside_the_timed_region_and_the_active_re
     rec = cs.stop()
     assert rec["sm_mhz"] == 1950.0 and rec["sm_max_mhz"] == 2032.0
     assert rec["reasons"] == ["sw_power_cap"] and rec["samples_in_timed_region"] == 3
+
+
+def test_reference_arm_line_has_the_contract_keys(monkeypatch):
+    """bench.py --impl reference: one JSON object with the contract's keys, its cpu_baseline
+    and an e2e object that moves no bytes (the oracle runs on the host). The oracle's timing is
+    replaced by a constant here; the arm's own arithmetic on it is what is checked."""
+    import argparse
+    monkeypatch.setattr(bench, "oracle_rate", lambda prob, nvis=None, seed=0: (1000.0, nvis or 64, (nvis or 64) / 1000.0))
+    args = argparse.Namespace(config="c2", steps=4, warmup=3)
+    out = bench.run_reference(args, 0, 1)
+    for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+                "scaling", "vs_baseline", "dtype", "data", "config", "impl", "cpu_baseline", "e2e"):
+        assert key in out, key
+    assert out["impl"] == "reference" and out["value"] == 1000.0 and out["higher_is_better"] is True
+    assert out["steps"] == 4 and out["warmup"] == 3 and out["n_gpus"] == 1
+    cb = out["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["value"] == out["value"] and cb["cores"] >= 1 and cb["sample"]
+    assert out["e2e"] == {"value": out["value"], "unit": out["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+    assert bench.run_reference(args, 1, 2) is None  # other ranks do no work

@@ -98,6 +98,17 @@ def _data_gradient_without_beam(orig):
     return f
 
 
+def _w_without_inverse_n(orig):
+    def f(img, cell, u, v, w=None):
+        if w is None:
+            return orig(img, cell, u, v)
+        img = np.asarray(img, dtype=np.float64)
+        c = (np.arange(img.shape[0]) - img.shape[0] // 2) * cell
+        n = np.sqrt(1.0 - c[:, None] ** 2 - c[None, :] ** 2)
+        return orig(img * n, cell, u, v, w)  # cancels the 1/n of Eq. 1
+    return f
+
+
 MUTANTS = [
     ("sign of the forward exponent", "model_vis", _conj_forward,
      [pins.test_forward_offset_source_phase_direction, pins.test_forward_on_grid_points_equals_fft2]),
@@ -116,6 +127,7 @@ MUTANTS = [
     ("re-projection grid's X and Y exchanged", "bilinear", _bilinear_xy_exchanged,
      [pins.test_bilinear_reproduces_linear_functions_and_matches_scipy]),
     ("sign of the w-term", "model_vis", _w_sign, [pins.test_wterm_phase_is_the_geometric_delay]),
+    ("1/n of Eq. 1 dropped", "model_vis", _w_without_inverse_n, [pins.test_wterm_phase_is_the_geometric_delay]),
     ("Toeplitz kernel conjugated", "psf_kernel", _psf_conjugated, [pins.test_psf_kernel_centre_symmetry_and_normal_matrix]),
     ("feathering weights exchanged", "feather", _feather_weights_exchanged, [pins.test_feather_limits_and_identities]),
     ("Laplacian with a periodic boundary", "laplacian", _laplacian_periodic,

@@ -179,3 +179,39 @@ int main(void) {
     assert out[0] == "1" and out[1] == "1"  # nb = 48 is not a power of two: IVIS_ERR_ARG, no plan
     import oracle
     assert abs(float(out[2]) - oracle.rayleigh_jeans_factor(1.4204058e9)) <= 1e-6 * float(out[2])
+
+
+def _prototypes():
+    """{name: [parameter declarations]} of every function include/ivis.h declares."""
+    protos = {}
+    for hdr in os.listdir(os.path.join(ROOT, "include")):
+        if not hdr.endswith(".h"):
+            continue
+        txt = open(os.path.join(ROOT, "include", hdr)).read()
+        txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+        for m in re.finditer(r"\b(ivis_\w+)\s*\(([^;{]*?)\)\s*;", txt, flags=re.S):
+            params = [p.strip() for p in m.group(2).split(",") if p.strip() and p.strip() != "void"]
+            protos[m.group(1)] = params
+    return protos
+
+
+def test_binding_prototypes_match_the_header():
+    """Every ctypes prototype of the binding has the header's parameter count and, per
+    parameter, a matching kind: pointer, int, int64_t, float or double."""
+    from paper_2609_17636_b300 import _lib
+    L = _lib.load()
+    protos = _prototypes()
+    assert set(protos) == set(_lib.EXPORTS)
+    kinds = {ctypes.c_int: "int", ctypes.c_int64: "int64_t", ctypes.c_double: "double", ctypes.c_float: "float"}
+    for name, params in protos.items():
+        argtypes = getattr(L, name).argtypes
+        assert argtypes is not None and len(argtypes) == len(params), (name, params, argtypes)
+        for decl, at in zip(params, argtypes):
+            if "*" in decl:
+                assert at is ctypes.c_void_p or issubclass(at, ctypes._Pointer) or at is ctypes.c_char_p, (name, decl, at)
+            else:
+                ctype = decl.rsplit(None, 1)[0].replace("const ", "").strip()
+                if ctype in ("ivis_plan_t", "ivis_unet_t"):
+                    assert at is ctypes.c_void_p, (name, decl, at)
+                else:
+                    assert kinds.get(at) == ctype, (name, decl, at)

@@ -81,3 +81,21 @@ def test_unrepresentable_directions_are_nan_and_bad_arguments_are_refused():
             reproject_grid(*args)
     with pytest.raises(ValueError):
         reproject_grid(8, 1e-3, 0, 0, 0, 0, 0, 0, "CAR")
+
+
+def test_pointings_on_the_sky_grid_become_integer_windows_the_others_grids():
+    """mosaic.place_pointing: the reference pointing itself is an integer window; a pointing a
+    few arcminutes off the reference needs a grid (the SIN frames differ by more than the
+    tolerance), and its window centre is its projected position rounded."""
+    from paper_2609_17636_b300.mosaic import place_pointing
+    nb, cell = 64, 7.0 * math.pi / (180 * 3600)
+    same = place_pointing(nb, cell, 1.4, -1.2, 1.4, -1.2, 256.0, 256.0)
+    assert same.kind == "window" and (same.cx, same.cy) == (256, 256) and same.max_offset == 0.0
+    off = place_pointing(nb, cell, 1.4 + 0.01, -1.2 + 0.003, 1.4, -1.2, 256.0, 256.0)
+    assert off.kind == "grid" and off.grid.shape == (nb, nb, 2) and off.max_offset > 1e-3
+    c = off.grid[nb // 2, nb // 2]
+    assert (off.cx, off.cy) == (int(np.rint(c[0])), int(np.rint(c[1])))
+    loose = place_pointing(nb, cell, 1.4 + 0.01, -1.2 + 0.003, 1.4, -1.2, 256.0, 256.0, tol_pix=10.0)
+    assert loose.kind == "window" and (loose.cx, loose.cy) == (off.cx, off.cy)
+    with pytest.raises(ValueError):  # the antipode cannot be shown
+        place_pointing(8, 1e-3, 0.2 + math.pi, -0.4, 0.2, 0.4, 0.0, 0.0)

@@ -68,7 +68,8 @@ force or the paper's printed numbers:
 * ``solve_lbfgsb``: scipy NNLS on a tiny well-conditioned problem, the
   point-source flux of Sect. 4.1 (one channel, and ten channels against the
   noise-propagated error), the noise-only behaviour of Sect. 4.2 (noise and
-  high spatial frequencies fall as lambda_r grows), the fusion property of
+  high spatial frequencies fall as lambda_r grows; noise grows away from the
+  pointing centre), the fusion property of
   Sects. 2.4 and 4.3 (the single-dish term restores the large scales and the
   total flux the interferometer misses), and the joint-deconvolution property
   of Sect. 4.3 (a jointly solved mosaic recovers the large scales better than

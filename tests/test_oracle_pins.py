@@ -471,6 +471,31 @@ def test_regularisation_strength_suppresses_noise_and_high_frequencies():
     assert high[-1] < 1e-2 * high[0], high
 
 
+def test_noise_grows_away_from_the_pointing_centre():
+    """Sect. 4.2: with the primary beam in the forward model, the noise of a reconstruction
+    from noise-only data grows away from the pointing centre, with and without the Laplacian
+    (the beam, not the regulariser, drives it). A 12 px FWHM beam on a 32^2 field: the image's
+    spread beyond one FWHM from the centre is more than 1.5 times that within half of it."""
+    n, cell, fwhm = 32, 3.0 * synth.ARCSEC, 12.0
+    rng = synth.make_rng(1020)
+    enu = synth.antenna_layout(rng, 24, 8000.0)
+    ha = (np.arange(12) + 0.5 - 6) * (3000.0 / 86400.0) * 2 * np.pi
+    uvw = synth.uvw_tracks(enu, ha, -69.04 * synth.DEG, -30.7 * synth.DEG, synth.HI_FREQ_HZ)
+    m, sig = uvw.shape[0], 5.0
+    pair = synth.VisSet(0, 0, uvw.astype(np.float32), np.full(m, 1 / sig ** 2, np.float32),
+                        synth.complex_noise(rng, m, sig))
+    beam = synth.gaussian_beam(n, fwhm).astype(np.float32)[None]
+    yy, xx = np.indices((n, n)) - n // 2
+    r = np.hypot(yy, xx)
+    for lr in (0.0, 1.0):
+        prob = synth.Problem("noise_only_beam", n, cell, 1, n, np.array([[n // 2, n // 2]]), beam, [pair],
+                             np.zeros((1, n, n)), lambda_r=lr, positivity=False)
+        _with_data(prob)
+        x, *_ = oracle.solve_lbfgsb(prob, maxiter=50)
+        inner, outer = x[0][r < fwhm / 2].std(), x[0][(r > fwhm) & (r < n / 2)].std()
+        assert outer > 1.5 * inner, (lr, inner, outer)
+
+
 def test_fusion_restores_the_large_scales_the_interferometer_misses():
     """Sect. 2.4 and 4.3: the interferometer cannot see the lowest spatial frequencies (here no
     baseline shorter than 3 cycles per field, and never k = 0); fused with a single-dish map of

@@ -67,7 +67,7 @@ force or the paper's printed numbers:
 * ``cost_grad``: the weighted sum of the three terms.
 * ``solve_lbfgsb``: scipy NNLS on a tiny well-conditioned problem, the
   point-source flux of Sect. 4.1 (one channel, and ten channels against the
-  noise-propagated error), the noise-only behaviour of Sect. 4.2 (noise and
+  noise-propagated error; a Laplacian spreads it to adjacent pixels), the noise-only behaviour of Sect. 4.2 (noise and
   high spatial frequencies fall as lambda_r grows; noise grows away from the
   pointing centre), the fusion property of
   Sects. 2.4 and 4.3 (the single-dish term restores the large scales and the

@@ -406,6 +406,36 @@ def test_solver_point_source_flux_recovery():
     assert pg < 1e-2 * np.abs(g0).max()
 
 
+def test_regularisation_spreads_point_source_flux_over_adjacent_pixels():
+    """Sect. 4.1: a regulariser moves an unresolved source's flux from its pixel to the adjacent
+    ones, so lambda_r = 0 is the setting for point-source photometry. Same problem as the
+    flux-recovery pin: with lambda_r = 0 each source pixel holds its flux within 1 %; with a
+    Laplacian strong enough to matter (lambda_r = 1e8, against sum w = 8.2e9 per pixel) every
+    source pixel loses more than 10 % and its eight neighbours gain."""
+    rng = synth.make_rng(1001)
+    n = 64
+    cell = 8.0 * synth.ARCSEC
+    enu = synth.antenna_layout(rng, 36, 6000.0)
+    ha = np.linspace(-5, 5, 13) * 15 * synth.DEG
+    uvw = synth.uvw_tracks(enu, ha, synth.DEC_LMC_RAD, synth.LAT_ASKAP_RAD, synth.HI_FREQ_HZ)
+    sky = synth.point_source_sky(rng, n, 5, 8, 56, 0.1, 1.0)[None]
+    beam = synth.gaussian_beam(n, synth.DEG / cell).astype(np.float32)[None]
+    pair = synth.VisSet(0, 0, uvw.astype(np.float32), np.full(uvw.shape[0], 1e6, np.float32),
+                        synth.complex_noise(rng, uvw.shape[0], 1e-3))
+    ys, xs = np.nonzero(sky[0])
+    peak, ring = {}, {}
+    for lr in (0.0, 1e8):
+        prob = synth.Problem("c1_lite", n, cell, 1, n, np.array([[n // 2, n // 2]]), beam, [pair], sky,
+                             lambda_r=lr, positivity=True)
+        _with_data(prob)
+        x, *_ = oracle.solve_lbfgsb(prob, maxiter=30)
+        peak[lr] = x[0][ys, xs] / sky[0][ys, xs]
+        ring[lr] = np.array([x[0][y - 1:y + 2, c - 1:c + 2].sum() - x[0][y, c] for y, c in zip(ys, xs)])
+    assert np.all(np.abs(peak[0.0] - 1.0) <= 0.01), peak[0.0]
+    assert np.all(peak[1e8] < 0.9), peak[1e8]
+    assert np.all(ring[1e8] > ring[0.0] + 0.05 * sky[0][ys, xs]), (ring[0.0], ring[1e8])
+
+
 def test_point_source_spectrum_fixture_matches_stated_law():
     rows, meta = _load_golden("point_source_spectrum.txt")
     assert rows.shape == (10, 2) and meta["noise_jy"] == 0.1

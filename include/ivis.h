@@ -99,6 +99,12 @@ typedef struct {
                            window corner. Each visibility is stored W times (once per plane of
                            its kernel support). Excludes toeplitz and serial_pairs; needs the
                            window within l^2 + m^2 < 1/4; ivis_dirty_image is not available. */
+    int grid_tile;      /* edge (fine-grid cells) of the tiles of the gridding work list
+                           (Eqs. 3-6: each tile's patch of the oversampled grids is staged in
+                           shared memory): 0 = default (64 in FP32 with kernel_width <= 8,
+                           else 32; with autotune = 1 the autotuner times both and keeps the
+                           faster), 32, or 64 (FP32 only; needs nb >= 32). Any other value:
+                           IVIS_ERR_ARG. The result does not depend on it beyond rounding.   */
 } ivis_config;
 
 typedef struct {

@@ -28,6 +28,7 @@
 #include "kernels_sdconv.cuh"
 #include "kernels_toeplitz.cuh"
 #include "kernels_wstack.cuh"
+#include "kernels_grid.cuh"
 
 using namespace ivis;
 
@@ -40,7 +41,7 @@ struct PairHost {
     int m = 0;
     void *coord = nullptr, *vis = nullptr, *w = nullptr;
     int *orig = nullptr;
-    std::vector<int> tile_count;  // per tile of the fine grid
+    std::vector<int> tile_count;  // per sort bin of the fine grid, in sort order
     // Toeplitz form (toeplitz = 1): spectrum of Re H [kx][ky], window b [nb][nb], constant C
     void *that = nullptr, *bwin = nullptr;
     double qconst = 0.0;
@@ -48,7 +49,7 @@ struct PairHost {
     int nplane = 0;
     double w0 = 0.0;                       // plane k sits at w0 + k dw
     std::vector<int> plane_start;          // first sorted entry of each plane (nplane + 1)
-    std::vector<int> plane_tile_count;     // [nplane][ntiles]
+    std::vector<int> plane_tile_count;     // [nplane][ntiles], bins in sort order
     void *e_coord = nullptr, *e_val = nullptr, *e_w = nullptr;
     int *e_orig = nullptr, *e_pos = nullptr;
     void *v_vis = nullptr, *v_w = nullptr, *v_phase = nullptr, *v_wk = nullptr;  // caller order
@@ -72,7 +73,8 @@ struct ivis_plan_s {
     size_t rsz = 8;  // sizeof(real)
     int nf = 0, lognf = 0, W = 0;
     double beta = 0.0;
-    int tile = 32, ntx = 0, ntiles = 0;
+    int tile = 32, ntx = 0, ntiles = 0;  // sort bins (32 x 32 cells) of the fine grid
+    int gtile = 32;                      // tile edge of the grid-pass work list (32 or 64)
     int logc_cols = 0;  // log2 columns per CTA in the column FFT passes
     int chunk_cap = 1024;  // max visibilities per grid-pass chunk
     std::string tuned;     // autotuner decision (for reporting)
@@ -92,7 +94,7 @@ struct ivis_plan_s {
     bool prepared = false;
     int nslot = 0;
     std::vector<int> slot_pair;            // slot -> pair index
-    std::vector<const int *> slot_tc;      // slot -> per-tile visibility (entry) counts
+    std::vector<const int *> slot_tc;      // slot -> per-bin visibility (entry) counts
     std::vector<int> slot_m;               // slot -> visibilities (entries)
     std::vector<int> chunk_first;          // slot -> first chunk (size nslot + 1)
     int nchunk = 0;
@@ -340,23 +342,46 @@ ivis_status upload_twiddles(ivis_plan_s *p) {
 }
 
 // ------------------------------------------------------------------ kernel dispatch on W
-template <typename T, int MODE>
-cudaError_t launch_grid_pass(ivis_plan_s *p, int first_chunk, int nchunk, double *jpart,
-                             void *pred) {
+// FP32 cost+gradient passes with kernel width <= 8 run k_grid_cg (one lane per kernel column);
+// the FP64 path, wider kernels, the predict and spread-only modes run k_grid_pass.
+inline bool use_grid_cg(const ivis_plan_s *p) { return !p->fp64 && p->W <= 8; }
+
+template <typename T, int MODE, int TS>
+cudaError_t launch_grid_pass_ts(ivis_plan_s *p, int first_chunk, int nchunk, double *jpart,
+                                void *pred) {
     typedef typename cplx_of<T>::type C;
-    if (nchunk <= 0) return cudaSuccess;
-    const int PW = p->tile + p->W - 1;
-    size_t smem = (size_t)PW * PW * sizeof(C) * (MODE == MODE_COSTGRAD ? 2 : 1);
     const Chunk *ch = p->chunks_d + first_chunk;
     const PairData<T> *pd = (const PairData<T> *)p->pdata_d;
     const C *F = (const C *)p->F;
     C *G = (C *)p->G;
+    if constexpr (MODE == MODE_COSTGRAD && sizeof(T) == 4) {
+        if (use_grid_cg(p)) {
+#define CG_CASE(WW)                                                                                   \
+    case WW: {                                                                                        \
+        auto kern = k_grid_cg<WW, TS>;                                                                \
+        const size_t sm = GridCG<WW, TS>::SMEM;                                                       \
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);             \
+        kern<<<nchunk, GridCG<WW, TS>::THREADS, sm, p->stream>>>(ch, (const PairData<float> *)pd,     \
+                                                                (const float2 *)F, (float2 *)G,       \
+                                                                p->lognf, p->kpoly_d, jpart);         \
+        return cudaGetLastError();                                                                    \
+    }
+            switch (p->W) {
+                CG_CASE(2) CG_CASE(3) CG_CASE(4) CG_CASE(5) CG_CASE(6) CG_CASE(7) CG_CASE(8)
+                default: return cudaErrorInvalidValue;
+            }
+#undef CG_CASE
+        }
+    }
+    const int PW = TS + p->W - 1;
+    size_t smem = (size_t)PW * PW * sizeof(C) * (MODE == MODE_COSTGRAD ? 2 : 1);
     T beta = (T)p->beta;
+    const int ntx = p->nf / TS;
 #define GP_CASE(WW)                                                                           \
     case WW: {                                                                                \
-        auto kern = k_grid_pass<T, WW, MODE>;                                                 \
+        auto kern = k_grid_pass<T, WW, MODE, TS>;                                             \
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);   \
-        kern<<<nchunk, 256, smem, p->stream>>>(ch, pd, F, G, p->lognf, p->ntx, beta, p->kpoly_d, \
+        kern<<<nchunk, 256, smem, p->stream>>>(ch, pd, F, G, p->lognf, ntx, beta, p->kpoly_d, \
                                                jpart, (C *)pred);                             \
         break;                                                                                \
     }
@@ -369,6 +394,19 @@ cudaError_t launch_grid_pass(ivis_plan_s *p, int first_chunk, int nchunk, double
     return cudaGetLastError();
 }
 
+template <typename T, int MODE>
+cudaError_t launch_grid_pass(ivis_plan_s *p, int first_chunk, int nchunk, double *jpart,
+                             void *pred) {
+    if (nchunk <= 0) return cudaSuccess;
+    if constexpr (sizeof(T) == 4) {
+        if (p->gtile == 64) return launch_grid_pass_ts<T, MODE, 64>(p, first_chunk, nchunk, jpart, pred);
+    }
+    return launch_grid_pass_ts<T, MODE, 32>(p, first_chunk, nchunk, jpart, pred);
+}
+
+void stage_begin(ivis_plan_s *p, const char *name, cudaStream_t st, int &si);
+void stage_end(ivis_plan_s *p, cudaStream_t st, int &si);
+
 // Row passes: 256 threads = lpb lines of nf/16 threads. Column passes: ncol x nf/16 threads.
 // Forward passes for slots [slot0, slot0 + nslots) (all slots by default).
 // Whole-plan passes over real windows (no w-planes) carry two slots per transform.
@@ -376,8 +414,10 @@ bool packed_pass(const ivis_plan_s *p, int slot0, int nslots) {
     return slot0 == 0 && nslots == p->nslot && !p->cfg.wterm && !p->cfg.serial_pairs;
 }
 
+// si: when given, the row and column passes of the packed path are recorded as two stages
+// of the profiled graph (fwd_rows, fwd_cols).
 template <typename T>
-cudaError_t launch_forward(ivis_plan_s *p, const void *sky, int slot0 = 0, int nslots = -1) {
+cudaError_t launch_forward(ivis_plan_s *p, const void *sky, int slot0 = 0, int nslots = -1, int *si = nullptr) {
     typedef typename cplx_of<T>::type C;
     const int nb = p->cfg.nb, nf = p->nf, tpl = nf / 16, lpb = 256 / tpl;
     if (nslots < 0) nslots = p->nslot;
@@ -386,14 +426,18 @@ cudaError_t launch_forward(ivis_plan_s *p, const void *sky, int slot0 = 0, int n
         dim3 gr((nb + lpb - 1) / lpb, npk);
         size_t smem_row = (size_t)fft_smem_elems(nf, lpb) * sizeof(C);
         cudaFuncSetAttribute(k_fwd_rows_pk<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_row);
+        if (si) stage_begin(p, "fwd_rows", p->stream, *si);
         k_fwd_rows_pk<T><<<gr, 256, smem_row, p->stream>>>(
             (const T *)sky, (const T *)p->wbeam_d, p->pinfo_d, nslots, (C *)p->rowbuf,
             p->cfg.n, nb, p->lognf, (const C *)p->tw_d, (const float2 *)p->grids_d);
+        if (si) stage_end(p, p->stream, *si);
         dim3 gc(nf / (2 << lc), npk);
         size_t smem_col = (size_t)fft_smem_elems(nf, 2 << lc) * sizeof(C);
         cudaFuncSetAttribute(k_fwd_cols_pk<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_col);
+        if (si) stage_begin(p, "fwd_cols", p->stream, *si);
         k_fwd_cols_pk<T><<<gc, tpl << (lc + 1), smem_col, p->stream>>>(
             (const C *)p->rowbuf, (C *)p->F, nslots, nb, p->lognf, lc, (const C *)p->tw_d);
+        if (si) stage_end(p, p->stream, *si);
         return cudaGetLastError();
     }
     const PairInfo *pinfo = p->pinfo_d + slot0;
@@ -416,7 +460,7 @@ cudaError_t launch_forward(ivis_plan_s *p, const void *sky, int slot0 = 0, int n
 
 // Adjoint passes for slots [slot0, slot0 + nslots) (all slots by default).
 template <typename T>
-cudaError_t launch_adjoint(ivis_plan_s *p, int slot0 = 0, int nslots = -1) {
+cudaError_t launch_adjoint(ivis_plan_s *p, int slot0 = 0, int nslots = -1, int *si = nullptr) {
     typedef typename cplx_of<T>::type C;
     const int nb = p->cfg.nb, nf = p->nf, tpl = nf / 16, lpb = 256 / tpl;
     if (nslots < 0) nslots = p->nslot;
@@ -425,14 +469,18 @@ cudaError_t launch_adjoint(ivis_plan_s *p, int slot0 = 0, int nslots = -1) {
         dim3 gc(nf / (2 << lc), npk);
         size_t smem_col = (size_t)fft_smem_elems(nf, 2 << lc) * sizeof(C);
         cudaFuncSetAttribute(k_adj_cols_pk<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_col);
+        if (si) stage_begin(p, "adj_cols", p->stream, *si);
         k_adj_cols_pk<T><<<gc, tpl << (lc + 1), smem_col, p->stream>>>((C *)p->G, (C *)p->rowbuf, nslots, nb,
                                                                        p->lognf, lc, (const C *)p->tw_d);
+        if (si) stage_end(p, p->stream, *si);
         dim3 gr((nb + lpb - 1) / lpb, npk);
         size_t smem_row = (size_t)fft_smem_elems(nf, lpb) * sizeof(C);
         cudaFuncSetAttribute(k_adj_rows_pk<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_row);
+        if (si) stage_begin(p, "adj_rows", p->stream, *si);
         k_adj_rows_pk<T><<<gr, 256, smem_row, p->stream>>>((const C *)p->rowbuf, (const T *)p->wbeam_d, p->pinfo_d,
                                                            nslots, (T *)p->contrib, p->cfg.n,
                                                            nb, p->lognf, (const C *)p->tw_d);
+        if (si) stage_end(p, p->stream, *si);
         return cudaGetLastError();
     }
     C *G = (C *)p->G + (size_t)slot0 * nf * nf;
@@ -610,19 +658,16 @@ cudaError_t enqueue_eval(ivis_plan_s *p, bool capture) {
             }
             stage_end(p, p->stream, si);
         } else {
-            stage_begin(p, "fwd_fft", p->stream, si);
-            if ((e = launch_forward<T>(p, p->x)) != cudaSuccess) return e;
+            // one stage per kernel: fwd_rows, fwd_cols, degrid_spread, adj_cols, adj_rows
+            if ((e = launch_forward<T>(p, p->x, 0, -1, &si)) != cudaSuccess) return e;
             launches += 2;
-            stage_end(p, p->stream, si);
             stage_begin(p, "degrid_spread", p->stream, si);
             if ((e = launch_grid_pass<T, MODE_COSTGRAD>(p, 0, p->nchunk, p->jpart, nullptr)) != cudaSuccess)
                 return e;
             launches += 1;
             stage_end(p, p->stream, si);
-            stage_begin(p, "adj_fft", p->stream, si);
-            if ((e = launch_adjoint<T>(p)) != cudaSuccess) return e;
+            if ((e = launch_adjoint<T>(p, 0, -1, &si)) != cudaSuccess) return e;
             launches += 2;
-            stage_end(p, p->stream, si);
         }
     }
     if (fork) cudaStreamWaitEvent(p->stream, p->ev_join, 0);
@@ -895,6 +940,7 @@ ivis_status toeplitz_pair(ivis_plan_s *p, PairHost &ph, int m, const float *uvw,
         c2.serial_pairs = 0;
         c2.autotune = 0;
         c2.toeplitz = 0;
+        c2.grid_tile = 0;
         // T and b enter the cost multiplied by the data's energy C, which near a fit's optimum
         // exceeds Q by orders of magnitude: compute them with the widest kernel (FP64, about
         // 1e-15) or one cell wider than the plan's (FP32, at its rounding floor)
@@ -1010,18 +1056,31 @@ void release_prepared(ivis_plan_s *p) {
     p->prepared = false;
 }
 
-// Work list of the grid pass: per slot, per non-empty tile, runs of at most cap visibilities.
-constexpr int TUNE_CHUNKS[] = {256, 512, 1024, 2048};
+// Work list of the grid pass: per slot, per non-empty tile (edge p->gtile), runs of at most
+// cap visibilities. The sort bins are 32 x 32 cells in quad order (bin_of_tile), so a 64-cell
+// tile is four consecutive bins.
+constexpr int TUNE_CHUNKS[] = {256, 512, 1024, 2048};       // candidates with 32-cell tiles
+constexpr int TUNE_CHUNKS64[] = {1024, 2048, 4096};         // candidates with 64-cell tiles
 
 void build_chunks(ivis_plan_s *p, int cap, std::vector<Chunk> &chunks, std::vector<int> &first) {
     chunks.clear();
     first.assign(p->nslot + 1, 0);
+    const int per = p->gtile == 64 ? 4 : 1;  // sort bins per tile
     for (int sl = 0; sl < p->nslot; ++sl) {
         const int *tc = p->slot_tc[sl];
         first[sl] = (int)chunks.size();
         int acc = 0;
-        for (int t = 0; t < p->ntiles; ++t) {
-            const int cnt = tc[t];
+        for (int j = 0; j < p->ntiles; j += per) {
+            int cnt = 0;
+            for (int s = 0; s < per; ++s) cnt += tc[j + s];
+            int t;
+            if (per == 4) {
+                t = j >> 2;  // quad index = row-major index of the 64-cell tile
+            } else {
+                int bx, by;
+                tile_of_bin(j, p->ntx, bx, by);
+                t = by * p->ntx + bx;
+            }
             for (int b = 0; b < cnt; b += cap) chunks.push_back(Chunk{sl, t, acc + b, acc + std::min(cnt, b + cap)});
             acc += cnt;
         }
@@ -1046,7 +1105,7 @@ template <typename T>
 ivis_status autotune(ivis_plan_s *p) {
     const std::string key = tune_key(p);
     const char *path = std::getenv("IVIS_AUTOTUNE_CACHE");
-    int best_cap = -1, best_logc = -1;
+    int best_cap = -1, best_logc = -1, best_ts = -1;
     if (path) {
         if (FILE *f = std::fopen(path, "r")) {
             char line[512];
@@ -1054,12 +1113,23 @@ ivis_status autotune(ivis_plan_s *p) {
                 std::string l(line);
                 const size_t bar = l.find('|');
                 if (bar == std::string::npos || l.substr(0, bar) != key) continue;
-                int cap = 0, lc = -1;
-                if (std::sscanf(l.c_str() + bar + 1, "%d %d", &cap, &lc) == 2) { best_cap = cap; best_logc = lc; }
+                int cap = 0, lc = -1, ts = 32;
+                const int got = std::sscanf(l.c_str() + bar + 1, "%d %d %d", &cap, &lc, &ts);
+                if (got >= 2) { best_cap = cap; best_logc = lc; best_ts = got == 3 ? ts : 32; }
             }
             std::fclose(f);
         }
     }
+    // tile edges the plan can use: 64 needs the FP32 path and at least 2 x 2 sort bins; a
+    // tile fixed in the configuration is the only candidate
+    auto tile_ok = [&](int ts) {
+        if (p->cfg.grid_tile && ts != p->cfg.grid_tile) return false;
+        return ts == 32 || (ts == 64 && !p->fp64 && p->ntx >= 2);
+    };
+    auto cap_ok = [&](int ts, int cap) {
+        return ts == 64 ? std::find(std::begin(TUNE_CHUNKS64), std::end(TUNE_CHUNKS64), cap) != std::end(TUNE_CHUNKS64)
+                        : std::find(std::begin(TUNE_CHUNKS), std::end(TUNE_CHUNKS), cap) != std::end(TUNE_CHUNKS);
+    };
     // column-FFT widths the kernels can run: shared memory, threads per CTA, columns per grid
     const size_t csz = sizeof(typename cplx_of<T>::type);
     const int tpl = p->nf / 16;
@@ -1069,9 +1139,8 @@ ivis_status autotune(ivis_plan_s *p) {
     };
     // a cached decision is used only if it is one the tuner itself could have made (the chunk
     // buffers are sized for the smallest candidate chunk)
-    if (best_cap > 0 && (std::find(std::begin(TUNE_CHUNKS), std::end(TUNE_CHUNKS), best_cap) == std::end(TUNE_CHUNKS) ||
-                         !feasible_logc(best_logc)))
-        best_cap = best_logc = -1;
+    if (best_cap > 0 && (!tile_ok(best_ts) || !cap_ok(best_ts, best_cap) || !feasible_logc(best_logc)))
+        best_cap = best_logc = best_ts = -1;
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
@@ -1103,28 +1172,33 @@ ivis_status autotune(ivis_plan_s *p) {
             });
             if (ms < bt) { bt = ms; best_logc = lc; }
         }
-        // grid-pass chunk size
+        // grid-pass tile edge (the sort bins the work list groups) and chunk size
         std::vector<Chunk> ch;
         std::vector<int> first;
         float bg = 1e30f;
-        for (int cap : TUNE_CHUNKS) {
-            build_chunks(p, cap, ch, first);
-            CK(cudaMemcpy(p->chunks_d, ch.data(), ch.size() * sizeof(Chunk), cudaMemcpyHostToDevice));
-            const int n = (int)ch.size();
-            const float ms = timed([&] {
-                if (p->cfg.wterm) {
-                    launch_grid_pass<T, MODE_PREDICT>(p, 0, n, nullptr, p->pv_d);
-                    launch_grid_pass<T, MODE_SPREAD>(p, 0, n, nullptr, nullptr);
-                } else {
-                    launch_grid_pass<T, MODE_COSTGRAD>(p, 0, n, p->jpart, nullptr);
-                }
-            });
-            if (ms < bg) { bg = ms; best_cap = cap; }
+        for (int ts : {32, 64}) {
+            if (!tile_ok(ts)) continue;
+            p->gtile = ts;
+            for (int cap : (ts == 64 ? std::vector<int>(std::begin(TUNE_CHUNKS64), std::end(TUNE_CHUNKS64))
+                                     : std::vector<int>(std::begin(TUNE_CHUNKS), std::end(TUNE_CHUNKS)))) {
+                build_chunks(p, cap, ch, first);
+                CK(cudaMemcpy(p->chunks_d, ch.data(), ch.size() * sizeof(Chunk), cudaMemcpyHostToDevice));
+                const int n = (int)ch.size();
+                const float ms = timed([&] {
+                    if (p->cfg.wterm) {
+                        launch_grid_pass<T, MODE_PREDICT>(p, 0, n, nullptr, p->pv_d);
+                        launch_grid_pass<T, MODE_SPREAD>(p, 0, n, nullptr, nullptr);
+                    } else {
+                        launch_grid_pass<T, MODE_COSTGRAD>(p, 0, n, p->jpart, nullptr);
+                    }
+                });
+                if (ms < bg) { bg = ms; best_cap = cap; best_ts = ts; }
+            }
         }
         CK(cudaGetLastError());
         if (path) {
             if (FILE *f = std::fopen(path, "a")) {
-                std::fprintf(f, "%s|%d %d\n", key.c_str(), best_cap, best_logc);
+                std::fprintf(f, "%s|%d %d %d\n", key.c_str(), best_cap, best_logc, best_ts);
                 std::fclose(f);
             }
         }
@@ -1133,13 +1207,15 @@ ivis_status autotune(ivis_plan_s *p) {
     cudaEventDestroy(e1);
     p->logc_cols = best_logc;
     p->chunk_cap = best_cap;
+    p->gtile = best_ts;
     std::vector<Chunk> ch;
     build_chunks(p, p->chunk_cap, ch, p->chunk_first);
     p->nchunk = (int)ch.size();
     CK(cudaMemcpy(p->chunks_d, ch.data(), ch.size() * sizeof(Chunk), cudaMemcpyHostToDevice));
     CK(cudaMemsetAsync(p->G, 0, (size_t)p->nslot * p->nf * p->nf * sizeof(typename cplx_of<T>::type), p->stream));
     CK(cudaStreamSynchronize(p->stream));
-    p->tuned = key + " -> chunk " + std::to_string(p->chunk_cap) + ", fft columns per CTA " +
+    p->tuned = key + " -> tile " + std::to_string(p->gtile) + ", chunk " + std::to_string(p->chunk_cap) +
+               ", fft columns per CTA " +
                std::to_string(1 << p->logc_cols) + (cached ? " (cached)" : " (timed)");
     return IVIS_OK;
 }
@@ -1231,10 +1307,13 @@ ivis_status prepare_impl(ivis_plan_s *p) {
     build_chunks(p, p->chunk_cap, chunks, p->chunk_first);
     p->nchunk = (int)chunks.size();
     size_t max_chunks = 0;  // work lists of every autotuner candidate fit the device arrays
-    {
+    {   // (32-cell tiles with the smallest chunk give the longest list)
         std::vector<Chunk> tmp;
         std::vector<int> tf;
+        const int gt = p->gtile;
+        p->gtile = 32;
         build_chunks(p, TUNE_CHUNKS[0], tmp, tf);
+        p->gtile = gt;
         max_chunks = std::max(tmp.size(), chunks.size());
     }
     for (int ch = 0; ch < c.nchan; ++ch) {
@@ -1725,6 +1804,16 @@ ivis_status ivis_plan(const ivis_config *cfg, void *stream, ivis_plan_t *out) {
     p->tile = GTILE;  // nf >= 32 always (nb >= 16)
     p->ntx = p->nf / p->tile;
     p->ntiles = p->ntx * p->ntx;
+    if (c.grid_tile != 0 && c.grid_tile != 32 && c.grid_tile != 64) {
+        delete p;
+        return fail(nullptr, IVIS_ERR_ARG, "grid_tile must be 0, 32 or 64");
+    }
+    if (c.grid_tile == 64 && (p->fp64 || p->ntx < 2)) {
+        delete p;
+        return fail(nullptr, IVIS_ERR_ARG, "grid_tile 64 needs IVIS_FP32 and nb >= 32");
+    }
+    p->gtile = c.grid_tile ? c.grid_tile : (!p->fp64 && p->W <= 8 && p->ntx >= 2 ? 64 : 32);
+    p->chunk_cap = p->gtile == 64 ? 2048 : 1024;
     {
         // columns per CTA in the column FFT passes: as many as fit 100 KB of shared memory
         // and 1024 threads; at least 4 (32-byte row segments) if 160 KB allows it

@@ -67,7 +67,7 @@ __device__ __forceinline__ void bilerp_adj(T *out, int n, float X, float Y, T v)
 
 struct Chunk {
     int slot;    // active pair slot
-    int tile;    // tile id within the pair's fine grid (ty * ntx + tx)
+    int tile;    // tile id within the pair's fine grid (ty * ntx + tx, ntx = nf / tile edge)
     int begin;   // first visibility (pair-local sorted index)
     int end;     // one past the last
 };
@@ -87,7 +87,22 @@ template <typename T> struct PairData {
 
 constexpr int FRAC_BITS = 20;
 constexpr unsigned FRAC_ONE = 1u << FRAC_BITS;
-constexpr int GTILE = 32;    // fine-grid tile edge (cells) of the gridding work list
+constexpr int GTILE = 32;    // fine-grid bin edge (cells) of the visibility sort
+
+// Order of the 32 x 32-cell bins in the sort: bins are grouped in 2 x 2 quads (row-major over
+// the quads, then row-major inside a quad), so that both a 32-cell tile and a 64-cell tile own
+// one contiguous run of the sorted visibilities. ntx = nf / 32 bins per row (a power of two).
+__host__ __device__ __forceinline__ int bin_of_tile(int tx, int ty, int ntx) {
+    if (ntx < 2) return ty * ntx + tx;
+    const int h = ntx >> 1;
+    return ((((ty >> 1) * h + (tx >> 1)) << 2) | ((ty & 1) << 1) | (tx & 1));
+}
+__host__ __device__ __forceinline__ void tile_of_bin(int j, int ntx, int &tx, int &ty) {
+    if (ntx < 2) { tx = 0; ty = 0; return; }
+    const int h = ntx >> 1, q = j >> 2, s = j & 3;
+    tx = 2 * (q % h) + (s & 1);
+    ty = 2 * (q / h) + (s >> 1);
+}
 constexpr int ES_MAXDEG = 18; // max degree of the per-tap kernel polynomials
 // Degree W + 1: for W = 7 the interpolation error is 5.8e-8 (degree W + 2: 5.4e-8; the kernel's
 // square-root edge sets the floor), far below the FP32 NUFFT's 1e-6.
@@ -148,7 +163,7 @@ __global__ void k_vis_prepare(int m, const float *__restrict__ uvw, const float 
     }
     // tile-major, then the first-tap cell within the tile (row-major): visibilities that share
     // a base cell end up adjacent, which the grid pass exploits
-    key[i] = ((g0[1] / tile) * ntx + (g0[0] / tile)) * tile * tile + (g0[1] % tile) * tile + (g0[0] % tile);
+    key[i] = bin_of_tile(g0[0] / tile, g0[1] / tile, ntx) * tile * tile + (g0[1] % tile) * tile + (g0[0] % tile);
 }
 
 __global__ void k_hist(int m, const int *__restrict__ key, int *count) {
@@ -216,7 +231,7 @@ __global__ void k_scan_add(int n, int *out, const int *__restrict__ bsum) {
         if (i + k < n) out[i + k] += off;
 }
 
-// start[t] = first sorted slot of tile t (t <= ntiles; start[ntiles] = m).
+// start[t] = first sorted slot of bin t in sort order (t <= ntiles; start[ntiles] = m).
 __global__ void k_tile_starts(int ntiles, int per_tile, int m, const int *__restrict__ cell_start,
                               int *start) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -373,7 +388,7 @@ __device__ __forceinline__ void red_add_c(double2 *p, double2 v) {
 // window are added to the shared sub-grid (atomics) before the window slides. MODE_PREDICT
 // writes V~ to pred[pred_off + orig] instead of spreading; MODE_SPREAD skips the
 // interpolation and spreads w times the record's value (the w-stacked entries).
-template <typename T, int W, int MODE>
+template <typename T, int W, int MODE, int TS = GTILE>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 5 : 2)
 k_grid_pass(const Chunk *__restrict__ chunks, const PairData<T> *__restrict__ pdata,
             const typename cplx_of<T>::type *__restrict__ F, typename cplx_of<T>::type *G,
@@ -382,7 +397,7 @@ k_grid_pass(const Chunk *__restrict__ chunks, const PairData<T> *__restrict__ pd
     typedef typename cplx_of<T>::type C;
     constexpr int GS = W <= 4 ? 4 : (W <= 8 ? 8 : 16);
     constexpr int NG = 256 / GS;  // groups per CTA
-    constexpr int tile = GTILE;
+    constexpr int tile = TS;
     constexpr int PW = tile + W - 1;
     constexpr bool POLY = sizeof(T) == 4;
     extern __shared__ __align__(16) unsigned char smem_raw[];

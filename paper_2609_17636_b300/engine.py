@@ -36,7 +36,8 @@ class Plan:
                  precision: str = "fp32", nufft_tol: float | None = None, kernel_width: int = 0,
                  lambda_r: float = 0.0, lambda_s: float = 0.0, positivity: bool = True,
                  stream: torch.cuda.Stream | None = None, serial_pairs: bool = False,
-                 autotune: bool = False, toeplitz: bool = False, wterm: bool = False):
+                 autotune: bool = False, toeplitz: bool = False, wterm: bool = False,
+                 grid_tile: int = 0):
         self.L = _lib.load()
         if precision not in ("fp32", "fp64"):
             raise ValueError("precision must be 'fp32' or 'fp64'")
@@ -48,7 +49,7 @@ class Plan:
                                IVIS_FP32 if precision == "fp32" else IVIS_FP64,
                                nufft_tol, kernel_width, lambda_r, lambda_s, int(bool(positivity)),
                                int(bool(serial_pairs)), int(bool(autotune)), int(bool(toeplitz)),
-                               int(bool(wterm)))
+                               int(bool(wterm)), int(grid_tile))
         self.shape = (nchan, n, n)
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         self._p = ctypes.c_void_p()

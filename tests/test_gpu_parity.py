@@ -31,15 +31,17 @@ def mosaic():
     return prob, x, f, g, terms
 
 
-def _plan(prob, precision):
+def _plan(prob, precision, **kw):
     from paper_2609_17636_b300 import plan_from_problem
-    return plan_from_problem(prob, precision)
+    return plan_from_problem(prob, precision, **kw)
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32"])
-def test_cost_and_gradient_match_oracle(mosaic, precision):
+@pytest.mark.parametrize("precision,tile", [("fp64", 0), ("fp32", 32), ("fp32", 64)])
+def test_cost_and_gradient_match_oracle(mosaic, precision, tile):
+    """FP32 runs the one-lane-per-kernel-column grid pass with 32- and 64-cell tiles (the
+    128^2 fine grids hold 2 x 2 tiles of 64 cells, each patch wrapping at the grid edge)."""
     prob, x, f, g, terms = mosaic
-    plan = _plan(prob, precision)
+    plan = _plan(prob, precision, grid_tile=tile)
     dt = torch.float64 if precision == "fp64" else torch.float32
     xs = torch.as_tensor(x, dtype=dt, device="cuda")
     fg, grad, tg = plan.cost_grad(xs)
@@ -76,13 +78,19 @@ def test_autotuned_plan_matches_oracle_and_caches_its_choice(mosaic, tmp_path, m
     p1 = plan_from_problem(prob, "fp32", autotune=True)
     f1, g1, _ = p1.cost_grad(xs)
     t1 = p1.tuning()
-    assert t1["chunk_cap"] in (256, 512, 1024, 2048) and t1["fft_cols"] in (1, 2, 4, 8, 16)
+    assert t1["chunk_cap"] in (256, 512, 1024, 2048, 4096) and t1["fft_cols"] in (1, 2, 4, 8, 16)
+    assert ("tile 32," in t1["decision"]) != ("tile 64," in t1["decision"])
+    if "tile 32," in t1["decision"]:
+        assert t1["chunk_cap"] <= 2048
+    else:
+        assert t1["chunk_cap"] >= 1024
     assert "(timed)" in t1["decision"] and cache.read_text().count("|") == 1
     assert abs(f1 - f) <= TOL["fp32"] * abs(f) and rel_l2(g1.cpu().numpy(), g) <= TOL["fp32"]
     p2 = plan_from_problem(prob, "fp32", autotune=True)
     p2.prepare()
     t2 = p2.tuning()
     assert "(cached)" in t2["decision"] and t2["chunk_cap"] == t1["chunk_cap"]
+    assert t2["decision"].split("->")[1].split(", fft")[0] == t1["decision"].split("->")[1].split(", fft")[0]
     p1.close()
     p2.close()
 
@@ -221,6 +229,28 @@ def test_dense_single_tile_many_chunks(precision):
     for pair in prob.pairs:
         got = plan.predict(torch.as_tensor(x, dtype=dt, device="cuda"), pair.k, pair.chan).cpu().numpy()
         assert rel_l2(got[:, 0] + 1j * got[:, 1], oracle.pair_model_vis(prob, x, pair)) <= tol
+    plan.close()
+
+
+@pytest.mark.parametrize("tile", [32, 64])
+def test_dense_single_64_cell_tile_many_chunks(tile):
+    """nb = 32 gives a 64^2 fine grid: one 64-cell tile (or four 32-cell tiles) holding ~6000
+    visibilities per pair, split into several chunks with a ragged last one; first taps on
+    every cell row and column including the wrap at the grid edge."""
+    prob = synth.small_mosaic(306, n=40, nb=32, nchan=1, npoint=2, ndump=8, n_ant=40,
+                              cell_arcsec=30.0, lambda_r=0.0, lambda_s=0.0)
+    attach_data(prob)
+    assert max(p.m for p in prob.pairs) > 4096
+    x = prob.sky_true * 0.6
+    f, g = oracle.cost_grad(prob, x)
+    plan = _plan(prob, "fp32", grid_tile=tile)
+    xs = torch.as_tensor(x, dtype=torch.float32, device="cuda")
+    fg, grad, _ = plan.cost_grad(xs)
+    assert abs(fg - f) <= TOL["fp32"] * abs(f)
+    assert rel_l2(grad.cpu().numpy(), g) <= TOL["fp32"]
+    for pair in prob.pairs:
+        got = plan.predict(xs, pair.k, pair.chan).cpu().numpy()
+        assert rel_l2(got[:, 0] + 1j * got[:, 1], oracle.pair_model_vis(prob, x, pair)) <= TOL["fp32"]
     plan.close()
 
 

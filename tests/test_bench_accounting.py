@@ -43,28 +43,146 @@ def test_pairs_without_data_move_nothing():
     assert sb["fwd_fft"] == 2 * (2 * 4 * 32 * 32 + 8 * 32 * 64 + 8 * 64 * 64)
 
 
+class _FakeNVML:
+    """Stand-in for pynvml: two GPUs in the machine; the visible one is found by UUID."""
+    NVML_CLOCK_SM = 1
+
+    def __init__(self, clocks, reasons):
+        self.clocks, self.reasons, self.lookups, self.i = clocks, reasons, [], 0
+
+    def nvmlInit(self):
+        pass
+
+    def nvmlDeviceGetHandleByUUID(self, uuid):
+        self.lookups.append(("uuid", uuid))
+        if uuid != "GPU-1111":
+            raise RuntimeError("unknown uuid")
+        return "h1"
+
+    def nvmlDeviceGetHandleByPciBusId(self, bus):
+        self.lookups.append(("bus", bus))
+        return "h-bus"
+
+    def nvmlDeviceGetMaxClockInfo(self, h, which):
+        assert h == "h1"
+        return 2032
+
+    def nvmlDeviceGetClockInfo(self, h, which):
+        assert h == "h1" and which == self.NVML_CLOCK_SM
+        v = self.clocks[min(self.i, len(self.clocks) - 1)]
+        return v
+
+    def nvmlDeviceGetPowerUsage(self, h):
+        return 900_000
+
+    def nvmlDeviceGetCurrentClocksEventReasons(self, h):
+        v = self.reasons[min(self.i, len(self.reasons) - 1)]
+        self.i += 1
+        return v
+
+
+def test_clock_sampler_finds_the_visible_gpu_by_uuid_and_samples_it():
+    """The sampler names the GPU by its UUID (NVML and nvidia-smi indices ignore
+    CUDA_VISIBLE_DEVICES) and collects samples from a thread until stop() joins it."""
+    import time
+    nv = _FakeNVML([1900, 1950, 2000], [0, 0x4, 0])
+    cs = bench.ClockSampler("GPU-1111", "00000000:18:00.0", period=0.001, nvml=nv).start()
+    cs.mark("t_begin")
+    time.sleep(0.05)
+    cs.mark("t_end")
+    rec = cs.stop()
+    assert nv.lookups[0] == ("uuid", "GPU-1111") and all(h != "bus" for h, _ in nv.lookups)
+    assert rec["samples_in_timed_region"] >= 3 and rec["sm_max_mhz"] == 2032.0
+    assert rec["reasons"] == ["sw_power_cap"] and rec["power_w_max"] == 900.0
+    assert not cs.thread.is_alive()
+
+
 def test_clock_record_takes_the_median_inside_the_timed_region_and_the_active_reasons():
     """The clocks object of the bench line: median SM clock of the samples taken inside the
     timed region, the maximum clock, and every throttle reason seen active there."""
+    cs = bench.ClockSampler("GPU-x")
+    cs.rows = [(0.5, 900.0, 2032.0, 500.0, 0),          # before the timed region
+               (1.1, 1900.0, 2032.0, 900.0, 0),
+               (1.2, 1950.0, 2032.0, 950.0, 0x4),       # sw_power_cap
+               (1.3, 2000.0, 2032.0, 901.0, 0),
+               (5.0, 700.0, 2032.0, 300.0, 0x8)]        # after it (hw_slowdown)
+    cs.t_begin, cs.t_end = 1.0, 1.4
+    rec = cs.stop()
+    assert rec["sm_mhz"] == 1950.0 and rec["sm_max_mhz"] == 2032.0 and rec["sm_mhz_min"] == 1900.0
+    assert rec["reasons"] == ["sw_power_cap"] and rec["samples_in_timed_region"] == 3
+
+
+def test_clock_sampler_without_nvml_reports_why():
+    class _NoGPU(_FakeNVML):
+        def nvmlDeviceGetHandleByUUID(self, uuid):
+            raise RuntimeError("no such device")
+
+        def nvmlDeviceGetHandleByPciBusId(self, bus):
+            raise RuntimeError("no such device")
+    cs = bench.ClockSampler("GPU-2", "0:1:0.0", nvml=_NoGPU([], [])).start()
+    rec = cs.stop()
+    assert rec["samples"] == 0 and "no NVML handle" in rec["error"]
+
+
+def test_clock_sampler_falls_back_to_nvidia_smi_with_its_own_timestamps(monkeypatch):
+    """Without NVML bindings the sampler runs nvidia-smi on the same GPU (by UUID) and places
+    each row by nvidia-smi's timestamp, not by when the line reached the reader."""
+    import datetime
+    import subprocess
+
+    class _NoNVML(_FakeNVML):
+        def nvmlInit(self):
+            raise RuntimeError("NVML bindings missing")
+
+    calls = []
+
+    def ts(sec):
+        return datetime.datetime.fromtimestamp(sec).strftime("%Y/%m/%d %H:%M:%S.%f")[:-3]
+
     class _Proc:
+        def __init__(self, cmd, **kw):
+            calls.append(cmd)
+            self.stdout = iter([f"{ts(100.2)}, 1000, 2032, 300.0, Not Active, Not Active, Not Active, Not Active\n",
+                                f"{ts(101.2)}, 1980, 2032, 800.0, Not Active, Not Active, Not Active, Active\n",
+                                f"{ts(101.4)}, 2000, 2032, 820.0, Not Active, Not Active, Not Active, Not Active\n",
+                                "garbage line\n"])
+
         def terminate(self):
             pass
 
         def wait(self, timeout=None):
             return 0
 
-    cs = bench.ClockSampler(0)
-    cs.proc = _Proc()
-    row = lambda sm, hw, pc: [str(sm), "2032", "900.0", "0x0", hw, "Not Active", "Not Active", pc]
-    cs.rows = [(0.5, row(900, "Not Active", "Not Active")),      # before the timed region
-               (1.1, row(1900, "Not Active", "Not Active")),
-               (1.2, row(1950, "Not Active", "Active")),
-               (1.3, row(2000, "Not Active", "Not Active")),
-               (5.0, row(700, "Active", "Not Active"))]          # after it
-    cs.t_begin, cs.t_end = 1.0, 1.4
+    monkeypatch.setattr(subprocess, "Popen", _Proc)
+    cs = bench.ClockSampler("GPU-abcd", "0:1:0.0", nvml=_NoNVML([], [])).start()
+    cs.t_begin, cs.t_end = 101.0, 101.5
     rec = cs.stop()
-    assert rec["sm_mhz"] == 1950.0 and rec["sm_max_mhz"] == 2032.0
-    assert rec["reasons"] == ["sw_power_cap"] and rec["samples_in_timed_region"] == 3
+    assert "--id=GPU-abcd" in calls[0] and rec["source"] == "nvidia-smi"
+    assert rec["samples"] == 3 and rec["samples_in_timed_region"] == 2
+    assert rec["sm_mhz"] == 1990.0 and rec["reasons"] == ["sw_power_cap"]
+
+
+def test_per_kernel_stage_bytes_add_up_to_the_packed_fft_totals():
+    prob = synth.config_c2()
+    nb, nf = 512, 1024
+    sb = bench.stage_bytes(prob, _Plan("fp32", nf))
+    assert sb["fwd_rows"] == 7 * (2 * 4 * nb * nb + 8 * nb * nf // 2)
+    assert sb["fwd_cols"] == 7 * (8 * nb * nf // 2 + 8 * nf * nf)
+    assert sb["adj_cols"] == 7 * (8 * nf * nf + 8 * nb * nf // 2)
+    assert sb["adj_rows"] == 7 * (8 * nb * nf // 2 + 2 * 4 * nb * nb)
+    assert sb["fwd_rows"] + sb["fwd_cols"] == sb["fwd_fft"] and sb["adj_cols"] + sb["adj_rows"] == sb["adj_fft"]
+
+
+def test_roofline_takes_the_longest_single_kernel_stage():
+    """The concurrent dish-convolution branch and multi-kernel stages are never chosen."""
+    prob = synth.config_c2()
+    stages = {"fusion_K": 9.0, "fwd_rows": 0.03, "fwd_cols": 0.04, "degrid_spread": 0.1,
+              "adj_cols": 0.2, "adj_rows": 0.02, "assemble_R": 5.0, "finalize": 0.01}
+    r = bench.roofline_of(prob, _Plan("fp32", 1024), stages, 6500.0, "measured")
+    sb = bench.stage_bytes(prob, _Plan("fp32", 1024))
+    assert r["stage"] == "adj_cols" and r["bound"] == "hbm" and r["launch_ms"] == 0.2
+    assert abs(r["achieved"] - sb["adj_cols"] / 0.2e-3 / 1e9) < 0.1
+    assert abs(r["frac"] - r["achieved"] / 6500.0) < 1e-4
 
 
 def test_reference_arm_line_has_the_contract_keys(monkeypatch):

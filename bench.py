@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--no-toeplitz", action="store_true")
     ap.add_argument("--no-wterm", action="store_true")
     ap.add_argument("--no-precision", action="store_true")
+    ap.add_argument("--grid-tile", type=int, default=0, choices=[0, 32, 64],
+                    help="fix the gridding tile edge (0: the autotuner chooses)")
     ap.add_argument("--c3-channels", type=int, default=32,
                     help="channels of the batched cube (fewer: the same per-pair density on a "
                          "smaller device footprint, for profiler captures)")
@@ -255,7 +257,7 @@ def attach_data_gpu(prob, plan_fp64_like):
         prob.sigma_sd = sig
 
 
-def build_plan(prob, precision, serial=False, autotune=False, toeplitz=False, wterm=False):
+def build_plan(prob, precision, serial=False, autotune=False, toeplitz=False, wterm=False, grid_tile=0):
     from paper_2609_17636_b300 import plan_from_problem
     for pair in prob.pairs:
         if pair.vis is None:
@@ -264,7 +266,7 @@ def build_plan(prob, precision, serial=False, autotune=False, toeplitz=False, wt
         prob.tsd = np.zeros((prob.nchan, prob.n, prob.n), np.float32)
         prob.sigma_sd = np.ones(prob.nchan)
     return plan_from_problem(prob, precision, serial_pairs=serial, autotune=autotune, toeplitz=toeplitz,
-                             wterm=wterm)
+                             wterm=wterm, grid_tile=grid_tile)
 
 
 # ----------------------------------------------------------------- roofline model
@@ -338,7 +340,7 @@ def run_ivis(args, rank, world):
     datagen = build_plan(prob, "fp64" if args.config in ("c1", "c2") else "fp32")
     attach_data_gpu(prob, datagen)
     datagen.close()
-    plan = build_plan(prob, args.precision, autotune=True)
+    plan = build_plan(prob, args.precision, autotune=True, grid_tile=args.grid_tile)
     plan.prepare()
     x = torch.as_tensor(prob.sky_true * 0.5, dtype=plan.dtype, device=dev)
     g = torch.empty_like(x)

@@ -42,6 +42,7 @@ struct PairHost {
     void *coord = nullptr, *vis = nullptr, *w = nullptr;
     int *orig = nullptr;
     std::vector<int> tile_count;  // per sort bin of the fine grid, in sort order
+    std::vector<int> block_start; // first sorted visibility of each 8 x 8-cell block (sort order)
     // Toeplitz form (toeplitz = 1): spectrum of Re H [kx][ky], window b [nb][nb], constant C
     void *that = nullptr, *bwin = nullptr;
     double qconst = 0.0;
@@ -74,7 +75,8 @@ struct ivis_plan_s {
     int nf = 0, lognf = 0, W = 0;
     double beta = 0.0;
     int tile = 32, ntx = 0, ntiles = 0;  // sort bins (32 x 32 cells) of the fine grid
-    int gtile = 32;                      // tile edge of the grid-pass work list (32 or 64)
+    int gtile = 32;                      // tile edge of the k_grid_pass work list (32 or 64)
+    int xtile = 32, item_len = 32;       // k_grid_cg work list: tile edge, visibilities per item
     int logc_cols = 0;  // log2 columns per CTA in the column FFT passes
     int chunk_cap = 1024;  // max visibilities per grid-pass chunk
     std::string tuned;     // autotuner decision (for reporting)
@@ -98,6 +100,11 @@ struct ivis_plan_s {
     std::vector<int> slot_m;               // slot -> visibilities (entries)
     std::vector<int> chunk_first;          // slot -> first chunk (size nslot + 1)
     int nchunk = 0;
+    std::vector<const int *> slot_bs;      // slot -> per-block visibility starts (k_grid_cg)
+    std::vector<int> xchunk_first;         // slot -> first k_grid_cg chunk (size nslot + 1)
+    int nxchunk = 0;
+    Chunk *xchunks_d = nullptr;            // k_grid_cg chunks: slot, tile, items [begin, end)
+    Item *items_d = nullptr;
     PairInfo *pinfo_d = nullptr;
     void *pdata_d = nullptr;
     Chunk *chunks_d = nullptr;
@@ -344,7 +351,7 @@ ivis_status upload_twiddles(ivis_plan_s *p) {
 // ------------------------------------------------------------------ kernel dispatch on W
 // FP32 cost+gradient passes with kernel width <= 8 run k_grid_cg (one lane per kernel column);
 // the FP64 path, wider kernels, the predict and spread-only modes run k_grid_pass.
-inline bool use_grid_cg(const ivis_plan_s *p) { return !p->fp64 && p->W <= 8; }
+inline bool use_grid_cg(const ivis_plan_s *p) { return !p->fp64 && p->W <= 8 && !p->cfg.wterm; }
 
 template <typename T, int MODE, int TS>
 cudaError_t launch_grid_pass_ts(ivis_plan_s *p, int first_chunk, int nchunk, double *jpart,
@@ -354,25 +361,6 @@ cudaError_t launch_grid_pass_ts(ivis_plan_s *p, int first_chunk, int nchunk, dou
     const PairData<T> *pd = (const PairData<T> *)p->pdata_d;
     const C *F = (const C *)p->F;
     C *G = (C *)p->G;
-    if constexpr (MODE == MODE_COSTGRAD && sizeof(T) == 4) {
-        if (use_grid_cg(p)) {
-#define CG_CASE(WW)                                                                                   \
-    case WW: {                                                                                        \
-        auto kern = k_grid_cg<WW, TS>;                                                                \
-        const size_t sm = GridCG<WW, TS>::SMEM;                                                       \
-        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);             \
-        kern<<<nchunk, GridCG<WW, TS>::THREADS, sm, p->stream>>>(ch, (const PairData<float> *)pd,     \
-                                                                (const float2 *)F, (float2 *)G,       \
-                                                                p->lognf, p->kpoly_d, jpart);         \
-        return cudaGetLastError();                                                                    \
-    }
-            switch (p->W) {
-                CG_CASE(2) CG_CASE(3) CG_CASE(4) CG_CASE(5) CG_CASE(6) CG_CASE(7) CG_CASE(8)
-                default: return cudaErrorInvalidValue;
-            }
-#undef CG_CASE
-        }
-    }
     const int PW = TS + p->W - 1;
     size_t smem = (size_t)PW * PW * sizeof(C) * (MODE == MODE_COSTGRAD ? 2 : 1);
     T beta = (T)p->beta;
@@ -394,6 +382,26 @@ cudaError_t launch_grid_pass_ts(ivis_plan_s *p, int first_chunk, int nchunk, dou
     return cudaGetLastError();
 }
 
+// k_grid_cg over chunks [first, first + n) of the item work list (p->xchunks_d).
+template <int TS>
+cudaError_t launch_grid_cg_ts(ivis_plan_s *p, int first, int n, double *jpart) {
+#define CG_CASE(WW)                                                                                   \
+    case WW: {                                                                                        \
+        auto kern = k_grid_cg<WW, TS>;                                                                \
+        const size_t sm = GridCG<WW, TS>::SMEM;                                                       \
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);             \
+        kern<<<n, GridCG<WW, TS>::THREADS, sm, p->stream>>>(                                          \
+            p->xchunks_d + first, p->items_d, (const PairData<float> *)p->pdata_d, (const float2 *)p->F, \
+            (float2 *)p->G, p->lognf, p->kpoly_d, jpart);                                             \
+        return cudaGetLastError();                                                                    \
+    }
+    switch (p->W) {
+        CG_CASE(2) CG_CASE(3) CG_CASE(4) CG_CASE(5) CG_CASE(6) CG_CASE(7) CG_CASE(8)
+        default: return cudaErrorInvalidValue;
+    }
+#undef CG_CASE
+}
+
 template <typename T, int MODE>
 cudaError_t launch_grid_pass(ivis_plan_s *p, int first_chunk, int nchunk, double *jpart,
                              void *pred) {
@@ -403,6 +411,25 @@ cudaError_t launch_grid_pass(ivis_plan_s *p, int first_chunk, int nchunk, double
     }
     return launch_grid_pass_ts<T, MODE, 32>(p, first_chunk, nchunk, jpart, pred);
 }
+
+// The cost+gradient grid pass for slots [slot0, slot0 + nslots): k_grid_cg on the item work
+// list (FP32, W <= 8) or k_grid_pass on the tile work list. The pass writes one FP64 J partial
+// per chunk at jpart + (the slot range's first chunk); returns the partials written in *nj.
+template <typename T>
+cudaError_t launch_costgrad(ivis_plan_s *p, int slot0, int nslots, double *jpart, int *nj = nullptr) {
+    if (use_grid_cg(p)) {
+        const int c0 = p->xchunk_first[slot0], n = p->xchunk_first[slot0 + nslots] - c0;
+        if (nj) *nj = n;
+        if (n <= 0) return cudaSuccess;
+        return p->xtile == 64 ? launch_grid_cg_ts<64>(p, c0, n, jpart + c0) : launch_grid_cg_ts<32>(p, c0, n, jpart + c0);
+    }
+    const int c0 = p->chunk_first[slot0], n = p->chunk_first[slot0 + nslots] - c0;
+    if (nj) *nj = n;
+    return launch_grid_pass<T, MODE_COSTGRAD>(p, c0, n, jpart + c0, nullptr);
+}
+
+// Number of FP64 J partials the cost+gradient pass of all slots writes.
+int cost_partials(const ivis_plan_s *p) { return use_grid_cg(p) ? p->nxchunk : p->nchunk; }
 
 void stage_begin(ivis_plan_s *p, const char *name, cudaStream_t st, int &si);
 void stage_end(ivis_plan_s *p, cudaStream_t st, int &si);
@@ -649,10 +676,9 @@ cudaError_t enqueue_eval(ivis_plan_s *p, bool capture) {
             // one (pointing, channel) pair at a time: the unbatched reference path
             stage_begin(p, "serial_pairs", p->stream, si);
             for (int sl = 0; sl < p->nslot; ++sl) {
-                const int c0 = p->chunk_first[sl], nc = p->chunk_first[sl + 1] - c0;
+                int nc = 0;
                 if ((e = launch_forward<T>(p, p->x, sl, 1)) != cudaSuccess) return e;
-                if ((e = launch_grid_pass<T, MODE_COSTGRAD>(p, c0, nc, p->jpart + c0, nullptr)) != cudaSuccess)
-                    return e;
+                if ((e = launch_costgrad<T>(p, sl, 1, p->jpart, &nc)) != cudaSuccess) return e;
                 if ((e = launch_adjoint<T>(p, sl, 1)) != cudaSuccess) return e;
                 launches += 4 + (nc > 0 ? 1 : 0);
             }
@@ -662,8 +688,7 @@ cudaError_t enqueue_eval(ivis_plan_s *p, bool capture) {
             if ((e = launch_forward<T>(p, p->x, 0, -1, &si)) != cudaSuccess) return e;
             launches += 2;
             stage_begin(p, "degrid_spread", p->stream, si);
-            if ((e = launch_grid_pass<T, MODE_COSTGRAD>(p, 0, p->nchunk, p->jpart, nullptr)) != cudaSuccess)
-                return e;
+            if ((e = launch_costgrad<T>(p, 0, p->nslot, p->jpart)) != cudaSuccess) return e;
             launches += 1;
             stage_end(p, p->stream, si);
             if ((e = launch_adjoint<T>(p, 0, -1, &si)) != cudaSuccess) return e;
@@ -687,7 +712,7 @@ cudaError_t enqueue_eval(ivis_plan_s *p, bool capture) {
     }
     stage_end(p, p->stream, si);
     stage_begin(p, "finalize", p->stream, si);
-    k_finalize<<<FIN_BLOCKS, 256, 0, p->stream>>>(p->jpart, (p->cfg.toeplitz || p->cfg.wterm) ? p->njpart : p->nchunk, p->kpart,
+    k_finalize<<<FIN_BLOCKS, 256, 0, p->stream>>>(p->jpart, (p->cfg.toeplitz || p->cfg.wterm) ? p->njpart : cost_partials(p), p->kpart,
                                          use_k ? p->nkpart : 0,
                                          p->rpart, use_r ? p->nrpart : 0, p->cfg.lambda_r,
                                          p->cfg.lambda_s, p->cost_d);
@@ -766,7 +791,7 @@ ivis_status set_vis_impl(ivis_plan_s *p, PairHost &ph, int m, const float *uvw, 
     ivis_status s;
     if ((s = alloc(p, &coord_tmp, (size_t)m * sizeof(CO))) || (s = alloc(p, &key, (size_t)m * sizeof(int))) ||
         (s = alloc(p, &cnt, (size_t)nbins * sizeof(int))) || (s = alloc(p, &cur, (size_t)nbins * sizeof(int))) ||
-        (s = alloc(p, &bsum, (size_t)nsb * sizeof(int))) || (s = alloc(p, &tst, (size_t)(p->ntiles + 1) * sizeof(int))) ||
+        (s = alloc(p, &bsum, (size_t)nsb * sizeof(int))) || (s = alloc(p, &tst, (size_t)(nbins / 64 + 1) * sizeof(int))) ||
         (s = alloc(p, &err, sizeof(int)))) {
         cleanup();
         return s;
@@ -774,6 +799,7 @@ ivis_status set_vis_impl(ivis_plan_s *p, PairHost &ph, int m, const float *uvw, 
     cudaMemsetAsync(err, 0, sizeof(int), p->stream);
     cudaMemsetAsync(cnt, 0, (size_t)nbins * sizeof(int), p->stream);
     const int nblk = (m + 255) / 256;
+    const int ncb = nbins / 64;  // 8 x 8-cell blocks, 16 per sort bin
     const double scale = p->cfg.cell_rad * p->nf;
     k_vis_prepare<T><<<nblk, 256, 0, p->stream>>>(m, uvw, vis, w, scale, p->lognf, p->W, p->tile,
                                                    p->ntx, (CO *)coord_tmp, (int *)key, (int *)err);
@@ -781,19 +807,18 @@ ivis_status set_vis_impl(ivis_plan_s *p, PairHost &ph, int m, const float *uvw, 
     k_scan_block<<<nsb, 256, 0, p->stream>>>(nbins, (const int *)cnt, (int *)cur, (int *)bsum);
     k_scan_top<<<1, 1024, 0, p->stream>>>(nsb, (int *)bsum);
     k_scan_add<<<nsb, 256, 0, p->stream>>>(nbins, (int *)cur, (const int *)bsum);
-    k_tile_starts<<<(p->ntiles + 256) / 256, 256, 0, p->stream>>>(p->ntiles, p->tile * p->tile, m,
-                                                                   (const int *)cur, (int *)tst);
+    k_tile_starts<<<(ncb + 256) / 256, 256, 0, p->stream>>>(ncb, 64, m, (const int *)cur, (int *)tst);
     int herr = 0;
-    std::vector<int> starts(p->ntiles + 1, 0);
+    ph.block_start.assign(ncb + 1, 0);
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, p->stream);
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(starts.data(), tst, (size_t)(p->ntiles + 1) * sizeof(int), cudaMemcpyDeviceToHost, p->stream);
+        e = cudaMemcpyAsync(ph.block_start.data(), tst, (size_t)(ncb + 1) * sizeof(int), cudaMemcpyDeviceToHost, p->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
     if (e != cudaSuccess) { cleanup(); return fail(p, IVIS_ERR_CUDA, std::string("set_vis: ") + cudaGetErrorString(e)); }
     if (herr) { cleanup(); return fail(p, IVIS_ERR_NONFINITE, "set_vis: non-finite uvw/vis/weight or negative weight"); }
-    ph.tile_count.assign(p->ntiles, 0);
-    for (int t = 0; t < p->ntiles; ++t) ph.tile_count[t] = starts[t + 1] - starts[t];
+    ph.tile_count.assign(p->ntiles, 0);  // per sort bin (16 blocks)
+    for (int t = 0; t < p->ntiles; ++t) ph.tile_count[t] = ph.block_start[16 * (t + 1)] - ph.block_start[16 * t];
     if ((s = alloc(p, &ph.coord, (size_t)m * sizeof(CO))) || (s = alloc(p, &ph.vis, (size_t)m * sizeof(C))) ||
         (s = alloc(p, &ph.w, (size_t)m * sizeof(T))) || (s = alloc(p, (void **)&ph.orig, (size_t)m * sizeof(int)))) {
         cleanup();
@@ -1017,6 +1042,8 @@ void free_pair(PairHost &ph) {
     ph.nplane = 0;
     ph.plane_start.clear();
     ph.plane_tile_count.clear();
+    ph.tile_count.clear();
+    ph.block_start.clear();
     dfree(ph.that);
     dfree(ph.bwin);
     ph.qconst = 0.0;
@@ -1036,6 +1063,10 @@ void release_prepared(ivis_plan_s *p) {
     void *pi = p->pinfo_d, *ck = p->chunks_d, *cs = p->chan_start_d, *cl = p->chan_list_d;
     dfree(pi); dfree(p->pdata_d); dfree(ck); dfree(cs); dfree(cl);
     p->pinfo_d = nullptr; p->chunks_d = nullptr; p->chan_start_d = nullptr; p->chan_list_d = nullptr;
+    void *xc = p->xchunks_d, *xi = p->items_d;
+    dfree(xc); dfree(xi);
+    p->xchunks_d = nullptr; p->items_d = nullptr;
+    p->nxchunk = 0;
     dfree(p->taps_d);
     dfree(p->sd_spec_d);
     dfree(p->sd_tw_d);
@@ -1061,6 +1092,7 @@ void release_prepared(ivis_plan_s *p) {
 // tile is four consecutive bins.
 constexpr int TUNE_CHUNKS[] = {256, 512, 1024, 2048};       // candidates with 32-cell tiles
 constexpr int TUNE_CHUNKS64[] = {1024, 2048, 4096};         // candidates with 64-cell tiles
+constexpr int TUNE_ITEMS[] = {16, 32, 64};                  // k_grid_cg: visibilities per item
 
 void build_chunks(ivis_plan_s *p, int cap, std::vector<Chunk> &chunks, std::vector<int> &first) {
     chunks.clear();
@@ -1088,6 +1120,52 @@ void build_chunks(ivis_plan_s *p, int cap, std::vector<Chunk> &chunks, std::vect
     first[p->nslot] = (int)chunks.size();
 }
 
+// Work list of k_grid_cg: per slot, per tile of edge ts (row-major tiles), per non-empty 8 x 8
+// block of the tile, items of at most len visibilities; chunks of at most GRID_ROUNDS rounds of
+// ng items of one tile, each chunk's items sorted by decreasing length (the groups of a warp,
+// which run in step, then get items of similar length). Blocks are 16 per 32-cell sort bin,
+// bins in quad order (bin_of_tile).
+constexpr int GRID_ROUNDS = 8;
+
+void build_items(const ivis_plan_s *p, int ts, int len, std::vector<Chunk> &chunks, std::vector<Item> &items,
+                 std::vector<int> &first) {
+    chunks.clear();
+    items.clear();
+    first.assign(p->nslot + 1, 0);
+    const int ng = (ts == 64 ? GridCG<7, 64>::NG : GridCG<7, 32>::NG) * GRID_ROUNDS;
+    const int nbx = ts / 8;
+    const int nt = p->nf / ts;
+    for (int sl = 0; sl < p->nslot; ++sl) {
+        const int *bs = p->slot_bs[sl];
+        first[sl] = (int)chunks.size();
+        for (int t = 0; t < nt * nt; ++t) {
+            const int tyi = t / nt, txi = t - tyi * nt;
+            const int i0 = (int)items.size();
+            // the tile's 32-cell bins (one, or the four of a quad) and their 16 blocks each
+            for (int sub = 0; sub < (ts == 64 ? 4 : 1); ++sub) {
+                const int bx32 = ts == 64 ? 2 * txi + (sub & 1) : txi, by32 = ts == 64 ? 2 * tyi + (sub >> 1) : tyi;
+                const int bin = bin_of_tile(bx32, by32, p->ntx);
+                for (int bib = 0; bib < 16; ++bib) {
+                    const int j = bin * 16 + bib;
+                    const int b0 = bs[j], b1 = bs[j + 1];
+                    const int bx = (ts == 64 ? 4 * (sub & 1) : 0) + (bib & 3);
+                    const int by = (ts == 64 ? 4 * (sub >> 1) : 0) + (bib >> 2);
+                    for (int v = b0; v < b1; v += len) items.push_back(Item{v, std::min(b1, v + len), by * nbx + bx, 0});
+                }
+            }
+            const int i1 = (int)items.size();
+            for (int c = i0; c < i1; c += ng) {
+                const int ce = std::min(i1, c + ng);
+                std::stable_sort(items.begin() + c, items.begin() + ce, [](const Item &x, const Item &y) {
+                    return x.end - x.begin > y.end - y.begin;
+                });
+                chunks.push_back(Chunk{sl, t, c, ce});
+            }
+        }
+    }
+    first[p->nslot] = (int)chunks.size();
+}
+
 std::string tune_key(const ivis_plan_s *p) {
     long long m = 0;
     for (int sl = 0; sl < p->nslot; ++sl) m += p->slot_m[sl];
@@ -1101,8 +1179,21 @@ std::string tune_key(const ivis_plan_s *p) {
 // Autotuner: picks the grid-pass chunk size and the number of columns per CTA of the column
 // FFT passes by timing candidates on this plan's data (CUDA events, after a warm-up launch).
 // Decisions are cached per shape class in the file named by IVIS_AUTOTUNE_CACHE, if set.
+// Build the k_grid_cg work list for (p->xtile, p->item_len) and copy it to the device arrays
+// (sized at prepare for the longest candidate list).
+ivis_status upload_items(ivis_plan_s *p) {
+    std::vector<Chunk> ch;
+    std::vector<Item> itv;
+    build_items(p, p->xtile, p->item_len, ch, itv, p->xchunk_first);
+    p->nxchunk = (int)ch.size();
+    if (!ch.empty()) CK(cudaMemcpy(p->xchunks_d, ch.data(), ch.size() * sizeof(Chunk), cudaMemcpyHostToDevice));
+    if (!itv.empty()) CK(cudaMemcpy(p->items_d, itv.data(), itv.size() * sizeof(Item), cudaMemcpyHostToDevice));
+    return IVIS_OK;
+}
+
 template <typename T>
 ivis_status autotune(ivis_plan_s *p) {
+    ivis_status s_;
     const std::string key = tune_key(p);
     const char *path = std::getenv("IVIS_AUTOTUNE_CACHE");
     int best_cap = -1, best_logc = -1, best_ts = -1;
@@ -1126,9 +1217,16 @@ ivis_status autotune(ivis_plan_s *p) {
         if (p->cfg.grid_tile && ts != p->cfg.grid_tile) return false;
         return ts == 32 || (ts == 64 && !p->fp64 && p->ntx >= 2);
     };
+    // chunk sizes (k_grid_pass) or visibilities per item (k_grid_cg) the tuner tries for a tile
+    const bool cg = use_grid_cg(p);
+    auto caps_of = [&](int ts) {
+        if (cg) return std::vector<int>(std::begin(TUNE_ITEMS), std::end(TUNE_ITEMS));
+        return ts == 64 ? std::vector<int>(std::begin(TUNE_CHUNKS64), std::end(TUNE_CHUNKS64))
+                        : std::vector<int>(std::begin(TUNE_CHUNKS), std::end(TUNE_CHUNKS));
+    };
     auto cap_ok = [&](int ts, int cap) {
-        return ts == 64 ? std::find(std::begin(TUNE_CHUNKS64), std::end(TUNE_CHUNKS64), cap) != std::end(TUNE_CHUNKS64)
-                        : std::find(std::begin(TUNE_CHUNKS), std::end(TUNE_CHUNKS), cap) != std::end(TUNE_CHUNKS);
+        const std::vector<int> c = caps_of(ts);
+        return std::find(c.begin(), c.end(), cap) != c.end();
     };
     // column-FFT widths the kernels can run: shared memory, threads per CTA, columns per grid
     const size_t csz = sizeof(typename cplx_of<T>::type);
@@ -1172,26 +1270,37 @@ ivis_status autotune(ivis_plan_s *p) {
             });
             if (ms < bt) { bt = ms; best_logc = lc; }
         }
-        // grid-pass tile edge (the sort bins the work list groups) and chunk size
+        // grid-pass tile edge (the sort bins the work list groups) and chunk size, or for
+        // k_grid_cg the tile edge and the visibilities per item
         std::vector<Chunk> ch;
+        std::vector<Item> itv;
         std::vector<int> first;
         float bg = 1e30f;
         for (int ts : {32, 64}) {
             if (!tile_ok(ts)) continue;
-            p->gtile = ts;
-            for (int cap : (ts == 64 ? std::vector<int>(std::begin(TUNE_CHUNKS64), std::end(TUNE_CHUNKS64))
-                                     : std::vector<int>(std::begin(TUNE_CHUNKS), std::end(TUNE_CHUNKS)))) {
-                build_chunks(p, cap, ch, first);
-                CK(cudaMemcpy(p->chunks_d, ch.data(), ch.size() * sizeof(Chunk), cudaMemcpyHostToDevice));
-                const int n = (int)ch.size();
-                const float ms = timed([&] {
-                    if (p->cfg.wterm) {
-                        launch_grid_pass<T, MODE_PREDICT>(p, 0, n, nullptr, p->pv_d);
-                        launch_grid_pass<T, MODE_SPREAD>(p, 0, n, nullptr, nullptr);
-                    } else {
-                        launch_grid_pass<T, MODE_COSTGRAD>(p, 0, n, p->jpart, nullptr);
-                    }
-                });
+            for (int cap : caps_of(ts)) {
+                float ms;
+                if (cg) {
+                    p->xtile = ts;
+                    build_items(p, ts, cap, ch, itv, first);
+                    CK(cudaMemcpy(p->xchunks_d, ch.data(), ch.size() * sizeof(Chunk), cudaMemcpyHostToDevice));
+                    CK(cudaMemcpy(p->items_d, itv.data(), itv.size() * sizeof(Item), cudaMemcpyHostToDevice));
+                    p->xchunk_first = first;
+                    ms = timed([&] { launch_costgrad<T>(p, 0, p->nslot, p->jpart); });
+                } else {
+                    p->gtile = ts;
+                    build_chunks(p, cap, ch, first);
+                    CK(cudaMemcpy(p->chunks_d, ch.data(), ch.size() * sizeof(Chunk), cudaMemcpyHostToDevice));
+                    const int n = (int)ch.size();
+                    ms = timed([&] {
+                        if (p->cfg.wterm) {
+                            launch_grid_pass<T, MODE_PREDICT>(p, 0, n, nullptr, p->pv_d);
+                            launch_grid_pass<T, MODE_SPREAD>(p, 0, n, nullptr, nullptr);
+                        } else {
+                            launch_grid_pass<T, MODE_COSTGRAD>(p, 0, n, p->jpart, nullptr);
+                        }
+                    });
+                }
                 if (ms < bg) { bg = ms; best_cap = cap; best_ts = ts; }
             }
         }
@@ -1206,16 +1315,24 @@ ivis_status autotune(ivis_plan_s *p) {
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     p->logc_cols = best_logc;
-    p->chunk_cap = best_cap;
-    p->gtile = best_ts;
-    std::vector<Chunk> ch;
-    build_chunks(p, p->chunk_cap, ch, p->chunk_first);
-    p->nchunk = (int)ch.size();
-    CK(cudaMemcpy(p->chunks_d, ch.data(), ch.size() * sizeof(Chunk), cudaMemcpyHostToDevice));
+    std::string grid;
+    if (cg) {
+        p->xtile = best_ts;
+        p->item_len = best_cap;
+        if ((s_ = upload_items(p))) return s_;
+        grid = "tile " + std::to_string(p->xtile) + ", items of " + std::to_string(p->item_len);
+    } else {
+        p->chunk_cap = best_cap;
+        p->gtile = best_ts;
+        std::vector<Chunk> ch;
+        build_chunks(p, p->chunk_cap, ch, p->chunk_first);
+        p->nchunk = (int)ch.size();
+        CK(cudaMemcpy(p->chunks_d, ch.data(), ch.size() * sizeof(Chunk), cudaMemcpyHostToDevice));
+        grid = "tile " + std::to_string(p->gtile) + ", chunk " + std::to_string(p->chunk_cap);
+    }
     CK(cudaMemsetAsync(p->G, 0, (size_t)p->nslot * p->nf * p->nf * sizeof(typename cplx_of<T>::type), p->stream));
     CK(cudaStreamSynchronize(p->stream));
-    p->tuned = key + " -> tile " + std::to_string(p->gtile) + ", chunk " + std::to_string(p->chunk_cap) +
-               ", fft columns per CTA " +
+    p->tuned = key + " -> " + grid + ", fft columns per CTA " +
                std::to_string(1 << p->logc_cols) + (cached ? " (cached)" : " (timed)");
     return IVIS_OK;
 }
@@ -1238,6 +1355,7 @@ ivis_status prepare_impl(ivis_plan_s *p) {
     // w-plane of each such pair
     p->slot_pair.clear();
     p->slot_tc.clear();
+    p->slot_bs.clear();
     p->slot_m.clear();
     std::vector<PairInfo> pinfo;
     std::vector<PairData<T>> pdata;
@@ -1265,6 +1383,7 @@ ivis_status prepare_impl(ivis_plan_s *p) {
             pdata.push_back(pd);
             p->slot_pair.push_back((int)i);
             p->slot_tc.push_back(ph.tile_count.data());
+            p->slot_bs.push_back(ph.block_start.data());
             p->slot_m.push_back(ph.m);
         } else {
             for (int pl = 0; pl < ph.nplane; ++pl) {
@@ -1281,6 +1400,7 @@ ivis_status prepare_impl(ivis_plan_s *p) {
                 pdata.push_back(pd);
                 p->slot_pair.push_back((int)i);
                 p->slot_tc.push_back(ph.plane_tile_count.data() + (size_t)pl * p->ntiles);
+                p->slot_bs.push_back(nullptr);
                 p->slot_m.push_back(e - b);
             }
             WPair<T> wp{};
@@ -1332,6 +1452,19 @@ ivis_status prepare_impl(ivis_plan_s *p) {
     if ((s = up(&p->pdata_d, pdata.data(), pdata.size() * sizeof(PairData<T>)))) return s;
     if ((s = alloc(p, (void **)&p->chunks_d, max_chunks * sizeof(Chunk)))) return s;
     if (!chunks.empty()) CK(cudaMemcpy(p->chunks_d, chunks.data(), chunks.size() * sizeof(Chunk), cudaMemcpyHostToDevice));
+    if (use_grid_cg(p)) {
+        // item work list: device arrays sized for the longest candidate (32-cell tiles, the
+        // shortest items), then the list of the current choice
+        std::vector<Chunk> xc;
+        std::vector<Item> xi;
+        std::vector<int> xf;
+        build_items(p, 32, TUNE_ITEMS[0], xc, xi, xf);
+        const size_t mx_c = std::max<size_t>(1, xc.size()), mx_i = std::max<size_t>(1, xi.size());
+        max_chunks = std::max(max_chunks, mx_c);
+        if ((s = alloc(p, (void **)&p->xchunks_d, mx_c * sizeof(Chunk)))) return s;
+        if ((s = alloc(p, (void **)&p->items_d, mx_i * sizeof(Item)))) return s;
+        if ((s = upload_items(p))) return s;
+    }
     if ((s = up((void **)&p->chan_start_d, chan_start.data(), chan_start.size() * sizeof(int)))) return s;
     if ((s = up((void **)&p->chan_list_d, chan_list.data(), chan_list.size() * sizeof(int)))) return s;
     const size_t nf2 = (size_t)p->nf * p->nf;
@@ -1628,7 +1761,7 @@ ivis_status dirty_impl(ivis_plan_s *p, void *dirty_dev, void *beamw_dev) {
         // gradient is the adjoint of -w V
         CK(cudaMemsetAsync(p->F, 0, (size_t)p->nslot * p->nf * p->nf * sizeof(C), p->stream));
         CK(cudaMemsetAsync(p->G, 0, (size_t)p->nslot * p->nf * p->nf * sizeof(C), p->stream));
-        cudaError_t e = launch_grid_pass<T, MODE_COSTGRAD>(p, 0, p->nchunk, p->jpart, nullptr);
+        cudaError_t e = launch_costgrad<T>(p, 0, p->nslot, p->jpart);
         if (e == cudaSuccess) e = launch_adjoint<T>(p);
         if (e != cudaSuccess) return fail(p, IVIS_ERR_CUDA, std::string("dirty: ") + cudaGetErrorString(e));
     }
@@ -1812,8 +1945,10 @@ ivis_status ivis_plan(const ivis_config *cfg, void *stream, ivis_plan_t *out) {
         delete p;
         return fail(nullptr, IVIS_ERR_ARG, "grid_tile 64 needs IVIS_FP32 and nb >= 32");
     }
-    p->gtile = c.grid_tile ? c.grid_tile : (!p->fp64 && p->W <= 8 && p->ntx >= 2 ? 64 : 32);
+    p->gtile = c.grid_tile ? c.grid_tile : 32;
     p->chunk_cap = p->gtile == 64 ? 2048 : 1024;
+    p->xtile = c.grid_tile ? c.grid_tile : 32;
+    p->item_len = 32;
     {
         // columns per CTA in the column FFT passes: as many as fit 100 KB of shared memory
         // and 1024 threads; at least 4 (32-byte row segments) if 160 KB allows it

@@ -161,9 +161,13 @@ __global__ void k_vis_prepare(int m, const float *__restrict__ uvw, const float 
     } else {
         coord_tmp[i] = make_double2(sc[0], sc[1]);
     }
-    // tile-major, then the first-tap cell within the tile (row-major): visibilities that share
-    // a base cell end up adjacent, which the grid pass exploits
-    key[i] = bin_of_tile(g0[0] / tile, g0[1] / tile, ntx) * tile * tile + (g0[1] % tile) * tile + (g0[0] % tile);
+    // bin-major (bins in quad order), then the 8 x 8-cell block within the bin (row-major), then
+    // the first-tap cell within the block (row-major): every bin and every block owns one
+    // contiguous run of the sorted visibilities, and visibilities that share a first-tap cell
+    // are adjacent
+    const int cx = g0[0] % tile, cy = g0[1] % tile;
+    key[i] = bin_of_tile(g0[0] / tile, g0[1] / tile, ntx) * tile * tile +
+             ((cy >> 3) * (tile >> 3) + (cx >> 3)) * 64 + (cy & 7) * 8 + (cx & 7);
 }
 
 __global__ void k_hist(int m, const int *__restrict__ key, int *count) {
@@ -382,10 +386,11 @@ __device__ __forceinline__ void red_add_c(double2 *p, double2 v) {
 // row r. Each lane evaluates one x and one y kernel value, the x values are exchanged by
 // shuffles, the row sums of the interpolation are reduced across the group, and the same 2W
 // kernel values serve the spreading. Each group walks a contiguous run of the chunk, whose
-// visibilities are sorted by first-tap cell (row-major within the tile): a lane keeps its row
-// of the spread in registers; while the cell repeats nothing is written, and when the next
-// first tap lies d < W cells further right on the same row only the d cells that leave the
-// window are added to the shared sub-grid (atomics) before the window slides. MODE_PREDICT
+// visibilities are sorted by first-tap cell (row-major within each 8 x 8-cell block): a lane
+// keeps its row of the spread in registers; while the cell repeats nothing is written, and
+// when the next first tap lies d < W cells further right on the same row only the d cells
+// that leave the window are added to the shared sub-grid (atomics) before the window slides
+// (any other step adds the whole row; adding early is always correct). MODE_PREDICT
 // writes V~ to pred[pred_off + orig] instead of spreading; MODE_SPREAD skips the
 // interpolation and spreads w times the record's value (the w-stacked entries).
 template <typename T, int W, int MODE, int TS = GTILE>

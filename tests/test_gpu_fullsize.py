@@ -1,6 +1,7 @@
-"""Parity at the benchmark's full size (the 7-pointing 512^2 mosaic, 1.36 M visibilities,
-Laplacian + fusion terms, FP32 grids), in the launch configuration bench.py times (the
-plan's captured evaluation graph).
+"""Parity at full sizes: the 7-pointing 512^2 mosaic (1.36 M visibilities, Laplacian +
+fusion terms, FP32 grids) and the batched cube's shape (36 beams x 8 of its channels, ragged
+U[1e5, 3e5] visibilities per pair), in the launch configuration bench.py times (the
+autotuned plan's captured evaluation graph).
 
 The oracle cannot evaluate a dense 512^2 sky against 1.36 M visibilities in seconds, so both
 the data and the evaluation point are sparse skies (the oracle's direct DFT skips zero
@@ -134,4 +135,46 @@ def test_maximum_window_size_sampled_parity(precision):
         idx = np.sort(rng.choice(pair.m, 800, replace=False))
         got = plan.predict(xs, pair.k, pair.chan).cpu().numpy()[idx]
         assert rel_l2(got[:, 0] + 1j * got[:, 1], oracle.pair_model_vis(prob, x, pair, idx)) <= tol
+    plan.close()
+
+
+def test_batched_cube_shape_sampled_parity():
+    """The batched cube's geometry and launch configuration: 36 beams on the 6 x 6 hexagonal
+    footprint (0.9 deg pitch, 1 deg beams, 512^2 windows on a 1024^2 sky at 25 arcsec, so
+    windows overlap and hang off the sky), 8 of its channels (288 pairs, uv scaled per
+    channel), ragged U[1e5, 3e5] visibilities per pair that fold several times over the fine
+    grid, the Laplacian term; the FP32 plan with the autotuner's tile and item choice. Sparse
+    data and evaluation skies per channel as above."""
+    from paper_2609_17636_b300 import plan_from_problem
+    prob = synth.config_c3(nchan=8)
+    assert len(prob.pairs) == 288 and min(p.m for p in prob.pairs) >= 100_000
+    rng = np.random.default_rng(3003)
+    truth = np.concatenate([_sparse_sky(rng, prob.n, 24) for _ in range(prob.nchan)])
+    for pair in prob.pairs:
+        pair.vis = (oracle.pair_model_vis(prob, truth, pair) + pair.noise).astype(np.complex64)
+    x = np.concatenate([_sparse_sky(rng, prob.n, 20) for _ in range(prob.nchan)])
+    plan = plan_from_problem(prob, "fp32", autotune=True)
+    xs = torch.as_tensor(x, dtype=torch.float32, device="cuda")
+    f, g, (Q, K, R) = plan.cost_grad(xs)
+    g = g.cpu().numpy()
+    resid = [oracle.pair_model_vis(prob, x, p) - p.vis.astype(np.complex128) for p in prob.pairs]
+    Q_ref = sum(0.5 * float(np.sum(p.weight.astype(np.float64) * np.abs(r) ** 2))
+                for p, r in zip(prob.pairs, resid))
+    R_ref, gR = oracle.reg_cost_grad(x)
+    f_ref = Q_ref + prob.lambda_r * R_ref
+    assert abs(Q - Q_ref) <= TOL * Q_ref and abs(R - R_ref) <= TOL * R_ref and K == 0.0
+    assert abs(f - f_ref) <= TOL * f_ref
+    # gradient at sampled pixels of two channels: random, beam centres (overlaps), sky corners
+    for chan in (0, 5):
+        ys = np.concatenate([rng.integers(0, prob.n, 30), prob.centres[::5, 1], [0, prob.n - 1]])
+        xx = np.concatenate([rng.integers(0, prob.n, 30), prob.centres[::5, 0], [prob.n - 1, 0]])
+        sub = [(i, p) for i, p in enumerate(prob.pairs) if p.chan == chan]
+        gq = oracle.data_grad_pixels(prob, x, chan, ys, xx,
+                                     residuals={i: resid[i] for i, _ in sub})
+        g_ref = gq + prob.lambda_r * gR[chan, ys, xx]
+        assert rel_l2(g[chan, ys, xx], g_ref) <= TOL, (chan, rel_l2(g[chan, ys, xx], g_ref))
+    for pair in prob.pairs[::47]:
+        idx = np.sort(rng.choice(pair.m, 1000, replace=False))
+        got = plan.predict(xs, pair.k, pair.chan).cpu().numpy()[idx]
+        assert rel_l2(got[:, 0] + 1j * got[:, 1], oracle.pair_model_vis(prob, x, pair, idx)) <= TOL
     plan.close()

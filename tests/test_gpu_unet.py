@@ -65,6 +65,41 @@ def test_unet_forward_and_gradient_match_oracle(c, H, W):
     net.close()
 
 
+def test_unet_training_and_inference_sizes_match_oracle():
+    """The sizes the network runs at: training batches of 256^2 crops (base width 32, batch 2:
+    M = 131072 rows in the first layers' GEMMs, many M tiles and split-K parameter-gradient
+    GEMMs) and 512^2 inference (M = 262144). Same tolerances as the small shapes: the output
+    and the loss within 2e-2 and 1e-2, the gradient within 2 delta + 1e-2 with delta measured
+    on the oracle at this size, cosine >= 0.99."""
+    from paper_2609_17636_b300 import UNet
+    c, B, H, W = 32, 2, 256, 256
+    shapes = synth.unet_layer_shapes(c)
+    p = synth.unet_init(c, 9)
+    inp, tgt = _batch(c, B, H, W, 10)
+    net = UNet(c, max_batch=B, max_hw=512 * 512)
+    net.set_params(p)
+    x = torch.as_tensor(inp, device="cuda")
+    out = net.forward(x).cpu().numpy()
+    ref = ou.forward(p, shapes, c, inp)
+    assert _rel(out, ref) <= 2e-2, _rel(out, ref)
+    loss = net.backward(x, torch.as_tensor(tgt, device="cuda"))
+    g = net.get_grads()
+    lref, gref = ou.loss_and_grad(p, shapes, c, inp, tgt)
+    pb = torch.as_tensor(p).to(torch.bfloat16).to(torch.float64).numpy()
+    _, gref_b = ou.loss_and_grad(pb, shapes, c, inp, tgt)
+    delta = _rel(gref_b, gref)
+    assert abs(loss - lref) <= 1e-2 * lref, (loss, lref)
+    assert _rel(g, gref) <= 2 * delta + 1e-2, (_rel(g, gref), delta)
+    cos = float(np.dot(g, gref) / (np.linalg.norm(g) * np.linalg.norm(gref)))
+    assert cos >= 0.99, cos
+    # inference at 512^2 (fully convolutional: the same weights)
+    inp1, _ = _batch(c, 1, 512, 512, 11)
+    out1 = net.forward(torch.as_tensor(inp1, device="cuda")).cpu().numpy()
+    ref1 = ou.forward(p, shapes, c, inp1)
+    assert _rel(out1, ref1) <= 2e-2, _rel(out1, ref1)
+    net.close()
+
+
 def test_unet_adam_training_reduces_loss_on_a_fixed_batch():
     from paper_2609_17636_b300 import UNet
     c, B, H, W = 8, 4, 32, 32

@@ -232,12 +232,17 @@ def data_cost_grad(prob, sky: np.ndarray, with_grad: bool = True):
 
 
 def data_grad_pixels(prob, sky, chan, ys, xs, residuals=None):
-    """dQ/dI at the listed sky pixels of channel ``chan`` only (sampled checks)."""
+    """dQ/dI at the listed sky pixels of channel ``chan`` only (sampled checks). Integer
+    windows only: a pointing re-projected through an interpolation grid (Eq. 2) spreads each
+    window pixel over four sky pixels, which this sampled form does not follow, so such a
+    pointing raises. ``residuals`` (list or dict by pair index) skips recomputing r."""
     sky = _f64(sky)
     out = np.zeros(len(ys))
     for i, pair in enumerate(prob.pairs):
         if pair.chan != chan:
             continue
+        if _grid_of(prob, pair.k) is not None:
+            raise NotImplementedError("data_grad_pixels: pointing %d uses a re-projection grid" % pair.k)
         cx, cy = (int(t) for t in prob.centres[pair.k])
         q = np.asarray(ys) - (cy - prob.nb // 2)
         p = np.asarray(xs) - (cx - prob.nb // 2)

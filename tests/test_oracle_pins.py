@@ -8,6 +8,7 @@ import math
 import os
 
 import numpy as np
+import pytest
 import scipy.ndimage
 import scipy.optimize
 import scipy.signal
@@ -660,6 +661,23 @@ def test_gridded_data_gradient_central_differences():
     x = prob.sky_true * rng.uniform(0.5, 1.5, prob.sky_true.shape)
     _fd_check(lambda z: oracle.data_cost_grad(prob, z), x, rng.choice(x.size, 15, replace=False),
               1e-4 * np.abs(x).max())
+
+
+
+def test_sampled_data_gradient_refuses_reprojected_pointings():
+    """The sampled gradient follows integer windows only; with a re-projection grid (Eq. 2) it
+    raises rather than answer with the wrong window, and pointings without a grid still work."""
+    prob = synth.small_mosaic(34, n=40, nb=32, nchan=1, npoint=2, ndump=3, n_ant=7)
+    prob.grids = {1: synth.projection_grid(32, 20.4, 19.6, rot_rad=0.2, scale=0.9)}
+    _with_data(prob)
+    x = prob.sky_true * 0.5
+    with pytest.raises(NotImplementedError):
+        oracle.data_grad_pixels(prob, x, 0, [10, 20], [11, 21])
+    prob.grids = {}
+    _with_data(prob)
+    _, g = oracle.data_cost_grad(prob, x)
+    assert np.allclose(oracle.data_grad_pixels(prob, x, 0, [10, 20], [11, 21]), g[0, [10, 20], [11, 21]],
+                       rtol=1e-10, atol=1e-12 * np.abs(g).max())
 
 
 # ------------------------------------------------- Toeplitz form of the data term (Eqs. 3-6)

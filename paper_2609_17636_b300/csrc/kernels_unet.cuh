@@ -235,9 +235,12 @@ k_gemm_tc(int M, int N, int K, const bf16 *__restrict__ A, const bf16 *__restric
         phase[st] = 0u;
         pending[st] = false;
     }
-    bool ok = true;
-    // bounded wait on stage st's barrier (about two seconds at most)
-    auto wait_stage = [&](int st) {
+    // this thread's bounded waits ran out (combined across the CTA at every barrier, so all
+    // threads take the same branches and reach the same barriers)
+    int fail = 0;
+    // bounded wait on stage st's barrier (about two seconds at most); a stage whose wait ran
+    // out stays pending, so the drain below waits for it again before tensor memory is freed
+    auto wait_stage = [&](int st) -> bool {
         uint32_t done = 0;
         const long long t_start = clock64();
         while (!done) {
@@ -245,9 +248,14 @@ k_gemm_tc(int M, int N, int K, const bf16 *__restrict__ A, const bf16 *__restric
                          "selp.u32 %0, 1, 0, p;\n}\n" : "=r"(done) : "r"(smem_u32(mbar + st)), "r"(phase[st]));
             if (!done && clock64() - t_start > 4000000000LL) break;
         }
-        if (!done) { ok = false; if (err) atomicExch(err, 1); }
+        if (!done) {
+            fail = 1;
+            if (err) atomicExch(err, 1);
+            return false;
+        }
         phase[st] ^= 1u;
         pending[st] = false;
+        return true;
     };
     // implicit GEMM: this thread always copies chunk kg = tid % 8 of the tile rows
     // tid / 8 + 16 i; their pixel coordinates are fixed for the whole K loop
@@ -321,11 +329,12 @@ k_gemm_tc(int M, int N, int K, const bf16 *__restrict__ A, const bf16 *__restric
         if (s0 < nk) load_slice(s0, s0);
         asm volatile("cp.async.commit_group;");
     }
-    for (int kb = 0; kb < nk && ok; ++kb) {
+    for (int kb = 0; kb < nk; ++kb) {
         const int st = kb % S;
         asm volatile("cp.async.wait_group %0;" :: "n"(S - 2));  // slice kb has landed
         asm volatile("fence.proxy.async.shared::cta;");
-        __syncthreads();
+        // one barrier per slice; a wait that ran out in any thread stops all of them here
+        if (__syncthreads_or(fail)) break;
         if (tid == 0) {
             bf16 *As = stage0 + st * STAGE, *Bs = As + TC_BM * TC_BK;
             asm volatile("tcgen05.fence::after_thread_sync;");
@@ -343,26 +352,24 @@ k_gemm_tc(int M, int N, int K, const bf16 *__restrict__ A, const bf16 *__restric
                          :: "r"(smem_u32(mbar + st)));
         }
         pending[st] = true;
-        // refill the stage of slice kb - 1 with slice kb + S - 1 once its MMAs are done
+        // refill the stage of slice kb - 1 with slice kb + S - 1 once its MMAs are done (not
+        // after a wait that ran out: its MMAs may still read it)
         const int nxt = kb + S - 1;
         if (nxt < nk) {
             const int sn = nxt % S;
-            if (pending[sn]) wait_stage(sn);
-            if (!ok) break;
-            load_slice(nxt, sn);
+            if (!pending[sn] || wait_stage(sn)) load_slice(nxt, sn);
         }
         asm volatile("cp.async.commit_group;");
     }
     asm volatile("cp.async.wait_group 0;");
-    // drain: the commits still unwaited complete in issue order; wait for all of them
-    for (int i = 0; i < nk && ok; ++i) {
-        const int st = (nk - 1 - i) % S;
-        if (i >= S) break;
+    // drain: every commit still pending (each stage has at most one), bounded, also after a
+    // failure, so that no MMA is in flight when the accumulator is read or freed
+#pragma unroll
+    for (int st = 0; st < S; ++st)
         if (pending[st]) wait_stage(st);
-    }
     asm volatile("tcgen05.fence::after_thread_sync;");
-    __syncthreads();
-    if (ok) {
+    const int any_fail = __syncthreads_or(fail);
+    if (!any_fail) {
         const int row = m0 + warp * 32 + lane;
         for (int c0 = 0; c0 < BN; c0 += 16) {
             uint32_t r[16];

@@ -65,8 +65,10 @@ typedef struct {
     int nb;             /* pointing window nb x nb, power of two, 16 <= nb <= 2048         */
     double cell_rad;    /* pixel size (radians); the same grid for sky and windows         */
     int precision;      /* IVIS_FP64: all arithmetic double. IVIS_FP32: gridding, FFTs and
-                           residuals in float; cost and solver sums: terms in float within a
-                           thread and a warp, combined in double across warps and CTAs      */
+                           residuals in float; the cost terms are summed in float within a
+                           thread (at most 64 visibilities or a few pixels) and a warp, then
+                           in double across warps and CTAs; the solver's inner products and
+                           line-search slopes are accumulated in double from the first term */
     double nufft_tol;   /* target relative accuracy of the NUFFT when kernel_width == 0    */
     int kernel_width;   /* ES kernel width w in grid cells (2..16); 0 = chosen from tol     */
     double lambda_r;    /* weight of R (Eq. 14)                                            */
@@ -249,15 +251,16 @@ ivis_status ivis_launches_per_eval(ivis_plan_t plan, int *count);
  * the same separable dish-beam convolution as ivis_sd_predict (Gaussian taps truncated at
  * +-ceil(4 sigma), unit sum, zero outside the image), computed without a plan and without
  * allocating: its scratch (taps and the row-pass image of one channel) lives in a
- * file-scope device array of 4 MiB + 16 KiB that every GPU loading the library keeps until
- * the process exits. sky_dev, out_dev: float [nchan][n][n] on the current device; stream: a
- * cudaStream_t (NULL = legacy default stream); the call returns after the work completes.
- * Limits: n * n <= 1,048,576 and 2 ceil(4 sigma) + 1 <= 4095, else IVIS_ERR_ARG with a
- * message. The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress); make that first call before any stream capture. Every call shares
- * the one array: calls that overlap on the GPU (other streams, other host threads) race and
- * must be serialised by the caller. Calls no cudaMalloc/cudaFree. Errors are reported by
- * ivis_last_error(NULL). */
+ * file-scope device array of about 4 MiB (1632 + 1,048,576 floats) that every GPU loading the
+ * library keeps until the process exits. sky_dev, out_dev: float [nchan][n][n] on the current
+ * device; stream: a cudaStream_t (NULL = legacy default stream). The call is synchronous: it
+ * copies the taps from host memory and returns after the work completes, so it cannot be
+ * recorded into a CUDA graph; on a stream that is capturing it returns IVIS_ERR_STATE without
+ * touching the stream. Limits: n * n <= 1,048,576 and ceil(4 sigma) <= 812 (FWHM <= 478
+ * pixels), else IVIS_ERR_ARG with a message. The first call on a device looks up the array's
+ * device address (cudaGetSymbolAddress). Every call shares the one array: calls that overlap
+ * on the GPU (other streams, other host threads) race and must be serialised by the caller.
+ * Calls no cudaMalloc/cudaFree. Errors are reported by ivis_last_error(NULL). */
 ivis_status ivis_sd_predict_noalloc(const float *sky_dev, int n, int nchan, double fwhm_pix,
                                     float *out_dev, void *stream);
 

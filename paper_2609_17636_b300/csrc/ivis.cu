@@ -1866,19 +1866,20 @@ ivis_status feather_impl(ivis_plan_s *p, const void *int_dev, const float *sd_de
 // intermediate image and the beam taps) in this file-scope device array instead of
 // plan-owned memory. Every device that loads the library holds the array until the process
 // exits.
-constexpr int NOALLOC_MAX_TAPS = 4096;                   // 2R + 1 <= 4095
+// Half-width limit: the direct-tap convolution keeps a strip of (32 + 2R) x 33 inputs plus the
+// 2R + 1 taps in shared memory, within 220 KiB for R <= 812 (68 R + 1057 <= 56320 floats).
+constexpr int NOALLOC_MAX_R = 812;
+constexpr int NOALLOC_TAP_WORDS = 1632;                  // >= 2 NOALLOC_MAX_R + 1, 128-byte multiple
 constexpr size_t NOALLOC_MAX_PIXELS = (size_t)1 << 20;   // n * n <= 1,048,576 per call
-static __device__ __align__(256) float g_noalloc_scratch[NOALLOC_MAX_TAPS + NOALLOC_MAX_PIXELS];
+static __device__ __align__(256) float g_noalloc_scratch[NOALLOC_TAP_WORDS + NOALLOC_MAX_PIXELS];
 
 namespace {
 constexpr int NOALLOC_MAX_DEVICES = 64;
 float *g_noalloc_ptr[NOALLOC_MAX_DEVICES] = {};
 std::mutex g_noalloc_mu;
-thread_local std::string g_noalloc_err;
 
 ivis_status noalloc_fail(ivis_status s, const std::string &msg) {
-    g_noalloc_err = msg;
-    g_plan_error = msg;
+    g_plan_error = msg;  // read by ivis_last_error(NULL)
     return s;
 }
 
@@ -2368,23 +2369,31 @@ ivis_status ivis_sd_predict_noalloc(const float *sky_dev, int n, int nchan, doub
                                               std::to_string(NOALLOC_MAX_PIXELS));
     const double sg = fwhm_pix / (2.0 * std::sqrt(2.0 * std::log(2.0)));
     const double rr = std::ceil(4.0 * sg);
-    if (rr > (NOALLOC_MAX_TAPS - 1) / 2)
-        return noalloc_fail(IVIS_ERR_ARG, "dish beam too wide for the allocation-free path: 2*ceil(4 sigma)+1 must be <= " +
-                                              std::to_string(NOALLOC_MAX_TAPS - 1));
+    if (rr > NOALLOC_MAX_R)
+        return noalloc_fail(IVIS_ERR_ARG, "dish beam too wide for the allocation-free path: ceil(4 sigma) must be <= " +
+                                              std::to_string(NOALLOC_MAX_R) + " (FWHM <= 478 pixels)");
     const int R = (int)rr;
     const size_t sm = conv_smem<float>(R);
     if (sm > 220 * 1024) return noalloc_fail(IVIS_ERR_ARG, "dish beam too wide for the convolution strip");
+    // the taps are copied from this function's stack and the call waits for its stream: it
+    // cannot be recorded into a graph
+    cudaStream_t cs = (cudaStream_t)stream;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(cs, &cap);
+    if (e != cudaSuccess) return noalloc_fail(IVIS_ERR_CUDA, std::string("sd_predict_noalloc: ") + cudaGetErrorString(e));
+    if (cap != cudaStreamCaptureStatusNone)
+        return noalloc_fail(IVIS_ERR_STATE, "sd_predict_noalloc: the stream is capturing; the call is synchronous and "
+                                            "copies its taps from host memory, so it cannot be captured");
     float *scratch = nullptr;
     ivis_status st = noalloc_scratch(&scratch);
     if (st) return st;
     float *taps_d = scratch;                       // [2R + 1]
-    float *mid_d = scratch + NOALLOC_MAX_TAPS;     // [n][n] row-pass output of one channel
-    float taps[NOALLOC_MAX_TAPS];
+    float *mid_d = scratch + NOALLOC_TAP_WORDS;    // [n][n] row-pass output of one channel
+    float taps[NOALLOC_TAP_WORDS];
     double sum = 0.0;
     for (int t = -R; t <= R; ++t) sum += std::exp(-0.5 * (t / sg) * (t / sg));
     for (int t = -R; t <= R; ++t) taps[R + t] = (float)(std::exp(-0.5 * (t / sg) * (t / sg)) / sum);
-    cudaStream_t cs = (cudaStream_t)stream;
-    cudaError_t e = cudaMemcpyAsync(taps_d, taps, (size_t)(2 * R + 1) * sizeof(float), cudaMemcpyHostToDevice, cs);
+    e = cudaMemcpyAsync(taps_d, taps, (size_t)(2 * R + 1) * sizeof(float), cudaMemcpyHostToDevice, cs);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_conv_axis<float, 0, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_conv_axis<float, 1, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     dim3 gr((n + 31) / 32, (n + CONV_TO - 1) / CONV_TO, 1);

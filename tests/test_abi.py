@@ -148,6 +148,13 @@ def test_network_and_allocation_free_entry_checks_run_on_the_host():
     assert L.ivis_unet_create(8, 0, 64, None, ctypes.byref(u)) == 1 and not u.value
     assert L.ivis_sd_predict_noalloc(None, 16, 1, 3.0, None, None) == 1
     assert b"null" in L.ivis_last_error(None)
+    # size limits are checked before any device call (the pointers are never dereferenced)
+    fake = ctypes.c_void_p(256)
+    assert L.ivis_sd_predict_noalloc(fake, 1025, 1, 3.0, fake, None) == 1
+    assert b"too large" in L.ivis_last_error(None)
+    for fwhm in (478.5, 1000.0):  # ceil(4 sigma) = 813 and 1699: past the 812 of the scratch
+        assert L.ivis_sd_predict_noalloc(fake, 64, 1, fwhm, fake, None) == 1
+        assert b"too wide" in L.ivis_last_error(None) and b"812" in L.ivis_last_error(None)
 
 
 def test_header_is_plain_c_and_the_library_links_from_c(tmp_path):

@@ -6,8 +6,11 @@
 // products S^T g_F, Y^T g_F (one pass over the history) and one combination pass. The free
 // set F = {i : not (I_i <= 0 and g_i > 0)} restricts the step to variables that can move
 // (projected quasi-Newton); the step is projected onto I >= 0 and accepted by an Armijo test
-// on the projected path. All inner products accumulate in FP64; history vectors are stored in
-// the plan's real type.
+// on the projected path. Every inner product (the 2m + 1 of the direction, g.d, the Armijo
+// slope and the 3m of a new pair) is accumulated in FP64 from its first term: each product of
+// two working-precision values is formed exactly in FP64 (24 + 24 bits fit its 53) and summed
+// in FP64 within the thread, the warp and the CTA. History vectors and the per-pixel
+// arithmetic of d and of the trial point stay in the plan's real type.
 #pragma once
 #include "common.cuh"
 
@@ -118,9 +121,8 @@ k_sol_dots(size_t n, const T *__restrict__ x, const T *__restrict__ g, int pos,
     __shared__ T gf[SOL_CHUNK];
     __shared__ double red[32];
     const size_t base = (size_t)blockIdx.x * SOL_CHUNK;
-    // per-thread terms (SOL_CHUNK / blockDim of them) in the working precision; FP64 from the
-    // warp partials on (block_sum_t)
-    T gg = (T)0, pg = (T)0;
+    double gg = 0.0;
+    T pg = (T)0;
     for (int i = threadIdx.x; i < SOL_CHUNK; i += blockDim.x) {
         const size_t idx = base + i;
         T v = (T)0;
@@ -129,7 +131,7 @@ k_sol_dots(size_t n, const T *__restrict__ x, const T *__restrict__ g, int pos,
             v = is_free(xi, gi, pos) ? gi : (T)0;
             const T pgi = pos ? fabs(fmax(xi - gi, (T)0) - xi) : fabs(gi);
             pg = fmax(pg, pgi);
-            gg += v * v;
+            gg = fma((double)v, (double)v, gg);
         }
         gf[i] = v;
     }
@@ -137,15 +139,15 @@ k_sol_dots(size_t n, const T *__restrict__ x, const T *__restrict__ g, int pos,
     double *out = part + (size_t)blockIdx.x * stride;
     for (int t = 0; t < 2 * ord.m; ++t) {
         const T *vec = (t < ord.m ? S : Y) + (size_t)ord.slot[t < ord.m ? t : t - ord.m] * n;
-        T acc = (T)0;
+        double acc = 0.0;
         for (int i = threadIdx.x; i < SOL_CHUNK; i += blockDim.x) {
             const size_t idx = base + i;
-            if (idx < n) acc += vec[idx] * gf[i];
+            if (idx < n) acc = fma((double)vec[idx], (double)gf[i], acc);
         }
-        const double sum = block_sum_t(acc, red);
+        const double sum = block_sum(acc, red);
         if (threadIdx.x == 0) out[t] = sum;
     }
-    const double ggs = block_sum_t(gg, red);
+    const double ggs = block_sum(gg, red);
     if (threadIdx.x == 0) out[2 * ord.m] = ggs;
     const double pgm = block_max((double)pg, red);
     if (threadIdx.x == 0) out[2 * ord.m + 1] = pgm;
@@ -220,7 +222,7 @@ k_sol_dir(size_t n, const T *__restrict__ x, const T *__restrict__ g, int pos,
     const T gamma = ord.m ? (T)scal[0] : (T)1;
     for (int t = threadIdx.x; t < 2 * ord.m; t += blockDim.x) cf[t] = (T)coef[t];
     __syncthreads();
-    T gd = (T)0;  // d is stored in the working precision; so is its per-pixel arithmetic
+    double gd = 0.0;  // d is stored in the working precision; so is its per-pixel arithmetic
     for (int i = threadIdx.x; i < SOL_CHUNK; i += blockDim.x) {
         const size_t idx = base + i;
         if (idx >= n) continue;
@@ -235,9 +237,9 @@ k_sol_dir(size_t n, const T *__restrict__ x, const T *__restrict__ g, int pos,
             dv = -acc;
         }
         d[idx] = dv;
-        gd += gi * dv;
+        gd = fma((double)gi, (double)dv, gd);
     }
-    const double gds = block_sum_t(gd, red);
+    const double gds = block_sum(gd, red);
     if (threadIdx.x == 0) part[(size_t)blockIdx.x * stride] = gds;
 }
 
@@ -259,7 +261,7 @@ k_sol_trial(size_t n, const T *__restrict__ xk, const T *__restrict__ gk, const 
     __shared__ double red[32];
     const size_t base = (size_t)blockIdx.x * SOL_CHUNK;
     const T al = (T)alpha;
-    T acc = (T)0;
+    double acc = 0.0;
     for (int i = threadIdx.x; i < SOL_CHUNK; i += blockDim.x) {
         const size_t idx = base + i;
         if (idx >= n) continue;
@@ -267,9 +269,9 @@ k_sol_trial(size_t n, const T *__restrict__ xk, const T *__restrict__ gk, const 
         T v = xo + al * d[idx];
         if (pos && v < (T)0) v = (T)0;
         x[idx] = v;
-        acc += gk[idx] * (v - xo);
+        acc = fma((double)gk[idx], (double)(v - xo), acc);
     }
-    const double sum = block_sum_t(acc, red);
+    const double sum = block_sum(acc, red);
     if (threadIdx.x == 0) part[(size_t)blockIdx.x * stride] = sum;
 }
 
@@ -301,19 +303,19 @@ k_sol_update(size_t n, const T *__restrict__ x, const T *__restrict__ g, T *xk, 
     double *out = part + (size_t)blockIdx.x * stride;
     for (int t = 0; t < ord.m; ++t) {
         const int st = ord.slot[t];
-        T a = (T)0, b = (T)0, c = (T)0;
+        double a = 0.0, b = 0.0, c = 0.0;
         for (int i = threadIdx.x; i < SOL_CHUNK; i += blockDim.x) {
             const size_t idx = base + i;
             if (idx >= n) continue;
             const T ys = st == slot ? yv[i] : Y[(size_t)st * n + idx];
             const T ss = st == slot ? sv[i] : S[(size_t)st * n + idx];
-            a += sv[i] * ys;
-            b += ss * yv[i];
-            c += yv[i] * ys;
+            a = fma((double)sv[i], (double)ys, a);
+            b = fma((double)ss, (double)yv[i], b);
+            c = fma((double)yv[i], (double)ys, c);
         }
-        const double as = block_sum_t(a, red);
-        const double bs = block_sum_t(b, red);
-        const double cs = block_sum_t(c, red);
+        const double as = block_sum(a, red);
+        const double bs = block_sum(b, red);
+        const double cs = block_sum(c, red);
         if (threadIdx.x == 0) {
             out[3 * t] = as;
             out[3 * t + 1] = bs;

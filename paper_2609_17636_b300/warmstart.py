@@ -105,10 +105,14 @@ def make_pairs(prob: SkyProblem, skies, crop: int, crops_per_sky: int, maxiter: 
     return ts
 
 
-def train(net: UNet, ts: TrainingSet, epochs: int, batch: int, lr: float, rng, log=None):
-    """Adam on the MSE loss over shuffled mini-batches; returns the per-epoch mean loss."""
+def train(net: UNet, ts: TrainingSet, epochs: int, batch: int, lr: float, rng, log=None,
+          lr_final: float | None = None):
+    """Adam on the MSE loss over shuffled mini-batches; returns the per-epoch mean loss. With
+    lr_final, the step size follows a cosine from lr down to lr_final over the whole run."""
     n = len(ts.inputs)
     hist = []
+    steps = max(1, epochs * (n // batch))
+    step = 0
     for ep in range(epochs):
         order = rng.permutation(n)
         tot, cnt = 0.0, 0
@@ -117,7 +121,9 @@ def train(net: UNet, ts: TrainingSet, epochs: int, batch: int, lr: float, rng, l
             xb = torch.stack([ts.inputs[i] for i in idx])
             yb = torch.stack([ts.targets[i] for i in idx])
             tot += net.backward(xb, yb)
-            net.adam_step(lr)
+            a = lr if lr_final is None else lr_final + 0.5 * (lr - lr_final) * (1.0 + np.cos(np.pi * step / steps))
+            net.adam_step(a)
+            step += 1
             cnt += 1
         hist.append(tot / max(cnt, 1))
         if log:

@@ -129,18 +129,27 @@ k_adj_cols_pk(typename cplx_of<T>::type *G, typename cplx_of<T>::type *rowbuf, i
     const int sa = 2 * pk, sb = sa + 1;
     const bool hasb = sb < nslot;
     C *Ga = G + (size_t)sa * nf * nf, *Gb = G + (size_t)sb * nf * nf;
-    for (int e = j0; e < nf; e += tpl) {
-        const size_t i0 = (size_t)e * nf + col, i1 = (size_t)((nf - e) & (nf - 1)) * nf + colm;
-        const C a = Ga[i0], am = Ga[i1];
-        C b = mk((T)0, (T)0), bm = b;
-        if (hasb) {
-            b = Gb[i0];
-            bm = Gb[i1];
+    // 16 rows per thread (nf / tpl), loaded 4 rows at a time so that 16 loads are in flight
+    constexpr int RB = 4;
+    for (int i0r = 0; i0r < 16; i0r += RB) {
+        C a[RB], am[RB], b[RB], bm[RB];
+#pragma unroll
+        for (int r = 0; r < RB; ++r) {
+            const int e = j0 + (i0r + r) * tpl;
+            const size_t i0 = (size_t)e * nf + col, i1 = (size_t)((nf - e) & (nf - 1)) * nf + colm;
+            a[r] = Ga[i0];
+            am[r] = Ga[i1];
+            b[r] = hasb ? Gb[i0] : mk((T)0, (T)0);
+            bm[r] = hasb ? Gb[i1] : mk((T)0, (T)0);
         }
-        // H_a = (a + conj am)/2, H_b = (b + conj bm)/2, Z = H_a + i H_b
-        const C ha = mk((T)0.5 * (a.x + am.x), (T)0.5 * (a.y - am.y));
-        const C hb = mk((T)0.5 * (b.x + bm.x), (T)0.5 * (b.y - bm.y));
-        s[pidx((e << lgl) + L)] = mk(ha.x - hb.y, ha.y + hb.x);
+#pragma unroll
+        for (int r = 0; r < RB; ++r) {
+            const int e = j0 + (i0r + r) * tpl;
+            // H_a = (a + conj am)/2, H_b = (b + conj bm)/2, Z = H_a + i H_b
+            const C ha = mk((T)0.5 * (a[r].x + am[r].x), (T)0.5 * (a[r].y - am[r].y));
+            const C hb = mk((T)0.5 * (b[r].x + bm[r].x), (T)0.5 * (b[r].y - bm[r].y));
+            s[pidx((e << lgl) + L)] = mk(ha.x - hb.y, ha.y + hb.x);
+        }
     }
     __syncthreads();
     for (int e = j0; e < nf; e += tpl) {  // every column of both grids is read by exactly one CTA
@@ -171,7 +180,14 @@ k_adj_rows_pk(const typename cplx_of<T>::type *__restrict__ rowbuf, const T *__r
     const int q = blockIdx.x * lpb + l;
     if (q < nb) {
         const C *src = rowbuf + ((size_t)blockIdx.y * nb + q) * nf;
-        for (int e = j0; e < nf; e += tpl) s[pidx(l * nf + e)] = src[e];
+        constexpr int RB = 8;  // nf / tpl = 16 elements per thread, loaded 8 at a time
+        for (int e0 = j0; e0 < nf; e0 += RB * tpl) {
+            C v[RB];
+#pragma unroll
+            for (int r = 0; r < RB; ++r) v[r] = src[e0 + r * tpl];
+#pragma unroll
+            for (int r = 0; r < RB; ++r) s[pidx(l * nf + e0 + r * tpl)] = v[r];
+        }
     }
     __syncthreads();
     line_fft<C, +1>(s, 1, l * nf, lognf, j0, tw);

@@ -77,6 +77,7 @@ struct ivis_plan_s {
     int tile = 32, ntx = 0, ntiles = 0;  // sort bins (32 x 32 cells) of the fine grid
     int gtile = 32;                      // tile edge of the k_grid_pass work list (32 or 64)
     int xtile = 32, item_len = 32;       // k_grid_cg work list: tile edge, visibilities per item
+    int f_half = 0;  // the last forward pass wrote rows 0 .. nf/2 of F only (packed, real windows)
     int logc_cols = 0;  // log2 columns per CTA in the column FFT passes
     int chunk_cap = 1024;  // max visibilities per grid-pass chunk
     std::string tuned;     // autotuner decision (for reporting)
@@ -369,8 +370,8 @@ cudaError_t launch_grid_pass_ts(ivis_plan_s *p, int first_chunk, int nchunk, dou
     case WW: {                                                                                \
         auto kern = k_grid_pass<T, WW, MODE, TS>;                                             \
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);   \
-        kern<<<nchunk, 256, smem, p->stream>>>(ch, pd, F, G, p->lognf, ntx, beta, p->kpoly_d, \
-                                               jpart, (C *)pred);                             \
+        kern<<<nchunk, 256, smem, p->stream>>>(ch, pd, F, G, p->lognf, ntx, p->f_half, beta,  \
+                                               p->kpoly_d, jpart, (C *)pred);                 \
         break;                                                                                \
     }
     switch (p->W) {
@@ -392,7 +393,7 @@ cudaError_t launch_grid_cg_ts(ivis_plan_s *p, int first, int n, double *jpart) {
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);             \
         kern<<<n, GridCG<WW, TS>::THREADS, sm, p->stream>>>(                                          \
             p->xchunks_d + first, p->items_d, (const PairData<float> *)p->pdata_d, (const float2 *)p->F, \
-            (float2 *)p->G, p->lognf, p->kpoly_d, jpart);                                             \
+            (float2 *)p->G, p->lognf, p->f_half, p->kpoly_d, jpart);                                  \
         return cudaGetLastError();                                                                    \
     }
     switch (p->W) {
@@ -448,6 +449,7 @@ cudaError_t launch_forward(ivis_plan_s *p, const void *sky, int slot0 = 0, int n
     typedef typename cplx_of<T>::type C;
     const int nb = p->cfg.nb, nf = p->nf, tpl = nf / 16, lpb = 256 / tpl;
     if (nslots < 0) nslots = p->nslot;
+    p->f_half = packed_pass(p, slot0, nslots) ? 1 : 0;  // read by the grid passes that follow
     if (packed_pass(p, slot0, nslots)) {
         const int npk = (nslots + 1) / 2, lc = std::max(0, p->logc_cols - 1);
         dim3 gr((nb + lpb - 1) / lpb, npk);

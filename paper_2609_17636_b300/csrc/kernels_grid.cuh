@@ -51,7 +51,7 @@ template <int W, int TS>
 __global__ void __launch_bounds__(GridCG<W, TS>::THREADS, GridCG<W, TS>::MINB)
 k_grid_cg(const Chunk *__restrict__ chunks, const Item *__restrict__ items,
           const PairData<float> *__restrict__ pdata, const float2 *__restrict__ F, float2 *G, int lognf,
-          const float *__restrict__ kpoly, double *jpart) {
+          int fhalf, const float *__restrict__ kpoly, double *jpart) {
     static_assert(W <= 8, "one lane per kernel column in groups of 8");
     typedef GridCG<W, TS> P;
     constexpr int PW = P::PW, BW = P::BW, BWP = P::BWP, NG = P::NG;
@@ -69,18 +69,31 @@ k_grid_cg(const Chunk *__restrict__ chunks, const Item *__restrict__ items,
     const float2 *Fp = F + (size_t)ch.slot * nf * nf;
     float2 *Gp = G + (size_t)ch.slot * nf * nf;
     // stage F (wrapped) two cells at a time; PW is even for odd W, so pairs never straddle a
-    // row, and the wrap point nf - x0 is a multiple of TS
+    // row, and the wrap point nf - x0 is a multiple of TS. With fhalf, rows past nf/2 are not
+    // stored: F(gy, gx) = conj F(-gy, -gx) (the window is real)
     if constexpr ((PW & 1) == 0) {
         constexpr int PH = PW / 2;
         for (int i = threadIdx.x; i < PW * PH; i += P::THREADS) {
             const int ly = i / PH, lp = i - ly * PH;
             const int gy = (y0 + ly) & (nf - 1), gx = (x0 + 2 * lp) & (nf - 1);
-            reinterpret_cast<float4 *>(Fs)[i] = *reinterpret_cast<const float4 *>(Fp + (size_t)gy * nf + gx);
+            if (!fhalf || gy <= nf / 2) {
+                reinterpret_cast<float4 *>(Fs)[i] = *reinterpret_cast<const float4 *>(Fp + (size_t)gy * nf + gx);
+            } else {
+                const float2 *row = Fp + (size_t)(nf - gy) * nf;
+                const float2 f0 = row[(nf - gx) & (nf - 1)], f1 = row[(nf - gx - 1) & (nf - 1)];
+                reinterpret_cast<float4 *>(Fs)[i] = make_float4(f0.x, -f0.y, f1.x, -f1.y);
+            }
         }
     } else {
         for (int i = threadIdx.x; i < PW * PW; i += P::THREADS) {
             const int ly = i / PW, lx = i - ly * PW;
-            Fs[i] = Fp[(size_t)((y0 + ly) & (nf - 1)) * nf + ((x0 + lx) & (nf - 1))];
+            const int gy = (y0 + ly) & (nf - 1), gx = (x0 + lx) & (nf - 1);
+            if (!fhalf || gy <= nf / 2) {
+                Fs[i] = Fp[(size_t)gy * nf + gx];
+            } else {
+                const float2 f = Fp[(size_t)(nf - gy) * nf + ((nf - gx) & (nf - 1))];
+                Fs[i] = make_float2(f.x, -f.y);
+            }
         }
     }
     const int g = threadIdx.x >> 3, a = threadIdx.x & 7;

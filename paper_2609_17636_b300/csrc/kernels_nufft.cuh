@@ -397,7 +397,7 @@ template <typename T, int W, int MODE, int TS = GTILE>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 5 : 2)
 k_grid_pass(const Chunk *__restrict__ chunks, const PairData<T> *__restrict__ pdata,
             const typename cplx_of<T>::type *__restrict__ F, typename cplx_of<T>::type *G,
-            int lognf, int ntx, T beta, const float *__restrict__ kpoly,
+            int lognf, int ntx, int fhalf, T beta, const float *__restrict__ kpoly,
             double *jpart, typename cplx_of<T>::type *pred) {
     typedef typename cplx_of<T>::type C;
     constexpr int GS = W <= 4 ? 4 : (W <= 8 ? 8 : 16);
@@ -416,10 +416,18 @@ k_grid_pass(const Chunk *__restrict__ chunks, const PairData<T> *__restrict__ pd
     const int x0 = tx * tile, y0 = ty * tile;
     const C *Fp = F + (size_t)ch.slot * nf * nf;
     constexpr bool SPREAD = MODE != MODE_PREDICT;
+    // with fhalf only the rows 0 .. nf/2 of F are stored: F(gy, gx) = conj F(-gy, -gx)
     for (int i = threadIdx.x; i < PW * PW; i += blockDim.x) {
         const int ly = i / PW, lx = i - ly * PW;
         const int gy = (y0 + ly) & (nf - 1), gx = (x0 + lx) & (nf - 1);
-        if (MODE != MODE_SPREAD) Fs[i] = Fp[(size_t)gy * nf + gx];
+        if (MODE != MODE_SPREAD) {
+            if (!fhalf || gy <= nf / 2) {
+                Fs[i] = Fp[(size_t)gy * nf + gx];
+            } else {
+                const C f = Fp[(size_t)(nf - gy) * nf + ((nf - gx) & (nf - 1))];
+                Fs[i] = mk(f.x, -f.y);
+            }
+        }
         if (SPREAD) Gs[i] = mk((T)0, (T)0);
     }
     __syncthreads();

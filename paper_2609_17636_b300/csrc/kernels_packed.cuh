@@ -81,7 +81,8 @@ k_fwd_rows_pk(const T *__restrict__ sky, const T *__restrict__ wts, const PairIn
 }
 
 // ---------------------------------------------------------------------- forward columns
-// DFT along y of the packed rows, then the two spectra to F[slot a] and F[slot b].
+// DFT along y of the packed rows, then the two spectra to F[slot a] and F[slot b] (rows
+// 0 .. nf/2; the rest follows from Hermitian symmetry).
 template <typename T>
 __global__ void __launch_bounds__(sizeof(T) == 8 ? 512 : 1024)
 k_fwd_cols_pk(const typename cplx_of<T>::type *__restrict__ rowbuf, typename cplx_of<T>::type *F,
@@ -104,7 +105,9 @@ k_fwd_cols_pk(const typename cplx_of<T>::type *__restrict__ rowbuf, typename cpl
     const int sa = 2 * pk, sb = sa + 1;
     C *Fa = F + (size_t)sa * nf * nf, *Fb = F + (size_t)sb * nf * nf;
     const bool hasb = sb < nslot;
-    for (int e = j0; e < nf; e += tpl) {
+    // each window is real, so its spectrum is Hermitian, F(-k) = conj F(k): only the rows
+    // 0 .. nf/2 are written; the gridding passes read the other half mirrored
+    for (int e = j0; e <= nf / 2; e += tpl) {
         const C z = s[pidx((e << lgl) + L)];
         const C zm = s[pidx((((nf - e) & (nf - 1)) << lgl) + Lm)];  // Z(-ky, -kx)
         Fa[(size_t)e * nf + col] = mk((T)0.5 * (z.x + zm.x), (T)0.5 * (z.y - zm.y));

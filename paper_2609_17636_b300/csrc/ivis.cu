@@ -356,7 +356,7 @@ inline bool use_grid_cg(const ivis_plan_s *p) { return !p->fp64 && p->W <= 8 && 
 
 template <typename T, int MODE, int TS>
 cudaError_t launch_grid_pass_ts(ivis_plan_s *p, int first_chunk, int nchunk, double *jpart,
-                                void *pred) {
+                                void *pred, int gfold) {
     typedef typename cplx_of<T>::type C;
     const Chunk *ch = p->chunks_d + first_chunk;
     const PairData<T> *pd = (const PairData<T> *)p->pdata_d;
@@ -370,8 +370,8 @@ cudaError_t launch_grid_pass_ts(ivis_plan_s *p, int first_chunk, int nchunk, dou
     case WW: {                                                                                \
         auto kern = k_grid_pass<T, WW, MODE, TS>;                                             \
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);   \
-        kern<<<nchunk, 256, smem, p->stream>>>(ch, pd, F, G, p->lognf, ntx, p->f_half, beta,  \
-                                               p->kpoly_d, jpart, (C *)pred);                 \
+        kern<<<nchunk, 256, smem, p->stream>>>(ch, pd, F, G, p->lognf, ntx, p->f_half, gfold, \
+                                               beta, p->kpoly_d, jpart, (C *)pred);           \
         break;                                                                                \
     }
     switch (p->W) {
@@ -385,7 +385,7 @@ cudaError_t launch_grid_pass_ts(ivis_plan_s *p, int first_chunk, int nchunk, dou
 
 // k_grid_cg over chunks [first, first + n) of the item work list (p->xchunks_d).
 template <int TS>
-cudaError_t launch_grid_cg_ts(ivis_plan_s *p, int first, int n, double *jpart) {
+cudaError_t launch_grid_cg_ts(ivis_plan_s *p, int first, int n, double *jpart, int gfold) {
 #define CG_CASE(WW)                                                                                   \
     case WW: {                                                                                        \
         auto kern = k_grid_cg<WW, TS>;                                                                \
@@ -393,7 +393,7 @@ cudaError_t launch_grid_cg_ts(ivis_plan_s *p, int first, int n, double *jpart) {
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);             \
         kern<<<n, GridCG<WW, TS>::THREADS, sm, p->stream>>>(                                          \
             p->xchunks_d + first, p->items_d, (const PairData<float> *)p->pdata_d, (const float2 *)p->F, \
-            (float2 *)p->G, p->lognf, p->f_half, p->kpoly_d, jpart);                                  \
+            (float2 *)p->G, p->lognf, p->f_half, gfold, p->kpoly_d, jpart);                           \
         return cudaGetLastError();                                                                    \
     }
     switch (p->W) {
@@ -403,30 +403,36 @@ cudaError_t launch_grid_cg_ts(ivis_plan_s *p, int first, int n, double *jpart) {
 #undef CG_CASE
 }
 
+// gfold: the adjoint grid is consumed by the packed adjoint column pass, which reads only the
+// Hermitian part folded onto rows 0 .. nf/2.
 template <typename T, int MODE>
 cudaError_t launch_grid_pass(ivis_plan_s *p, int first_chunk, int nchunk, double *jpart,
-                             void *pred) {
+                             void *pred, int gfold = 0) {
     if (nchunk <= 0) return cudaSuccess;
     if constexpr (sizeof(T) == 4) {
-        if (p->gtile == 64) return launch_grid_pass_ts<T, MODE, 64>(p, first_chunk, nchunk, jpart, pred);
+        if (p->gtile == 64) return launch_grid_pass_ts<T, MODE, 64>(p, first_chunk, nchunk, jpart, pred, gfold);
     }
-    return launch_grid_pass_ts<T, MODE, 32>(p, first_chunk, nchunk, jpart, pred);
+    return launch_grid_pass_ts<T, MODE, 32>(p, first_chunk, nchunk, jpart, pred, gfold);
 }
 
 // The cost+gradient grid pass for slots [slot0, slot0 + nslots): k_grid_cg on the item work
 // list (FP32, W <= 8) or k_grid_pass on the tile work list. The pass writes one FP64 J partial
 // per chunk at jpart + (the slot range's first chunk); returns the partials written in *nj.
+bool packed_pass(const ivis_plan_s *p, int slot0, int nslots);
+
 template <typename T>
 cudaError_t launch_costgrad(ivis_plan_s *p, int slot0, int nslots, double *jpart, int *nj = nullptr) {
+    const int gfold = packed_pass(p, slot0, nslots) ? 1 : 0;  // the adjoint of these slots is packed
     if (use_grid_cg(p)) {
         const int c0 = p->xchunk_first[slot0], n = p->xchunk_first[slot0 + nslots] - c0;
         if (nj) *nj = n;
         if (n <= 0) return cudaSuccess;
-        return p->xtile == 64 ? launch_grid_cg_ts<64>(p, c0, n, jpart + c0) : launch_grid_cg_ts<32>(p, c0, n, jpart + c0);
+        return p->xtile == 64 ? launch_grid_cg_ts<64>(p, c0, n, jpart + c0, gfold)
+                              : launch_grid_cg_ts<32>(p, c0, n, jpart + c0, gfold);
     }
     const int c0 = p->chunk_first[slot0], n = p->chunk_first[slot0 + nslots] - c0;
     if (nj) *nj = n;
-    return launch_grid_pass<T, MODE_COSTGRAD>(p, c0, n, jpart + c0, nullptr);
+    return launch_grid_pass<T, MODE_COSTGRAD>(p, c0, n, jpart + c0, nullptr, gfold);
 }
 
 // Number of FP64 J partials the cost+gradient pass of all slots writes.
@@ -1299,7 +1305,8 @@ ivis_status autotune(ivis_plan_s *p) {
                             launch_grid_pass<T, MODE_PREDICT>(p, 0, n, nullptr, p->pv_d);
                             launch_grid_pass<T, MODE_SPREAD>(p, 0, n, nullptr, nullptr);
                         } else {
-                            launch_grid_pass<T, MODE_COSTGRAD>(p, 0, n, p->jpart, nullptr);
+                            launch_grid_pass<T, MODE_COSTGRAD>(p, 0, n, p->jpart, nullptr,
+                                                               packed_pass(p, 0, p->nslot) ? 1 : 0);
                         }
                     });
                 }

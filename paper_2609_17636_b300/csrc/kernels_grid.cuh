@@ -22,6 +22,9 @@
 //     column in the group's buffer.
 //   * After each item the group adds its buffer to the global adjoint grid with 16-byte vector
 //     reductions (two cells each; neighbouring blocks overlap by W - 1 cells) and clears it.
+//     The adjoint passes use only the Hermitian part (G(k) + conj G(-k)) / 2 of each grid, so
+//     with gfold a cell in a row past nf/2 is added, conjugated, to its mirror -k instead: the
+//     rows past nf/2 stay zero and are neither read nor cleared.
 #pragma once
 #include "common.cuh"
 #include "kernels_nufft.cuh"
@@ -51,7 +54,7 @@ template <int W, int TS>
 __global__ void __launch_bounds__(GridCG<W, TS>::THREADS, GridCG<W, TS>::MINB)
 k_grid_cg(const Chunk *__restrict__ chunks, const Item *__restrict__ items,
           const PairData<float> *__restrict__ pdata, const float2 *__restrict__ F, float2 *G, int lognf,
-          int fhalf, const float *__restrict__ kpoly, double *jpart) {
+          int fhalf, int gfold, const float *__restrict__ kpoly, double *jpart) {
     static_assert(W <= 8, "one lane per kernel column in groups of 8");
     typedef GridCG<W, TS> P;
     constexpr int PW = P::PW, BW = P::BW, BWP = P::BWP, NG = P::NG;
@@ -181,17 +184,36 @@ k_grid_cg(const Chunk *__restrict__ chunks, const Item *__restrict__ items,
         }
         // add the block's buffer to the adjoint grid, two cells per vector reduction, and clear
         // it for the next round (pitch BWP is even and x0 + ox is a multiple of 8, so pairs are
-        // 16-byte aligned in both memories and never straddle the grid's wrap)
+        // 16-byte aligned in both memories and never straddle the grid's wrap). A folded row
+        // (gfold, gy past nf/2) goes to row nf - gy conjugated and mirrored: buffer cells
+        // (c - 1, c), c even, land on the aligned pair (-(X + c), -(X + c) + 1), X = x0 + ox.
         if (n > 0) {
-            constexpr int BH = BWP / 2;
-            for (int i = a; i < BW * BH; i += 8) {
-                const int r = i / BH, c2 = 2 * (i - r * BH);
-                float4 *q = reinterpret_cast<float4 *>(B + r * BWP + c2);
-                const float4 val = *q;
-                *q = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (val.x == 0.f && val.y == 0.f && val.z == 0.f && val.w == 0.f) continue;
-                const int gy = (y0 + oy + r) & (nf - 1), gxx = (x0 + ox + c2) & (nf - 1);
-                atomicAdd(reinterpret_cast<float4 *>(Gp + (size_t)gy * nf + gxx), val);
+            constexpr int BH = BWP / 2;                      // pairs of a plain row
+            constexpr int BF = (BW - 1 + ((BW - 1) & 1)) / 2 + 1;  // pairs of a folded row
+            constexpr int NJ = BH > BF ? BH : BF;
+            const int X = x0 + ox;
+            for (int i = a; i < BW * NJ; i += 8) {
+                const int r = i / NJ, j = i - r * NJ;
+                const int gy = (y0 + oy + r) & (nf - 1);
+                float2 *br = B + r * BWP;
+                if (!gfold || gy <= nf / 2) {
+                    if (j >= BH) continue;
+                    float4 *q = reinterpret_cast<float4 *>(br + 2 * j);
+                    const float4 val = *q;
+                    *q = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (val.x == 0.f && val.y == 0.f && val.z == 0.f && val.w == 0.f) continue;
+                    atomicAdd(reinterpret_cast<float4 *>(Gp + (size_t)gy * nf + ((X + 2 * j) & (nf - 1))), val);
+                } else {
+                    if (j >= BF) continue;
+                    // the adjoint uses only the Hermitian part of G: c at k counts as conj(c) at -k
+                    const int c = 2 * j;
+                    float2 v0 = make_float2(0.f, 0.f), v1 = make_float2(0.f, 0.f);
+                    if (c >= 1) { v0 = br[c - 1]; br[c - 1] = make_float2(0.f, 0.f); }
+                    if (c < BW) { v1 = br[c]; br[c] = make_float2(0.f, 0.f); }
+                    if (v0.x == 0.f && v0.y == 0.f && v1.x == 0.f && v1.y == 0.f) continue;
+                    atomicAdd(reinterpret_cast<float4 *>(Gp + (size_t)(nf - gy) * nf + ((nf - X - c) & (nf - 1))),
+                              make_float4(v1.x, -v1.y, v0.x, -v0.y));
+                }
             }
         }
         __syncwarp();  // cleared before the next round's writes

@@ -397,7 +397,7 @@ template <typename T, int W, int MODE, int TS = GTILE>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 5 : 2)
 k_grid_pass(const Chunk *__restrict__ chunks, const PairData<T> *__restrict__ pdata,
             const typename cplx_of<T>::type *__restrict__ F, typename cplx_of<T>::type *G,
-            int lognf, int ntx, int fhalf, T beta, const float *__restrict__ kpoly,
+            int lognf, int ntx, int fhalf, int gfold, T beta, const float *__restrict__ kpoly,
             double *jpart, typename cplx_of<T>::type *pred) {
     typedef typename cplx_of<T>::type C;
     constexpr int GS = W <= 4 ? 4 : (W <= 8 ? 8 : 16);
@@ -572,7 +572,10 @@ k_grid_pass(const Chunk *__restrict__ chunks, const PairData<T> *__restrict__ pd
         if (g.x == (T)0 && g.y == (T)0) continue;
         const int ly = i / PW, lx = i - ly * PW;
         const int gy = (y0 + ly) & (nf - 1), gx = (x0 + lx) & (nf - 1);
-        red_add_c(&Gp[(size_t)gy * nf + gx], g);
+        // gfold: the adjoint uses the Hermitian part of G only, so a row past nf/2 is added,
+        // conjugated, to its mirror instead
+        if (!gfold || gy <= nf / 2) red_add_c(&Gp[(size_t)gy * nf + gx], g);
+        else red_add_c(&Gp[(size_t)(nf - gy) * nf + ((nf - gx) & (nf - 1))], mk(g.x, -g.y));
     }
 }
 

@@ -117,7 +117,8 @@ k_fwd_cols_pk(const typename cplx_of<T>::type *__restrict__ rowbuf, typename cpl
 
 // ---------------------------------------------------------------------- adjoint columns
 // Z = H_a + i H_b from the two adjoint grids (which are consumed and zeroed), inverse DFT along
-// y, the nb window rows to the packed row buffer.
+// y, the nb window rows to the packed row buffer. The grids arrive folded onto rows 0 .. nf/2
+// (the rows past nf/2 are zero and stay so): only those rows are read and cleared.
 template <typename T>
 __global__ void __launch_bounds__(sizeof(T) == 8 ? 512 : 1024)
 k_adj_cols_pk(typename cplx_of<T>::type *G, typename cplx_of<T>::type *rowbuf, int nslot, int nb,
@@ -140,10 +141,13 @@ k_adj_cols_pk(typename cplx_of<T>::type *G, typename cplx_of<T>::type *rowbuf, i
         for (int r = 0; r < RB; ++r) {
             const int e = j0 + (i0r + r) * tpl;
             const size_t i0 = (size_t)e * nf + col, i1 = (size_t)((nf - e) & (nf - 1)) * nf + colm;
-            a[r] = Ga[i0];
-            am[r] = Ga[i1];
-            b[r] = hasb ? Gb[i0] : mk((T)0, (T)0);
-            bm[r] = hasb ? Gb[i1] : mk((T)0, (T)0);
+            // the gridding pass folds rows past nf/2 onto their mirrors: those rows are zero
+            const bool lo = e <= nf / 2, hi = e == 0 || e >= nf / 2;
+            const C z0 = mk((T)0, (T)0);
+            a[r] = lo ? Ga[i0] : z0;
+            am[r] = hi ? Ga[i1] : z0;
+            b[r] = hasb && lo ? Gb[i0] : z0;
+            bm[r] = hasb && hi ? Gb[i1] : z0;
         }
 #pragma unroll
         for (int r = 0; r < RB; ++r) {
@@ -155,7 +159,7 @@ k_adj_cols_pk(typename cplx_of<T>::type *G, typename cplx_of<T>::type *rowbuf, i
         }
     }
     __syncthreads();
-    for (int e = j0; e < nf; e += tpl) {  // every column of both grids is read by exactly one CTA
+    for (int e = j0; e <= nf / 2; e += tpl) {  // every stored column is read by exactly one CTA
         Ga[(size_t)e * nf + col] = mk((T)0, (T)0);
         if (hasb) Gb[(size_t)e * nf + col] = mk((T)0, (T)0);
     }

@@ -286,8 +286,10 @@ def stage_bytes(prob, plan):
                      FP64) + per pair the fine grid read (F) and written (G)
       fwd_rows       per pair the window and its beam x deapodisation (nb^2 reals each) in, half
                      of a complex nb x nf row buffer out (two windows share one buffer)
-      fwd_cols       per pair half a row buffer in, the nf^2 grid out
-      adj_cols       per pair the nf^2 adjoint grid in, half a row buffer out
+      fwd_cols       per pair half a row buffer in, the stored half of the grid out (rows
+                     0 .. nf/2: the window is real, so F(-k) = conj F(k) gives the rest)
+      adj_cols       per pair the stored half of the adjoint grid in (the gridding pass folds
+                     the rest onto it), half a row buffer out
       adj_rows       per pair half a row buffer in, the beam in and the window contribution out
       assemble_R     sky and gradient images + per pair the nb^2 window contribution"""
     w, beta, nf = plan.nufft_params()
@@ -299,11 +301,12 @@ def stage_bytes(prob, plan):
     M = prob.total_vis
     npix = prob.nchan * prob.n * prob.n
     half_row = cs * nb * nf // 2
+    half_grid = cs * (nf // 2 + 1) * nf              # rows 0 .. nf/2 of a fine grid
     out = {
         "degrid_spread": vis_b * M + 2 * cs * nf * nf * npair,
         "fwd_rows": npair * (2 * rs * nb * nb + half_row),
-        "fwd_cols": npair * (half_row + cs * nf * nf),
-        "adj_cols": npair * (cs * nf * nf + half_row),
+        "fwd_cols": npair * (half_row + half_grid),
+        "adj_cols": npair * (half_grid + half_row),
         "adj_rows": npair * (half_row + 2 * rs * nb * nb),
         "assemble_R": npix * rs * 2 + npair * nb * nb * rs,
     }
@@ -316,7 +319,7 @@ def roofline_of(prob, plan, stages, hbm, peak_source):
     """Roofline of the dominant kernel: the single-kernel stage with the longest measured time
     in the data-term chain. The dish-beam convolution branch (fusion_K, present when
     lambda_s != 0) runs on a forked stream concurrently with that chain; its stage time
-    overlaps the others and it is four launches, so it is reported in stage_ms but not chosen."""
+    overlaps the others and it is several launches, so it is reported in stage_ms but not chosen."""
     sb = stage_bytes(prob, plan)
     single = {k: v for k, v in stages.items() if k in SINGLE_KERNEL_STAGES and v > 0}
     dom = max(single, key=single.get)

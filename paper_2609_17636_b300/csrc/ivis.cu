@@ -591,11 +591,10 @@ cudaError_t launch_fusion(ivis_plan_s *p, cudaStream_t st, const void *sky, void
                                                       nullptr, nullptr, nullptr);
             return cudaGetLastError();
         }
+        // the fused column pass leaves the column convolution of e; one row pass finishes B^T e
         k_sdconv_cols<T, 1><<<gc, ntc, smc, st>>>((const T *)p->tmp1, (T *)p->tmp2, sp, n, p->sd_logN, logc, tw,
                                                   (const T *)p->tsd_d, p->inv_sig2_d, p->kpart);
-        k_sdconv_rows<T><<<gr, nt, smr, st>>>((const T *)p->tmp2, (T *)p->tmp1, sp, n, p->sd_logN, tw);
-        k_sdconv_cols<T, 0><<<gc, ntc, smc, st>>>((const T *)p->tmp1, (T *)gradK_out, sp, n, p->sd_logN, logc, tw,
-                                                  nullptr, nullptr, nullptr);
+        k_sdconv_rows<T><<<gr, nt, smr, st>>>((const T *)p->tmp2, (T *)gradK_out, sp, n, p->sd_logN, tw);
         return cudaGetLastError();
     }
     const size_t sm = conv_smem<T>(R);
@@ -650,7 +649,7 @@ cudaError_t enqueue_eval(ivis_plan_s *p, bool capture) {
         }
         stage_begin(p, "fusion_K", st, si);
         if ((e = launch_fusion<T>(p, st, p->x, nullptr, p->gradK, true)) != cudaSuccess) return e;
-        launches += 4;
+        launches += p->sd_N ? 3 : 4;  // line-DFT passes, or the direct-tap passes
         stage_end(p, st, si);
         if (fork) cudaEventRecord(p->ev_join, p->side);
     }

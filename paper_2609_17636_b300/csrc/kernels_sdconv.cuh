@@ -8,7 +8,10 @@
 // spectrum spec[k] = (b[0] + 2 sum_{t>=1} b[t] cos(2 pi k t / N)) / N (real and even), inverse
 // DFT, crop. Two real lines share one complex line (the real-even filter keeps the real and
 // imaginary parts apart). The column pass can fuse the single-dish residual
-// e = (t - T) / sigma^2 and the per-CTA partials of K = 1/2 sum (t - T)^2 / sigma^2.
+// e = (t - T) / sigma^2, the per-CTA partials of K = 1/2 sum (t - T)^2 / sigma^2 and the first
+// pass of the gradient B^T e: the taps are symmetric (B^T = B) and the two axes' passes
+// commute, so the column pass convolves e along its column at once and one row pass finishes
+// the gradient (three launches in all instead of four).
 #pragma once
 #include "common.cuh"
 #include "fft.cuh"
@@ -53,8 +56,8 @@ k_sdconv_rows(const T *__restrict__ in, T *out, const T *__restrict__ spec, int 
 }
 
 // Columns: a CTA owns 2 * ncol adjacent columns of channel blockIdx.y; complex line q carries
-// columns x0 + q and x0 + ncol + q. FUSED: out = (t - tsd) * inv_sig2[c] and this CTA's share
-// of K to kpart[c * gridDim.x + blockIdx.x].
+// columns x0 + q and x0 + ncol + q. FUSED: with e = (t - tsd) * inv_sig2[c], out = the column
+// convolution of e, and this CTA's share of K to kpart[c * gridDim.x + blockIdx.x].
 template <typename T, int FUSED>
 __global__ void __launch_bounds__(sizeof(T) == 8 ? 512 : 1024)
 k_sdconv_cols(const T *__restrict__ in, T *out, const T *__restrict__ spec, int n, int logN, int logc,
@@ -84,30 +87,45 @@ k_sdconv_cols(const T *__restrict__ in, T *out, const T *__restrict__ spec, int 
     }
     __syncthreads();
     line_fft<C, +1>(s, ncol, q, logN, j0, tw);
-    T kloc = (T)0;  // at most 2 n / tpl terms per thread in the working precision, then FP64
-    const T is2 = FUSED ? (T)inv_sig2[c] : (T)0;
+    if (FUSED) {
+        // e in place of t (zero outside the image: the padding of the second convolution)
+        T kloc = (T)0;  // at most 2 n / tpl terms per thread in the working precision, then FP64
+        const T is2 = (T)inv_sig2[c];
+        for (int e = j0; e < N; e += tpl) {
+            C &v = s[pidx((e << logc) + q)];
+            C o = mk((T)0, (T)0);
+            if (e < n) {
+                const size_t ia = img + (size_t)e * n + xa, ib = img + (size_t)e * n + xb;
+                if (xa < n) {
+                    const T d = v.x - tsd[ia];
+                    kloc += (T)0.5 * d * d * is2;
+                    o.x = d * is2;
+                }
+                if (xb < n) {
+                    const T d = v.y - tsd[ib];
+                    kloc += (T)0.5 * d * d * is2;
+                    o.y = d * is2;
+                }
+            }
+            v = o;
+        }
+        __syncthreads();
+        line_fft<C, -1>(s, ncol, q, logN, j0, tw);
+        for (int e = j0; e < N; e += tpl) {
+            C &v = s[pidx((e << logc) + q)];
+            const T b = sp[e];
+            v = mk(v.x * b, v.y * b);
+        }
+        __syncthreads();
+        line_fft<C, +1>(s, ncol, q, logN, j0, tw);
+        const double ks = block_sum((double)kloc, red);
+        if (threadIdx.x == 0) kpart[(size_t)c * gridDim.x + blockIdx.x] = ks;
+    }
     for (int e = j0; e < n; e += tpl) {
         const C v = s[pidx((e << logc) + q)];
         const size_t ia = img + (size_t)e * n + xa, ib = img + (size_t)e * n + xb;
-        if (FUSED) {
-            if (xa < n) {
-                const T d = v.x - tsd[ia];
-                kloc += (T)0.5 * d * d * is2;
-                out[ia] = d * is2;
-            }
-            if (xb < n) {
-                const T d = v.y - tsd[ib];
-                kloc += (T)0.5 * d * d * is2;
-                out[ib] = d * is2;
-            }
-        } else {
-            if (xa < n) out[ia] = v.x;
-            if (xb < n) out[ib] = v.y;
-        }
-    }
-    if (FUSED) {
-        const double ks = block_sum((double)kloc, red);
-        if (threadIdx.x == 0) kpart[(size_t)c * gridDim.x + blockIdx.x] = ks;
+        if (xa < n) out[ia] = v.x;
+        if (xb < n) out[ib] = v.y;
     }
 }
 

@@ -31,7 +31,8 @@ def test_fft_bytes_count_the_packed_passes_once():
     prob = synth.config_c2()
     nb, nf = 512, 1024
     sb = bench.stage_bytes(prob, _Plan("fp32", nf))
-    per_pair = 2 * 4 * nb * nb + 8 * nb * nf + 8 * nf * nf  # window + beam, half a row buffer each way, grid
+    # window + beam, half a row buffer each way, the stored half (rows 0 .. nf/2) of the grid
+    per_pair = 2 * 4 * nb * nb + 8 * nb * nf + 8 * (nf // 2 + 1) * nf
     assert sb["fwd_fft"] == sb["adj_fft"] == 7 * per_pair
     assert sb["assemble_R"] == 2 * 4 * 512 * 512 + 7 * 4 * nb * nb
 
@@ -40,7 +41,7 @@ def test_pairs_without_data_move_nothing():
     prob = synth.small_mosaic(3, n=48, nb=32, nchan=1, npoint=3, ndump=2, n_ant=5)
     prob.pairs[1].uvw = prob.pairs[1].uvw[:0]
     sb = bench.stage_bytes(prob, _Plan("fp32", 64))
-    assert sb["fwd_fft"] == 2 * (2 * 4 * 32 * 32 + 8 * 32 * 64 + 8 * 64 * 64)
+    assert sb["fwd_fft"] == 2 * (2 * 4 * 32 * 32 + 8 * 32 * 64 + 8 * 33 * 64)
 
 
 class _FakeNVML:
@@ -167,8 +168,9 @@ def test_per_kernel_stage_bytes_add_up_to_the_packed_fft_totals():
     nb, nf = 512, 1024
     sb = bench.stage_bytes(prob, _Plan("fp32", nf))
     assert sb["fwd_rows"] == 7 * (2 * 4 * nb * nb + 8 * nb * nf // 2)
-    assert sb["fwd_cols"] == 7 * (8 * nb * nf // 2 + 8 * nf * nf)
-    assert sb["adj_cols"] == 7 * (8 * nf * nf + 8 * nb * nf // 2)
+    # the column passes store and read only rows 0 .. nf/2 of each fine grid
+    assert sb["fwd_cols"] == 7 * (8 * nb * nf // 2 + 8 * (nf // 2 + 1) * nf)
+    assert sb["adj_cols"] == 7 * (8 * (nf // 2 + 1) * nf + 8 * nb * nf // 2)
     assert sb["adj_rows"] == 7 * (8 * nb * nf // 2 + 2 * 4 * nb * nb)
     assert sb["fwd_rows"] + sb["fwd_cols"] == sb["fwd_fft"] and sb["adj_cols"] + sb["adj_rows"] == sb["adj_fft"]
 

@@ -43,12 +43,20 @@ struct GridCG {
     static constexpr int FCELLS = (PW * PW + 1) & ~1;  // F patch cells, even: buffers 16-byte aligned
     static constexpr int BW = 8 + W - 1;          // block buffer edge (cells)
     static constexpr int BWP = BW + (BW & 1);     // buffer row pitch: even, 16-byte cell pairs
+    static constexpr int BSEG = (BW * BWP + 7) / 8;  // 8-cell segments of one group buffer
     static constexpr int NBX = TS / 8;            // blocks per tile row
     static constexpr int NG = TS == 64 ? 32 : 16; // groups of 8 lanes
     static constexpr int THREADS = NG * 8;
     static constexpr int MINB = TS == 64 ? 2 : 5;
-    static constexpr size_t SMEM = (size_t)FCELLS * sizeof(float2) + (size_t)NG * BW * BWP * sizeof(float2);
+    static constexpr size_t SMEM = (size_t)FCELLS * sizeof(float2) + (size_t)(NG / 2) * BSEG * 16 * sizeof(float2);
 };
+
+// Group buffers in "half lines": buffer cell i (row-major, pitch BWP) of group g sits in half
+// g & 1 (64 bytes, 16 banks) of the 128-byte line i / 8 of its group pair, at position i % 8.
+// A group's 8 lanes touch 8 consecutive cells, which have distinct positions, so they cover
+// exactly their half's banks, and the two groups of a half-warp (served together for 8-byte
+// accesses) never meet on a bank: the spreading read-modify-writes are conflict-free.
+__device__ __forceinline__ int hl_off(int i) { return i + (i & ~7); }  // float2 offset in the pair's lines
 
 template <int W, int TS>
 __global__ void __launch_bounds__(GridCG<W, TS>::THREADS, GridCG<W, TS>::MINB)
@@ -62,7 +70,7 @@ k_grid_cg(const Chunk *__restrict__ chunks, const Item *__restrict__ items,
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double red[32];
     float2 *Fs = reinterpret_cast<float2 *>(smem_raw);   // [PW][PW] tile patch of F
-    float2 *buf = Fs + P::FCELLS;                         // [NG][BW][BWP] group buffers
+    float2 *buf = Fs + P::FCELLS;                         // [NG/2][BSEG][2][8] group buffers
     const int nf = 1 << lognf, ntx = nf / TS;
     const Chunk ch = chunks[blockIdx.x];  // begin/end: this chunk's items
     const int nitem = ch.end - ch.begin;
@@ -100,8 +108,8 @@ k_grid_cg(const Chunk *__restrict__ chunks, const Item *__restrict__ items,
         }
     }
     const int g = threadIdx.x >> 3, a = threadIdx.x & 7;
-    float2 *B = buf + (size_t)g * BW * BWP;
-    for (int i = a; i < BW * BWP / 2; i += 8) reinterpret_cast<float4 *>(B)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    float2 *B = buf + (size_t)(g >> 1) * P::BSEG * 16 + 8 * (g & 1);  // cell i at B[hl_off(i)]
+    for (int l = 0; l < P::BSEG; ++l) B[l * 16 + a] = make_float2(0.f, 0.f);
     __syncthreads();  // F staged, buffers clear
     const bool col_on = a < W;
     float pc[KD + 1];
@@ -171,20 +179,22 @@ k_grid_cg(const Chunk *__restrict__ chunks, const Item *__restrict__ items,
             if (on) {
                 const float s = kxa * w;
                 const float cx = s * rx, cy = s * ry;
-                float2 *br = B + ly * BWP + lx + a;
+                const int i0 = ly * BWP + lx + a;
 #pragma unroll
                 for (int b = 0; b < W; ++b) {
-                    float2 t = br[b * BWP];
+                    float2 *q = B + hl_off(i0 + b * BWP);
+                    float2 t = *q;
                     t.x = fmaf(ky[b], cx, t.x);
                     t.y = fmaf(ky[b], cy, t.y);
-                    br[b * BWP] = t;
+                    *q = t;
                 }
             }
             __syncwarp();  // this visibility's buffer writes before the next one's reads
         }
         // add the block's buffer to the adjoint grid, two cells per vector reduction, and clear
-        // it for the next round (pitch BWP is even and x0 + ox is a multiple of 8, so pairs are
-        // 16-byte aligned in both memories and never straddle the grid's wrap). A folded row
+        // it for the next round (pitch BWP is even and x0 + ox is a multiple of 8, so pairs
+        // start at even cells: 16-byte aligned in both memories, inside one half line, and
+        // never across the grid's wrap). A folded row
         // (gfold, gy past nf/2) goes to row nf - gy conjugated and mirrored: buffer cells
         // (c - 1, c), c even, land on the aligned pair (-(X + c), -(X + c) + 1), X = x0 + ox.
         if (n > 0) {
@@ -195,10 +205,10 @@ k_grid_cg(const Chunk *__restrict__ chunks, const Item *__restrict__ items,
             for (int i = a; i < BW * NJ; i += 8) {
                 const int r = i / NJ, j = i - r * NJ;
                 const int gy = (y0 + oy + r) & (nf - 1);
-                float2 *br = B + r * BWP;
+                const int ir = r * BWP;
                 if (!gfold || gy <= nf / 2) {
                     if (j >= BH) continue;
-                    float4 *q = reinterpret_cast<float4 *>(br + 2 * j);
+                    float4 *q = reinterpret_cast<float4 *>(B + hl_off(ir + 2 * j));
                     const float4 val = *q;
                     *q = make_float4(0.f, 0.f, 0.f, 0.f);
                     if (val.x == 0.f && val.y == 0.f && val.z == 0.f && val.w == 0.f) continue;
@@ -208,8 +218,16 @@ k_grid_cg(const Chunk *__restrict__ chunks, const Item *__restrict__ items,
                     // the adjoint uses only the Hermitian part of G: c at k counts as conj(c) at -k
                     const int c = 2 * j;
                     float2 v0 = make_float2(0.f, 0.f), v1 = make_float2(0.f, 0.f);
-                    if (c >= 1) { v0 = br[c - 1]; br[c - 1] = make_float2(0.f, 0.f); }
-                    if (c < BW) { v1 = br[c]; br[c] = make_float2(0.f, 0.f); }
+                    if (c >= 1) {
+                        float2 *q0 = B + hl_off(ir + c - 1);
+                        v0 = *q0;
+                        *q0 = make_float2(0.f, 0.f);
+                    }
+                    if (c < BW) {
+                        float2 *q1 = B + hl_off(ir + c);
+                        v1 = *q1;
+                        *q1 = make_float2(0.f, 0.f);
+                    }
                     if (v0.x == 0.f && v0.y == 0.f && v1.x == 0.f && v1.y == 0.f) continue;
                     atomicAdd(reinterpret_cast<float4 *>(Gp + (size_t)(nf - gy) * nf + ((nf - X - c) & (nf - 1))),
                               make_float4(v1.x, -v1.y, v0.x, -v0.y));

@@ -276,6 +276,7 @@ SINGLE_KERNEL_STAGES = {
     "fwd_cols": "k_fwd_cols_pk (column FFT, spectra of the two windows separated)",
     "degrid_spread": "k_grid_cg (fused interpolation + residual + J partial + spreading)",
     "adj_cols": "k_adj_cols_pk (adjoint column FFT, Hermitian parts, nb rows kept)",
+    "clear_G": "k_clear_half (the read halves of the adjoint grids back to zero)",
     "adj_rows": "k_adj_rows_pk (adjoint row FFT + deapodisation + Re + beam)",
 }
 
@@ -290,6 +291,7 @@ def stage_bytes(prob, plan):
                      0 .. nf/2: the window is real, so F(-k) = conj F(k) gives the rest)
       adj_cols       per pair the stored half of the adjoint grid in (the gridding pass folds
                      the rest onto it), half a row buffer out
+      clear_G        per pair the stored half of the adjoint grid written (zeros)
       adj_rows       per pair half a row buffer in, the beam in and the window contribution out
       assemble_R     sky and gradient images + per pair the nb^2 window contribution"""
     w, beta, nf = plan.nufft_params()
@@ -307,6 +309,7 @@ def stage_bytes(prob, plan):
         "fwd_rows": npair * (2 * rs * nb * nb + half_row),
         "fwd_cols": npair * (half_row + half_grid),
         "adj_cols": npair * (half_grid + half_row),
+        "clear_G": npair * half_grid,
         "adj_rows": npair * (half_row + 2 * rs * nb * nb),
         "assemble_R": npix * rs * 2 + npair * nb * nb * rs,
     }
@@ -409,6 +412,9 @@ def run_ivis(args, rank, world):
         if tr.get("stage") == roofline["stage"] and tr.get("tile", "") in tuning:
             roofline["traffic"] = tr.get("dram_bytes_per_launch")
             roofline["traffic_source"] = tr.get("source")
+            if tr.get("bottleneck"):
+                # what the same capture shows the kernel is bound by, when it is not HBM
+                roofline["measured_bottleneck"] = tr["bottleneck"]
 
     # end to end through the host-buffer entry point
     xh = torch.empty_like(x, device="cpu").pin_memory()

@@ -69,7 +69,9 @@ struct ivis_plan_s {
     ivis_config cfg{};
     cudaStream_t user_stream = nullptr;      // the caller's stream (may be the legacy default)
     cudaStream_t stream = nullptr, side = nullptr;  // the plan's own capturable streams
+    cudaStream_t side2 = nullptr;                     // clearing of G beside the adjoint row pass
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_in = nullptr;
+    cudaEvent_t ev_cfork = nullptr, ev_cjoin = nullptr;
     bool fp64 = true;
     size_t rsz = 8;  // sizeof(real)
     int nf = 0, lognf = 0, W = 0;
@@ -79,6 +81,7 @@ struct ivis_plan_s {
     int xtile = 32, item_len = 32;       // k_grid_cg work list: tile edge, visibilities per item
     int f_half = 0;  // the last forward pass wrote rows 0 .. nf/2 of F only (packed, real windows)
     int logc_cols = 0;  // log2 columns per CTA in the column FFT passes
+    int clear_blocks = 8 * 148;  // CTAs of the grid-stride clearing kernel (8 per SM)
     int chunk_cap = 1024;  // max visibilities per grid-pass chunk
     std::string tuned;     // autotuner decision (for reporting)
     std::vector<double> dinv_h;
@@ -493,9 +496,12 @@ cudaError_t launch_forward(ivis_plan_s *p, const void *sky, int slot0 = 0, int n
     return cudaGetLastError();
 }
 
-// Adjoint passes for slots [slot0, slot0 + nslots) (all slots by default).
+// Adjoint passes for slots [slot0, slot0 + nslots) (all slots by default). clear_st: when
+// given, the packed path clears G on that stream (forked after the column pass; the caller
+// joins p->ev_cjoin), concurrently with the row pass.
 template <typename T>
-cudaError_t launch_adjoint(ivis_plan_s *p, int slot0 = 0, int nslots = -1, int *si = nullptr) {
+cudaError_t launch_adjoint(ivis_plan_s *p, int slot0 = 0, int nslots = -1, int *si = nullptr,
+                           cudaStream_t clear_st = nullptr) {
     typedef typename cplx_of<T>::type C;
     const int nb = p->cfg.nb, nf = p->nf, tpl = nf / 16, lpb = 256 / tpl;
     if (nslots < 0) nslots = p->nslot;
@@ -508,6 +514,17 @@ cudaError_t launch_adjoint(ivis_plan_s *p, int slot0 = 0, int nslots = -1, int *
         k_adj_cols_pk<T><<<gc, tpl << (lc + 1), smem_col, p->stream>>>((C *)p->G, (C *)p->rowbuf, nslots, nb,
                                                                        p->lognf, lc, (const C *)p->tw_d);
         if (si) stage_end(p, p->stream, *si);
+        // the read halves of G back to zero for the next gridding pass
+        cudaStream_t cs = p->stream;
+        if (clear_st) {
+            cudaEventRecord(p->ev_cfork, p->stream);
+            cudaStreamWaitEvent(clear_st, p->ev_cfork, 0);
+            cs = clear_st;
+        }
+        if (si) stage_begin(p, "clear_G", cs, *si);
+        k_clear_half<T><<<dim3(std::max(1, p->clear_blocks / nslots), nslots), 256, 0, cs>>>((C *)p->G, p->lognf);
+        if (si) stage_end(p, cs, *si);
+        if (clear_st) cudaEventRecord(p->ev_cjoin, clear_st);
         dim3 gr((nb + lpb - 1) / lpb, npk);
         size_t smem_row = (size_t)fft_smem_elems(nf, lpb) * sizeof(C);
         cudaFuncSetAttribute(k_adj_rows_pk<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_row);
@@ -640,6 +657,7 @@ cudaError_t enqueue_eval(ivis_plan_s *p, bool capture) {
     int si = 0;
     int launches = 0;
     const bool fork = capture && use_k;
+    bool cjoin = false;  // G cleared on side2: join before the end
     if (use_k) {
         cudaStream_t st = p->stream;
         if (fork) {
@@ -691,18 +709,20 @@ cudaError_t enqueue_eval(ivis_plan_s *p, bool capture) {
             }
             stage_end(p, p->stream, si);
         } else {
-            // one stage per kernel: fwd_rows, fwd_cols, degrid_spread, adj_cols, adj_rows
+            // one stage per kernel: fwd_rows, fwd_cols, degrid_spread, adj_cols, clear_G, adj_rows
             if ((e = launch_forward<T>(p, p->x, 0, -1, &si)) != cudaSuccess) return e;
             launches += 2;
             stage_begin(p, "degrid_spread", p->stream, si);
             if ((e = launch_costgrad<T>(p, 0, p->nslot, p->jpart)) != cudaSuccess) return e;
             launches += 1;
             stage_end(p, p->stream, si);
-            if ((e = launch_adjoint<T>(p, 0, -1, &si)) != cudaSuccess) return e;
-            launches += 2;
+            if ((e = launch_adjoint<T>(p, 0, -1, &si, capture ? p->side2 : nullptr)) != cudaSuccess) return e;
+            launches += 3;  // adjoint columns, clearing of G (beside the rows when captured), adjoint rows
+            cjoin = capture;
         }
     }
     if (fork) cudaStreamWaitEvent(p->stream, p->ev_join, 0);
+    if (cjoin) cudaStreamWaitEvent(p->stream, p->ev_cjoin, 0);
     const int n = p->cfg.n, nchan = p->cfg.nchan;
     const size_t npix = (size_t)nchan * n * n;
     stage_begin(p, "assemble_R", p->stream, si);
@@ -1939,6 +1959,13 @@ ivis_status ivis_plan(const ivis_config *cfg, void *stream, ivis_plan_t *out) {
     p->rsz = p->fp64 ? 8 : 4;
     p->nf = 2 * c.nb;
     p->lognf = ilog2(p->nf);
+    {
+        int dev = 0, sms = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && sms > 0)
+            p->clear_blocks = 8 * sms;
+        cudaGetLastError();  // no device here: keep the default
+    }
     if (!p->fp64 && p->nf > 4096) { delete p; return fail(nullptr, IVIS_ERR_ARG, "IVIS_FP32 supports nb <= 2048"); }
     if (c.kernel_width) p->W = c.kernel_width;
     else p->W = std::min(16, std::max(2, (int)std::ceil(-std::log10(c.nufft_tol)) + 1));
@@ -2016,12 +2043,15 @@ ivis_status ivis_plan(const ivis_config *cfg, void *stream, ivis_plan_t *out) {
         if (!s) s = p->fp64 ? upload_real<double>(p, &p->wcorr_d, wcorr) : upload_real<float>(p, &p->wcorr_d, wcorr);
     }
     if (!s && cudaStreamCreateWithFlags(&p->side, cudaStreamNonBlocking) != cudaSuccess) s = IVIS_ERR_CUDA;
+    if (!s && cudaStreamCreateWithFlags(&p->side2, cudaStreamNonBlocking) != cudaSuccess) s = IVIS_ERR_CUDA;
     if (!s && cudaEventCreateWithFlags(&p->ev_in, cudaEventDisableTiming) != cudaSuccess) s = IVIS_ERR_CUDA;
     for (int i = 0; i < MAX_STAGES && !s; ++i)
         if (cudaEventCreate(&p->stages[i].b) != cudaSuccess || cudaEventCreate(&p->stages[i].e) != cudaSuccess)
             s = IVIS_ERR_CUDA;
     if (!s && cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming) != cudaSuccess) s = IVIS_ERR_CUDA;
     if (!s && cudaEventCreateWithFlags(&p->ev_join, cudaEventDisableTiming) != cudaSuccess) s = IVIS_ERR_CUDA;
+    if (!s && cudaEventCreateWithFlags(&p->ev_cfork, cudaEventDisableTiming) != cudaSuccess) s = IVIS_ERR_CUDA;
+    if (!s && cudaEventCreateWithFlags(&p->ev_cjoin, cudaEventDisableTiming) != cudaSuccess) s = IVIS_ERR_CUDA;
     if (!s && cudaMallocHost((void **)&p->cost_h, 4 * sizeof(double)) != cudaSuccess) s = IVIS_ERR_OOM;
     if (s) {
         g_plan_error = p->err.empty() ? "plan set-up failed" : p->err;
@@ -2444,7 +2474,10 @@ ivis_status ivis_destroy(ivis_plan_t p) {
     }
     if (p->ev_fork) cudaEventDestroy(p->ev_fork);
     if (p->ev_join) cudaEventDestroy(p->ev_join);
+    if (p->ev_cfork) cudaEventDestroy(p->ev_cfork);
+    if (p->ev_cjoin) cudaEventDestroy(p->ev_cjoin);
     if (p->side) cudaStreamDestroy(p->side);
+    if (p->side2) cudaStreamDestroy(p->side2);
     if (p->ev_in) cudaEventDestroy(p->ev_in);
     if (p->stream) cudaStreamDestroy(p->stream);
     if (p->cost_h) cudaFreeHost(p->cost_h);

@@ -49,7 +49,7 @@ __device__ __forceinline__ int pk_mirror_line(int L, int c0, int ncol) {
 // ------------------------------------------------------------------------- forward rows
 // Line l: window row q of the slot pair (2 blockIdx.y, 2 blockIdx.y + 1) -> DFT along x.
 template <typename T>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, sizeof(T) == 8 ? 1 : 4)
 k_fwd_rows_pk(const T *__restrict__ sky, const T *__restrict__ wts, const PairInfo *__restrict__ pinfo,
               int nslot, typename cplx_of<T>::type *rowbuf, int n, int nb,
               int lognf, const typename cplx_of<T>::type *__restrict__ tw, const float2 *__restrict__ grids) {
@@ -63,14 +63,16 @@ k_fwd_rows_pk(const T *__restrict__ sky, const T *__restrict__ wts, const PairIn
     const PairInfo pb = hasb ? pinfo[sb] : pa;
     const int l = threadIdx.x / tpl, j0 = threadIdx.x - l * tpl;
     const int q = blockIdx.x * lpb + l;
-    for (int e = j0; e < nf; e += tpl) s[pidx(l * nf + e)] = mk((T)0, (T)0);
-    __syncthreads();
-    if (q < nb) {
-        for (int p = j0; p < nb; p += tpl) {
+    // entry e of the line holds window column p = e + nb/2 (mod nf) if p < nb, else zero
+    for (int e = j0; e < nf; e += tpl) {
+        const int p = (e + nb / 2) & (nf - 1);
+        C v = mk((T)0, (T)0);
+        if (q < nb && p < nb) {
             const T va = window_value(pa, q, p, sky, wts, grids, n, nb);
             const T vb = hasb ? window_value(pb, q, p, sky, wts, grids, n, nb) : (T)0;
-            s[pidx(l * nf + ((p - nb / 2) & (nf - 1)))] = mk(va, vb);
+            v = mk(va, vb);
         }
+        s[pidx(l * nf + e)] = v;
     }
     __syncthreads();
     line_fft<C, -1>(s, 1, l * nf, lognf, j0, tw);
@@ -116,9 +118,9 @@ k_fwd_cols_pk(const typename cplx_of<T>::type *__restrict__ rowbuf, typename cpl
 }
 
 // ---------------------------------------------------------------------- adjoint columns
-// Z = H_a + i H_b from the two adjoint grids (which are consumed and zeroed), inverse DFT along
-// y, the nb window rows to the packed row buffer. The grids arrive folded onto rows 0 .. nf/2
-// (the rows past nf/2 are zero and stay so): only those rows are read and cleared.
+// Z = H_a + i H_b from the two adjoint grids, inverse DFT along y, the nb window rows to the
+// packed row buffer. The grids arrive folded onto rows 0 .. nf/2 (the rows past nf/2 are zero
+// and stay so): only those rows are read; k_clear_half clears them afterwards.
 template <typename T>
 __global__ void __launch_bounds__(sizeof(T) == 8 ? 512 : 1024)
 k_adj_cols_pk(typename cplx_of<T>::type *G, typename cplx_of<T>::type *rowbuf, int nslot, int nb,
@@ -159,13 +161,24 @@ k_adj_cols_pk(typename cplx_of<T>::type *G, typename cplx_of<T>::type *rowbuf, i
         }
     }
     __syncthreads();
-    for (int e = j0; e <= nf / 2; e += tpl) {  // every stored column is read by exactly one CTA
-        Ga[(size_t)e * nf + col] = mk((T)0, (T)0);
-        if (hasb) Gb[(size_t)e * nf + col] = mk((T)0, (T)0);
-    }
     line_fft<C, +1>(s, nl, L, lognf, j0, tw);
     C *dst = rowbuf + (size_t)pk * nb * nf;
     for (int q = j0; q < nb; q += tpl) dst[(size_t)q * nf + col] = s[pidx((((q - nb / 2) & (nf - 1)) << lgl) + L)];
+}
+
+// Rows 0 .. nf/2 of each of nslot adjoint grids back to zero for the next gridding pass: one
+// contiguous run of (nf/2 + 1) nf cells per grid, cleared with 16-byte stores (whole cache
+// lines, unlike zero stores from the column pass, which would cover 64-byte column segments).
+// Grid: (CTAs per grid, nslot).
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_clear_half(typename cplx_of<T>::type *G, int lognf) {
+    const int nf = 1 << lognf;
+    // 16-byte stores per grid: rows 0 .. nf/2, (nf/2 + 1) nf cells of 8 (FP32) or 16 (FP64) bytes
+    const int run = (int)((size_t)(nf / 2 + 1) * nf * sizeof(typename cplx_of<T>::type) / 16);
+    float4 *g = reinterpret_cast<float4 *>(G + (size_t)blockIdx.y * nf * nf);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < run; i += gridDim.x * blockDim.x)
+        g[i] = make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
 // ------------------------------------------------------------------------- adjoint rows

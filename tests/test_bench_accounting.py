@@ -171,6 +171,7 @@ def test_per_kernel_stage_bytes_add_up_to_the_packed_fft_totals():
     # the column passes store and read only rows 0 .. nf/2 of each fine grid
     assert sb["fwd_cols"] == 7 * (8 * nb * nf // 2 + 8 * (nf // 2 + 1) * nf)
     assert sb["adj_cols"] == 7 * (8 * (nf // 2 + 1) * nf + 8 * nb * nf // 2)
+    assert sb["clear_G"] == 7 * 8 * (nf // 2 + 1) * nf
     assert sb["adj_rows"] == 7 * (8 * nb * nf // 2 + 2 * 4 * nb * nb)
     assert sb["fwd_rows"] + sb["fwd_cols"] == sb["fwd_fft"] and sb["adj_cols"] + sb["adj_rows"] == sb["adj_fft"]
 

@@ -99,8 +99,12 @@ k_fwd_cols_pk(const typename cplx_of<T>::type *__restrict__ rowbuf, typename cpl
     for (int e = j0; e < nf; e += tpl) s[pidx((e << lgl) + L)] = mk((T)0, (T)0);
     __syncthreads();
     const C *src = rowbuf + (size_t)pk * nb * nf;
-    for (int q = j0; q < nb; q += tpl)
-        s[pidx((((q - nb / 2) & (nf - 1)) << lgl) + L)] = src[(size_t)q * nf + col];
+    // nb = nf / 2 rows: 8 per thread, all loaded before they are stored
+    C v[8];
+#pragma unroll
+    for (int r = 0; r < 8; ++r) v[r] = src[(size_t)(j0 + r * tpl) * nf + col];
+#pragma unroll
+    for (int r = 0; r < 8; ++r) s[pidx((((j0 + r * tpl - nb / 2) & (nf - 1)) << lgl) + L)] = v[r];
     __syncthreads();
     line_fft<C, -1>(s, nl, L, lognf, j0, tw);
     const int Lm = pk_mirror_line(L, c0, ncol);
@@ -135,28 +139,36 @@ k_adj_cols_pk(typename cplx_of<T>::type *G, typename cplx_of<T>::type *rowbuf, i
     const int sa = 2 * pk, sb = sa + 1;
     const bool hasb = sb < nslot;
     C *Ga = G + (size_t)sa * nf * nf, *Gb = G + (size_t)sb * nf * nf;
-    // 16 rows per thread (nf / tpl), loaded 4 rows at a time so that 16 loads are in flight
-    constexpr int RB = 4;
-    for (int i0r = 0; i0r < 16; i0r += RB) {
-        C a[RB], am[RB], b[RB], bm[RB];
+    // 16 rows e = j0 + k tpl per thread. The gridding pass folded the rows past nf/2 onto their
+    // mirrors, so a row below nf/2 (k < 8) has only its own cells (a, b) and a row past it
+    // (k >= 8) only its mirrors' (am, bm); rows 0 and nf/2 (k = 0 and 8 of thread j0 = 0) have
+    // both. Eight rows are loaded at a time: 16 loads in flight.
+    const C z0 = mk((T)0, (T)0);
 #pragma unroll
-        for (int r = 0; r < RB; ++r) {
-            const int e = j0 + (i0r + r) * tpl;
-            const size_t i0 = (size_t)e * nf + col, i1 = (size_t)((nf - e) & (nf - 1)) * nf + colm;
-            // the gridding pass folds rows past nf/2 onto their mirrors: those rows are zero
-            const bool lo = e <= nf / 2, hi = e == 0 || e >= nf / 2;
-            const C z0 = mk((T)0, (T)0);
-            a[r] = lo ? Ga[i0] : z0;
-            am[r] = hi ? Ga[i1] : z0;
-            b[r] = hasb && lo ? Gb[i0] : z0;
-            bm[r] = hasb && hi ? Gb[i1] : z0;
+    for (int h = 0; h < 2; ++h) {
+        C x[8], y[8];
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+            const int e = j0 + (8 * h + r) * tpl;
+            const size_t i = h == 0 ? (size_t)e * nf + col : (size_t)(nf - e) * nf + colm;
+            x[r] = Ga[i];
+            y[r] = hasb ? Gb[i] : z0;
+        }
+        C xe = z0, ye = z0;  // row 0's mirror cell (h = 0) or row nf/2's own cell (h = 1)
+        if (j0 == 0) {
+            const size_t i = h == 0 ? (size_t)colm : (size_t)(nf / 2) * nf + col;
+            xe = Ga[i];
+            ye = hasb ? Gb[i] : z0;
         }
 #pragma unroll
-        for (int r = 0; r < RB; ++r) {
-            const int e = j0 + (i0r + r) * tpl;
+        for (int r = 0; r < 8; ++r) {
+            const int e = j0 + (8 * h + r) * tpl;
+            const bool edge = r == 0 && j0 == 0;
+            const C a = h == 0 ? x[r] : (edge ? xe : z0), am = h == 0 ? (edge ? xe : z0) : x[r];
+            const C b = h == 0 ? y[r] : (edge ? ye : z0), bm = h == 0 ? (edge ? ye : z0) : y[r];
             // H_a = (a + conj am)/2, H_b = (b + conj bm)/2, Z = H_a + i H_b
-            const C ha = mk((T)0.5 * (a[r].x + am[r].x), (T)0.5 * (a[r].y - am[r].y));
-            const C hb = mk((T)0.5 * (b[r].x + bm[r].x), (T)0.5 * (b[r].y - bm[r].y));
+            const C ha = mk((T)0.5 * (a.x + am.x), (T)0.5 * (a.y - am.y));
+            const C hb = mk((T)0.5 * (b.x + bm.x), (T)0.5 * (b.y - bm.y));
             s[pidx((e << lgl) + L)] = mk(ha.x - hb.y, ha.y + hb.x);
         }
     }

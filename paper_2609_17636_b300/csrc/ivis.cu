@@ -724,9 +724,8 @@ cudaError_t enqueue_eval(ivis_plan_s *p, bool capture) {
     if (fork) cudaStreamWaitEvent(p->stream, p->ev_join, 0);
     if (cjoin) cudaStreamWaitEvent(p->stream, p->ev_cjoin, 0);
     const int n = p->cfg.n, nchan = p->cfg.nchan;
-    const size_t npix = (size_t)nchan * n * n;
     stage_begin(p, "assemble_R", p->stream, si);
-    k_assemble<T><<<(unsigned)((npix + 255) / 256), 256, 0, p->stream>>>(
+    k_assemble<T><<<assemble_grid(n, nchan), 256, 0, p->stream>>>(
         (const T *)p->x, (const T *)p->contrib, p->pinfo_d, p->chan_start_d, p->chan_list_d,
         (const T *)p->gradK, (T *)p->g, n, p->cfg.nb, nchan, (T)p->cfg.lambda_r,
         (T)p->cfg.lambda_s, use_r ? 1 : 0, use_k ? 1 : 0, p->rpart);
@@ -1543,7 +1542,10 @@ ivis_status prepare_impl(ivis_plan_s *p) {
         }
     }
     if ((s = alloc(p, (void **)&p->jpart, njp * sizeof(double)))) return s;
-    p->nrpart = (int)((npix + 255) / 256);
+    {
+        const dim3 ag = assemble_grid(c.n, c.nchan);  // one R partial per k_assemble CTA
+        p->nrpart = (int)(ag.x * ag.y);
+    }
     if ((s = alloc(p, (void **)&p->rpart, (size_t)p->nrpart * sizeof(double)))) return s;
     if ((s = alloc(p, (void **)&p->cost_d, FIN_WORDS * sizeof(double)))) return s;
     CK(cudaMemset(p->cost_d, 0, FIN_WORDS * sizeof(double)));  // the reduction's ticket starts at 0
@@ -1793,7 +1795,7 @@ ivis_status dirty_impl(ivis_plan_s *p, void *dirty_dev, void *beamw_dev) {
         if (e == cudaSuccess) e = launch_adjoint<T>(p);
         if (e != cudaSuccess) return fail(p, IVIS_ERR_CUDA, std::string("dirty: ") + cudaGetErrorString(e));
     }
-    k_assemble<T><<<(unsigned)((npix + 255) / 256), 256, 0, p->stream>>>(
+    k_assemble<T><<<assemble_grid(n, nchan), 256, 0, p->stream>>>(
         (const T *)p->x, (const T *)p->contrib, p->pinfo_d, p->chan_start_d, p->chan_list_d, nullptr,
         (T *)p->g, n, p->cfg.nb, nchan, (T)0, (T)0, 0, 0, p->rpart);
     if (p->any_grid && p->nslot > 0) {

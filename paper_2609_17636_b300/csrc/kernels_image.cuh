@@ -23,45 +23,110 @@ __device__ __forceinline__ T lap(const T *__restrict__ I, int n, int y, int x) {
            pix(I, n, y, x - 1) - pix(I, n, y, x + 1);
 }
 
+// One CTA per 32 x 32 pixel tile of one channel (256 threads, 4 pixels each). The Laplacian
+// terms come from the tile's sky with a 2-pixel halo and its Laplacian with a 1-pixel halo,
+// both staged in shared memory; the window contributions from the channel's pairs whose windows
+// meet the tile, listed once per CTA in the channel's slot order (the per-pixel sum runs in
+// that order, as it would over all the channel's pairs). One R partial per CTA.
+constexpr int ASM_TE = 32;
+
 template <typename T>
 __global__ void __launch_bounds__(256)
 k_assemble(const T *__restrict__ sky, const T *__restrict__ contrib,
            const PairInfo *__restrict__ pinfo, const int *__restrict__ chan_start,
            const int *__restrict__ chan_list, const T *__restrict__ gradK, T *grad, int n, int nb,
            int nchan, T lr, T ls, int use_r, int use_k, double *rpart) {
+    constexpr int TE = ASM_TE;
+    __shared__ T xs[TE + 4][TE + 5];  // sky, 2-pixel halo, zero off the image
+    __shared__ T lp[TE + 2][TE + 3];  // Laplacian, 1-pixel halo
+    __shared__ int list[256];
+    __shared__ int nlist;
     __shared__ double red[32];
+    (void)nchan;
+    const int ntx = (n + TE - 1) / TE;
+    const int chan = blockIdx.y;
+    const int y0 = (blockIdx.x / ntx) * TE, x0 = (blockIdx.x % ntx) * TE;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // pixel (y0 + ty + 8 j, x0 + tx)
     const size_t npix = (size_t)n * n;
-    const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    T rloc = (T)0;
-    if (idx < npix * nchan) {
-        const int chan = (int)(idx / npix);
-        const int rem = (int)(idx - (size_t)chan * npix);
-        const int y = rem / n, x = rem - y * n;
-        T g = (T)0;
-        for (int t = chan_start[chan]; t < chan_start[chan + 1]; ++t) {
-            const int slot = chan_list[t];
+    const T *I = sky + (size_t)chan * npix;
+    if (use_r) {
+        for (int i = threadIdx.x; i < (TE + 4) * (TE + 4); i += blockDim.x) {
+            const int yy = i / (TE + 4), xx = i - yy * (TE + 4);
+            xs[yy][xx] = pix(I, n, y0 - 2 + yy, x0 - 2 + xx);
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < (TE + 2) * (TE + 2); i += blockDim.x) {
+            const int yy = i / (TE + 2), xx = i - yy * (TE + 2);
+            lp[yy][xx] = (T)4 * xs[yy + 1][xx + 1] - xs[yy][xx + 1] - xs[yy + 2][xx + 1] - xs[yy + 1][xx] -
+                         xs[yy + 1][xx + 2];
+        }
+    }
+    T g[4] = {(T)0, (T)0, (T)0, (T)0};
+    const int t0 = chan_start[chan], t1 = chan_start[chan + 1];
+    for (int b0 = t0; b0 < t1; b0 += 256) {
+        const int b1 = min(t1, b0 + 256);
+        __syncthreads();  // the previous batch's list is read
+        if (threadIdx.x < 32) {  // warp 0 lists the batch's windows that meet the tile, in order
+            int cnt = 0;
+            for (int c0 = b0; c0 < b1; c0 += 32) {
+                const int t = c0 + threadIdx.x;
+                bool cov = false;
+                int slot = 0;
+                if (t < b1) {
+                    slot = chan_list[t];
+                    const PairInfo pi = pinfo[slot];
+                    const int wy = pi.cy - nb / 2, wx = pi.cx - nb / 2;
+                    // pointings with a re-projection grid are added by k_grid_scatter
+                    cov = !pi.gridded && wy < y0 + TE && wy + nb > y0 && wx < x0 + TE && wx + nb > x0;
+                }
+                const unsigned m = __ballot_sync(0xffffffffu, cov);
+                if (cov) list[cnt + __popc(m & ((1u << threadIdx.x) - 1u))] = slot;
+                cnt += __popc(m);
+            }
+            if (threadIdx.x == 0) nlist = cnt;
+        }
+        __syncthreads();
+        for (int k = 0; k < nlist; ++k) {
+            const int slot = list[k];
             const PairInfo pi = pinfo[slot];
-            if (pi.gridded) continue;  // added by k_grid_scatter
-            const int q = y - (pi.cy - nb / 2), p = x - (pi.cx - nb / 2);
-            if ((unsigned)q < (unsigned)nb && (unsigned)p < (unsigned)nb)
-                g += contrib[((size_t)slot * nb + q) * nb + p];
+            const int p = x0 + tx - (pi.cx - nb / 2);
+            const T *cs = contrib + (size_t)slot * nb * nb;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int q = y0 + ty + 8 * j - (pi.cy - nb / 2);
+                if ((unsigned)q < (unsigned)nb && (unsigned)p < (unsigned)nb) g[j] += cs[(size_t)q * nb + p];
+            }
         }
+    }
+    __syncthreads();  // the Laplacian tile is complete
+    T rloc = (T)0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int ly = ty + 8 * j, y = y0 + ly, x = x0 + tx;
+        if (y >= n || x >= n) continue;
+        const size_t idx = (size_t)chan * npix + (size_t)y * n + x;
+        T gj = g[j];
         if (use_r) {
-            const T *I = sky + (size_t)chan * npix;
-            const T d0 = lap(I, n, y, x);
+            const T d0 = lp[ly + 1][tx + 1];
             T gr = (T)4 * d0;
-            if (y > 0) gr -= lap(I, n, y - 1, x);
-            if (y < n - 1) gr -= lap(I, n, y + 1, x);
-            if (x > 0) gr -= lap(I, n, y, x - 1);
-            if (x < n - 1) gr -= lap(I, n, y, x + 1);
-            g += lr * gr;
-            rloc = (T)0.5 * d0 * d0;
+            if (y > 0) gr -= lp[ly][tx + 1];
+            if (y < n - 1) gr -= lp[ly + 2][tx + 1];
+            if (x > 0) gr -= lp[ly + 1][tx];
+            if (x < n - 1) gr -= lp[ly + 1][tx + 2];
+            gj += lr * gr;
+            rloc += (T)0.5 * d0 * d0;
         }
-        if (use_k) g += ls * gradK[idx];
-        grad[idx] = g;
+        if (use_k) gj += ls * gradK[idx];
+        grad[idx] = gj;
     }
     const double s = block_sum_t(rloc, red);
-    if (threadIdx.x == 0) rpart[blockIdx.x] = s;
+    if (threadIdx.x == 0) rpart[(size_t)blockIdx.y * gridDim.x + blockIdx.x] = s;
+}
+
+// CTAs of k_assemble: (tiles per channel, channels).
+inline dim3 assemble_grid(int n, int nchan) {
+    const int nt = (n + ASM_TE - 1) / ASM_TE;
+    return dim3((unsigned)(nt * nt), (unsigned)nchan);
 }
 
 // Separable dish-beam convolution, one axis per launch: out = sum_{t=-R..R} b_c[t] in(. - t),

@@ -84,13 +84,14 @@ __device__ __forceinline__ void stockham_pass(C *base, int stride, int off, int 
     for (int g = 0; g < G; ++g) {
         const int j = j0 + g * tpl;
         const int k = j & (Ns - 1);
-        // twiddle of input r: exp(SIGN 2 pi i k r / (Ns RP)) = tw[k r L / (Ns RP)]
-        const int tstep = k << (logL - logNs) >> (RP == 16 ? 4 : (RP == 8 ? 3 : (RP == 4 ? 2 : 1)));
+        // twiddle of input r: exp(SIGN 2 pi i k r / (Ns RP)), from this pass's block of the
+        // table (adjacent k adjacent, so the lanes of a warp read one or two sectors)
+        const int toff = 16 * (Ns - 1) / 15 + k;
 #pragma unroll
         for (int r = 0; r < RP; ++r) {
             C x = base[pidx((j + r * LR) * stride + off)];
             if (r > 0 && k != 0) {
-                C w = __ldg(&tw[(tstep * r) & (L - 1)]);
+                C w = __ldg(&tw[toff + r * Ns]);
                 if (SIGN > 0) w.y = -w.y;
                 x = cmul(x, w);
             }
@@ -113,7 +114,9 @@ __device__ __forceinline__ void stockham_pass(C *base, int stride, int off, int 
 
 // Full FFT of one line of length L = 2^logL (logL >= 4) held at base[pidx(n*stride + off)],
 // by tpl = L/16 threads with line-local index j0. The caller synchronises before the call;
-// the call ends synchronised. tw[m] = exp(-2 pi i m / L), m < L.
+// the call ends synchronised. tw: the twiddles in pass order (built by fft_twiddles): for the pass
+// with Ns = 2^logNs and radix R, tw[16 (Ns - 1) / 15 + r Ns + k] = exp(-2 pi i k r / (Ns R)),
+// k < Ns, r < R (16 (Ns - 1) / 15 entries precede it: the earlier passes' 16 + 256 + ...).
 template <typename C, int SIGN>
 __device__ __forceinline__ void line_fft(C *base, int stride, int off, int logL, int j0,
                                          const C *__restrict__ tw) {

@@ -336,19 +336,37 @@ ivis_status upload_real(ivis_plan_s *p, void **dst, const std::vector<double> &s
     return IVIS_OK;
 }
 
+// Twiddles of line_fft for lines of length L, in pass order: for each Stockham pass (Ns, R) the
+// R x Ns block exp(-2 pi i k r / (Ns R)) at [16 (Ns - 1) / 15 + r Ns + k]; each value is
+// exp(-2 pi i m / L) at m = k r L / (Ns R), computed in double and rounded once.
+template <typename T>
+std::vector<typename cplx_of<T>::type> fft_twiddles(int L) {
+    typedef typename cplx_of<T>::type C;
+    int logL = 0;
+    while ((1 << logL) < L) ++logL;
+    std::vector<C> tw;
+    for (int logNs = 0; logNs < logL; logNs += 4) {
+        const int R = 1 << std::min(4, logL - logNs), Ns = 1 << logNs;
+        for (int r = 0; r < R; ++r)
+            for (int k = 0; k < Ns; ++k) {
+                const long long m = (long long)k * r * (L / (Ns * R));
+                const double a = 2.0 * M_PI * m / L;
+                C w;
+                w.x = (T)std::cos(a);
+                w.y = (T)(-std::sin(a));
+                tw.push_back(w);
+            }
+    }
+    return tw;
+}
+
 template <typename T>
 ivis_status upload_twiddles(ivis_plan_s *p) {
     typedef typename cplx_of<T>::type C;
-    const int L = p->nf;
-    std::vector<C> tw(L);
-    for (int j = 0; j < L; ++j) {
-        double a = 2.0 * M_PI * j / L;
-        tw[j].x = (T)std::cos(a);
-        tw[j].y = (T)(-std::sin(a));
-    }
-    ivis_status s = alloc(p, &p->tw_d, L * sizeof(C));
+    const std::vector<C> tw = fft_twiddles<T>(p->nf);
+    ivis_status s = alloc(p, &p->tw_d, tw.size() * sizeof(C));
     if (s) return s;
-    CK(cudaMemcpy(p->tw_d, tw.data(), L * sizeof(C), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(p->tw_d, tw.data(), tw.size() * sizeof(C), cudaMemcpyHostToDevice));
     return IVIS_OK;
 }
 
@@ -1600,14 +1618,10 @@ ivis_status prepare_impl(ivis_plan_s *p) {
                         spec[(size_t)ch * N + k] = acc / N;
                     }
                 }
-                std::vector<C> tw(N);
-                for (int j = 0; j < N; ++j) {
-                    tw[j].x = (T)std::cos(2.0 * M_PI * j / N);
-                    tw[j].y = (T)(-std::sin(2.0 * M_PI * j / N));
-                }
+                const std::vector<C> tw = fft_twiddles<T>(N);
                 if ((s = upload_real<T>(p, &p->sd_spec_d, spec))) return s;
-                if ((s = alloc(p, &p->sd_tw_d, N * sizeof(C)))) return s;
-                CK(cudaMemcpy(p->sd_tw_d, tw.data(), N * sizeof(C), cudaMemcpyHostToDevice));
+                if ((s = alloc(p, &p->sd_tw_d, tw.size() * sizeof(C)))) return s;
+                CK(cudaMemcpy(p->sd_tw_d, tw.data(), tw.size() * sizeof(C), cudaMemcpyHostToDevice));
                 p->sd_N = N;
                 p->sd_logN = ilog2(N);
                 p->sd_logc = logc;
@@ -1842,14 +1856,9 @@ ivis_status feather_impl(ivis_plan_s *p, const void *int_dev, const float *sd_de
     const int n = p->cfg.n, nchan = p->cfg.nchan, logn = ilog2(n);
     ivis_status s;
     if (!p->feather_tw_d) {
-        std::vector<C> tw(n);
-        for (int j = 0; j < n; ++j) {
-            const double a = 2.0 * M_PI * j / n;
-            tw[j].x = (T)std::cos(a);
-            tw[j].y = (T)(-std::sin(a));
-        }
-        if ((s = alloc(p, &p->feather_tw_d, n * sizeof(C)))) return s;
-        const cudaError_t e0 = cudaMemcpy(p->feather_tw_d, tw.data(), n * sizeof(C), cudaMemcpyHostToDevice);
+        const std::vector<C> tw = fft_twiddles<T>(n);
+        if ((s = alloc(p, &p->feather_tw_d, tw.size() * sizeof(C)))) return s;
+        const cudaError_t e0 = cudaMemcpy(p->feather_tw_d, tw.data(), tw.size() * sizeof(C), cudaMemcpyHostToDevice);
         if (e0 != cudaSuccess || (s = alloc(p, &p->feather_b1_d, n * sizeof(T)))) {
             dfree(p->feather_tw_d);  // set up both tables again on the next call
             return e0 != cudaSuccess ? fail(p, IVIS_ERR_CUDA, std::string("feather twiddles: ") + cudaGetErrorString(e0)) : s;

@@ -334,9 +334,10 @@ ivis_status ivis_unet_backward(ivis_unet_t net, const float *in_dev, const float
 ivis_status ivis_unet_get_grads(ivis_unet_t net, float *host_grads);
 /* One Adam update with the last gradient (Kingma & Ba 2015, bias-corrected). */
 ivis_status ivis_unet_adam_step(ivis_unet_t net, float lr, float beta1, float beta2, float eps);
-/* Forward convolutions on the 5th-generation tensor cores (tcgen05.mma, accumulators in
- * tensor memory; default) or on mma.sync (enable = 0). The backward GEMMs use mma.sync.
- * A tensor-core completion wait that runs out returns IVIS_ERR_TIMEOUT. */
+/* Forward convolutions and the parameter-gradient GEMMs of the backward on the 5th-generation
+ * tensor cores (tcgen05.mma, accumulators in tensor memory; default), or all GEMMs on mma.sync
+ * (enable = 0). The activation-gradient GEMMs use mma.sync in both modes. A tensor-core
+ * completion wait that runs out returns IVIS_ERR_TIMEOUT. */
 ivis_status ivis_unet_use_tcgen05(ivis_unet_t net, int enable);
 ivis_status ivis_unet_destroy(ivis_unet_t net);
 const char *ivis_unet_last_error(ivis_unet_t net);

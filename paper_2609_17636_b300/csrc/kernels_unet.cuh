@@ -3,9 +3,11 @@
 //
 // Convolutions are lowered to GEMMs: an im2col gather (which also folds in the nearest-
 // neighbour 2x upsampling and the channel concatenation of the decoder inputs) followed by a
-// BF16 tensor-core GEMM with FP32 accumulation (mma.sync m16n8k16). Activations are NHWC BF16;
-// activation gradients are FP32 and are rounded to BF16 only as GEMM operands; weights are
-// FP32 masters with BF16 copies; Adam runs in FP32.
+// BF16 tensor-core GEMM with FP32 accumulation: tcgen05 (TMEM accumulators) for the forward
+// convolutions and the parameter gradients, mma.sync m16n8k16 for the activation gradients
+// (and for everything when tcgen05 is switched off). Activations are NHWC BF16; activation
+// gradients are FP32 and are rounded to BF16 only as GEMM operands; weights are FP32 masters
+// with BF16 copies; Adam runs in FP32.
 #pragma once
 #include <cuda_bf16.h>
 
@@ -161,9 +163,12 @@ k_gemm_bf16(int M, int N, int K, int kchunk, const bf16 *__restrict__ A, const b
             }
 }
 
-// ------------------------------------------------------- tcgen05 GEMM (forward convolution)
-// C[M x N] = relu(A[M x K] B[N x K]^T + bias) in bf16, both operands K-major bf16, FP32
-// accumulation in tensor memory. One CTA of 4 warps per 128 x BN output tile. The K loop moves
+// ------------------------------------------------------------------------- tcgen05 GEMM
+// acc[M x N] = A[M x K] B[N x K]^T, both operands K-major bf16 (row stride K), FP32
+// accumulation in tensor memory; EPI 0: C bf16 [M][N] = relu?(acc + bias) (forward
+// convolutions, stored through shared memory so that a store covers two rows of 16 columns);
+// EPI 2: C fp32 [N][M] += acc (parameter gradients, atomic and coalesced along M: the K range
+// is split over gridDim.z in chunks of kchunk). One CTA of 4 warps per 128 x BN output tile. The K loop moves
 // 128 x 64 slices of A and BN x 64 slices of B into shared memory with 16-byte cp.async copies
 // (zero-filled past the edges) in the canonical no-swizzle layout (8-row x 16-byte core
 // matrices; core matrices adjacent in K are LBO bytes apart, adjacent in M/N 128 bytes apart),
@@ -172,7 +177,8 @@ k_gemm_bf16(int M, int N, int K, int kchunk, const bf16 *__restrict__ A, const b
 // tcgen05.commit signals that stage's mbarrier; a stage is refilled only after its barrier
 // (bounded wait). Operands whose K is not a multiple of 8 (the first layer) are staged through
 // registers. The epilogue reads the accumulator rows with tcgen05.ld (warp w owns TMEM lanes
-// 32w..32w+31 = tile rows), adds the bias, applies the ReLU and stores bf16.
+// 32w..32w+31 = tile rows) and, per EPI (below), adds the bias, applies the ReLU and stores
+// bf16, or reduces into the fp32 parameter gradient.
 constexpr int TC_BM = 128, TC_BK = 64;
 template <int BN> struct tc_stages { static constexpr int value = BN <= 64 ? 4 : 3; };
 
@@ -197,10 +203,11 @@ struct ConvGeom {
     int ca, ua, cb, H, W;
 };
 
-template <int BN, bool IMPLICIT>
+template <int BN, bool IMPLICIT, int EPI>
 __global__ void __launch_bounds__(128)
-k_gemm_tc(int M, int N, int K, const bf16 *__restrict__ A, const bf16 *__restrict__ B,
-          bf16 *C, const float *__restrict__ bias, int relu, int *err, ConvGeom cg) {
+k_gemm_tc(int M, int N, int K, int kchunk, const bf16 *__restrict__ A, const bf16 *__restrict__ B,
+          void *C, const float *__restrict__ bias, int relu, int *err, ConvGeom cg) {
+    static_assert(EPI == 0 || EPI == 2, "bf16 forward output or fp32 parameter-gradient reduction");
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     constexpr int S = tc_stages<BN>::value;
     constexpr int STAGE = (TC_BM + BN) * TC_BK;  // bf16 elements per stage (A then B)
@@ -227,7 +234,9 @@ k_gemm_tc(int M, int N, int K, const bf16 *__restrict__ A, const bf16 *__restric
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t tmem = *tmem_holder;
     const bool vec = (K % 8) == 0;
-    const int nk = (K + TC_BK - 1) / TC_BK;
+    // this CTA's K range (kchunk is a multiple of TC_BK; the whole of K without a split)
+    const int kbeg = blockIdx.z * kchunk, kend = min(K, kbeg + kchunk);
+    const int nk = (kend - kbeg + TC_BK - 1) / TC_BK;
     uint32_t phase[S];
     bool pending[S];
 #pragma unroll
@@ -273,10 +282,10 @@ k_gemm_tc(int M, int N, int K, const bf16 *__restrict__ A, const bf16 *__restric
     // copies of slice kb into stage st (asynchronous when K is a multiple of 8)
     auto load_slice = [&](int kb, int st) {
         bf16 *As = stage0 + st * STAGE, *Bs = As + TC_BM * TC_BK;
-        const int k0 = kb * TC_BK;
+        const int k0 = kbeg + kb * TC_BK;
         if constexpr (IMPLICIT) {
             const int kg = tid & 7, kglob = k0 + kg * 8, cin = cg.ca + cg.cb;
-            const bool kin = kglob < K;
+            const bool kin = kglob < kend;
             const int tap = kin ? kglob / cin : 0, ci = kglob - tap * cin;
             const int dy = tap / 3 - 1, dx = tap - (tap / 3) * 3 - 1;
             const int Ha = cg.H / cg.ua, Wa = cg.W / cg.ua;
@@ -308,7 +317,7 @@ k_gemm_tc(int M, int N, int K, const bf16 *__restrict__ A, const bf16 *__restric
             unsigned char *dst = reinterpret_cast<unsigned char *>(isA ? As : Bs) + kg * lbo +
                                  (row >> 3) * 128 + (row & 7) * 16;
             if (vec) {
-                const bool in = grow < rows && gk < K;
+                const bool in = grow < rows && gk < kend;
                 const bf16 *g = in ? src + (size_t)grow * K + gk : src;
                 asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;"
                              :: "r"(smem_u32(dst)), "l"(g), "r"(in ? 16 : 0));
@@ -317,7 +326,7 @@ k_gemm_tc(int M, int N, int K, const bf16 *__restrict__ A, const bf16 *__restric
                 if (grow < rows) {
                     bf16 *e = reinterpret_cast<bf16 *>(&q);
                     for (int t = 0; t < 8; ++t)
-                        if (gk + t < K) e[t] = src[(size_t)grow * K + gk + t];
+                        if (gk + t < kend) e[t] = src[(size_t)grow * K + gk + t];
                 }
                 *reinterpret_cast<uint4 *>(dst) = q;
             }
@@ -381,15 +390,41 @@ k_gemm_tc(int M, int N, int K, const bf16 *__restrict__ A, const bf16 *__restric
                            "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
                          : "r"(taddr));
             asm volatile("tcgen05.wait::ld.sync.aligned;");
-            if (row < M) {
+            if constexpr (EPI == 2) {
+                // C[col][row]: the lanes' rows are adjacent, so each reduction is coalesced
+                if (row < M) {
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        const int col = n0 + c0 + j;
+                        if (col < N) atomicAdd(reinterpret_cast<float *>(C) + (size_t)col * M + row, __uint_as_float(r[j]));
+                    }
+                }
+            } else {
+                // C[row][col] (bf16): through this warp's 32 x 16 block of shared memory (the stages are
+                // free after the drain) so that a store instruction covers two rows of 16
+                // adjacent columns instead of 32 rows of one
+                float *stg = reinterpret_cast<float *>(smem_raw) + warp * (32 * 17);
 #pragma unroll
                 for (int j = 0; j < 16; ++j) {
-                    const int col = n0 + c0 + j;
-                    if (col >= N) continue;
-                    float v = __uint_as_float(r[j]) + (bias ? bias[col] : 0.f);
-                    if (relu) v = fmaxf(v, 0.f);
-                    C[(size_t)row * N + col] = __float2bfloat16(v);
+                    float v = __uint_as_float(r[j]);
+                    if constexpr (EPI == 0) {
+                        const int col = n0 + c0 + j;
+                        v += (bias && col < N) ? bias[col] : 0.f;
+                        if (relu) v = fmaxf(v, 0.f);
+                    }
+                    stg[lane * 17 + j] = v;
                 }
+                __syncwarp();
+#pragma unroll
+                for (int it = 0; it < 16; ++it) {
+                    const int idx = it * 32 + lane, rl = idx >> 4, cl = idx & 15;
+                    const int grow = m0 + warp * 32 + rl, col = n0 + c0 + cl;
+                    if (grow < M && col < N) {
+                        const float v = stg[rl * 17 + cl];
+                        reinterpret_cast<bf16 *>(C)[(size_t)grow * N + col] = __float2bfloat16(v);
+                    }
+                }
+                __syncwarp();
             }
         }
     }
@@ -479,6 +514,27 @@ __global__ void k_col2im(int B, int H, int W, const float *__restrict__ dcol, fl
             }
             db[j] = s;
         }
+    }
+}
+
+// out[c][r] = in[r][c] for a bf16 matrix of R rows and C columns (32 x 32 tiles through shared
+// memory, coalesced on both sides): the K-major operands of the backward tcgen05 GEMMs.
+// Grid: (ceil(R / 32), ceil(C / 32)) (rows, the long side, on x), 256 threads.
+__global__ void __launch_bounds__(256)
+k_transpose_bf16(const bf16 *__restrict__ in, bf16 *out, int R, int C) {
+    __shared__ bf16 t[32][34];
+    const int r0 = blockIdx.x * 32, c0 = blockIdx.y * 32;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+#pragma unroll
+    for (int j = 0; j < 32; j += 8) {
+        const int r = r0 + ty + j, c = c0 + tx;
+        if (r < R && c < C) t[ty + j][tx] = in[(size_t)r * C + c];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < 32; j += 8) {
+        const int c = c0 + ty + j, r = r0 + tx;
+        if (r < R && c < C) out[(size_t)c * R + r] = t[tx][ty + j];
     }
 }
 

@@ -44,11 +44,12 @@ struct ivis_unet_s {
     std::vector<bf16 *> act;             // activations (bf16 NHWC)
     std::vector<float *> dact;           // their gradients (fp32)
     bf16 *col = nullptr, *dz = nullptr;
+    bf16 *colT = nullptr, *dzT = nullptr;  // K-major operands of the tcgen05 parameter gradients
     float *dcol = nullptr, *out = nullptr, *dout = nullptr, *tgt = nullptr;
     double *part = nullptr, *part_h = nullptr;
     size_t col_cap = 0, dz_cap = 0;
     long long step = 0;
-    bool use_tc = true;   // forward convolutions on tcgen05 (else mma.sync)
+    bool use_tc = true;   // convolutions and their gradients on tcgen05 (else mma.sync)
     int *tc_err = nullptr;
     std::string err;
 };
@@ -119,9 +120,11 @@ ivis_status ensure_scratch(ivis_unet_s *u, size_t col_elems, size_t dz_elems) {
     if (col_elems > u->col_cap) {
         if (u->col) cudaFree(u->col);
         if (u->dcol) cudaFree(u->dcol);
-        u->col = nullptr; u->dcol = nullptr;
+        if (u->colT) cudaFree(u->colT);
+        u->col = nullptr; u->dcol = nullptr; u->colT = nullptr;
         if (cudaMalloc(&u->col, col_elems * sizeof(bf16)) != cudaSuccess ||
-            cudaMalloc(&u->dcol, col_elems * sizeof(float)) != cudaSuccess) {
+            cudaMalloc(&u->dcol, col_elems * sizeof(float)) != cudaSuccess ||
+            cudaMalloc(&u->colT, col_elems * sizeof(bf16)) != cudaSuccess) {
             cudaGetLastError();
             u->col_cap = 0;
             return ufail(u, IVIS_ERR_OOM, "U-Net scratch allocation failed");
@@ -130,8 +133,10 @@ ivis_status ensure_scratch(ivis_unet_s *u, size_t col_elems, size_t dz_elems) {
     }
     if (dz_elems > u->dz_cap) {
         if (u->dz) cudaFree(u->dz);
-        u->dz = nullptr;
-        if (cudaMalloc(&u->dz, dz_elems * sizeof(bf16)) != cudaSuccess) {
+        if (u->dzT) cudaFree(u->dzT);
+        u->dz = nullptr; u->dzT = nullptr;
+        if (cudaMalloc(&u->dz, dz_elems * sizeof(bf16)) != cudaSuccess ||
+            cudaMalloc(&u->dzT, dz_elems * sizeof(bf16)) != cudaSuccess) {
             cudaGetLastError();
             u->dz_cap = 0;
             return ufail(u, IVIS_ERR_OOM, "U-Net scratch allocation failed");
@@ -141,34 +146,43 @@ ivis_status ensure_scratch(ivis_unet_s *u, size_t col_elems, size_t dz_elems) {
     return IVIS_OK;
 }
 
-template <int BN, bool IMPLICIT>
-void gemm_tc_launch(cudaStream_t st, int M, int N, int K, const bf16 *A, const bf16 *B, bf16 *C,
+template <int BN, bool IMPLICIT, int EPI>
+void gemm_tc_launch(cudaStream_t st, int M, int N, int K, int kchunk, const bf16 *A, const bf16 *B, void *C,
                     const float *bias, int relu, int *err, ConvGeom cg) {
     constexpr int NCOL = BN < 32 ? 32 : BN;
     const size_t need = (size_t)tc_stages<BN>::value * (TC_BM + BN) * TC_BK * sizeof(bf16) + 64;
     // keep the CTAs resident on one SM within its 512 TMEM columns
     const int allowed = 512 / NCOL;
     const size_t smem = std::max(need, (size_t)(228 * 1024) / (allowed + 1) + 1024);
-    cudaFuncSetAttribute(k_gemm_tc<BN, IMPLICIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    dim3 g((M + TC_BM - 1) / TC_BM, (N + BN - 1) / BN);
-    k_gemm_tc<BN, IMPLICIT><<<g, 128, smem, st>>>(M, N, K, A, B, C, bias, relu, err, cg);
+    cudaFuncSetAttribute(k_gemm_tc<BN, IMPLICIT, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    dim3 g((M + TC_BM - 1) / TC_BM, (N + BN - 1) / BN, (K + kchunk - 1) / kchunk);
+    k_gemm_tc<BN, IMPLICIT, EPI><<<g, 128, smem, st>>>(M, N, K, kchunk, A, B, C, bias, relu, err, cg);
 }
 
 // cg.a == nullptr: explicit A (an im2col matrix); otherwise A is gathered from cg.
-template <bool IMPLICIT>
-void gemm_tc_n(cudaStream_t st, int M, int N, int K, const bf16 *A, const bf16 *B, bf16 *C,
+// kchunk: split of K over gridDim.z (rounded up to a multiple of TC_BK; EPI 2 only), 0 = none.
+template <bool IMPLICIT, int EPI>
+void gemm_tc_n(cudaStream_t st, int M, int N, int K, int kchunk, const bf16 *A, const bf16 *B, void *C,
                const float *bias, int relu, int *err, ConvGeom cg) {
-    if (N <= 16) gemm_tc_launch<16, IMPLICIT>(st, M, N, K, A, B, C, bias, relu, err, cg);
-    else if (N <= 32) gemm_tc_launch<32, IMPLICIT>(st, M, N, K, A, B, C, bias, relu, err, cg);
-    else if (N <= 64) gemm_tc_launch<64, IMPLICIT>(st, M, N, K, A, B, C, bias, relu, err, cg);
-    else if (N <= 128) gemm_tc_launch<128, IMPLICIT>(st, M, N, K, A, B, C, bias, relu, err, cg);
-    else gemm_tc_launch<256, IMPLICIT>(st, M, N, K, A, B, C, bias, relu, err, cg);
+    kchunk = kchunk > 0 ? (kchunk + TC_BK - 1) / TC_BK * TC_BK : K;
+    if (N <= 16) gemm_tc_launch<16, IMPLICIT, EPI>(st, M, N, K, kchunk, A, B, C, bias, relu, err, cg);
+    else if (N <= 32) gemm_tc_launch<32, IMPLICIT, EPI>(st, M, N, K, kchunk, A, B, C, bias, relu, err, cg);
+    else if (N <= 64) gemm_tc_launch<64, IMPLICIT, EPI>(st, M, N, K, kchunk, A, B, C, bias, relu, err, cg);
+    else if (N <= 128) gemm_tc_launch<128, IMPLICIT, EPI>(st, M, N, K, kchunk, A, B, C, bias, relu, err, cg);
+    else gemm_tc_launch<256, IMPLICIT, EPI>(st, M, N, K, kchunk, A, B, C, bias, relu, err, cg);
 }
 
 void gemm_tc(cudaStream_t st, int M, int N, int K, const bf16 *A, const bf16 *B, bf16 *C,
              const float *bias, int relu, int *err, ConvGeom cg = ConvGeom{}) {
-    if (cg.a) gemm_tc_n<true>(st, M, N, K, A, B, C, bias, relu, err, cg);
-    else gemm_tc_n<false>(st, M, N, K, A, B, C, bias, relu, err, cg);
+    if (cg.a) gemm_tc_n<true, 0>(st, M, N, K, 0, A, B, C, bias, relu, err, cg);
+    else gemm_tc_n<false, 0>(st, M, N, K, 0, A, B, C, bias, relu, err, cg);
+}
+
+// Parameter-gradient GEMM on tcgen05: C fp32 [N][M] += A B^T with K split into chunks of kchunk
+// (EPI 2); both operands K-major bf16.
+void gemm_tc_wgrad(cudaStream_t st, int M, int N, int K, int kchunk, const bf16 *A, const bf16 *B, float *C,
+                   int *err) {
+    gemm_tc_n<false, 2>(st, M, N, K, kchunk, A, B, C, nullptr, 0, err, ConvGeom{});
 }
 
 void gemm(cudaStream_t st, int ta, int tb, int epi, int M, int N, int K, const bf16 *A, const bf16 *B,
@@ -397,10 +411,23 @@ ivis_status ivis_unet_backward(ivis_unet_t u, const float *in_dev, const float *
         k_im2col<<<nblk(P * K), 256, 0, st>>>(B, h, w, u->act[c.src_a], c.ca, c.ua,
                                                c.src_b >= 0 ? u->act[c.src_b] : nullptr, c.cb, u->col);
         // dW += dz^T col (split over pixels), db += sum dz, dcol = dz W
-        gemm(st, 1, 0, 2, c.cout, K, (int)P, u->dz, u->col, u->g + c.w_off, nullptr, 0, 8192);
+        if (u->use_tc) {
+            // tcgen05 wants both operands K-major: dW^T [K][cout] += col^T (dz^T)^T over the
+            // pixels (split in chunks of 8192), from transposed copies of col and dz
+            k_transpose_bf16<<<dim3((unsigned)((P + 31) / 32), (c.cout + 31) / 32), 256, 0, st>>>(u->dz, u->dzT,
+                                                                                               (int)P, c.cout);
+            k_transpose_bf16<<<dim3((unsigned)((P + 31) / 32), (K + 31) / 32), 256, 0, st>>>(u->col, u->colT,
+                                                                                          (int)P, K);
+            gemm_tc_wgrad(st, K, c.cout, (int)P, 8192, u->colT, u->dzT, u->g + c.w_off, u->tc_err);
+        } else {
+            gemm(st, 1, 0, 2, c.cout, K, (int)P, u->dz, u->col, u->g + c.w_off, nullptr, 0, 8192);
+        }
         dim3 gb(std::min<size_t>(P, 1024), (c.cout + 127) / 128);
         k_bias_grad<<<gb, 128, 0, st>>>(P, c.cout, u->dz, u->g + c.b_off);
         if (li == 0) continue;  // no gradient needed for the network input
+        // dcol = dz W on mma.sync in both modes: its K is the output channels (32-256), one to
+        // four 64-deep slices per tcgen05 tile, where tile set-up and the fp32 epilogue made
+        // the tcgen05 version slower (3.98 ms against 2.94 ms per backward, batch 8 x 256^2)
         gemm(st, 0, 0, 1, (int)P, K, c.cout, u->dz, u->wb + c.w_off, u->dcol, nullptr, 0);
         const int ha = h / c.ua, wa = w / c.ua;
         const size_t nsrc = (size_t)B * ha * wa * c.ca + (c.src_b >= 0 ? P * c.cb : 0);
@@ -417,7 +444,10 @@ ivis_status ivis_unet_backward(ivis_unet_t u, const float *in_dev, const float *
     }
     UCK(cudaGetLastError());
     UCK(cudaMemcpyAsync(u->part_h, u->part, nb_mse * sizeof(double), cudaMemcpyDeviceToHost, st));
+    int herr = 0;
+    if (u->use_tc) UCK(cudaMemcpyAsync(&herr, u->tc_err, sizeof(int), cudaMemcpyDeviceToHost, st));
     UCK(cudaStreamSynchronize(st));
+    if (herr) return ufail(u, IVIS_ERR_TIMEOUT, "tensor-core GEMM: completion wait timed out");
     if (loss_out) {
         double sum = 0.0;
         for (unsigned i = 0; i < nb_mse; ++i) sum += u->part_h[i];
@@ -440,8 +470,8 @@ ivis_status ivis_unet_adam_step(ivis_unet_t u, float lr, float beta1, float beta
 ivis_status ivis_unet_destroy(ivis_unet_t u) {
     if (!u) return IVIS_OK;
     if (u->stream) cudaStreamSynchronize(u->stream);
-    void *ptrs[] = {u->w, u->g, u->m, u->v, u->wb, u->col, u->dz, u->dcol, u->out, u->dout, u->tgt, u->part,
-                    u->tc_err};
+    void *ptrs[] = {u->w, u->g, u->m, u->v, u->wb, u->col, u->colT, u->dz, u->dzT, u->dcol, u->out,
+                    u->dout, u->tgt, u->part, u->tc_err};
     for (void *q : ptrs)
         if (q) cudaFree(q);
     for (auto q : u->act) if (q) cudaFree(q);

@@ -8,9 +8,11 @@
 // g + k NG in round k; items sorted by length, so the groups of a warp get similar lengths).
 //
 //   * The CTA stages the tile's patch of the forward grid F (TS + W - 1 cells square,
-//     wrapped) in shared memory.
+//     wrapped) in shared memory; with fhalf only rows 0 .. nf/2 of F are stored and a row past
+//     nf/2 is read from its mirror, conjugated (F(-k) = conj F(k) for a real window).
 //   * Each group owns a private (8 + W - 1)^2 buffer of the adjoint grid for its current
-//     item's block, so its spreading is a plain read-modify-write: no atomics. Shared-memory
+//     item's block (in half lines, see hl_off), so its spreading is a plain
+//     read-modify-write: no atomics. Shared-memory
 //     float atomics are emulated on this part (a load and a compare-and-swap per value) and
 //     cost about four times a plain access, which made them the bound of a spreading pass
 //     built on them.

@@ -631,15 +631,32 @@ __global__ void k_head_bwd(size_t P, int C, const bf16 *__restrict__ in, const f
     if (threadIdx.x == 0) atomicAdd(db, sb);
 }
 
-// Bias gradient: db[c] += sum_p dz[p][c].
-__global__ void k_bias_grad(size_t P, int C, const bf16 *__restrict__ dz, float *db) {
-    const int c = blockIdx.y * blockDim.x + threadIdx.x;
-    if (c >= C) return;
-    float s = 0.f;
-    for (size_t p = blockIdx.x; p < P; p += gridDim.x) s += __bfloat162float(dz[p * C + c]);
-    atomicAdd(&db[c], s);
+// Bias gradient: db[c] += sum_p dz[p][c] (C a multiple of 8). Thread t reads 16 bytes (8
+// channels) of rows t / (C / 8) + k (blockDim.x / (C / 8)) of its CTA's row range; the CTA sums
+// its threads' partials per channel in shared memory and adds them once. blockDim.x = 256.
+__global__ void __launch_bounds__(256) k_bias_grad(size_t P, int C, const bf16 *__restrict__ dz, float *db) {
+    __shared__ float part[256 * 8];
+    const int nq = C >> 3, rows = blockDim.x / nq;
+    const int q = threadIdx.x % nq, r0 = threadIdx.x / nq;
+    float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    if (r0 < rows) {
+        for (size_t p = (size_t)blockIdx.x * rows + r0; p < P; p += (size_t)gridDim.x * rows) {
+            const uint4 v = *reinterpret_cast<const uint4 *>(dz + p * C + (size_t)q * 8);
+            const bf16 *e = reinterpret_cast<const bf16 *>(&v);
+#pragma unroll
+            for (int j = 0; j < 8; ++j) acc[j] += __bfloat162float(e[j]);
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j) part[threadIdx.x * 8 + j] = acc[j];
+    __syncthreads();
+    for (int c = threadIdx.x; c < C; c += blockDim.x) {
+        const int cq = c >> 3, cj = c & 7;
+        float s = 0.f;
+        for (int r = 0; r < rows; ++r) s += part[(r * nq + cq) * 8 + cj];
+        atomicAdd(&db[c], s);
+    }
 }
-
 // Pack the two network inputs (fp32 planes [B][2][H][W]) into NHWC bf16 [B][H][W][2].
 __global__ void k_pack_input(int B, int H, int W, const float *__restrict__ in, bf16 *out) {
     const size_t total = (size_t)B * H * W;

@@ -422,8 +422,9 @@ ivis_status ivis_unet_backward(ivis_unet_t u, const float *in_dev, const float *
         } else {
             gemm(st, 1, 0, 2, c.cout, K, (int)P, u->dz, u->col, u->g + c.w_off, nullptr, 0, 8192);
         }
-        dim3 gb(std::min<size_t>(P, 1024), (c.cout + 127) / 128);
-        k_bias_grad<<<gb, 128, 0, st>>>(P, c.cout, u->dz, u->g + c.b_off);
+        const size_t brows = 256 / (c.cout / 8);  // rows per CTA pass of k_bias_grad
+        k_bias_grad<<<(unsigned)std::min<size_t>((P + brows - 1) / brows, 148 * 4), 256, 0, st>>>(P, c.cout, u->dz,
+                                                                                           u->g + c.b_off);
         if (li == 0) continue;  // no gradient needed for the network input
         // dcol = dz W on mma.sync in both modes: its K is the output channels (32-256), one to
         // four 64-deep slices per tcgen05 tile, where tile set-up and the fp32 epilogue made

@@ -1465,6 +1465,9 @@ ivis_status prepare_impl(ivis_plan_s *p) {
         p->pair_nslot[i] = (int)pinfo.size() - p->pair_slot0[i];
     }
     p->nslot = (int)pinfo.size();
+    // per-slot kernels index the slot (or the two-window transform) on the grid's y dimension
+    if (p->nslot > 65535)
+        return fail(p, IVIS_ERR_ARG, "more than 65535 (pointing, channel) slots with data in one plan");
     std::vector<Chunk> chunks;
     std::vector<int> chan_start(c.nchan + 1, 0), chan_list;
     p->any_grid = false;

@@ -180,7 +180,8 @@ ivis_status ivis_set_sd(ivis_plan_t plan, int chan, const float *tsd_dev, double
 /* Build work lists, allocate grids and capture the evaluation graph. Called implicitly by
  * the first evaluation; call it explicitly to keep that cost out of timed regions.
  * Errors: IVIS_ERR_STATE if a pointing, a channel's single-dish map (lambda_s != 0) or
- * every pair of a channel is missing. */
+ * every pair of a channel is missing; IVIS_ERR_ARG if more than 65535 slots (pairs with
+ * visibilities, times the w-planes of a wterm plan) would be batched; IVIS_ERR_OOM. */
 ivis_status ivis_prepare(ivis_plan_t plan);
 
 /* Q_tot and its gradient at sky_dev (real [nchan][n][n]). cost_out (host) receives

@@ -1,7 +1,7 @@
 """Parity at full sizes: the 7-pointing 512^2 mosaic (1.36 M visibilities, Laplacian +
-fusion terms, FP32 grids) and the batched cube's shape (36 beams x 8 of its channels, ragged
-U[1e5, 3e5] visibilities per pair), in the launch configuration bench.py times (the
-autotuned plan's captured evaluation graph).
+fusion terms, FP32 grids) and the batched cube (36 beams x 32 channels, 1152 pairs, ragged
+U[1e5, 3e5] visibilities per pair, 2.3e8 in all), in the launch configuration bench.py times
+(the autotuned plan's captured evaluation graph).
 
 The oracle cannot evaluate a dense 512^2 sky against 1.36 M visibilities in seconds, so both
 the data and the evaluation point are sparse skies (the oracle's direct DFT skips zero
@@ -138,16 +138,16 @@ def test_maximum_window_size_sampled_parity(precision):
     plan.close()
 
 
-def test_batched_cube_shape_sampled_parity():
-    """The batched cube's geometry and launch configuration: 36 beams on the 6 x 6 hexagonal
-    footprint (0.9 deg pitch, 1 deg beams, 512^2 windows on a 1024^2 sky at 25 arcsec, so
-    windows overlap and hang off the sky), 8 of its channels (288 pairs, uv scaled per
-    channel), ragged U[1e5, 3e5] visibilities per pair that fold several times over the fine
-    grid, the Laplacian term; the FP32 plan with the autotuner's tile and item choice. Sparse
-    data and evaluation skies per channel as above."""
+def test_batched_cube_sampled_parity():
+    """The batched cube at its full size and in the bench's launch configuration: 36 beams on
+    the 6 x 6 hexagonal footprint (0.9 deg pitch, 1 deg beams, 512^2 windows on a 1024^2 sky
+    at 25 arcsec, so windows overlap and hang off the sky), 32 channels (1152 pairs, uv scaled
+    per channel), ragged U[1e5, 3e5] visibilities per pair that fold several times over the
+    fine grid, the Laplacian term; the FP32 plan with the autotuner's tile and item choice.
+    Sparse data and evaluation skies per channel as above."""
     from paper_2609_17636_b300 import plan_from_problem
-    prob = synth.config_c3(nchan=8)
-    assert len(prob.pairs) == 288 and min(p.m for p in prob.pairs) >= 100_000
+    prob = synth.config_c3()
+    assert len(prob.pairs) == 1152 and min(p.m for p in prob.pairs) >= 100_000
     rng = np.random.default_rng(3003)
     truth = np.concatenate([_sparse_sky(rng, prob.n, 24) for _ in range(prob.nchan)])
     for pair in prob.pairs:
@@ -165,7 +165,7 @@ def test_batched_cube_shape_sampled_parity():
     assert abs(Q - Q_ref) <= TOL * Q_ref and abs(R - R_ref) <= TOL * R_ref and K == 0.0
     assert abs(f - f_ref) <= TOL * f_ref
     # gradient at sampled pixels of two channels: random, beam centres (overlaps), sky corners
-    for chan in (0, 5):
+    for chan in (0, 17, 31):
         ys = np.concatenate([rng.integers(0, prob.n, 30), prob.centres[::5, 1], [0, prob.n - 1]])
         xx = np.concatenate([rng.integers(0, prob.n, 30), prob.centres[::5, 0], [prob.n - 1, 0]])
         sub = [(i, p) for i, p in enumerate(prob.pairs) if p.chan == chan]
@@ -173,7 +173,7 @@ def test_batched_cube_shape_sampled_parity():
                                      residuals={i: resid[i] for i, _ in sub})
         g_ref = gq + prob.lambda_r * gR[chan, ys, xx]
         assert rel_l2(g[chan, ys, xx], g_ref) <= TOL, (chan, rel_l2(g[chan, ys, xx], g_ref))
-    for pair in prob.pairs[::47]:
+    for pair in prob.pairs[::97]:
         idx = np.sort(rng.choice(pair.m, 1000, replace=False))
         got = plan.predict(xs, pair.k, pair.chan).cpu().numpy()[idx]
         assert rel_l2(got[:, 0] + 1j * got[:, 1], oracle.pair_model_vis(prob, x, pair, idx)) <= TOL

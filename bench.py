@@ -10,7 +10,9 @@ The default workload is the batched cube (32 channels x 36 beams, 2.3e8 visibili
 evaluation), the largest configuration that fits one GPU; --config selects the others.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ivis|reference]
-                  [--config c3|c1|c2|c4|c5] [--no-solve] [--no-precision]
+                  [--config c3|c1|c2|c4|c5|unet] [--no-solve] [--no-precision]
+
+(--config unet times the warm-start network's training step instead: a separate line.)
 
 N > 1 (torchrun): every rank runs its own independent copy of the workload (channels and
 problems are independent in the method: no collective on the data path); ranks meet only
@@ -41,7 +43,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ivis", choices=["ivis", "reference"])
-    ap.add_argument("--config", default="c3", choices=["c1", "c2", "c3", "c4", "c5"])
+    ap.add_argument("--config", default="c3", choices=["c1", "c2", "c3", "c4", "c5", "unet"])
     ap.add_argument("--c5-skies", type=int, default=500)
     ap.add_argument("--c5-crops", type=int, default=4)
     ap.add_argument("--c5-epochs", type=int, default=30)
@@ -632,6 +634,53 @@ def solve_compare(prob, args, maxiter=30, toeplitz=True):
     return res
 
 
+def run_unet_step(args):
+    """The warm-start network's training step (forward + backward, batch 8 x 256^2, base width
+    32, random weights and data): CUDA-event time per step with the tcgen05 GEMMs and with
+    mma.sync throughout, and the forward alone. One step of each runs inside
+    cudaProfilerStart/Stop for launch-list and counter captures."""
+    import torch
+    import synth
+    from paper_2609_17636_b300 import UNet
+    torch.cuda.set_device(0)
+    c, B, H, W = 32, 8, 256, 256
+    net = UNet(c, max_batch=B, max_hw=H * W)
+    net.set_params(synth.unet_init(c, 3))
+    rng = np.random.default_rng(0)
+    x = torch.as_tensor(rng.standard_normal((B, 2, H, W)).astype(np.float32), device="cuda")
+    t = torch.as_tensor(rng.standard_normal((B, H, W)).astype(np.float32), device="cuda")
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    res = {}
+    for tc in (True, False):
+        net.use_tcgen05(tc)
+        for _ in range(args.warmup):
+            net.backward(x, t)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.start()
+        net.backward(x, t)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
+        e0.record()
+        for _ in range(args.steps):
+            net.backward(x, t)
+        e1.record()
+        torch.cuda.synchronize()
+        step = e0.elapsed_time(e1) / args.steps
+        e0.record()
+        for _ in range(args.steps):
+            net.forward(x)
+        e1.record()
+        torch.cuda.synchronize()
+        res["tcgen05" if tc else "mma_sync"] = {"step_ms": round(step, 3),
+                                                "forward_ms": round(e0.elapsed_time(e1) / args.steps, 3)}
+    net.close()
+    return {"metric": "U-Net training step time (forward + backward + parameter gradient)",
+            "value": res["tcgen05"]["step_ms"], "unit": "ms", "higher_is_better": False,
+            "steps": args.steps, "warmup": args.warmup, "dtype": "bf16 operands / fp32 accumulate",
+            "data": "synthetic (random inputs and weights)",
+            "config": {"workload": "U-Net base 32, batch 8 x 256^2 crops"}, "modes": res}
+
+
 def run_c5(args):
     """Learned warm start: time and iterations to reach the cold start's final cost."""
     import torch
@@ -848,6 +897,10 @@ def main():
     if args.config == "c5":
         if rank == 0:
             print(json.dumps(run_c5(args)), flush=True)
+        return
+    if args.config == "unet":
+        if rank == 0:
+            print(json.dumps(run_unet_step(args)), flush=True)
         return
     out, prob = run_ivis(args, rank, world)
     if rank == 0:

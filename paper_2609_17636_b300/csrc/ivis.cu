@@ -743,10 +743,13 @@ cudaError_t enqueue_eval(ivis_plan_s *p, bool capture) {
     if (cjoin) cudaStreamWaitEvent(p->stream, p->ev_cjoin, 0);
     const int n = p->cfg.n, nchan = p->cfg.nchan;
     stage_begin(p, "assemble_R", p->stream, si);
-    k_assemble<T><<<assemble_grid(n, nchan), 256, 0, p->stream>>>(
-        (const T *)p->x, (const T *)p->contrib, p->pinfo_d, p->chan_start_d, p->chan_list_d,
-        (const T *)p->gradK, (T *)p->g, n, p->cfg.nb, nchan, (T)p->cfg.lambda_r,
-        (T)p->cfg.lambda_s, use_r ? 1 : 0, use_k ? 1 : 0, p->rpart);
+    {
+        auto kas = assemble_te(n, nchan) == 16 ? k_assemble<T, 16> : k_assemble<T, 32>;
+        kas<<<assemble_grid(n, nchan), 256, 0, p->stream>>>(
+            (const T *)p->x, (const T *)p->contrib, p->pinfo_d, p->chan_start_d, p->chan_list_d,
+            (const T *)p->gradK, (T *)p->g, n, p->cfg.nb, nchan, (T)p->cfg.lambda_r,
+            (T)p->cfg.lambda_s, use_r ? 1 : 0, use_k ? 1 : 0, p->rpart);
+    }
     launches += 1;
     if (p->any_grid && p->nslot > 0) {
         dim3 gs((p->cfg.nb * p->cfg.nb + 255) / 256, p->nslot);
@@ -1812,9 +1815,12 @@ ivis_status dirty_impl(ivis_plan_s *p, void *dirty_dev, void *beamw_dev) {
         if (e == cudaSuccess) e = launch_adjoint<T>(p);
         if (e != cudaSuccess) return fail(p, IVIS_ERR_CUDA, std::string("dirty: ") + cudaGetErrorString(e));
     }
-    k_assemble<T><<<assemble_grid(n, nchan), 256, 0, p->stream>>>(
-        (const T *)p->x, (const T *)p->contrib, p->pinfo_d, p->chan_start_d, p->chan_list_d, nullptr,
-        (T *)p->g, n, p->cfg.nb, nchan, (T)0, (T)0, 0, 0, p->rpart);
+    {
+        auto kas = assemble_te(n, nchan) == 16 ? k_assemble<T, 16> : k_assemble<T, 32>;
+        kas<<<assemble_grid(n, nchan), 256, 0, p->stream>>>(
+            (const T *)p->x, (const T *)p->contrib, p->pinfo_d, p->chan_start_d, p->chan_list_d, nullptr,
+            (T *)p->g, n, p->cfg.nb, nchan, (T)0, (T)0, 0, 0, p->rpart);
+    }
     if (p->any_grid && p->nslot > 0) {
         dim3 gs((p->cfg.nb * p->cfg.nb + 255) / 256, p->nslot);
         k_grid_scatter<T><<<gs, 256, 0, p->stream>>>((const T *)p->contrib, p->pinfo_d,

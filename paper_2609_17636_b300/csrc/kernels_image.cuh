@@ -23,20 +23,19 @@ __device__ __forceinline__ T lap(const T *__restrict__ I, int n, int y, int x) {
            pix(I, n, y, x - 1) - pix(I, n, y, x + 1);
 }
 
-// One CTA per 32 x 32 pixel tile of one channel (256 threads, 4 pixels each). The Laplacian
+// One CTA per TE x TE pixel tile of one channel (256 threads; TE = 32: 4 pixels each, TE = 16
+// for small images so that the grid still fills the GPU: 1 pixel each). The Laplacian
 // terms come from the tile's sky with a 2-pixel halo and its Laplacian with a 1-pixel halo,
 // both staged in shared memory; the window contributions from the channel's pairs whose windows
 // meet the tile, listed once per CTA in the channel's slot order (the per-pixel sum runs in
 // that order, as it would over all the channel's pairs). One R partial per CTA.
-constexpr int ASM_TE = 32;
-
-template <typename T>
+template <typename T, int TE>
 __global__ void __launch_bounds__(256)
 k_assemble(const T *__restrict__ sky, const T *__restrict__ contrib,
            const PairInfo *__restrict__ pinfo, const int *__restrict__ chan_start,
            const int *__restrict__ chan_list, const T *__restrict__ gradK, T *grad, int n, int nb,
            int nchan, T lr, T ls, int use_r, int use_k, double *rpart) {
-    constexpr int TE = ASM_TE;
+    constexpr int PPT = TE * TE / 256, RSTEP = 256 / TE;  // pixels per thread, rows per pass
     __shared__ T xs[TE + 4][TE + 5];  // sky, 2-pixel halo, zero off the image
     __shared__ T lp[TE + 2][TE + 3];  // Laplacian, 1-pixel halo
     __shared__ int list[256];
@@ -46,7 +45,7 @@ k_assemble(const T *__restrict__ sky, const T *__restrict__ contrib,
     const int ntx = (n + TE - 1) / TE;
     const int chan = blockIdx.y;
     const int y0 = (blockIdx.x / ntx) * TE, x0 = (blockIdx.x % ntx) * TE;
-    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // pixel (y0 + ty + 8 j, x0 + tx)
+    const int tx = threadIdx.x % TE, ty = threadIdx.x / TE;  // pixel (y0 + ty + RSTEP j, x0 + tx)
     const size_t npix = (size_t)n * n;
     const T *I = sky + (size_t)chan * npix;
     if (use_r) {
@@ -61,7 +60,9 @@ k_assemble(const T *__restrict__ sky, const T *__restrict__ contrib,
                          xs[yy + 1][xx + 2];
         }
     }
-    T g[4] = {(T)0, (T)0, (T)0, (T)0};
+    T g[PPT];
+#pragma unroll
+    for (int j = 0; j < PPT; ++j) g[j] = (T)0;
     const int t0 = chan_start[chan], t1 = chan_start[chan + 1];
     for (int b0 = t0; b0 < t1; b0 += 256) {
         const int b1 = min(t1, b0 + 256);
@@ -92,8 +93,8 @@ k_assemble(const T *__restrict__ sky, const T *__restrict__ contrib,
             const int p = x0 + tx - (pi.cx - nb / 2);
             const T *cs = contrib + (size_t)slot * nb * nb;
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const int q = y0 + ty + 8 * j - (pi.cy - nb / 2);
+            for (int j = 0; j < PPT; ++j) {
+                const int q = y0 + ty + RSTEP * j - (pi.cy - nb / 2);
                 if ((unsigned)q < (unsigned)nb && (unsigned)p < (unsigned)nb) g[j] += cs[(size_t)q * nb + p];
             }
         }
@@ -101,8 +102,8 @@ k_assemble(const T *__restrict__ sky, const T *__restrict__ contrib,
     __syncthreads();  // the Laplacian tile is complete
     T rloc = (T)0;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        const int ly = ty + 8 * j, y = y0 + ly, x = x0 + tx;
+    for (int j = 0; j < PPT; ++j) {
+        const int ly = ty + RSTEP * j, y = y0 + ly, x = x0 + tx;
         if (y >= n || x >= n) continue;
         const size_t idx = (size_t)chan * npix + (size_t)y * n + x;
         T gj = g[j];
@@ -123,9 +124,14 @@ k_assemble(const T *__restrict__ sky, const T *__restrict__ contrib,
     if (threadIdx.x == 0) rpart[(size_t)blockIdx.y * gridDim.x + blockIdx.x] = s;
 }
 
+// Tile edge of k_assemble: 32, or 16 when 32-pixel tiles would give fewer than 1184 CTAs.
+inline int assemble_te(int n, int nchan) {
+    const long long nt = (n + 31) / 32;
+    return nt * nt * nchan < 1184 ? 16 : 32;
+}
 // CTAs of k_assemble: (tiles per channel, channels).
 inline dim3 assemble_grid(int n, int nchan) {
-    const int nt = (n + ASM_TE - 1) / ASM_TE;
+    const int te = assemble_te(n, nchan), nt = (n + te - 1) / te;
     return dim3((unsigned)(nt * nt), (unsigned)nchan);
 }
 

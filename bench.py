@@ -56,6 +56,9 @@ def parse():
     ap.add_argument("--no-precision", action="store_true")
     ap.add_argument("--grid-tile", type=int, default=0, choices=[0, 32, 64],
                     help="fix the gridding tile edge (0: the autotuner chooses)")
+    ap.add_argument("--grid-kernel", type=int, default=0, choices=[0, 1, 2],
+                    help="fix the FP32 item pass: 1 scalar, 2 tensor-core (0: the autotuner "
+                         "times both)")
     ap.add_argument("--c3-channels", type=int, default=32,
                     help="channels of the batched cube (fewer: the same per-pair density on a "
                          "smaller device footprint, for profiler captures)")
@@ -259,7 +262,8 @@ def attach_data_gpu(prob, plan_fp64_like):
         prob.sigma_sd = sig
 
 
-def build_plan(prob, precision, serial=False, autotune=False, toeplitz=False, wterm=False, grid_tile=0):
+def build_plan(prob, precision, serial=False, autotune=False, toeplitz=False, wterm=False, grid_tile=0,
+               grid_kernel=0):
     from paper_2609_17636_b300 import plan_from_problem
     for pair in prob.pairs:
         if pair.vis is None:
@@ -268,7 +272,7 @@ def build_plan(prob, precision, serial=False, autotune=False, toeplitz=False, wt
         prob.tsd = np.zeros((prob.nchan, prob.n, prob.n), np.float32)
         prob.sigma_sd = np.ones(prob.nchan)
     return plan_from_problem(prob, precision, serial_pairs=serial, autotune=autotune, toeplitz=toeplitz,
-                             wterm=wterm, grid_tile=grid_tile)
+                             wterm=wterm, grid_tile=grid_tile, grid_kernel=grid_kernel)
 
 
 # ----------------------------------------------------------------- roofline model
@@ -348,7 +352,8 @@ def run_ivis(args, rank, world):
     datagen = build_plan(prob, "fp64" if args.config in ("c1", "c2") else "fp32")
     attach_data_gpu(prob, datagen)
     datagen.close()
-    plan = build_plan(prob, args.precision, autotune=True, grid_tile=args.grid_tile)
+    plan = build_plan(prob, args.precision, autotune=True, grid_tile=args.grid_tile,
+                      grid_kernel=args.grid_kernel)
     plan.prepare()
     x = torch.as_tensor(prob.sky_true * 0.5, dtype=plan.dtype, device=dev)
     g = torch.empty_like(x)

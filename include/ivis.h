@@ -107,6 +107,15 @@ typedef struct {
                            else 32; with autotune = 1 the autotuner times both and keeps the
                            faster), 32, or 64 (FP32 only; needs nb >= 32). Any other value:
                            IVIS_ERR_ARG. The result does not depend on it beyond rounding.   */
+    int grid_kernel;    /* the fused interpolation / residual / spreading pass of the FP32
+                           cost and gradient (kernel_width <= 8, no wterm): 0 = default (the
+                           scalar pass; with autotune = 1 the autotuner times both and keeps
+                           the faster), 1 = scalar pass (one lane per kernel column,
+                           per-group adjoint buffers in shared memory), 2 = tensor-core pass
+                           (per 8 x 8 block of first taps, interpolation F^T Ky and spreading
+                           Ky diag(w r) Kx^T as TF32 mma with split operands, FP32-accurate).
+                           Ignored where the pass does not apply. Any other value:
+                           IVIS_ERR_ARG. The result does not depend on it beyond rounding.   */
 } ivis_config;
 
 typedef struct {

@@ -45,7 +45,8 @@ class Config(ctypes.Structure):
                 ("lambda_r", ctypes.c_double), ("lambda_s", ctypes.c_double),
                 ("positivity", ctypes.c_int), ("serial_pairs", ctypes.c_int),
                 ("autotune", ctypes.c_int), ("toeplitz", ctypes.c_int), ("wterm", ctypes.c_int),
-                ("grid_tile", ctypes.c_int)]
+                ("grid_tile", ctypes.c_int),
+                ("grid_kernel", ctypes.c_int)]
 
 
 class SolveReport(ctypes.Structure):

@@ -29,6 +29,7 @@
 #include "kernels_toeplitz.cuh"
 #include "kernels_wstack.cuh"
 #include "kernels_grid.cuh"
+#include "kernels_gridtc.cuh"
 
 using namespace ivis;
 
@@ -78,7 +79,8 @@ struct ivis_plan_s {
     double beta = 0.0;
     int tile = 32, ntx = 0, ntiles = 0;  // sort bins (32 x 32 cells) of the fine grid
     int gtile = 32;                      // tile edge of the k_grid_pass work list (32 or 64)
-    int xtile = 32, item_len = 32;       // k_grid_cg work list: tile edge, visibilities per item
+    int xtile = 32, item_len = 32;       // item work list: tile edge, visibilities per item
+    int xkern = 1;                       // item pass: 1 scalar (k_grid_cg), 2 tensor-core (k_grid_tc)
     int f_half = 0;  // the last forward pass wrote rows 0 .. nf/2 of F only (packed, real windows)
     int logc_cols = 0;  // log2 columns per CTA in the column FFT passes
     int clear_blocks = 8 * 148;  // CTAs of the grid-stride clearing kernel (8 per SM)
@@ -404,11 +406,21 @@ cudaError_t launch_grid_pass_ts(ivis_plan_s *p, int first_chunk, int nchunk, dou
     return cudaGetLastError();
 }
 
-// k_grid_cg over chunks [first, first + n) of the item work list (p->xchunks_d).
+// The item pass (k_grid_cg, or k_grid_tc with p->xkern == 2) over chunks [first, first + n)
+// of the item work list (p->xchunks_d).
 template <int TS>
 cudaError_t launch_grid_cg_ts(ivis_plan_s *p, int first, int n, double *jpart, int gfold) {
 #define CG_CASE(WW)                                                                                   \
     case WW: {                                                                                        \
+        if (p->xkern == 2) {                                                                          \
+            auto kern = k_grid_tc<WW, TS>;                                                            \
+            const size_t sm = GridTC<WW, TS>::SMEM;                                                   \
+            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);         \
+            kern<<<n, GridTC<WW, TS>::THREADS, sm, p->stream>>>(                                      \
+                p->xchunks_d + first, p->items_d, (const PairData<float> *)p->pdata_d,                \
+                (const float2 *)p->F, (float2 *)p->G, p->lognf, p->f_half, gfold, p->kpoly_d, jpart); \
+            return cudaGetLastError();                                                                \
+        }                                                                                             \
         auto kern = k_grid_cg<WW, TS>;                                                                \
         const size_t sm = GridCG<WW, TS>::SMEM;                                                       \
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);             \
@@ -1243,7 +1255,7 @@ ivis_status autotune(ivis_plan_s *p) {
     ivis_status s_;
     const std::string key = tune_key(p);
     const char *path = std::getenv("IVIS_AUTOTUNE_CACHE");
-    int best_cap = -1, best_logc = -1, best_ts = -1;
+    int best_cap = -1, best_logc = -1, best_ts = -1, best_kern = -1;
     if (path) {
         if (FILE *f = std::fopen(path, "r")) {
             char line[512];
@@ -1251,9 +1263,14 @@ ivis_status autotune(ivis_plan_s *p) {
                 std::string l(line);
                 const size_t bar = l.find('|');
                 if (bar == std::string::npos || l.substr(0, bar) != key) continue;
-                int cap = 0, lc = -1, ts = 32;
-                const int got = std::sscanf(l.c_str() + bar + 1, "%d %d %d", &cap, &lc, &ts);
-                if (got >= 2) { best_cap = cap; best_logc = lc; best_ts = got == 3 ? ts : 32; }
+                int cap = 0, lc = -1, ts = 32, kn = 1;
+                const int got = std::sscanf(l.c_str() + bar + 1, "%d %d %d %d", &cap, &lc, &ts, &kn);
+                if (got >= 2) {
+                    best_cap = cap;
+                    best_logc = lc;
+                    best_ts = got >= 3 ? ts : 32;
+                    best_kern = got >= 4 ? kn : 1;
+                }
             }
             std::fclose(f);
         }
@@ -1284,8 +1301,11 @@ ivis_status autotune(ivis_plan_s *p) {
     };
     // a cached decision is used only if it is one the tuner itself could have made (the chunk
     // buffers are sized for the smallest candidate chunk)
-    if (best_cap > 0 && (!tile_ok(best_ts) || !cap_ok(best_ts, best_cap) || !feasible_logc(best_logc)))
-        best_cap = best_logc = best_ts = -1;
+    // item-pass kinds the plan can use: the configured one, else both
+    auto kern_ok = [&](int k) { return cg && (k == 1 || k == 2) && (!p->cfg.grid_kernel || k == p->cfg.grid_kernel); };
+    if (best_cap > 0 && (!tile_ok(best_ts) || !cap_ok(best_ts, best_cap) || !feasible_logc(best_logc) ||
+                         (cg && !kern_ok(best_kern))))
+        best_cap = best_logc = best_ts = best_kern = -1;
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
@@ -1323,11 +1343,13 @@ ivis_status autotune(ivis_plan_s *p) {
         std::vector<Item> itv;
         std::vector<int> first;
         float bg = 1e30f;
+        for (int kn : {1, 2})
         for (int ts : {32, 64}) {
-            if (!tile_ok(ts)) continue;
+            if (!tile_ok(ts) || (cg ? !kern_ok(kn) : kn != 1)) continue;
             for (int cap : caps_of(ts)) {
                 float ms;
                 if (cg) {
+                    p->xkern = kn;
                     p->xtile = ts;
                     build_items(p, ts, cap, ch, itv, first);
                     CK(cudaMemcpy(p->xchunks_d, ch.data(), ch.size() * sizeof(Chunk), cudaMemcpyHostToDevice));
@@ -1349,13 +1371,13 @@ ivis_status autotune(ivis_plan_s *p) {
                         }
                     });
                 }
-                if (ms < bg) { bg = ms; best_cap = cap; best_ts = ts; }
+                if (ms < bg) { bg = ms; best_cap = cap; best_ts = ts; best_kern = kn; }
             }
         }
         CK(cudaGetLastError());
         if (path) {
             if (FILE *f = std::fopen(path, "a")) {
-                std::fprintf(f, "%s|%d %d %d\n", key.c_str(), best_cap, best_logc, best_ts);
+                std::fprintf(f, "%s|%d %d %d %d\n", key.c_str(), best_cap, best_logc, best_ts, best_kern);
                 std::fclose(f);
             }
         }
@@ -1365,10 +1387,12 @@ ivis_status autotune(ivis_plan_s *p) {
     p->logc_cols = best_logc;
     std::string grid;
     if (cg) {
+        p->xkern = best_kern;
         p->xtile = best_ts;
         p->item_len = best_cap;
         if ((s_ = upload_items(p))) return s_;
-        grid = "tile " + std::to_string(p->xtile) + ", items of " + std::to_string(p->item_len);
+        grid = std::string(p->xkern == 2 ? "tensor-core" : "scalar") + " item pass, tile " +
+               std::to_string(p->xtile) + ", items of " + std::to_string(p->item_len);
     } else {
         p->chunk_cap = best_cap;
         p->gtile = best_ts;
@@ -1997,6 +2021,10 @@ ivis_status ivis_plan(const ivis_config *cfg, void *stream, ivis_plan_t *out) {
         delete p;
         return fail(nullptr, IVIS_ERR_ARG, "grid_tile must be 0, 32 or 64");
     }
+    if (c.grid_kernel < 0 || c.grid_kernel > 2) {
+        delete p;
+        return fail(nullptr, IVIS_ERR_ARG, "grid_kernel must be 0, 1 or 2");
+    }
     if (c.grid_tile == 64 && (p->fp64 || p->ntx < 2)) {
         delete p;
         return fail(nullptr, IVIS_ERR_ARG, "grid_tile 64 needs IVIS_FP32 and nb >= 32");
@@ -2005,6 +2033,7 @@ ivis_status ivis_plan(const ivis_config *cfg, void *stream, ivis_plan_t *out) {
     p->chunk_cap = p->gtile == 64 ? 2048 : 1024;
     p->xtile = c.grid_tile ? c.grid_tile : 32;
     p->item_len = 32;
+    p->xkern = c.grid_kernel ? c.grid_kernel : 1;
     {
         // columns per CTA in the column FFT passes: as many as fit 100 KB of shared memory
         // and 1024 threads; at least 4 (32-byte row segments) if 160 KB allows it

@@ -37,7 +37,7 @@ class Plan:
                  lambda_r: float = 0.0, lambda_s: float = 0.0, positivity: bool = True,
                  stream: torch.cuda.Stream | None = None, serial_pairs: bool = False,
                  autotune: bool = False, toeplitz: bool = False, wterm: bool = False,
-                 grid_tile: int = 0):
+                 grid_tile: int = 0, grid_kernel: int = 0):
         self.L = _lib.load()
         if precision not in ("fp32", "fp64"):
             raise ValueError("precision must be 'fp32' or 'fp64'")
@@ -49,7 +49,7 @@ class Plan:
                                IVIS_FP32 if precision == "fp32" else IVIS_FP64,
                                nufft_tol, kernel_width, lambda_r, lambda_s, int(bool(positivity)),
                                int(bool(serial_pairs)), int(bool(autotune)), int(bool(toeplitz)),
-                               int(bool(wterm)), int(grid_tile))
+                               int(bool(wterm)), int(grid_tile), int(grid_kernel))
         self.shape = (nchan, n, n)
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         self._p = ctypes.c_void_p()

@@ -66,7 +66,7 @@ def test_rayleigh_jeans_entry_point_matches_the_oracle():
 
 GOOD = dict(n=64, nchan=1, npoint=1, nb=32, cell_rad=1e-5, precision=1, nufft_tol=1e-6,
             kernel_width=0, lambda_r=0.0, lambda_s=0.0, positivity=1, serial_pairs=0, autotune=0,
-            toeplitz=0, wterm=0, grid_tile=0)
+            toeplitz=0, wterm=0, grid_tile=0, grid_kernel=0)
 
 # (overrides of a valid configuration, expected status, fragment of the error message)
 BAD = [
@@ -89,6 +89,8 @@ BAD = [
     ({"grid_tile": 48}, 1, b"grid_tile"),
     ({"grid_tile": 64, "precision": 0}, 1, b"grid_tile 64"),
     ({"grid_tile": 64, "nb": 16}, 1, b"grid_tile 64"),
+    ({"grid_kernel": 3}, 1, b"grid_kernel"),
+    ({"grid_kernel": -1}, 1, b"grid_kernel"),
 ]
 
 

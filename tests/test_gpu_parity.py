@@ -36,12 +36,14 @@ def _plan(prob, precision, **kw):
     return plan_from_problem(prob, precision, **kw)
 
 
-@pytest.mark.parametrize("precision,tile", [("fp64", 0), ("fp32", 32), ("fp32", 64)])
-def test_cost_and_gradient_match_oracle(mosaic, precision, tile):
-    """FP32 runs the one-lane-per-kernel-column grid pass with 32- and 64-cell tiles (the
-    128^2 fine grids hold 2 x 2 tiles of 64 cells, each patch wrapping at the grid edge)."""
+@pytest.mark.parametrize("precision,tile,kern", [("fp64", 0, 0), ("fp32", 32, 1), ("fp32", 64, 1),
+                                                 ("fp32", 32, 2), ("fp32", 64, 2)])
+def test_cost_and_gradient_match_oracle(mosaic, precision, tile, kern):
+    """FP32 runs the scalar item pass (kern 1: one lane per kernel column) and the tensor-core
+    item pass (kern 2: split-TF32 mma per 8 x 8 block) with 32- and 64-cell tiles (the 128^2
+    fine grids hold 2 x 2 tiles of 64 cells, each patch wrapping at the grid edge)."""
     prob, x, f, g, terms = mosaic
-    plan = _plan(prob, precision, grid_tile=tile)
+    plan = _plan(prob, precision, grid_tile=tile, grid_kernel=kern)
     dt = torch.float64 if precision == "fp64" else torch.float32
     xs = torch.as_tensor(x, dtype=dt, device="cuda")
     fg, grad, tg = plan.cost_grad(xs)
@@ -51,6 +53,27 @@ def test_cost_and_gradient_match_oracle(mosaic, precision, tile):
         assert abs(a - b) <= tol * abs(b) + 1e-300, (tg, terms)
     assert rel_l2(grad.cpu().numpy(), g) <= tol, rel_l2(grad.cpu().numpy(), g)
     plan.close()
+
+
+@pytest.mark.parametrize("width", [3, 5, 8])
+def test_item_passes_at_other_kernel_widths(mosaic, width):
+    """The scalar and tensor-core item passes at kernel widths 3, 5 and 8 (a quad's lanes then
+    hold one or two taps each, and the footprint of an 8 x 8 block fills 10 to 15 of its 16 rows
+    and columns): both within the NUFFT's error of the oracle (about 10^-(W - 1)), and the same
+    cost and gradient to FP32 rounding."""
+    prob, x, f, g, terms = mosaic
+    res = {}
+    for kern in (1, 2):
+        plan = _plan(prob, "fp32", kernel_width=width, grid_kernel=kern)
+        fg, grad, _ = plan.cost_grad(torch.as_tensor(x, dtype=torch.float32, device="cuda"))
+        res[kern] = (fg, grad.cpu().numpy())
+        plan.close()
+    bound = max(TOL["fp32"], 10.0 ** -(width - 2))
+    for fg, gr in res.values():
+        assert abs(fg - f) <= bound * abs(f), (fg, f)
+        assert rel_l2(gr, g) <= bound
+    assert abs(res[1][0] - res[2][0]) <= 2e-6 * abs(res[1][0]), (res[1][0], res[2][0])
+    assert rel_l2(res[2][1], res[1][1]) <= 2e-6, rel_l2(res[2][1], res[1][1])
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
@@ -263,8 +286,8 @@ def test_dense_single_tile_many_chunks(precision):
     plan.close()
 
 
-@pytest.mark.parametrize("tile", [32, 64])
-def test_dense_single_64_cell_tile_many_chunks(tile):
+@pytest.mark.parametrize("tile,kern", [(32, 1), (64, 1), (32, 2), (64, 2)])
+def test_dense_single_64_cell_tile_many_chunks(tile, kern):
     """nb = 32 gives a 64^2 fine grid: one 64-cell tile (or four 32-cell tiles) holding ~6000
     visibilities per pair, split into several chunks with a ragged last one; first taps on
     every cell row and column including the wrap at the grid edge."""
@@ -274,7 +297,7 @@ def test_dense_single_64_cell_tile_many_chunks(tile):
     assert max(p.m for p in prob.pairs) > 4096
     x = prob.sky_true * 0.6
     f, g = oracle.cost_grad(prob, x)
-    plan = _plan(prob, "fp32", grid_tile=tile)
+    plan = _plan(prob, "fp32", grid_tile=tile, grid_kernel=kern)
     xs = torch.as_tensor(x, dtype=torch.float32, device="cuda")
     fg, grad, _ = plan.cost_grad(xs)
     assert abs(fg - f) <= TOL["fp32"] * abs(f)

@@ -131,6 +131,76 @@ __device__ __forceinline__ void line_fft(C *base, int stride, int off, int logL,
     else if (rem == 1) stockham_pass<C, 2, SIGN>(base, stride, off, L, logL, 1 << logNs, logNs, j0, tpl, tw);
 }
 
+// The first pass of line_fft (Ns = 1, radix 16) on an input held in registers: in[r] is the
+// line's element j0 + r L/16, the inputs of this thread's butterfly. Writes the pass's output to
+// the line; the caller synchronises before the next pass (line_fft_from with logNs0 = 4).
+template <typename C, int SIGN>
+__device__ __forceinline__ void first_pass_regs(C *base, int stride, int off, int j0, C (&in)[16]) {
+    dft_regs<C, 16, SIGN>(in);
+#pragma unroll
+    for (int r = 0; r < 16; ++r) base[pidx((j0 * 16 + r) * stride + off)] = in[brev_c<16>(r)];
+}
+
+// The passes of line_fft from Ns = 2^logNs0 on (logNs0 a multiple of 4); with last_in_regs the
+// final pass is left out (last_pass_regs runs it).
+template <typename C, int SIGN>
+__device__ __forceinline__ void line_fft_from(C *base, int stride, int off, int logL, int j0,
+                                              const C *__restrict__ tw, int logNs0, bool last_in_regs) {
+    const int L = 1 << logL;
+    const int tpl = L >> 4;
+    const int rem = logL & 3, n16 = logL >> 2;  // n16 radix-16 passes, then one of radix 2^rem
+    const int n16_run = (rem == 0 && last_in_regs) ? n16 - 1 : n16;
+    int logNs = logNs0;
+    for (; logNs < 4 * n16_run; logNs += 4)
+        stockham_pass<C, 16, SIGN>(base, stride, off, L, logL, 1 << logNs, logNs, j0, tpl, tw);
+    if (rem == 0 || last_in_regs) return;
+    if (rem == 3) stockham_pass<C, 8, SIGN>(base, stride, off, L, logL, 1 << logNs, logNs, j0, tpl, tw);
+    else if (rem == 2) stockham_pass<C, 4, SIGN>(base, stride, off, L, logL, 1 << logNs, logNs, j0, tpl, tw);
+    else stockham_pass<C, 2, SIGN>(base, stride, off, L, logL, 1 << logNs, logNs, j0, tpl, tw);
+}
+
+// The final pass (Ns = L / RP) of line_fft with its output handed to emit(m, value) as each
+// butterfly finishes: m indexes the line's element j0 + m L/16 (the butterflies of this pass
+// write exactly those elements, since each of the thread's G = 16 / RP groups j = j0 + g L/16
+// has j < Ns). No shared-memory writes, so nothing to synchronise after it.
+template <typename C, int RP, int SIGN, typename E>
+__device__ __forceinline__ void last_pass_regs_rp(const C *base, int stride, int off, int L, int logNs, int j0,
+                                                  const C *__restrict__ tw, E &&emit) {
+    constexpr int G = 16 / RP;
+    const int Ns = 1 << logNs, tpl = L >> 4, LR = L / RP;
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+        const int j = j0 + g * tpl;  // < Ns: k = j, output elements j + r Ns
+        const int toff = 16 * (Ns - 1) / 15 + j;
+        C v[RP];
+#pragma unroll
+        for (int r = 0; r < RP; ++r) {
+            C x = base[pidx((j + r * LR) * stride + off)];
+            if (r > 0 && j != 0) {
+                C w = __ldg(&tw[toff + r * Ns]);
+                if (SIGN > 0) w.y = -w.y;
+                x = cmul(x, w);
+            }
+            v[r] = x;
+        }
+        dft_regs<C, RP, SIGN>(v);
+#pragma unroll
+        for (int r = 0; r < RP; ++r) emit(g + r * G, v[brev_c<RP>(r)]);  // element j0 + (g + r G) L/16
+    }
+}
+
+template <typename C, int SIGN, typename E>
+__device__ __forceinline__ void last_pass_regs(const C *base, int stride, int off, int logL, int j0,
+                                               const C *__restrict__ tw, E &&emit) {
+    const int L = 1 << logL;
+    const int rem = logL & 3;
+    const int logNs = rem == 0 ? logL - 4 : logL - rem;
+    if (rem == 0) last_pass_regs_rp<C, 16, SIGN>(base, stride, off, L, logNs, j0, tw, emit);
+    else if (rem == 3) last_pass_regs_rp<C, 8, SIGN>(base, stride, off, L, logNs, j0, tw, emit);
+    else if (rem == 2) last_pass_regs_rp<C, 4, SIGN>(base, stride, off, L, logNs, j0, tw, emit);
+    else last_pass_regs_rp<C, 2, SIGN>(base, stride, off, L, logNs, j0, tw, emit);
+}
+
 // Shared-memory elements needed for `lines` lines of length L (padded addressing).
 __host__ __device__ inline int fft_smem_elems(int L, int lines) { return pidx(L * lines - 1) + 1; }
 

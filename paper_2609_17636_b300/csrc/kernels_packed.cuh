@@ -63,19 +63,24 @@ k_fwd_rows_pk(const T *__restrict__ sky, const T *__restrict__ wts, const PairIn
     const PairInfo pb = hasb ? pinfo[sb] : pa;
     const int l = threadIdx.x / tpl, j0 = threadIdx.x - l * tpl;
     const int q = blockIdx.x * lpb + l;
-    // entry e of the line holds window column p = e + nb/2 (mod nf) if p < nb, else zero
-    for (int e = j0; e < nf; e += tpl) {
-        const int p = (e + nb / 2) & (nf - 1);
+    // element e of the line holds window column p = e + nb/2 (mod nf) if p < nb, else zero: the
+    // thread's elements j0 + m tpl (the inputs of its first-pass butterfly, which runs from
+    // registers) hold the columns j0 + ((m + 4) mod 16) tpl, those with (m + 4) mod 16 < 8 inside
+    C in[16];
+#pragma unroll
+    for (int m = 0; m < 16; ++m) {
+        const int mp = (m + 4) & 15, p = j0 + mp * tpl;
         C v = mk((T)0, (T)0);
-        if (q < nb && p < nb) {
+        if (mp < 8 && q < nb) {
             const T va = window_value(pa, q, p, sky, wts, grids, n, nb);
             const T vb = hasb ? window_value(pb, q, p, sky, wts, grids, n, nb) : (T)0;
             v = mk(va, vb);
         }
-        s[pidx(l * nf + e)] = v;
+        in[m] = v;
     }
+    first_pass_regs<C, -1>(s, 1, l * nf, j0, in);
     __syncthreads();
-    line_fft<C, -1>(s, 1, l * nf, lognf, j0, tw);
+    line_fft_from<C, -1>(s, 1, l * nf, lognf, j0, tw, 4, false);
     if (q < nb) {
         C *out = rowbuf + ((size_t)blockIdx.y * nb + q) * nf;
         for (int e = j0; e < nf; e += tpl) out[e] = s[pidx(l * nf + e)];
@@ -96,17 +101,19 @@ k_fwd_cols_pk(const typename cplx_of<T>::type *__restrict__ rowbuf, typename cpl
     const int c0 = blockIdx.x * ncol, pk = blockIdx.y;
     const int L = threadIdx.x & (nl - 1), j0 = threadIdx.x >> lgl;
     const int col = pk_col(L, c0, ncol, nf);
-    for (int e = j0; e < nf; e += tpl) s[pidx((e << lgl) + L)] = mk((T)0, (T)0);
-    __syncthreads();
     const C *src = rowbuf + (size_t)pk * nb * nf;
-    // nb = nf / 2 rows: 8 per thread, all loaded before they are stored
+    // nb = nf / 2 rows: 8 per thread (rows j0 + r tpl). Element e of the line holds row
+    // (e + nb/2) mod nf (zero past nb), so element j0 + m tpl holds row j0 + ((m + 4) mod 16) tpl:
+    // the thread's rows are the inputs of its own first-pass butterfly, which runs from registers
     C v[8];
 #pragma unroll
     for (int r = 0; r < 8; ++r) v[r] = src[(size_t)(j0 + r * tpl) * nf + col];
+    C in[16];
 #pragma unroll
-    for (int r = 0; r < 8; ++r) s[pidx((((j0 + r * tpl - nb / 2) & (nf - 1)) << lgl) + L)] = v[r];
+    for (int m = 0; m < 16; ++m) in[m] = ((m + 4) & 15) < 8 ? v[(m + 4) & 15] : mk((T)0, (T)0);
+    first_pass_regs<C, -1>(s, nl, L, j0, in);
     __syncthreads();
-    line_fft<C, -1>(s, nl, L, lognf, j0, tw);
+    line_fft_from<C, -1>(s, nl, L, lognf, j0, tw, 4, false);
     const int Lm = pk_mirror_line(L, c0, ncol);
     const int sa = 2 * pk, sb = sa + 1;
     C *Fa = F + (size_t)sa * nf * nf, *Fb = F + (size_t)sb * nf * nf;
@@ -173,9 +180,14 @@ k_adj_cols_pk(typename cplx_of<T>::type *G, typename cplx_of<T>::type *rowbuf, i
         }
     }
     __syncthreads();
-    line_fft<C, +1>(s, nl, L, lognf, j0, tw);
+    line_fft_from<C, +1>(s, nl, L, lognf, j0, tw, 0, true);
+    // element j0 + m tpl is window row j0 + ((m + 4) mod 16) tpl (row q at (q - nb/2) mod nf);
+    // the rows q < nb go to the packed row buffer straight from registers
     C *dst = rowbuf + (size_t)pk * nb * nf;
-    for (int q = j0; q < nb; q += tpl) dst[(size_t)q * nf + col] = s[pidx((((q - nb / 2) & (nf - 1)) << lgl) + L)];
+    last_pass_regs<C, +1>(s, nl, L, lognf, j0, tw, [&](int m, const C &v) {
+        const int mq = (m + 4) & 15;
+        if (mq < 8) dst[(size_t)(j0 + mq * tpl) * nf + col] = v;
+    });
 }
 
 // Rows 0 .. nf/2 of each of nslot adjoint grids back to zero for the next gridding pass: one
@@ -196,7 +208,7 @@ k_clear_half(typename cplx_of<T>::type *G, int lognf) {
 // ------------------------------------------------------------------------- adjoint rows
 // Inverse DFT along x; the real part is slot a's window gradient, the imaginary part slot b's.
 template <typename T>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, sizeof(T) == 8 ? 1 : 4)
 k_adj_rows_pk(const typename cplx_of<T>::type *__restrict__ rowbuf, const T *__restrict__ wts,
               const PairInfo *__restrict__ pinfo, int nslot, T *contrib, int n,
               int nb, int lognf, const typename cplx_of<T>::type *__restrict__ tw) {
@@ -222,17 +234,20 @@ k_adj_rows_pk(const typename cplx_of<T>::type *__restrict__ rowbuf, const T *__r
         }
     }
     __syncthreads();
-    line_fft<C, +1>(s, 1, l * nf, lognf, j0, tw);
-    if (q >= nb) return;
+    line_fft_from<C, +1>(s, 1, l * nf, lognf, j0, tw, 0, true);
+    if (q >= nb) return;  // the line's last pass only feeds this row's outputs
     const int ya = pa.cy - nb / 2 + q, yb = pb.cy - nb / 2 + q;
     const bool ona = pa.gridded || (ya >= 0 && ya < n), onb = hasb && (pb.gridded || (yb >= 0 && yb < n));
     T *oa = contrib + ((size_t)sa * nb + q) * nb, *ob = contrib + ((size_t)sb * nb + q) * nb;
     const T *ba = wts + ((size_t)pa.k * nb + q) * nb, *bb = wts + ((size_t)pb.k * nb + q) * nb;
-    for (int p = j0; p < nb; p += tpl) {
-        const C v = s[pidx(l * nf + ((p - nb / 2) & (nf - 1)))];
+    // element j0 + m tpl is window column j0 + ((m + 4) mod 16) tpl (column p at (p - nb/2) mod
+    // nf); the columns p < nb straight from registers
+    last_pass_regs<C, +1>(s, 1, l * nf, lognf, j0, tw, [&](int m, const C &v) {
+        const int mp = (m + 4) & 15, p = j0 + mp * tpl;
+        if (mp >= 8) return;
         if (ona) oa[p] = v.x * ba[p];
         if (onb) ob[p] = v.y * bb[p];
-    }
+    });
 }
 
 // ---------------------------------------------------------------- Toeplitz, packed pairs

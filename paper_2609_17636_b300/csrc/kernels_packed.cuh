@@ -289,8 +289,12 @@ k_toep_cols_pk(typename cplx_of<T>::type *rowbuf, const T *const *__restrict__ t
 #pragma unroll
     for (int i = 0; i < 16; ++i) s[pidx(((j0 + i * tpl) << lgl) + L)] = w[i];
     __syncthreads();
-    line_fft<C, +1>(s, nl, L, lognf, j0, tw);
-    for (int q = j0; q < nb; q += tpl) buf[(size_t)q * nf + col] = s[pidx((((q - nb / 2) & (nf - 1)) << lgl) + L)];
+    line_fft_from<C, +1>(s, nl, L, lognf, j0, tw, 0, true);
+    // the window rows q < nb (element j0 + m tpl is row j0 + ((m + 4) mod 16) tpl) from registers
+    last_pass_regs<C, +1>(s, nl, L, lognf, j0, tw, [&](int m, const C &v) {
+        const int mq = (m + 4) & 15;
+        if (mq < 8) buf[(size_t)(j0 + mq * tpl) * nf + col] = v;
+    });
 }
 
 // Row pass of the packed Toeplitz form: y_a = Re, y_b = Im of the inverse row DFT; per slot
@@ -318,7 +322,7 @@ k_toep_rows_pk(const typename cplx_of<T>::type *__restrict__ rowbuf, const T *__
         for (int e = j0; e < nf; e += tpl) s[pidx(l * nf + e)] = src[e];
     }
     __syncthreads();
-    line_fft<C, +1>(s, 1, l * nf, lognf, j0, tw);
+    line_fft_from<C, +1>(s, 1, l * nf, lognf, j0, tw, 0, true);
     T acc_a = (T)0, acc_b = (T)0;  // nb / tpl terms per thread in the working precision
     if (q < nb) {
         const int ya = pa.cy - nb / 2 + q, yb = pb.cy - nb / 2 + q;
@@ -326,8 +330,10 @@ k_toep_rows_pk(const typename cplx_of<T>::type *__restrict__ rowbuf, const T *__
         T *oa = contrib + ((size_t)sa * nb + q) * nb, *ob = contrib + ((size_t)sb * nb + q) * nb;
         const T *ba = beams + ((size_t)pa.k * nb + q) * nb, *bb = beams + ((size_t)pb.k * nb + q) * nb;
         const T *wa = bwin_ptr[sa] + (size_t)q * nb, *wb = hasb ? bwin_ptr[sb] + (size_t)q * nb : wa;
-        for (int p = j0; p < nb; p += tpl) {
-            const C v = s[pidx(l * nf + ((p - nb / 2) & (nf - 1)))];
+        // the last pass in registers: element j0 + m tpl is window column j0 + ((m + 4) mod 16) tpl
+        last_pass_regs<C, +1>(s, 1, l * nf, lognf, j0, tw, [&](int m, const C &v) {
+            const int mp = (m + 4) & 15, p = j0 + mp * tpl;
+            if (mp >= 8) return;
             if (ona) {
                 const T z = window_value(pa, q, p, sky, beams, grids, n, nb);
                 oa[p] = ba[p] * (v.x - wa[p]);
@@ -338,7 +344,7 @@ k_toep_rows_pk(const typename cplx_of<T>::type *__restrict__ rowbuf, const T *__
                 ob[p] = bb[p] * (v.y - wb[p]);
                 acc_b += z * (v.y * (T)0.5 - wb[p]);
             }
-        }
+        });
     }
     const double sa_ = block_sum_t(acc_a, red);
     if (threadIdx.x == 0) jpart[(size_t)sa * gridDim.x + blockIdx.x] = sa_ + (blockIdx.x == 0 ? qconst[sa] : 0.0);

@@ -151,6 +151,7 @@ k_adj_cols_pk(typename cplx_of<T>::type *G, typename cplx_of<T>::type *rowbuf, i
     // (k >= 8) only its mirrors' (am, bm); rows 0 and nf/2 (k = 0 and 8 of thread j0 = 0) have
     // both. Eight rows are loaded at a time: 16 loads in flight.
     const C z0 = mk((T)0, (T)0);
+    C in[16];  // element j0 + k tpl of the line, k = 8h + r: the inputs of this thread's first-pass butterfly
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
         C x[8], y[8];
@@ -176,11 +177,13 @@ k_adj_cols_pk(typename cplx_of<T>::type *G, typename cplx_of<T>::type *rowbuf, i
             // H_a = (a + conj am)/2, H_b = (b + conj bm)/2, Z = H_a + i H_b
             const C ha = mk((T)0.5 * (a.x + am.x), (T)0.5 * (a.y - am.y));
             const C hb = mk((T)0.5 * (b.x + bm.x), (T)0.5 * (b.y - bm.y));
-            s[pidx((e << lgl) + L)] = mk(ha.x - hb.y, ha.y + hb.x);
+            in[8 * h + r] = mk(ha.x - hb.y, ha.y + hb.x);
+            (void)e;
         }
     }
+    first_pass_regs<C, +1>(s, nl, L, j0, in);
     __syncthreads();
-    line_fft_from<C, +1>(s, nl, L, lognf, j0, tw, 0, true);
+    line_fft_from<C, +1>(s, nl, L, lognf, j0, tw, 4, true);
     // element j0 + m tpl is window row j0 + ((m + 4) mod 16) tpl (row q at (q - nb/2) mod nf);
     // the rows q < nb go to the packed row buffer straight from registers
     C *dst = rowbuf + (size_t)pk * nb * nf;
@@ -222,19 +225,15 @@ k_adj_rows_pk(const typename cplx_of<T>::type *__restrict__ rowbuf, const T *__r
     const PairInfo pb = hasb ? pinfo[sb] : pa;
     const int l = threadIdx.x / tpl, j0 = threadIdx.x - l * tpl;
     const int q = blockIdx.x * lpb + l;
-    if (q < nb) {
-        const C *src = rowbuf + ((size_t)blockIdx.y * nb + q) * nf;
-        constexpr int RB = 8;  // nf / tpl = 16 elements per thread, loaded 8 at a time
-        for (int e0 = j0; e0 < nf; e0 += RB * tpl) {
-            C v[RB];
+    {   // elements j0 + k tpl: the inputs of this thread's first-pass butterfly, from registers
+        C in[16];
+        const C *src = rowbuf + ((size_t)blockIdx.y * nb + (q < nb ? q : 0)) * nf;
 #pragma unroll
-            for (int r = 0; r < RB; ++r) v[r] = src[e0 + r * tpl];
-#pragma unroll
-            for (int r = 0; r < RB; ++r) s[pidx(l * nf + e0 + r * tpl)] = v[r];
-        }
+        for (int k = 0; k < 16; ++k) in[k] = q < nb ? src[j0 + k * tpl] : mk((T)0, (T)0);
+        first_pass_regs<C, +1>(s, 1, l * nf, j0, in);
     }
     __syncthreads();
-    line_fft_from<C, +1>(s, 1, l * nf, lognf, j0, tw, 0, true);
+    line_fft_from<C, +1>(s, 1, l * nf, lognf, j0, tw, 4, true);
     if (q >= nb) return;  // the line's last pass only feeds this row's outputs
     const int ya = pa.cy - nb / 2 + q, yb = pb.cy - nb / 2 + q;
     const bool ona = pa.gridded || (ya >= 0 && ya < n), onb = hasb && (pb.gridded || (yb >= 0 && yb < n));

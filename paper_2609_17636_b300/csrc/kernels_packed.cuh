@@ -80,10 +80,10 @@ k_fwd_rows_pk(const T *__restrict__ sky, const T *__restrict__ wts, const PairIn
     }
     first_pass_regs<C, -1>(s, 1, l * nf, j0, in);
     __syncthreads();
-    line_fft_from<C, -1>(s, 1, l * nf, lognf, j0, tw, 4, false);
-    if (q < nb) {
+    line_fft_from<C, -1>(s, 1, l * nf, lognf, j0, tw, 4, true);
+    if (q < nb) {  // the last pass's elements j0 + m tpl straight to the packed row buffer
         C *out = rowbuf + ((size_t)blockIdx.y * nb + q) * nf;
-        for (int e = j0; e < nf; e += tpl) out[e] = s[pidx(l * nf + e)];
+        last_pass_regs<C, -1>(s, 1, l * nf, lognf, j0, tw, [&](int m, const C &v) { out[j0 + m * tpl] = v; });
     }
 }
 

@@ -149,36 +149,35 @@ k_adj_cols_pk(typename cplx_of<T>::type *G, typename cplx_of<T>::type *rowbuf, i
     // 16 rows e = j0 + k tpl per thread. The gridding pass folded the rows past nf/2 onto their
     // mirrors, so a row below nf/2 (k < 8) has only its own cells (a, b) and a row past it
     // (k >= 8) only its mirrors' (am, bm); rows 0 and nf/2 (k = 0 and 8 of thread j0 = 0) have
-    // both. Eight rows are loaded at a time: 16 loads in flight.
+    // both. Four rows are loaded at a time (8 loads in flight), into the first-pass inputs.
     const C z0 = mk((T)0, (T)0);
-    C in[16];  // element j0 + k tpl of the line, k = 8h + r: the inputs of this thread's first-pass butterfly
+    C in[16];  // element j0 + k tpl of the line, k = 4h + r: the inputs of this thread's first-pass butterfly
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-        C x[8], y[8];
+    for (int h = 0; h < 4; ++h) {
+        const bool own = h < 2;  // rows k < 8 hold their own cells, rows k >= 8 their mirrors'
+        C x[4], y[4];
 #pragma unroll
-        for (int r = 0; r < 8; ++r) {
-            const int e = j0 + (8 * h + r) * tpl;
-            const size_t i = h == 0 ? (size_t)e * nf + col : (size_t)(nf - e) * nf + colm;
+        for (int r = 0; r < 4; ++r) {
+            const int e = j0 + (4 * h + r) * tpl;
+            const size_t i = own ? (size_t)e * nf + col : (size_t)(nf - e) * nf + colm;
             x[r] = Ga[i];
             y[r] = hasb ? Gb[i] : z0;
         }
-        C xe = z0, ye = z0;  // row 0's mirror cell (h = 0) or row nf/2's own cell (h = 1)
-        if (j0 == 0) {
-            const size_t i = h == 0 ? (size_t)colm : (size_t)(nf / 2) * nf + col;
+        C xe = z0, ye = z0;  // row 0's mirror cell (h = 0) or row nf/2's own cell (h = 2)
+        if (j0 == 0 && (h & 1) == 0) {
+            const size_t i = own ? (size_t)colm : (size_t)(nf / 2) * nf + col;
             xe = Ga[i];
             ye = hasb ? Gb[i] : z0;
         }
 #pragma unroll
-        for (int r = 0; r < 8; ++r) {
-            const int e = j0 + (8 * h + r) * tpl;
-            const bool edge = r == 0 && j0 == 0;
-            const C a = h == 0 ? x[r] : (edge ? xe : z0), am = h == 0 ? (edge ? xe : z0) : x[r];
-            const C b = h == 0 ? y[r] : (edge ? ye : z0), bm = h == 0 ? (edge ? ye : z0) : y[r];
+        for (int r = 0; r < 4; ++r) {
+            const bool edge = r == 0 && j0 == 0 && (h & 1) == 0;
+            const C a = own ? x[r] : (edge ? xe : z0), am = own ? (edge ? xe : z0) : x[r];
+            const C b = own ? y[r] : (edge ? ye : z0), bm = own ? (edge ? ye : z0) : y[r];
             // H_a = (a + conj am)/2, H_b = (b + conj bm)/2, Z = H_a + i H_b
             const C ha = mk((T)0.5 * (a.x + am.x), (T)0.5 * (a.y - am.y));
             const C hb = mk((T)0.5 * (b.x + bm.x), (T)0.5 * (b.y - bm.y));
-            in[8 * h + r] = mk(ha.x - hb.y, ha.y + hb.x);
-            (void)e;
+            in[4 * h + r] = mk(ha.x - hb.y, ha.y + hb.x);
         }
     }
     first_pass_regs<C, +1>(s, nl, L, j0, in);

@@ -528,7 +528,8 @@ cudaError_t launch_forward(ivis_plan_s *p, const void *sky, int slot0 = 0, int n
 
 // Adjoint passes for slots [slot0, slot0 + nslots) (all slots by default). clear_st: when
 // given, the packed path clears G on that stream (forked after the column pass; the caller
-// joins p->ev_cjoin), concurrently with the row pass.
+// joins p->ev_cjoin at the end of the evaluation), concurrently with the row pass and what
+// follows it.
 template <typename T>
 cudaError_t launch_adjoint(ivis_plan_s *p, int slot0 = 0, int nslots = -1, int *si = nullptr,
                            cudaStream_t clear_st = nullptr) {
@@ -752,7 +753,6 @@ cudaError_t enqueue_eval(ivis_plan_s *p, bool capture) {
         }
     }
     if (fork) cudaStreamWaitEvent(p->stream, p->ev_join, 0);
-    if (cjoin) cudaStreamWaitEvent(p->stream, p->ev_cjoin, 0);
     const int n = p->cfg.n, nchan = p->cfg.nchan;
     stage_begin(p, "assemble_R", p->stream, si);
     {
@@ -777,6 +777,9 @@ cudaError_t enqueue_eval(ivis_plan_s *p, bool capture) {
                                          p->cfg.lambda_s, p->cost_d);
     launches += 1;
     stage_end(p, p->stream, si);
+    // the clearing of G (side stream) overlaps the row pass, the joint sum and the reductions,
+    // none of which touches G; the next evaluation's gridding starts after this join
+    if (cjoin) cudaStreamWaitEvent(p->stream, p->ev_cjoin, 0);
     cudaMemcpyAsync(p->cost_h, p->cost_d, 4 * sizeof(double), cudaMemcpyDeviceToHost, p->stream);
     p->launches = launches;
     return cudaGetLastError();

@@ -67,16 +67,39 @@ k_fwd_rows_pk(const T *__restrict__ sky, const T *__restrict__ wts, const PairIn
     // thread's elements j0 + m tpl (the inputs of its first-pass butterfly, which runs from
     // registers) hold the columns j0 + ((m + 4) mod 16) tpl, those with (m + 4) mod 16 < 8 inside
     C in[16];
+    if (!pa.gridded && !(hasb && pb.gridded)) {
+        // windows on the sky grid (no re-projection): every gather is a predicated load with
+        // no branch between them, so all of the thread's loads can be in flight at once
+        const int qq = q < nb ? q : 0;
+        const int ya = pa.cy - nb / 2 + qq, yb = pb.cy - nb / 2 + qq;
+        const bool ra = q < nb && ya >= 0 && ya < n, rb = hasb && q < nb && yb >= 0 && yb < n;
+        const T *wa = wts + ((size_t)pa.k * nb + qq) * nb, *wb = wts + ((size_t)pb.k * nb + qq) * nb;
+        const T *ia = sky + (size_t)pa.chan * n * n + (size_t)(ra ? ya : 0) * n;
+        const T *ib = sky + (size_t)pb.chan * n * n + (size_t)(rb ? yb : 0) * n;
+        const int xa0 = pa.cx - nb / 2, xb0 = pb.cx - nb / 2;
 #pragma unroll
-    for (int m = 0; m < 16; ++m) {
-        const int mp = (m + 4) & 15, p = j0 + mp * tpl;
-        C v = mk((T)0, (T)0);
-        if (mp < 8 && q < nb) {
-            const T va = window_value(pa, q, p, sky, wts, grids, n, nb);
-            const T vb = hasb ? window_value(pb, q, p, sky, wts, grids, n, nb) : (T)0;
-            v = mk(va, vb);
+        for (int m = 0; m < 16; ++m) {
+            const int mp = (m + 4) & 15, p = j0 + mp * tpl;
+            T va = (T)0, vb = (T)0;
+            if (mp < 8) {
+                const int xa = xa0 + p, xb = xb0 + p;
+                if (ra && xa >= 0 && xa < n) va = wa[p] * ia[xa];
+                if (rb && xb >= 0 && xb < n) vb = wb[p] * ib[xb];
+            }
+            in[m] = mk(va, vb);
         }
-        in[m] = v;
+    } else {
+#pragma unroll
+        for (int m = 0; m < 16; ++m) {
+            const int mp = (m + 4) & 15, p = j0 + mp * tpl;
+            C v = mk((T)0, (T)0);
+            if (mp < 8 && q < nb) {
+                const T va = window_value(pa, q, p, sky, wts, grids, n, nb);
+                const T vb = hasb ? window_value(pb, q, p, sky, wts, grids, n, nb) : (T)0;
+                v = mk(va, vb);
+            }
+            in[m] = v;
+        }
     }
     first_pass_regs<C, -1>(s, 1, l * nf, j0, in);
     __syncthreads();

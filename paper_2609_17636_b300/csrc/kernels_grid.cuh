@@ -85,17 +85,32 @@ k_grid_cg(const Chunk *__restrict__ chunks, const Item *__restrict__ items,
     // row, and the wrap point nf - x0 is a multiple of TS. With fhalf, rows past nf/2 are not
     // stored: F(gy, gx) = conj F(-gy, -gx) (the window is real)
     if constexpr ((PW & 1) == 0) {
+        // all of a thread's loads first, then its stores: a mirrored row is read at the mirrored
+        // cells and conjugated by a sign, with no branch between the loads
         constexpr int PH = PW / 2;
-        for (int i = threadIdx.x; i < PW * PH; i += P::THREADS) {
-            const int ly = i / PH, lp = i - ly * PH;
-            const int gy = (y0 + ly) & (nf - 1), gx = (x0 + 2 * lp) & (nf - 1);
-            if (!fhalf || gy <= nf / 2) {
-                reinterpret_cast<float4 *>(Fs)[i] = *reinterpret_cast<const float4 *>(Fp + (size_t)gy * nf + gx);
-            } else {
-                const float2 *row = Fp + (size_t)(nf - gy) * nf;
-                const float2 f0 = row[(nf - gx) & (nf - 1)], f1 = row[(nf - gx - 1) & (nf - 1)];
-                reinterpret_cast<float4 *>(Fs)[i] = make_float4(f0.x, -f0.y, f1.x, -f1.y);
+        constexpr int NIT = (PW * PH + P::THREADS - 1) / P::THREADS;
+        float2 f0[NIT], f1[NIT];
+        float sg[NIT];
+#pragma unroll
+        for (int k = 0; k < NIT; ++k) {
+            const int i = threadIdx.x + k * P::THREADS;
+            f0[k] = f1[k] = make_float2(0.f, 0.f);
+            sg[k] = 1.f;
+            if (i < PW * PH) {
+                const int ly = i / PH, lp = i - ly * PH;
+                const int gy = (y0 + ly) & (nf - 1), gx = (x0 + 2 * lp) & (nf - 1);
+                const bool mir = fhalf && gy > nf / 2;
+                const float2 *row = Fp + (size_t)(mir ? nf - gy : gy) * nf;
+                f0[k] = row[mir ? (nf - gx) & (nf - 1) : gx];
+                f1[k] = row[mir ? (nf - gx - 1) & (nf - 1) : gx + 1];
+                sg[k] = mir ? -1.f : 1.f;
             }
+        }
+#pragma unroll
+        for (int k = 0; k < NIT; ++k) {
+            const int i = threadIdx.x + k * P::THREADS;
+            if (i < PW * PH)
+                reinterpret_cast<float4 *>(Fs)[i] = make_float4(f0[k].x, sg[k] * f0[k].y, f1[k].x, sg[k] * f1[k].y);
         }
     } else {
         for (int i = threadIdx.x; i < PW * PW; i += P::THREADS) {

@@ -112,20 +112,37 @@ k_grid_tc(const Chunk *__restrict__ chunks, const Item *__restrict__ items,
     // stage F (wrapped) two cells at a time: TS + 8 is even and the wrap point nf - x0 is a
     // multiple of TS, so pairs never straddle a row end or the wrap. With fhalf, rows past nf/2
     // are not stored: F(gy, gx) = conj F(-gy, -gx) (the window is real)
-    {
+    {   // all of a thread's loads first, then its stores (a mirrored row: mirrored cells, sign)
         constexpr int PH = (TS + 8) / 2;
-        for (int i = threadIdx.x; i < P::PR * PH; i += P::THREADS) {
-            const int ly = i / PH, lp = i - ly * PH;
-            const int gy = (y0 + ly) & (nf - 1), gx = (x0 + 2 * lp) & (nf - 1);
-            float4 v;
-            if (!fhalf || gy <= nf / 2) {
-                v = *reinterpret_cast<const float4 *>(Fp + (size_t)gy * nf + gx);
-            } else {
-                const float2 *row = Fp + (size_t)(nf - gy) * nf;
-                const float2 f0 = row[(nf - gx) & (nf - 1)], f1 = row[(nf - gx - 1) & (nf - 1)];
-                v = make_float4(f0.x, -f0.y, f1.x, -f1.y);
+        constexpr int NIT = (P::PR * PH + P::THREADS - 1) / P::THREADS;
+#pragma unroll
+        for (int k0 = 0; k0 < NIT; k0 += 8) {
+            float2 f0[8], f1[8];
+            float sg[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const int i = threadIdx.x + (k0 + k) * P::THREADS;
+                f0[k] = f1[k] = make_float2(0.f, 0.f);
+                sg[k] = 1.f;
+                if (k0 + k < NIT && i < P::PR * PH) {
+                    const int ly = i / PH, lp = i - ly * PH;
+                    const int gy = (y0 + ly) & (nf - 1), gx = (x0 + 2 * lp) & (nf - 1);
+                    const bool mir = fhalf && gy > nf / 2;
+                    const float2 *row = Fp + (size_t)(mir ? nf - gy : gy) * nf;
+                    f0[k] = row[mir ? (nf - gx) & (nf - 1) : gx];
+                    f1[k] = row[mir ? (nf - gx - 1) & (nf - 1) : gx + 1];
+                    sg[k] = mir ? -1.f : 1.f;
+                }
             }
-            *reinterpret_cast<float4 *>(Fs + ly * FP + 2 * lp) = v;
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const int i = threadIdx.x + (k0 + k) * P::THREADS;
+                if (k0 + k < NIT && i < P::PR * PH) {
+                    const int ly = i / PH, lp = i - ly * PH;
+                    *reinterpret_cast<float4 *>(Fs + ly * FP + 2 * lp) =
+                        make_float4(f0[k].x, sg[k] * f0[k].y, f1[k].x, sg[k] * f1[k].y);
+                }
+            }
         }
     }
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;

@@ -13,6 +13,13 @@
 // with one final pass of radix 2, 4 or 8 when logL is not a multiple of 4. Shared-memory
 // addresses are padded by one element every 16 (pidx) so the strided stores of the early
 // passes do not pile onto one bank.
+//
+// The first pass's butterfly of thread j0 takes the line's elements j0 + r L/16 and the last
+// pass's butterflies of that thread write exactly the elements j0 + m L/16. A kernel whose
+// thread loads those elements itself (the packed passes: with an oversampling factor of 2,
+// half of a forward line is zero padding and half of an adjoint line is dropped) can run the
+// first pass from registers (first_pass_regs) and take the last pass's outputs in registers
+// (last_pass_regs), skipping the staging round trip through shared memory at either end.
 #pragma once
 #include "common.cuh"
 

@@ -324,7 +324,25 @@ def stage_bytes(prob, plan):
     return out
 
 
-def roofline_of(prob, plan, stages, hbm, peak_source):
+def grid_pass_kernel(plan, tuning=""):
+    """The kernel that ran the degrid_spread stage: the FP32 item pass the autotuner kept (its
+    decision text names it), the scalar item pass by default, k_grid_pass for FP64 plans."""
+    if "tensor-core item pass" in tuning:
+        return "k_grid_tc (fused interpolation + residual + J partial + spreading, split-TF32 mma per 8x8 block)"
+    if "scalar item pass" in tuning or (not tuning and plan.precision == "fp32"):
+        return SINGLE_KERNEL_STAGES["degrid_spread"]
+    return "k_grid_pass (fused interpolation + residual + J partial + spreading, tile work list)"
+
+
+def traffic_applies(tr, roofline, tuning):
+    """A stored DRAM-traffic record describes this launch only if it was taken on the same
+    stage, kernel and tile shape."""
+    kern = roofline["kernel"].split(" ")[0]
+    return (tr.get("stage") == roofline["stage"] and tr.get("kernel", "").split("<")[0] == kern
+            and tr.get("tile", "") in tuning)
+
+
+def roofline_of(prob, plan, stages, hbm, peak_source, tuning=""):
     """Roofline of the dominant kernel: the single-kernel stage with the longest measured time
     in the data-term chain. The dish-beam convolution branch (fusion_K, present when
     lambda_s != 0) runs on a forked stream concurrently with that chain; its stage time
@@ -333,7 +351,8 @@ def roofline_of(prob, plan, stages, hbm, peak_source):
     single = {k: v for k, v in stages.items() if k in SINGLE_KERNEL_STAGES and v > 0}
     dom = max(single, key=single.get)
     ach = sb[dom] / (stages[dom] / 1e3) / 1e9
-    return {"kernel": SINGLE_KERNEL_STAGES[dom], "stage": dom, "bound": "hbm",
+    kernel = grid_pass_kernel(plan, tuning) if dom == "degrid_spread" else SINGLE_KERNEL_STAGES[dom]
+    return {"kernel": kernel, "stage": dom, "bound": "hbm",
             "achieved": round(ach, 1), "peak": hbm, "unit": "GB/s",
             "frac": round(ach / hbm, 4), "traffic": None, "peak_source": peak_source,
             "algorithmic_bytes_per_launch": sb[dom], "launch_ms": round(stages[dom], 4),
@@ -410,13 +429,14 @@ def run_ivis(args, rank, world):
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
     hbm = peaks.get("hbm_gbs", 6400.0)
-    roofline = roofline_of(prob, plan, stages, hbm, "measured" if "hbm_gbs" in peaks else "fallback")
     tuning = plan.tuning()["decision"]
+    roofline = roofline_of(prob, plan, stages, hbm, "measured" if "hbm_gbs" in peaks else "fallback", tuning)
     tfile = os.path.join(ROOT, "profiles", f"traffic_{args.config}_{args.precision}.json")
-    if os.path.exists(tfile):
+    # the stored record is per launch of the full workload (a reduced cube moves less)
+    if os.path.exists(tfile) and (args.config != "c3" or args.c3_channels == 32):
         tr = json.load(open(tfile))
         # counters taken on another kernel or tile shape do not describe this launch
-        if tr.get("stage") == roofline["stage"] and tr.get("tile", "") in tuning:
+        if traffic_applies(tr, roofline, tuning):
             roofline["traffic"] = tr.get("dram_bytes_per_launch")
             roofline["traffic_source"] = tr.get("source")
             if tr.get("bottleneck"):

@@ -188,6 +188,29 @@ def test_roofline_takes_the_longest_single_kernel_stage():
     assert abs(r["frac"] - r["achieved"] / 6500.0) < 1e-4
 
 
+def test_roofline_names_the_grid_pass_that_ran():
+    """The degrid_spread stage is labelled with the item pass the autotuner kept (its decision
+    text), the scalar pass when untuned, and k_grid_pass for FP64; a stored traffic record is
+    attached only when its stage, kernel and tile match the launch."""
+    prob = synth.config_c2()
+    stages = {"fwd_rows": 0.03, "fwd_cols": 0.04, "degrid_spread": 0.3, "adj_cols": 0.03,
+              "adj_rows": 0.02, "assemble_R": 0.01, "finalize": 0.01}
+    tc = "nf=1024 w=7 fp64=0 nslot=7 m2=21 -> tensor-core item pass, tile 64, items of 64"
+    cg = "nf=1024 w=7 fp64=0 nslot=7 m2=21 -> scalar item pass, tile 32, items of 16"
+    r_tc = bench.roofline_of(prob, _Plan("fp32", 1024), stages, 6500.0, "measured", tc)
+    r_cg = bench.roofline_of(prob, _Plan("fp32", 1024), stages, 6500.0, "measured", cg)
+    r_un = bench.roofline_of(prob, _Plan("fp32", 1024), stages, 6500.0, "measured")
+    r_64 = bench.roofline_of(prob, _Plan("fp64", 1024), stages, 6500.0, "measured", "tile 32, chunk 1024")
+    assert r_tc["kernel"].startswith("k_grid_tc ") and r_cg["kernel"].startswith("k_grid_cg ")
+    assert r_un["kernel"].startswith("k_grid_cg ") and r_64["kernel"].startswith("k_grid_pass ")
+    rec = {"kernel": "k_grid_cg<7, 32>", "stage": "degrid_spread", "tile": "tile 32"}
+    assert bench.traffic_applies(rec, r_cg, cg)
+    assert not bench.traffic_applies(rec, r_tc, tc)          # another kernel
+    assert not bench.traffic_applies(rec, r_cg, cg.replace("tile 32", "tile 64"))  # another tile
+    r_fft = bench.roofline_of(prob, _Plan("fp32", 1024), dict(stages, degrid_spread=0.001), 6500.0, "measured", cg)
+    assert not bench.traffic_applies(rec, r_fft, cg)        # another stage
+
+
 def test_reference_arm_line_has_the_contract_keys(monkeypatch):
     """bench.py --impl reference: one JSON object with the contract's keys, its cpu_baseline
     and an e2e object that moves no bytes (the oracle runs on the host). The oracle's timing is
